@@ -1,0 +1,362 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: values printed in
+the paper (tests/golden/*), closed forms, textbook special cases, invariants and
+brute-force solves.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from numpy.polynomial import Polynomial
+
+from oracle.fe import (SpaceFE, TimeFE, gauss_legendre, gauss_lobatto, legendre_unit,
+                       pressure_modes, radau_right, slab_size)
+from oracle.stokes import (MGConfig, Multigrid, Slab, cell_patches, default_hierarchy, errors,
+                           fgmres, march, slab_prolongation, vanka_patch_entries,
+                           vertex_star_patches)
+from workloads import manufactured_2d, polynomial_2d, taylor_green_3d
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rows(name):
+    out = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                out.append(line.split())
+    return out
+
+
+def _mono_integral(j):
+    """exact integral of t^j over [-1, 1]"""
+    return (1 - (-1) ** (j + 1)) / (j + 1)
+
+
+# --------------------------------------------------------------------------- quadrature
+def test_radau_closed_forms():
+    x, w = radau_right(0)
+    assert np.allclose(x, [1.0]) and np.allclose(w, [2.0])
+    x, w = radau_right(1)
+    assert np.allclose(x, [-1 / 3, 1.0], atol=1e-15) and np.allclose(w, [1.5, 0.5], atol=1e-15)
+
+
+@pytest.mark.parametrize("k", range(0, 6))
+def test_radau_exactness(k):
+    x, w = radau_right(k)
+    assert x[-1] == 1.0 and np.all(np.diff(x) > 0) and x[0] > -1
+    for j in range(2 * k + 1):
+        assert abs(w @ x ** j - _mono_integral(j)) < 1e-13
+    # not exact one degree higher (sharpness of the 2k bound)
+    assert abs(w @ x ** (2 * k + 1) - _mono_integral(2 * k + 1)) > 1e-6
+
+
+@pytest.mark.parametrize("n", range(2, 8))
+def test_gauss_lobatto_gauss_exactness(n):
+    x, w = gauss_lobatto(n)
+    assert x[0] == -1 and x[-1] == 1
+    for j in range(2 * n - 2):
+        assert abs(w @ x ** j - _mono_integral(j)) < 1e-13
+    xg, wg = gauss_legendre(n)
+    for j in range(2 * n):
+        assert abs(wg @ xg ** j - _mono_integral(j)) < 1e-13
+
+
+# --------------------------------------------------------------------------- time
+def test_time_matrices_k0_backward_euler():
+    t = TimeFE(0, 0.25)
+    assert np.allclose(t.K, [[1.0]]) and np.allclose(t.M, [[0.25]]) and np.allclose(t.C, [[1.0]])
+
+
+def test_time_matrices_k1_closed_form():
+    tau = 0.3
+    t = TimeFE(1, tau)
+    # phi_1 = 3(1-t)/4, phi_2 = (3t+1)/4 on [-1,1]; hand-integrated
+    assert np.allclose(t.K, [[9 / 8, 3 / 8], [-9 / 8, 5 / 8]], atol=1e-14)
+    assert np.allclose(t.M, tau * np.diag([3 / 4, 1 / 4]), atol=1e-15)
+    assert np.allclose(t.C, [[0, 1.5], [0, -0.5]], atol=1e-14)
+
+
+@pytest.mark.parametrize("k", range(0, 5))
+def test_time_matrix_invariants(k):
+    t = TimeFE(k, 0.5)
+    # constants are reproduced: sum_b K[a,b] = phi_a(-1)
+    assert np.allclose(t.K.sum(1), t.phi_left, atol=1e-12)
+    # Radau exactness for P_2k makes the mass lumped
+    assert np.allclose(t.M - np.diag(np.diag(t.M)), 0, atol=1e-13)
+    assert np.allclose(np.diag(t.M), 0.25 * t.weights, atol=1e-13)
+
+
+@pytest.mark.parametrize("k", range(0, 4))
+def test_dg_time_scalar_ode(k):
+    """u' + lam u = g: DG(k) march; k=0 equals backward Euler, and polynomial solutions of
+    degree <= k are reproduced exactly at every slab end."""
+    lam, N, T = 2.0, 5, 1.0
+    tau = T / N
+    t = TimeFE(k, tau)
+    # exact u = t^k (u(0)=0 for k>0; for k=0 use u = 1 with u(0) = 1)
+    u_ex = (lambda s: s ** k) if k > 0 else (lambda s: 1.0)
+    du_ex = (lambda s: k * s ** (k - 1)) if k > 0 else (lambda s: 0.0)
+    u_prev = u_ex(0.0)
+    be = u_ex(0.0)
+    for n in range(N):
+        tn = n * tau + tau / 2 * (t.nodes + 1)
+        g = np.array([du_ex(s) + lam * u_ex(s) for s in tn])
+        rhs = t.M @ g + t.C[:, k] * u_prev
+        U = np.linalg.solve(t.K + lam * t.M, rhs)
+        u_prev = U[-1]
+        assert abs(U[-1] - u_ex((n + 1) * tau)) < 1e-12
+        if k == 0:
+            be = (be + tau * g[0]) / (1 + lam * tau)
+            assert abs(U[0] - be) < 1e-14
+
+
+# --------------------------------------------------------------------------- space
+def _lagrange_polys(nodes):
+    ps = []
+    for j, xj in enumerate(nodes):
+        others = [x for m, x in enumerate(nodes) if m != j]
+        p = Polynomial.fromroots(others)
+        ps.append(p / p(xj))
+    return ps
+
+
+def _integ01(p):
+    P = p.integ()
+    return P(1.0) - P(0.0)
+
+
+@pytest.mark.parametrize("dim,r", [(2, 1), (2, 2), (2, 3), (3, 1), (3, 2)])
+def test_element_matrices_tensor_structure(dim, r):
+    """Element matrices from d-dimensional quadrature equal Kronecker products of 1D
+    matrices obtained by exact polynomial integration (x fastest => kron(..., Mx))."""
+    s = SpaceFE(dim, 2, r)
+    h = s.h
+    ell = _lagrange_polys(s.xi)
+    M1 = np.array([[_integ01(a * b) for b in ell] for a in ell])
+    K1 = np.array([[_integ01(a.deriv() * b.deriv()) for b in ell] for a in ell])
+    if dim == 2:
+        Me = np.kron(M1, M1) * h ** 2
+        Ae = np.kron(M1, K1) + np.kron(K1, M1)
+    else:
+        Me = np.kron(np.kron(M1, M1), M1) * h ** 3
+        Ae = (np.kron(np.kron(M1, M1), K1) + np.kron(np.kron(M1, K1), M1)
+              + np.kron(np.kron(K1, M1), M1)) * h
+    assert np.abs(s.Me - Me).max() < 1e-11 * abs(Me).max()
+    assert np.abs(s.Ae - Ae).max() < 1e-11 * abs(Ae).max()
+    # divergence: Be_c[m, p] = h^(d-1) prod_dirs (int L_{m_dir} ell_{p_dir}' or ell_{p_dir})
+    legs = []
+    for i in range(r + 1):
+        c = np.zeros(i + 1)
+        c[i] = 1
+        P = np.polynomial.Legendre(c).convert(kind=Polynomial)
+        legs.append(math.sqrt(2 * i + 1) * P(Polynomial([-1, 2])))
+    G1 = np.array([[_integ01(L * a.deriv()) for a in ell] for L in legs])
+    N1 = np.array([[_integ01(L * a) for a in ell] for L in legs])
+    loc = s.local_nodes()
+    for comp in range(dim):
+        ref = np.zeros((s.n_pm, len(loc)))
+        for mi, e in enumerate(s.modes):
+            for pi, p in enumerate(loc):
+                v = h ** (dim - 1)
+                for dd in range(dim):
+                    v *= (G1 if dd == comp else N1)[e[dd], p[dd]]
+                ref[mi, pi] = v
+        assert np.abs(s.Be[comp] - ref).max() < 1e-11   # power-basis reference loses ~1e-13
+
+
+@pytest.mark.parametrize("dim,n,r", [(2, 3, 1), (2, 2, 3), (3, 2, 1)])
+def test_global_matrix_invariants(dim, n, r):
+    s = SpaceFE(dim, n, r)
+    M, A, B = s.mass(), s.laplace(), s.divergence()
+    one = np.ones(s.n_vel)
+    assert abs(one @ M @ one - dim) < 1e-12                     # d |Omega|
+    assert np.abs(A @ one).max() < 1e-11                         # constants in the kernel
+    free = ~s.vel_dirichlet()
+    const_p = np.zeros(s.n_pres)
+    const_p[::s.n_pm] = 1.0                                      # p = 1 (mode 0 of every cell)
+    assert np.abs((B.T @ const_p)[free]).max() < 1e-12           # int div v = 0 for v in H^1_0
+    Mp = s.pressure_mass().toarray()
+    assert np.allclose(Mp, np.eye(s.n_pres) * s.h ** dim, atol=1e-14)
+    # exactness on a linear field: int div(x e_x) q = int q for q = mode 0
+    xv = np.zeros(s.n_vel)
+    xv[:s.n_nodes] = s.node_coords[:, 0]
+    assert np.allclose((B @ xv).reshape(s.n_cells, s.n_pm)[:, 0], s.h ** dim)
+
+
+def test_pressure_modes_order():
+    assert pressure_modes(2, 2) == [(0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2)]
+    m3 = pressure_modes(3, 2)
+    assert m3[:4] == [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)] and len(m3) == 10
+
+
+def test_dof_counts_match_paper():
+    for c, r, spatial, per_slab, total in _rows("dof_counts.txt"):
+        c, r, total = int(c), int(r), int(total)
+        n = 2 ** c
+        D = slab_size(3, n, r, r)
+        if spatial != "-":
+            assert D // (r + 1) == int(spatial)
+            assert D == int(per_slab)
+        assert D * 16 * n == total
+    # the oracle's own numbering agrees with the count formula
+    for dim, n, r, k in [(2, 8, 1, 1), (2, 4, 2, 2), (3, 2, 2, 1)]:
+        s = Slab(dim, n, r, k, 1.0, 0.1)
+        assert s.size == slab_size(dim, n, r, k)
+    assert slab_size(2, 8, 1, 1) == 1540 and slab_size(2, 64, 2, 2) == 297222
+    assert slab_size(3, 32, 2, 1) == 6131398
+
+
+# --------------------------------------------------------------------------- hierarchy
+def test_hierarchy_table2b():
+    """All 72 entries of Table 2(b): hp column via the decoded Alg. 2/3 rule, h-MG column
+    via purely geometric levels at fixed (r, k)."""
+    for label, c, hp, hmg in _rows("table2b_patch_entries.txt"):
+        label, c = int(label), int(c)
+        r = k = label - 1
+        n = 2 ** c
+        assert vanka_patch_entries(default_hierarchy(n, r, k), 2) == int(hp)
+        hlevels = [(n >> j, r, k) for j in range(c + 1)]
+        assert vanka_patch_entries(hlevels, 2) == int(hmg)
+
+
+def test_hierarchy_examples():
+    assert default_hierarchy(8, 1, 1) == [(8, 1, 1), (4, 1, 1), (2, 1, 1), (1, 1, 1)]
+    assert default_hierarchy(64, 2, 2) == [(64, 2, 2), (64, 1, 2), (32, 1, 2), (16, 1, 2), (8, 1, 2),
+                                           (4, 1, 2), (2, 1, 1), (1, 1, 1)]
+    assert default_hierarchy(32, 2, 1)[:2] == [(32, 2, 1), (32, 1, 1)]
+    assert default_hierarchy(4, 0 + 4, 2)[:3] == [(4, 4, 2), (4, 2, 2), (4, 1, 2)]
+
+
+# --------------------------------------------------------------------------- transfers
+@pytest.mark.parametrize("fine,coarse", [
+    ((2, 4, 1, 1), (2, 2, 1, 1)),     # h in space
+    ((2, 2, 2, 1), (2, 2, 1, 1)),     # p in space
+    ((2, 2, 3, 2), (2, 2, 1, 1)),     # p in space and time
+    ((2, 4, 1, 2), (2, 2, 1, 1)),     # h in space, p in time
+    ((3, 2, 1, 1), (3, 1, 1, 1)),     # 3D h
+])
+def test_galerkin_identity(fine, coarse):
+    """Nested conforming spaces, same forms, exact integration => P^T S_f P = S_c on free dofs."""
+    tau = 0.2
+    sf = Slab(*fine, 1.3, tau)
+    sc = Slab(*coarse, 1.3, tau)
+    P = slab_prolongation(sc, sf)
+    G = (P.T @ sf.S @ P).toarray()
+    Sc = sc.S.toarray()
+    free = ~sc.dirichlet
+    assert np.abs(G[np.ix_(free, free)] - Sc[np.ix_(free, free)]).max() < 1e-12 * np.abs(Sc).max()
+    # constant pressures are mapped to constant pressures
+    N = sc.pressure_nullspace()
+    Nf = sf.pressure_nullspace()
+    PN = P @ N
+    coef, *_ = np.linalg.lstsq(Nf, PN, rcond=None)
+    assert np.abs(Nf @ coef - PN).max() < 1e-13
+
+
+# --------------------------------------------------------------------------- discretisation
+def test_exact_reproduction_polynomial_solution():
+    """v = t curl(x^2(1-x)^2 y^2(1-y)^2) in Q4, p = t(x-1/2)(y-1/2) in P1: Q4/P3/DG(1) reproduces
+    both exactly (only the pressure constant is free)."""
+    pb = polynomial_2d(m=1, nu=0.7)
+    sols, _, slab, _ = march(pb, 2, 3, 1, 3, solver="direct")
+    e = errors(pb, slab, sols)
+    assert e["v_L2L2"] < 1e-11 and e["v_L2H1"] < 1e-10 and e["p_L2L2"] < 1e-10
+
+
+def test_table1_errors_golden():
+    """Table 1: Q5/P4/DG(4) and Q6/P5/DG(5), h = tau = 1/2, 1/4 on [0,1]^2 x [0,1].
+    Reproduced with nu = 1 (the text says 0.1; nu = 1 is what reproduces every column),
+    velocity norms with r+2 and pressure norms with r+1 Gauss points per direction."""
+    pb = manufactured_2d(nu=1.0, time="sin")
+    rows = [r_ for r_ in _rows("table1_errors.txt") if float(r_[1]) >= 0.25]
+    assert len(rows) == 4
+    for r, h, ev, ep, eh1, ediv in rows:
+        r, n = int(r), int(round(1 / float(h)))
+        sols, _, slab, _ = march(pb, n, r, r, n, solver="direct")
+        e = errors(pb, slab, sols, nq_v=r + 2, nq_p=r + 1)
+        assert abs(e["v_L2L2"] / float(ev) - 1) < 1e-3
+        assert abs(e["v_L2H1"] / float(eh1) - 1) < 1e-3
+        assert abs(e["div_L2L2"] / float(ediv) - 1) < 2e-3
+        assert abs(e["p_L2L2"] / float(ep) - 1) < 5e-3
+
+
+def test_convergence_orders_3d():
+    """Q2/P1/DG(1) on the 3D field: H1 and divergence errors fall with the mesh
+    (pre-asymptotic at n = 2 -> 4, so the thresholds are below the orders r+1 = 2)."""
+    pb = taylor_green_3d(nu=1.0)
+    res = []
+    for n in (2, 4):
+        sols, _, slab, _ = march(pb, n, 1, 1, 2, solver="direct")
+        res.append(errors(pb, slab, sols))
+    assert res[0]["v_L2H1"] / res[1]["v_L2H1"] > 1.8
+    assert res[0]["div_L2L2"] / res[1]["div_L2L2"] > 3.0
+
+
+# --------------------------------------------------------------------------- smoother, solver
+def test_vanka_patch_sizes_and_invariants():
+    s = Slab(2, 4, 2, 2, 1.0, 0.25)
+    pats = cell_patches(s)
+    assert all(len(p) == 3 * (2 * 16 + 6) for p in pats)
+    assert len(set(np.concatenate(pats))) == s.size
+    mg = Multigrid(2, [(4, 2, 2), (4, 1, 2), (2, 1, 1), (1, 1, 1)], 1.0, 0.25)
+    W = mg.smoothers[0]
+    # translation invariance: the two interior cells (1,1), (2,1) have identical inverses
+    assert np.allclose(W.inv[5], W.inv[6], atol=1e-12)
+    # valence: interior vertex velocity nodes are shared by 4 cells
+    node = (3 * 1) + 13 * 3          # global node (3, 3) = a cell vertex
+    assert abs(W.weight[node] - 0.25) < 1e-15
+    vs = vertex_star_patches(s)
+    B_int = 3 * (2 * (2 * 3 + 1) ** 2 + 4 * 6)
+    assert max(len(p) for p in vs) == B_int == 366
+
+
+def test_vanka_recovers_error_on_exclusive_dofs():
+    """If the error e lives on dofs that only patch T contains (its interior velocity nodes
+    and its pressure modes), then R_T S e = S_TT e_T, so one step with omega = 1 from x = 0
+    and b = S e returns e exactly there (valence 1, only T's correction reaches them)."""
+    s = Slab(2, 3, 2, 1, 1.0, 0.5)
+    mg = Multigrid(2, [(3, 2, 1), (3, 1, 1)], 1.0, 0.5, MGConfig(omega=1.0))
+    W = mg.smoothers[0]
+    T = 4                                             # centre cell (1, 1)
+    sp_ = s.space
+    loc = sp_.local_nodes()
+    inner = sp_.cell_nodes[T][np.all((loc > 0) & (loc < sp_.np1 - 1), axis=1)]
+    excl = []
+    for a in range(s.kt):
+        for comp in range(2):
+            excl.extend(a * s.nv + comp * sp_.n_nodes + inner)
+        excl.extend(s.kt * s.nv + a * s.npr + T * sp_.n_pm + np.arange(sp_.n_pm))
+    excl = np.array(excl)
+    e = np.zeros(s.size)
+    e[excl] = np.random.default_rng(1).standard_normal(len(excl))
+    x = W.step(mg.slabs[0].S @ e, np.zeros(s.size))
+    assert np.abs(x[excl] - e[excl]).max() < 1e-11
+
+
+@pytest.mark.parametrize("smoother", ["cell", "vsp"])
+def test_mg_fgmres_equals_direct_solve(smoother):
+    pb = manufactured_2d(nu=1.0)
+    cfg = MGConfig(smoother=smoother)
+    sols, infos, slab, mg = march(pb, 4, 1, 1, 2, cfg=cfg, tol=1e-12)
+    solsd, _, _, _ = march(pb, 4, 1, 1, 2, solver="direct")
+    for x, xd, info in zip(sols, solsd, infos):
+        assert info.converged
+        d = slab.remove_pressure_mean(x) - slab.remove_pressure_mean(xd)
+        assert np.abs(d).max() < 1e-9 * np.abs(xd).max()
+        for a in range(slab.kt):
+            assert np.abs(slab.B @ slab.vel(x, a)).max() < 1e-10
+
+
+def test_mg_iterations_bounded_in_h():
+    """h-robustness (Sec. 5.1, Table 2a): with tau = h the FGMRES+V-cycle iteration counts
+    stay bounded under refinement (the paper reports 10.6-15 for Q2/P1/DG(1))."""
+    pb = manufactured_2d(nu=1.0, time="sin")
+    its = []
+    for n in (2, 4, 8, 16):
+        _, infos, _, _ = march(pb, n, 1, 1, n, tol=1e-8, slabs_to_run=2)
+        its.append(max(i.iterations for i in infos))
+    assert max(its) <= 15 and its[-1] <= its[1] + 3
