@@ -1,0 +1,287 @@
+/*
+ * stmg.h - C ABI of the GB300 hp space-time multigrid library (libstmg.so).
+ *
+ * The library solves the slab systems of the tensor-product space-time finite element
+ * discretisation of the instationary Stokes equations of Margenberg, Bause and Munch,
+ * "An hp multigrid approach for tensor-product space-time finite element
+ * discretizations of the Stokes equations" (arXiv 2502.09159):
+ * Q_{r+1}/P_r^disc in space on a uniform mesh of [0,1]^d (d = 2, 3), DG(k) in time,
+ * time marching slab by slab (Problem LocAlg), FGMRES preconditioned by one hp
+ * space-time V-cycle (Alg. 1) with cell or vertex-star Vanka smoothing (Eq. vanka).
+ * All compute runs in the library's own CUDA kernels for sm_103a.
+ *
+ * ---------------------------------------------------------------------------------
+ * Conventions shared by every call
+ * ---------------------------------------------------------------------------------
+ * Status.  Every call returns STMG_OK (0) or one of the STMG_ERR_* codes below; no
+ *   exception or abort crosses the ABI.  stmg_status_string() names a code.
+ *
+ * Memory.  Vector arguments are DEVICE pointers on the current CUDA device, owned by
+ *   the caller, 256-byte aligned (what cudaMalloc / torch return), not aliasing one
+ *   another unless a call says so.  "prec" selects their element type:
+ *   STMG_FP64 -> double, STMG_FP32 -> float.  The handle owns its hierarchy, patch
+ *   inverses and work vectors; stmg_destroy frees them.  The only host-pointer calls
+ *   are stmg_solve_slab_host (host vectors in, host vectors out) and the info/config
+ *   structs.
+ *
+ * Streams.  Calls enqueue work on the handle's stream (stmg_set_stream; default: the
+ *   legacy default stream) and return without waiting, except stmg_create,
+ *   stmg_solve_slab, stmg_solve_slab_host and stmg_get_profile, which synchronise
+ *   the stream.  A handle must not be used from two host threads at once.
+ *
+ * Slab vector layout (Eq. DefX / DefSubvec, per slab):
+ *     [ V^1 ... V^{k+1} , P^1 ... P^{k+1} ]                      length D
+ *   V^a  velocity at temporal dof a (Lagrange basis at the right Gauss-Radau points,
+ *        Eq. BasYk), component-major: v_x over all velocity nodes, then v_y (, v_z).
+ *        Velocity nodes: the ((r+1) n + 1)^d grid of the Q_{r+1} Gauss-Lobatto nodes,
+ *        lexicographic with x fastest.
+ *   P^a  pressure at temporal dof a, cell-major (cells lexicographic, x fastest),
+ *        C(r+d, d) modes per cell: the orthonormal Legendre products
+ *        L_i(xi) L_j(eta) (L_l(zeta)) of total degree <= r on the cell,
+ *        L_i(xi) = sqrt(2i+1) P_i(2 xi - 1), ordered by total degree, then z degree,
+ *        then y degree.
+ *   D = (k+1) (d ((r+1) n + 1)^d + C(r+d, d) n^d); boundary velocity dofs included.
+ *
+ * Slab operator (Eq. InAlg, DefDtauh, with the viscosity of Problem DVP):
+ *     S = [ K_tau (x) M_h + M_tau (x) nu A_h    -M_tau (x) B_h^T ]
+ *         [ -M_tau (x) B_h                       0               ]
+ *   with the boundary velocity rows and columns replaced by the identity (homogeneous
+ *   Dirichlet data).  The continuity rows carry a minus sign (the spatial part is
+ *   symmetric); solutions and smoother corrections are unaffected by that choice.
+ *   The pressure is determined up to one constant per temporal dof; solutions from
+ *   stmg_solve_slab are returned as computed (compare them after removing the mean).
+ */
+#ifndef STMG_H
+#define STMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define STMG_OK                0
+#define STMG_ERR_ARG           1   /* invalid argument (NULL, out of range, bad config)   */
+#define STMG_ERR_OOM           2   /* device or host allocation failed / does not fit      */
+#define STMG_ERR_NOT_CONVERGED 3   /* FGMRES hit gmres_max_iter before rel_tol            */
+#define STMG_ERR_BREAKDOWN     4   /* Arnoldi breakdown without convergence               */
+#define STMG_ERR_NONFINITE     5   /* NaN/Inf in the right-hand side or the iteration     */
+#define STMG_ERR_CUDA          6   /* a CUDA runtime call failed                           */
+#define STMG_ERR_UNIMPLEMENTED 7   /* combination not built (e.g. r > 4 on the GPU)       */
+#define STMG_ERR_SINGULAR      8   /* a patch or coarse matrix could not be inverted       */
+
+/* precisions */
+#define STMG_FP64 0
+#define STMG_FP32 1
+
+/* smoother kinds (per level) */
+#define STMG_CELL 0   /* cell patches (Eq. vanka0)                                  */
+#define STMG_VSP  1   /* vertex-star patches (remark after Eq. vanka)               */
+
+#define STMG_MAX_LEVELS 24
+
+typedef struct stmg_handle stmg_handle;
+
+/* Problem and solver configuration.  stmg_default_config fills every field. */
+typedef struct {
+  int    dim;              /* 2 or 3                                                     */
+  int    n_cells;          /* cells per direction on the finest level (>= 1)             */
+  int    r, k;             /* Q_{r+1}/P_r^disc in space (1 <= r <= 4), DG(k) (0 <= k <= 3)*/
+  double nu;               /* viscosity                                                  */
+  double T;                /* final time; slabs have length tau = T / n_slabs           */
+  int    n_slabs;
+  /* hierarchy: n_levels = 0 selects the default rule (Alg. 2/3, the reading pinned by
+     Table 2(b)); otherwise level_n/r/k[0..n_levels-1] list the levels fine -> coarse.
+     Consecutive levels must differ by n -> n/2 (h in space) or r -> r' < r (p in space)
+     or neither, and optionally k -> k' <= k (p in time).  The last level is solved
+     directly. */
+  int    n_levels;
+  int    level_n[STMG_MAX_LEVELS], level_r[STMG_MAX_LEVELS], level_k[STMG_MAX_LEVELS];
+  int    smoother[STMG_MAX_LEVELS];   /* STMG_CELL or STMG_VSP, per level (fine -> coarse) */
+  double omega;            /* Vanka damping (Eq. vanka), default 0.7                     */
+  int    nu1, nu2;         /* pre/post smoothing steps, default 1, 1                     */
+  int    precond_precision;/* precision of the V-cycle inside stmg_solve_slab            */
+  int    precisions;       /* bit mask of precisions to set up: 1 = FP64, 2 = FP32      */
+  int    gmres_max_iter;   /* Krylov basis size; no restarts (default 200)               */
+  double rel_tol;          /* stop when ||b - S x||_2 <= rel_tol ||b||_2 (default 1e-8) */
+  int    use_graphs;       /* capture each V-cycle in a CUDA graph (default 1)           */
+} stmg_config;
+
+typedef struct {
+  int       n, r, k;       /* cells per direction, spatial and temporal degree          */
+  long long size;          /* D of this level                                            */
+  long long n_vel;         /* velocity dofs per temporal dof (d ((r+1)n+1)^d)           */
+  long long n_pres;        /* pressure dofs per temporal dof (C(r+d,d) n^d)             */
+  int       smoother;      /* STMG_CELL / STMG_VSP (coarsest level: -1, direct solve)    */
+  int       patch_size;    /* B, dofs per patch (0 on the coarsest level)               */
+  long long n_patches;
+  int       n_patch_classes;/* distinct patch matrices inverted at setup                 */
+  long long inverse_bytes[2]; /* stored patch-inverse bytes for FP64 / FP32 (0: none)    */
+} stmg_level_info_t;
+
+typedef struct {
+  int    iterations;       /* FGMRES iterations (= V-cycles) used                        */
+  double rel_residual;     /* true ||b - S x||_2 / ||b||_2 at exit, in FP64             */
+  int    status;           /* STMG_OK or STMG_ERR_NOT_CONVERGED / _BREAKDOWN / _NONFINITE */
+  double seconds;          /* wall time of the call                                      */
+} stmg_solve_info;
+
+/* Per-category device time, the split of Sec. 5.2 (Fig. lid-strong-scale-rel). */
+#define STMG_PROF_SMOOTHER    0   /* Vanka sweeps inside the V-cycle                        */
+#define STMG_PROF_MG_OTHER    1   /* residuals, transfers, coarse solve inside the V-cycle  */
+#define STMG_PROF_OPERATOR    2   /* operator applications outside the V-cycle (FGMRES)     */
+#define STMG_PROF_OTHER       3   /* orthogonalisation, vector updates, right-hand sides    */
+#define STMG_PROF_FINE_SWEEP  4   /* finest-level sweeps only (subset of SMOOTHER)          */
+#define STMG_PROF_N           5
+
+/* ---- setup ----------------------------------------------------------------------- */
+
+/* Fill *cfg with defaults: dim 2, n 8, r 1, k 1, nu 1, T 1, 4 slabs, default hierarchy,
+   cell smoothers, omega 0.7, nu1 = nu2 = 1, FP64 preconditioner, both precisions set
+   up, 200 iterations, rel_tol 1e-8, graphs on. */
+int  stmg_default_config(stmg_config* cfg);
+
+/* Build the hierarchy (Alg. 2/3 or the explicit list), the level operators, transfers,
+   Vanka patch inverses (Eq. vanka0: the global submatrix R_T S R_T^T of every patch,
+   inverted in FP64 by Gauss-Jordan elimination with partial pivoting once per distinct
+   patch matrix and stored per patch, rounded to FP32 where requested) and the coarsest
+   level's bordered inverse.  Synchronous.  On failure *out is NULL. */
+int  stmg_create(const stmg_config* cfg, stmg_handle** out);
+
+/* Free everything the handle owns (NULL is accepted). */
+void stmg_destroy(stmg_handle* h);
+
+/* Enqueue all further work on `stream` (a cudaStream_t; NULL = legacy default stream). */
+int  stmg_set_stream(stmg_handle* h, void* stream);
+
+int  stmg_num_levels(const stmg_handle* h, int* n_levels);
+
+/* Level 0 is the finest, n_levels-1 the coarsest. */
+int  stmg_level_info(const stmg_handle* h, int lvl, stmg_level_info_t* info);
+
+/* ---- the hot path ------------------------------------------------------------------ */
+
+/* y = S_lvl x, matrix-free (Sec. 4.5): per cell, sum-factorised Q_{r+1} mass and
+   Laplacian, B_h and B_h^T for all k+1 temporal dofs, combined with K_tau and M_tau.
+   x, y: length D_lvl, precision prec; must not alias. */
+int  stmg_apply(stmg_handle* h, int lvl, int prec, const void* x, void* y);
+
+/* r = b - S_lvl x (App. B, step 1 of Alg. 4/5).  r must not alias b or x. */
+int  stmg_residual(stmg_handle* h, int lvl, int prec, const void* b, const void* x, void* r);
+
+/* `steps` Vanka smoothing iterations x <- x + omega W (b - S x) (Eq. vanka) on level
+   lvl (not the coarsest), W = sum_T R_T^T D_T [R_T S R_T^T]^{-1} R_T with the valence
+   weights D_T.  x is updated in place. */
+int  stmg_smooth(stmg_handle* h, int lvl, int prec, const void* b, void* x, int steps);
+
+/* One Vanka correction without the residual: x += omega W res.  (The sweep kernel.) */
+int  stmg_vanka_sweep(stmg_handle* h, int lvl, int prec, const void* res, void* x);
+
+/* b_c = T_restrict r_f between level lvl_fine and lvl_fine+1 (App. A: transpose of the
+   canonical prolongation, in space (h or p) and in time (p)).  b_c is overwritten. */
+int  stmg_restrict(stmg_handle* h, int lvl_fine, int prec, const void* r_f, void* b_c);
+
+/* x_f += T_prolong y_c between level lvl_fine+1 and lvl_fine (App. A, Eq. DeftTps,
+   DefoTsl); boundary velocity entries of x_f are left unchanged. */
+int  stmg_prolongate_add(stmg_handle* h, int lvl_fine, int prec, const void* y_c, void* x_f);
+
+/* Direct solve on the coarsest level (Alg. 1, step 3): x = G b with the FP64 bordered
+   inverse that fixes the pressure mean of every temporal dof; FP32 vectors are
+   converted on the fly, the product runs in FP64. */
+int  stmg_coarse_solve(stmg_handle* h, int prec, const void* b, void* x);
+
+/* x = V(b): one hp space-time V-cycle (Alg. 1, App. B) from a zero initial guess on the
+   finest level; the multigrid runs in precision prec (FP32: b is rounded, x returned in
+   FP64).  b, x: FP64, length D_0. */
+int  stmg_vcycle(stmg_handle* h, int prec, const double* b, double* x);
+
+/* b = F + (C_tau (x) M_h) V_prev (right-hand side of Eq. AlgSysTMS): velocity rows of
+   temporal dof a get phi_a(t_{n-1}^+) M_h v_prev, v_prev = the last temporal velocity
+   V^{k+1} of x_prev (a full previous-slab vector); x_prev = NULL means v_prev = 0.
+   F: the forcing part (Eq. DefFn), FP64, length D_0; b must not alias F or x_prev. */
+int  stmg_slab_rhs(stmg_handle* h, const double* F, const double* x_prev, double* b);
+
+/* Solve S x = b on the finest level with FGMRES (right preconditioning by one V-cycle
+   in cfg.precond_precision, CGS2 orthogonalisation in FP64, no restart).  x: initial
+   guess in, solution out (FP64).  Synchronous.  Returns info->status. */
+int  stmg_solve_slab(stmg_handle* h, const double* b, double* x, stmg_solve_info* info);
+
+/* Same with HOST vectors (any host memory; pinned memory gives faster copies): copies b
+   and x in, solves, copies x out.  For end-to-end measurement and callers without
+   device buffers.  Synchronous. */
+int  stmg_solve_slab_host(stmg_handle* h, const double* b_host, double* x_host,
+                          stmg_solve_info* info);
+
+/* ---- forcing (Eq. DefFn) ----------------------------------------------------------- */
+
+/* Number of quadrature points per cell used for the forcing: (r+4)^d Gauss points. */
+int  stmg_forcing_npoints(const stmg_handle* h, int* nq_per_cell);
+
+/* Physical coordinates of the forcing quadrature points, device FP64 array
+   [cell][q][dim] (cells lexicographic, points x fastest). */
+int  stmg_forcing_points(stmg_handle* h, double* xq);
+
+/* Times t_n^a of the k+1 Radau points of slab `slab` (0-based), host FP64 array. */
+int  stmg_slab_times(const stmg_handle* h, int slab, double* t_host);
+
+/* F: (F^a)_i = tau/2 w_a <f(t_n^a), chi_i> by the Gauss rule above, from fq = device FP64
+   [a][cell][q][dim] samples of f at the points and times above.  F (device FP64,
+   length D_0) is overwritten; boundary and pressure entries are 0. */
+int  stmg_assemble_forcing(stmg_handle* h, const double* fq, double* F);
+
+/* ---- instrumentation ------------------------------------------------------------- */
+
+/* Turn per-category CUDA-event timing on/off (off by default; adds events around
+   kernels, so leave it off for headline timings). */
+int  stmg_set_profiling(stmg_handle* h, int on);
+
+/* Milliseconds and launch counts per STMG_PROF_* category since the last reset;
+   synchronises.  reset != 0 zeroes the counters afterwards. */
+int  stmg_get_profile(stmg_handle* h, double* ms, long long* launches, int reset);
+
+/* Total number of this library's kernel launches since the handle was created. */
+long long stmg_kernel_launches(const stmg_handle* h);
+
+/* Algorithmic bytes of one Vanka sweep on level lvl in precision prec (stored inverses +
+   gathered residual + weights + updated iterate). */
+int  stmg_sweep_bytes(const stmg_handle* h, int lvl, int prec, double* bytes);
+
+const char* stmg_status_string(int status);
+
+/* ---- host-side introspection (no GPU needed) ---------------------------------------
+ * The setup numerics that stmg_create runs on the host before uploading, callable from
+ * a CPU-only process.  Host pointers; sizes as stated; no allocation is returned. */
+
+/* Default level list (Alg. 2/3, the rule pinned by Table 2(b)): levels[3*i..3*i+2] =
+   (n, r, k) fine -> coarse, *count levels (<= STMG_MAX_LEVELS). */
+int  stmg_host_default_hierarchy(int n, int r, int k, int* levels, int* count);
+
+/* 1D tables on [0,1] for degree r: Gauss-Lobatto nodes xi[r+2], M1/K1 [(r+2)^2] (mass,
+   stiffness of the Lagrange basis), G1/N1 [(r+1)(r+2)] (int L_i ell_p', int L_i ell_p).
+   NULL outputs are skipped. */
+int  stmg_host_tables_1d(int r, double* xi, double* M1, double* K1, double* G1, double* N1);
+
+/* DG(k) tables (Eq. GF, DefKMC): right Radau nodes/weights on [-1,1] [k+1], K [(k+1)^2]
+   row-major, diagonal of M_tau [k+1], phi_a(t_{n-1}^+) [k+1]. */
+int  stmg_host_time_tables(int k, double tau, double* nodes, double* weights, double* K,
+                           double* Mdiag, double* phi_left);
+
+/* Patch `patch` (STMG_CELL: cells lexicographic; STMG_VSP: vertices lexicographic) of the
+   level (dim, n, r, k): dof list (slab indices, -1 boundary, -2 padding) [*B] and its FP64
+   inverse [*B x *B] row-major.  dofs = inv = NULL only queries *B, *n_patches and the
+   number of distinct patch matrices *n_classes. */
+int  stmg_host_patch(int dim, int n, int r, int k, double nu, double tau, int kind,
+                     long long patch, int* dofs, double* inv, int* B, long long* n_patches,
+                     int* n_classes);
+
+/* Number of patches containing each slab dof [*size]; valence = NULL queries *size. */
+int  stmg_host_valence(int dim, int n, int r, int k, int kind, int* valence, long long* size);
+
+/* Bordered coarse inverse of the level (dim, n, r, k) as used by stmg_coarse_solve,
+   column-major [*D x *D] (D <= 6000); G = NULL queries *D. */
+int  stmg_host_coarse_inverse(int dim, int n, int r, int k, double nu, double tau, double* G,
+                              long long* D);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STMG_H */

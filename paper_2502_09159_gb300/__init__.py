@@ -1,0 +1,353 @@
+"""GB300 hp space-time multigrid for the instationary Stokes equations.
+
+Python face of libstmg (include/stmg.h): argument marshalling only.  Every step of the
+method runs in the library's CUDA kernels; PyTorch supplies device memory and streams.
+There is no CPU fallback: if libstmg.so has not been built, importing works but every
+call raises.
+
+    from paper_2502_09159_gb300 import SpaceTimeMG
+    mg = SpaceTimeMG(dim=2, n_cells=64, r=2, k=2, n_slabs=16, precond_precision="fp32")
+    b = mg.slab_rhs(mg.forcing(f, slab=0))
+    x, info = mg.solve_slab(b)
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Callable, Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import CELL, FP32, FP64, VSP, StmgError, check, load
+
+__all__ = ["SpaceTimeMG", "StmgError", "FP64", "FP32", "CELL", "VSP", "host_default_hierarchy",
+           "host_tables_1d", "host_time_tables", "host_patch", "host_valence", "host_coarse_inverse",
+           "build"]
+
+_PREC = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}
+
+
+def build(force: bool = False) -> str:
+    from .build import build as _b
+    return _b(force=force)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class SpaceTimeMG:
+    """One slab system of the space-time Stokes discretisation plus its hp multigrid."""
+
+    def __init__(self, dim: int = 2, n_cells: int = 8, r: int = 1, k: int = 1, nu: float = 1.0,
+                 T: float = 1.0, n_slabs: int = 4, levels: Optional[Sequence[Sequence[int]]] = None,
+                 smoothers: Optional[Sequence[int]] = None, omega: float = 0.7, nu1: int = 1,
+                 nu2: int = 1, precond_precision="fp64", precisions=("fp64", "fp32"),
+                 gmres_max_iter: int = 200, rel_tol: float = 1e-8, use_graphs: bool = True):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("SpaceTimeMG needs a CUDA device (no CPU fallback)")
+        lib = load()
+        cfg = _lib.Config()
+        check("stmg_default_config", lib.stmg_default_config(C.byref(cfg)))
+        cfg.dim, cfg.n_cells, cfg.r, cfg.k = dim, n_cells, r, k
+        cfg.nu, cfg.T, cfg.n_slabs = nu, T, n_slabs
+        if levels:
+            cfg.n_levels = len(levels)
+            for i, (ln, lr, lk) in enumerate(levels):
+                cfg.level_n[i], cfg.level_r[i], cfg.level_k[i] = ln, lr, lk
+        if smoothers is not None:
+            for i, s in enumerate(smoothers):
+                cfg.smoother[i] = s
+        cfg.omega, cfg.nu1, cfg.nu2 = omega, nu1, nu2
+        cfg.precond_precision = _PREC[precond_precision]
+        cfg.precisions = sum(1 << _PREC[p] for p in precisions)
+        cfg.gmres_max_iter, cfg.rel_tol = gmres_max_iter, rel_tol
+        cfg.use_graphs = int(use_graphs)
+        self.cfg = cfg
+        self.dim, self.r, self.k = dim, r, k
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h = C.c_void_p()
+        check("stmg_create", lib.stmg_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._lib = lib
+        n = C.c_int()
+        check("stmg_num_levels", lib.stmg_num_levels(h, C.byref(n)))
+        self.levels = []
+        for l in range(n.value):
+            li = _lib.LevelInfo()
+            check("stmg_level_info", lib.stmg_level_info(h, l, C.byref(li)))
+            self.levels.append({"n": li.n, "r": li.r, "k": li.k, "size": li.size, "n_vel": li.n_vel,
+                                "n_pres": li.n_pres, "smoother": li.smoother, "patch_size": li.patch_size,
+                                "n_patches": li.n_patches, "n_patch_classes": li.n_patch_classes,
+                                "inverse_bytes": tuple(li.inverse_bytes)})
+
+    # ---------------------------------------------------------------- plumbing
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.stmg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        torch = _torch()
+        self._lib.stmg_set_stream(self._h, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    def _vec(self, t, lvl, name):
+        torch = _torch()
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name}: need a contiguous CUDA tensor")
+        if t.dtype not in (torch.float64, torch.float32):
+            raise ValueError(f"{name}: dtype must be float64 or float32")
+        if t.numel() != self.levels[lvl]["size"]:
+            raise ValueError(f"{name}: length {t.numel()} != level size {self.levels[lvl]['size']}")
+        return FP64 if t.dtype == torch.float64 else FP32
+
+    def size(self, lvl: int = 0) -> int:
+        return self.levels[lvl]["size"]
+
+    def empty(self, lvl: int = 0, dtype=None):
+        torch = _torch()
+        return torch.empty(self.size(lvl), dtype=dtype or torch.float64, device=self.device)
+
+    def zeros(self, lvl: int = 0, dtype=None):
+        torch = _torch()
+        return torch.zeros(self.size(lvl), dtype=dtype or torch.float64, device=self.device)
+
+    # ---------------------------------------------------------------- hot path
+    def apply(self, x, lvl: int = 0, out=None):
+        """y = S_lvl x (matrix-free)."""
+        p = self._vec(x, lvl, "x")
+        y = out if out is not None else self.empty(lvl, x.dtype)
+        self._stream()
+        check("stmg_apply", self._lib.stmg_apply(self._h, lvl, p, _ptr(x), _ptr(y)))
+        return y
+
+    def residual(self, b, x, lvl: int = 0, out=None):
+        """r = b - S_lvl x."""
+        p = self._vec(x, lvl, "x")
+        self._vec(b, lvl, "b")
+        r = out if out is not None else self.empty(lvl, x.dtype)
+        self._stream()
+        check("stmg_residual", self._lib.stmg_residual(self._h, lvl, p, _ptr(b), _ptr(x), _ptr(r)))
+        return r
+
+    def smooth(self, b, x, lvl: int = 0, steps: int = 1):
+        """x <- x + omega W (b - S x), `steps` times, in place."""
+        p = self._vec(x, lvl, "x")
+        self._vec(b, lvl, "b")
+        self._stream()
+        check("stmg_smooth", self._lib.stmg_smooth(self._h, lvl, p, _ptr(b), _ptr(x), steps))
+        return x
+
+    def vanka_sweep(self, res, x, lvl: int = 0):
+        """x += omega W res (one additive Vanka correction), in place."""
+        p = self._vec(x, lvl, "x")
+        self._vec(res, lvl, "res")
+        self._stream()
+        check("stmg_vanka_sweep", self._lib.stmg_vanka_sweep(self._h, lvl, p, _ptr(res), _ptr(x)))
+        return x
+
+    def restrict(self, r_f, lvl_fine: int, out=None):
+        p = self._vec(r_f, lvl_fine, "r_f")
+        b_c = out if out is not None else self.empty(lvl_fine + 1, r_f.dtype)
+        self._stream()
+        check("stmg_restrict", self._lib.stmg_restrict(self._h, lvl_fine, p, _ptr(r_f), _ptr(b_c)))
+        return b_c
+
+    def prolongate_add(self, y_c, x_f, lvl_fine: int):
+        p = self._vec(x_f, lvl_fine, "x_f")
+        self._vec(y_c, lvl_fine + 1, "y_c")
+        self._stream()
+        check("stmg_prolongate_add", self._lib.stmg_prolongate_add(self._h, lvl_fine, p, _ptr(y_c), _ptr(x_f)))
+        return x_f
+
+    def coarse_solve(self, b, out=None):
+        lvl = len(self.levels) - 1
+        p = self._vec(b, lvl, "b")
+        x = out if out is not None else self.empty(lvl, b.dtype)
+        self._stream()
+        check("stmg_coarse_solve", self._lib.stmg_coarse_solve(self._h, p, _ptr(b), _ptr(x)))
+        return x
+
+    def vcycle(self, b, prec="fp64", out=None):
+        """x = V(b), one hp space-time V-cycle from zero; b, x FP64."""
+        torch = _torch()
+        if b.dtype != torch.float64:
+            raise ValueError("vcycle: b must be float64")
+        self._vec(b, 0, "b")
+        x = out if out is not None else self.empty(0)
+        self._stream()
+        check("stmg_vcycle", self._lib.stmg_vcycle(self._h, _PREC[prec], _ptr(b), _ptr(x)))
+        return x
+
+    def slab_rhs(self, F, x_prev=None, out=None):
+        """b = F + (C_tau (x) M_h) V_prev^{k+1}."""
+        self._vec(F, 0, "F")
+        if x_prev is not None:
+            self._vec(x_prev, 0, "x_prev")
+        b = out if out is not None else self.empty(0)
+        self._stream()
+        check("stmg_slab_rhs", self._lib.stmg_slab_rhs(
+            self._h, _ptr(F), _ptr(x_prev) if x_prev is not None else None, _ptr(b)))
+        return b
+
+    def solve_slab(self, b, x0=None, out=None):
+        """FGMRES + V-cycle solve of S x = b; returns (x, info dict)."""
+        self._vec(b, 0, "b")
+        x = out if out is not None else (x0.clone() if x0 is not None else self.zeros(0))
+        if out is not None and x0 is not None and out.data_ptr() != x0.data_ptr():
+            x.copy_(x0)
+        self._stream()
+        info = _lib.SolveInfo()
+        st = self._lib.stmg_solve_slab(self._h, _ptr(b), _ptr(x), C.byref(info))
+        if st not in (_lib.OK, _lib.ERR_NOT_CONVERGED, _lib.ERR_BREAKDOWN):
+            raise StmgError("stmg_solve_slab", st)
+        return x, {"iterations": info.iterations, "rel_residual": info.rel_residual,
+                   "status": info.status, "seconds": info.seconds}
+
+    def solve_slab_host(self, b: np.ndarray, x: np.ndarray):
+        """Same with host arrays (float64, contiguous); x is overwritten with the solution."""
+        if b.dtype != np.float64 or x.dtype != np.float64 or not b.flags.c_contiguous or not x.flags.c_contiguous:
+            raise ValueError("solve_slab_host: contiguous float64 arrays")
+        if b.size != self.size(0) or x.size != self.size(0):
+            raise ValueError("solve_slab_host: wrong length")
+        self._stream()
+        info = _lib.SolveInfo()
+        st = self._lib.stmg_solve_slab_host(self._h, b.ctypes.data_as(C.c_void_p), x.ctypes.data_as(C.c_void_p),
+                                            C.byref(info))
+        if st not in (_lib.OK, _lib.ERR_NOT_CONVERGED, _lib.ERR_BREAKDOWN):
+            raise StmgError("stmg_solve_slab_host", st)
+        return {"iterations": info.iterations, "rel_residual": info.rel_residual, "status": info.status,
+                "seconds": info.seconds}
+
+    # ---------------------------------------------------------------- forcing
+    def forcing_points(self):
+        torch = _torch()
+        nq = C.c_int()
+        check("stmg_forcing_npoints", self._lib.stmg_forcing_npoints(self._h, C.byref(nq)))
+        ncell = self.levels[0]["n"] ** self.dim
+        pts = torch.empty((ncell, nq.value, self.dim), dtype=torch.float64, device=self.device)
+        check("stmg_forcing_points", self._lib.stmg_forcing_points(self._h, _ptr(pts)))
+        return pts
+
+    def slab_times(self, slab: int):
+        t = (C.c_double * (self.k + 1))()
+        check("stmg_slab_times", self._lib.stmg_slab_times(self._h, slab, t))
+        return list(t)
+
+    def assemble_forcing(self, fq, out=None):
+        """F from samples fq[a][cell][q][dim] of f at forcing_points() and slab_times()."""
+        torch = _torch()
+        if fq.dtype != torch.float64 or not fq.is_cuda or not fq.is_contiguous():
+            raise ValueError("fq: contiguous float64 CUDA tensor")
+        F = out if out is not None else self.empty(0)
+        self._stream()
+        check("stmg_assemble_forcing", self._lib.stmg_assemble_forcing(self._h, _ptr(fq), _ptr(F)))
+        return F
+
+    def sample_forcing(self, f: Callable, slab: int, points=None):
+        """Evaluate f(x_tuple, t) -> tuple of dim arrays at the forcing points of `slab`
+        (input preparation on the host); returns fq ready for assemble_forcing."""
+        torch = _torch()
+        pts = (points if points is not None else self.forcing_points()).cpu().numpy()
+        X = tuple(pts[..., d] for d in range(self.dim))
+        fq = np.stack([np.stack(f(X, t), axis=-1) for t in self.slab_times(slab)])
+        return torch.from_numpy(np.ascontiguousarray(fq)).to(self.device)
+
+    def forcing(self, f: Callable, slab: int, points=None):
+        return self.assemble_forcing(self.sample_forcing(f, slab, points))
+
+    # ---------------------------------------------------------------- instrumentation
+    def set_profiling(self, level: int):
+        check("stmg_set_profiling", self._lib.stmg_set_profiling(self._h, level))
+
+    def profile(self, reset: bool = False):
+        ms = (C.c_double * _lib.PROF_N)()
+        n = (C.c_longlong * _lib.PROF_N)()
+        check("stmg_get_profile", self._lib.stmg_get_profile(self._h, ms, n, int(reset)))
+        names = ["smoother", "mg_other", "operator", "other", "fine_sweep"]
+        return {nm: {"ms": ms[i], "launches": n[i]} for i, nm in enumerate(names)}
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self._lib.stmg_kernel_launches(self._h))
+
+    def sweep_bytes(self, lvl: int = 0, prec="fp32") -> float:
+        b = C.c_double()
+        check("stmg_sweep_bytes", self._lib.stmg_sweep_bytes(self._h, lvl, _PREC[prec], C.byref(b)))
+        return b.value
+
+
+# -------------------------------------------------------------------- host introspection
+def host_default_hierarchy(n: int, r: int, k: int):
+    lib = load()
+    buf = (C.c_int * (3 * _lib.MAX_LEVELS))()
+    cnt = C.c_int()
+    check("stmg_host_default_hierarchy", lib.stmg_host_default_hierarchy(n, r, k, buf, C.byref(cnt)))
+    return [tuple(buf[3 * i:3 * i + 3]) for i in range(cnt.value)]
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def host_tables_1d(r: int):
+    lib = load()
+    np1 = r + 2
+    xi, M1, K1 = np.zeros(np1), np.zeros(np1 * np1), np.zeros(np1 * np1)
+    G1, N1 = np.zeros((r + 1) * np1), np.zeros((r + 1) * np1)
+    check("stmg_host_tables_1d", lib.stmg_host_tables_1d(r, _dp(xi), _dp(M1), _dp(K1), _dp(G1), _dp(N1)))
+    return {"xi": xi, "M1": M1.reshape(np1, np1), "K1": K1.reshape(np1, np1),
+            "G1": G1.reshape(r + 1, np1), "N1": N1.reshape(r + 1, np1)}
+
+
+def host_time_tables(k: int, tau: float):
+    lib = load()
+    kt = k + 1
+    nodes, w, K, M, phi = np.zeros(kt), np.zeros(kt), np.zeros(kt * kt), np.zeros(kt), np.zeros(kt)
+    check("stmg_host_time_tables", lib.stmg_host_time_tables(k, tau, _dp(nodes), _dp(w), _dp(K), _dp(M), _dp(phi)))
+    return {"nodes": nodes, "weights": w, "K": K.reshape(kt, kt), "M": M, "phi_left": phi}
+
+
+def host_patch(dim, n, r, k, nu, tau, kind, patch, with_inverse=True):
+    lib = load()
+    B, npat, ncls = C.c_int(), C.c_longlong(), C.c_int()
+    check("stmg_host_patch", lib.stmg_host_patch(dim, n, r, k, nu, tau, kind, 0, None, None, C.byref(B),
+                                                 C.byref(npat), C.byref(ncls)))
+    dofs = np.zeros(B.value, dtype=np.int32)
+    inv = np.zeros((B.value, B.value)) if with_inverse else None
+    check("stmg_host_patch", lib.stmg_host_patch(dim, n, r, k, nu, tau, kind, patch,
+                                                 dofs.ctypes.data_as(C.POINTER(C.c_int)),
+                                                 _dp(inv) if with_inverse else None, C.byref(B),
+                                                 C.byref(npat), C.byref(ncls)))
+    return {"dofs": dofs, "inverse": inv, "B": B.value, "n_patches": npat.value, "n_classes": ncls.value}
+
+
+def host_valence(dim, n, r, k, kind):
+    lib = load()
+    size = C.c_longlong()
+    check("stmg_host_valence", lib.stmg_host_valence(dim, n, r, k, kind, None, C.byref(size)))
+    v = np.zeros(size.value, dtype=np.int32)
+    check("stmg_host_valence", lib.stmg_host_valence(dim, n, r, k, kind, v.ctypes.data_as(C.POINTER(C.c_int)),
+                                                     C.byref(size)))
+    return v
+
+
+def host_coarse_inverse(dim, n, r, k, nu, tau):
+    lib = load()
+    D = C.c_longlong()
+    check("stmg_host_coarse_inverse", lib.stmg_host_coarse_inverse(dim, n, r, k, nu, tau, None, C.byref(D)))
+    G = np.zeros(D.value * D.value)
+    check("stmg_host_coarse_inverse", lib.stmg_host_coarse_inverse(dim, n, r, k, nu, tau, _dp(G), C.byref(D)))
+    return G.reshape(D.value, D.value).T.copy()     # column-major -> row-major

@@ -1,0 +1,106 @@
+"""ctypes declarations of libstmg (include/stmg.h).  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+MAX_LEVELS = 24
+OK, ERR_ARG, ERR_OOM, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_NONFINITE, ERR_CUDA, \
+    ERR_UNIMPLEMENTED, ERR_SINGULAR = range(9)
+FP64, FP32 = 0, 1
+CELL, VSP = 0, 1
+PROF_SMOOTHER, PROF_MG_OTHER, PROF_OPERATOR, PROF_OTHER, PROF_FINE_SWEEP, PROF_N = range(6)
+
+
+class Config(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_cells", C.c_int), ("r", C.c_int), ("k", C.c_int),
+                ("nu", C.c_double), ("T", C.c_double), ("n_slabs", C.c_int),
+                ("n_levels", C.c_int),
+                ("level_n", C.c_int * MAX_LEVELS), ("level_r", C.c_int * MAX_LEVELS),
+                ("level_k", C.c_int * MAX_LEVELS), ("smoother", C.c_int * MAX_LEVELS),
+                ("omega", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
+                ("precond_precision", C.c_int), ("precisions", C.c_int),
+                ("gmres_max_iter", C.c_int), ("rel_tol", C.c_double), ("use_graphs", C.c_int)]
+
+
+class LevelInfo(C.Structure):
+    _fields_ = [("n", C.c_int), ("r", C.c_int), ("k", C.c_int),
+                ("size", C.c_longlong), ("n_vel", C.c_longlong), ("n_pres", C.c_longlong),
+                ("smoother", C.c_int), ("patch_size", C.c_int), ("n_patches", C.c_longlong),
+                ("n_patch_classes", C.c_int), ("inverse_bytes", C.c_longlong * 2)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("status", C.c_int),
+                ("seconds", C.c_double)]
+
+
+_VP, _I, _D, _LL = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+_SIGS = {
+    "stmg_default_config": (_I, [C.POINTER(Config)]),
+    "stmg_create": (_I, [C.POINTER(Config), C.POINTER(_VP)]),
+    "stmg_destroy": (None, [_VP]),
+    "stmg_set_stream": (_I, [_VP, _VP]),
+    "stmg_num_levels": (_I, [_VP, C.POINTER(_I)]),
+    "stmg_level_info": (_I, [_VP, _I, C.POINTER(LevelInfo)]),
+    "stmg_apply": (_I, [_VP, _I, _I, _VP, _VP]),
+    "stmg_residual": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
+    "stmg_smooth": (_I, [_VP, _I, _I, _VP, _VP, _I]),
+    "stmg_vanka_sweep": (_I, [_VP, _I, _I, _VP, _VP]),
+    "stmg_restrict": (_I, [_VP, _I, _I, _VP, _VP]),
+    "stmg_prolongate_add": (_I, [_VP, _I, _I, _VP, _VP]),
+    "stmg_coarse_solve": (_I, [_VP, _I, _VP, _VP]),
+    "stmg_vcycle": (_I, [_VP, _I, _VP, _VP]),
+    "stmg_slab_rhs": (_I, [_VP, _VP, _VP, _VP]),
+    "stmg_solve_slab": (_I, [_VP, _VP, _VP, C.POINTER(SolveInfo)]),
+    "stmg_solve_slab_host": (_I, [_VP, _VP, _VP, C.POINTER(SolveInfo)]),
+    "stmg_forcing_npoints": (_I, [_VP, C.POINTER(_I)]),
+    "stmg_forcing_points": (_I, [_VP, _VP]),
+    "stmg_slab_times": (_I, [_VP, _I, C.POINTER(_D)]),
+    "stmg_assemble_forcing": (_I, [_VP, _VP, _VP]),
+    "stmg_set_profiling": (_I, [_VP, _I]),
+    "stmg_get_profile": (_I, [_VP, C.POINTER(_D), C.POINTER(_LL), _I]),
+    "stmg_kernel_launches": (_LL, [_VP]),
+    "stmg_sweep_bytes": (_I, [_VP, _I, _I, C.POINTER(_D)]),
+    "stmg_status_string": (C.c_char_p, [_I]),
+    "stmg_host_default_hierarchy": (_I, [_I, _I, _I, C.POINTER(_I), C.POINTER(_I)]),
+    "stmg_host_tables_1d": (_I, [_I] + [C.POINTER(_D)] * 5),
+    "stmg_host_time_tables": (_I, [_I, _D] + [C.POINTER(_D)] * 5),
+    "stmg_host_patch": (_I, [_I, _I, _I, _I, _D, _D, _I, _LL, C.POINTER(_I), C.POINTER(_D),
+                             C.POINTER(_I), C.POINTER(_LL), C.POINTER(_I)]),
+    "stmg_host_valence": (_I, [_I, _I, _I, _I, _I, C.POINTER(_I), C.POINTER(_LL)]),
+    "stmg_host_coarse_inverse": (_I, [_I, _I, _I, _I, _D, _D, C.POINTER(_D), C.POINTER(_LL)]),
+}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libstmg.so")
+_lib = None
+
+
+class StmgError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        msg = load().stmg_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{fn} failed: {msg} ({status})")
+
+
+def load():
+    """Load libstmg.so from the package directory; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libstmg.so is missing ({LIB_PATH}): build it with "
+                           "`python -m paper_2502_09159_gb300.build` (there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(fn, status):
+    if status != OK:
+        raise StmgError(fn, status)
+    return status

@@ -1,0 +1,934 @@
+// C ABI of libstmg: handle, setup uploads, hot-path entry points, the hp space-time
+// V-cycle (Alg. 1 with the subroutines of App. B) and FGMRES per slab.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "levels.h"
+
+using namespace stmg;
+
+namespace {
+
+template <typename T>
+struct PrecDev {
+  T* inv = nullptr;   // per-patch inverses, interleaved layout
+  T* wgt = nullptr;   // omega / valence per slab dof
+  T* b = nullptr;     // V-cycle right-hand side of this level
+  T* x = nullptr;     // V-cycle iterate of this level
+  T* r = nullptr;     // residual work vector
+  ApplyParams<T> ap{};
+  TransferParams<T> tp{};   // transfer between this level and the next coarser one
+  bool has_inv = false;
+};
+
+struct LevelDev {
+  LevelHost H;
+  int* dofs = nullptr;
+  PrecDev<double> d;
+  PrecDev<float> f;
+  double* G = nullptr;      // coarsest level: bordered inverse, column-major
+  int streaming = 0;        // read the inverses with evict-first loads
+  int ppb = 1;              // patches per block of the sweep kernel
+  template <typename T> PrecDev<T>& pd();
+};
+template <> PrecDev<double>& LevelDev::pd<double>() { return d; }
+template <> PrecDev<float>& LevelDev::pd<float>() { return f; }
+
+struct ProfPair { int cat; cudaEvent_t a, b; };
+constexpr int PROF_VCYCLE = STMG_PROF_N;   // internal: whole V-cycles (MG w/o smoother = this - smoother)
+
+}  // namespace
+
+struct stmg_handle {
+  stmg_config cfg{};
+  std::vector<LevelDev> L;
+  cudaStream_t st = nullptr;      // caller's stream (nullptr: legacy default stream)
+  cudaStream_t gst = nullptr;     // internal stream that launches the captured V-cycles
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  double tau = 0.0;
+  // FGMRES storage
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *hcol = nullptr, *tmp = nullptr, *partial = nullptr;
+  double *bnorm = nullptr, *xhost_b = nullptr, *xhost_x = nullptr;
+  int m_alloc = 0;
+  ForcingParams fp{};
+  MassParams mp{};
+  // instrumentation
+  int prof = 0;
+  std::vector<ProfPair> pending;        // eager pairs not yet read
+  std::vector<ProfPair> graph_pairs[2]; // pairs recorded inside the captured V-cycles
+  std::vector<cudaEvent_t> all_events;
+  double prof_ms[STMG_PROF_N + 1] = {};
+  long long prof_n[STMG_PROF_N + 1] = {};
+  long long launches = 0;
+  long long graph_kernels[2] = {0, 0};
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool graph_pending[2] = {false, false};
+  std::vector<cudaEvent_t> free_events;
+  bool capturing = false;
+};
+
+// ------------------------------------------------------------------------------------
+// helpers
+// ------------------------------------------------------------------------------------
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      std::fprintf(stderr, "stmg: %s failed: %s (%s:%d)\n", #call,                  \
+                   cudaGetErrorString(e_), __FILE__, __LINE__);                    \
+      return e_ == cudaErrorMemoryAllocation ? STMG_ERR_OOM : STMG_ERR_CUDA;       \
+    }                                                                              \
+  } while (0)
+
+#define CKS(call)                      \
+  do {                                 \
+    int s_ = (call);                   \
+    if (s_ != STMG_OK) return s_;      \
+  } while (0)
+
+static cudaEvent_t new_event(stmg_handle* h) {
+  if (!h->capturing && !h->free_events.empty()) {
+    cudaEvent_t e = h->free_events.back();
+    h->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  h->all_events.push_back(e);
+  return e;
+}
+
+static void rec(stmg_handle* h, cudaEvent_t e, cudaStream_t s) {
+  if (h->capturing) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else cudaEventRecord(e, s);
+}
+
+// profiling bracket: level 1 records only STMG_PROF_FINE_SWEEP, level 2 everything
+struct Prof {
+  stmg_handle* h; int cat; cudaStream_t s; cudaEvent_t a = nullptr, b = nullptr; int which;
+  Prof(stmg_handle* h_, int cat_, cudaStream_t s_, int which_ = -1) : h(h_), cat(cat_), s(s_), which(which_) {
+    const int need = cat == STMG_PROF_FINE_SWEEP ? 1 : 2;
+    if (h->prof >= need) {
+      a = new_event(h); b = new_event(h);
+      if (a && b) rec(h, a, s);
+    }
+  }
+  ~Prof() {
+    if (a && b) {
+      rec(h, b, s);
+      if (h->capturing) h->graph_pairs[which].push_back({cat, a, b});
+      else h->pending.push_back({cat, a, b});
+    }
+  }
+};
+
+static void harvest(stmg_handle* h, std::vector<ProfPair>& v, bool keep) {
+  for (auto& p : v) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      h->prof_ms[p.cat] += ms;
+      h->prof_n[p.cat] += 1;
+      if (p.cat == STMG_PROF_FINE_SWEEP) { h->prof_ms[STMG_PROF_SMOOTHER] += ms; h->prof_n[STMG_PROF_SMOOTHER] += 1; }
+    }
+    if (!keep) { h->free_events.push_back(p.a); h->free_events.push_back(p.b); }
+  }
+  if (!keep) v.clear();
+}
+
+// read every completed profiling pair (call after the stream has been synchronised)
+static void harvest_all(stmg_handle* h) {
+  harvest(h, h->pending, false);
+  for (int w = 0; w < 2; ++w)
+    if (h->graph_pending[w]) { harvest(h, h->graph_pairs[w], true); h->graph_pending[w] = false; }
+}
+
+template <typename T> constexpr int prec_of();
+template <> constexpr int prec_of<double>() { return STMG_FP64; }
+template <> constexpr int prec_of<float>() { return STMG_FP32; }
+
+static int ipow(int b, int e) { int r = 1; while (e-- > 0) r *= b; return r; }
+
+template <typename T>
+static void fill_apply_params(const LevelHost& H, ApplyParams<T>* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->n = H.n; p->G = H.G; p->kt = H.kt; p->npm = H.npm;
+  p->n_nodes = H.n_nodes; p->n_vel = H.n_vel; p->n_pres = H.n_pres;
+  const int np = H.np;
+  for (int i = 0; i < np * np; ++i) { p->M1[i] = (T)H.t1.M1[i]; p->K1[i] = (T)H.t1.K1[i]; }
+  for (int i = 0; i < (H.r + 1) * np; ++i) { p->G1[i] = (T)H.t1.G1[i]; p->N1[i] = (T)H.t1.N1[i]; }
+  for (int a = 0; a < H.kt; ++a) {
+    for (int b = 0; b < H.kt; ++b) p->Kt[a * MAXKT + b] = (T)H.tt.K[a * H.kt + b];
+    p->beta[a] = (T)(H.tt.M[a] * H.nu * std::pow(H.h, H.dim - 2));
+    p->bscale[a] = (T)(-H.tt.M[a] * std::pow(H.h, H.dim - 1));
+  }
+  p->hd = (T)std::pow(H.h, H.dim);
+  for (int m = 0; m < H.npm; ++m)
+    for (int d = 0; d < 3; ++d) p->modes[m][d] = (signed char)H.modes[m][d];
+  // cells per block: enough lines for ~128-256 threads, shared memory <= 64 KB
+  const int lines = H.kt * H.dim * ipow(np, H.dim - 1);
+  int cpb = std::max(1, 192 / lines);
+  while (cpb > 1 && apply_smem_bytes<T>(H.dim, np, H.kt, H.npm, cpb) > 64 * 1024) --cpb;
+  cpb = std::min(cpb, H.n_cells);
+  p->cpb = cpb;
+}
+
+template <typename T>
+static void fill_transfer_params(const LevelHost& F, const LevelHost& C, TransferParams<T>* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->dim = F.dim;
+  p->h_type = F.n == 2 * C.n ? 1 : 0;
+  p->nc = C.n; p->nf = F.n; p->npc = C.np; p->npf = F.np;
+  p->ns = p->h_type ? 2 * (F.np - 1) + 1 : F.np;
+  p->Gc = C.G; p->Gf = F.G; p->ktc = C.kt; p->ktf = F.kt; p->npmc = C.npm; p->npmf = F.npm;
+  p->nnc = C.n_nodes; p->nnf = F.n_nodes; p->nvc = C.n_vel; p->nvf = F.n_vel;
+  p->npc_tot = C.n_pres; p->npf_tot = F.n_pres;
+  p->rc = C.r;
+  for (int s = 0; s < p->ns; ++s) {
+    double xi;
+    if (p->h_type) {
+      int child = std::min(s / (F.np - 1), 1);
+      int loc = s - child * (F.np - 1);
+      xi = 0.5 * (child + F.t1.xi[loc]);
+    } else {
+      xi = F.t1.xi[s];
+    }
+    for (int j = 0; j < C.np; ++j) {
+      double v = lagrange_eval(C.t1.xi, C.np, j, xi);
+      for (int jj = 0; jj < C.np; ++jj)
+        if (std::fabs(xi - C.t1.xi[jj]) < 1e-14) v = (jj == j) ? 1.0 : 0.0;
+      p->P1[s * MAXNP + j] = (T)v;
+    }
+  }
+  for (int af = 0; af < F.kt; ++af)
+    for (int ac = 0; ac < C.kt; ++ac) {
+      double v = lagrange_eval(C.tt.nodes, C.kt, ac, F.tt.nodes[af]);
+      for (int jj = 0; jj < C.kt; ++jj)
+        if (std::fabs(F.tt.nodes[af] - C.tt.nodes[jj]) < 1e-14) v = (jj == ac) ? 1.0 : 0.0;
+      p->Pt[af * MAXKT + ac] = (T)v;
+    }
+  // E[o][i' * (rc+1) + i] = int_0^1 L_i((o + xi)/2) L_i'(xi) dxi
+  double gx[16], gw[16];
+  const int nq = C.r + 2;
+  gauss_legendre(nq, gx, gw);
+  for (int o = 0; o < 2; ++o)
+    for (int ip = 0; ip <= C.r; ++ip)
+      for (int i = 0; i <= C.r; ++i) {
+        double s = 0.0;
+        for (int q = 0; q < nq; ++q) {
+          const double xi = 0.5 * (gx[q] + 1.0), w = 0.5 * gw[q];
+          s += w * legendre_unit(i, 0.5 * (o + xi)) * legendre_unit(ip, xi);
+        }
+        p->E[o][ip * (C.r + 1) + i] = (T)(std::fabs(s) < 1e-15 ? 0.0 : s);
+      }
+  for (int m = 0; m < C.npm; ++m) for (int d = 0; d < 3; ++d) p->modes_c[m][d] = (signed char)C.modes[m][d];
+  for (int m = 0; m < F.npm; ++m) for (int d = 0; d < 3; ++d) p->modes_f[m][d] = (signed char)F.modes[m][d];
+}
+
+template <typename T>
+static int dalloc(T** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? STMG_ERR_OOM : STMG_ERR_CUDA;
+  }
+  return STMG_OK;
+}
+
+template <typename T>
+static int setup_precision(stmg_handle* h, LevelDev& lv, const double* d_cls, const int* d_cls_of) {
+  PrecDev<T>& P = lv.pd<T>();
+  const LevelHost& H = lv.H;
+  fill_apply_params<T>(H, &P.ap);
+  CKS(dalloc(&P.b, H.size));
+  CKS(dalloc(&P.x, H.size));
+  CKS(dalloc(&P.r, H.size));
+  if (H.smoother >= 0) {
+    CKS(dalloc(&P.inv, (size_t)H.n_patches * H.B * H.Bc));
+    CK(launch_replicate_inverses<T>(d_cls, d_cls_of, P.inv, H.n_patches, H.B, H.Bc, h->st));
+    std::vector<T> w(H.size, T(0));
+    for (long long i = 0; i < H.size; ++i)
+      if (H.valence[i] > 0) w[i] = (T)(h->cfg.omega / H.valence[i]);
+    CKS(dalloc(&P.wgt, H.size));
+    CK(cudaMemcpy(P.wgt, w.data(), sizeof(T) * H.size, cudaMemcpyHostToDevice));
+    P.has_inv = true;
+  }
+  return STMG_OK;
+}
+
+static void free_level(LevelDev& lv) {
+  auto f = [](void* p) { if (p) cudaFree(p); };
+  f(lv.dofs); f(lv.G);
+  f(lv.d.inv); f(lv.d.wgt); f(lv.d.b); f(lv.d.x); f(lv.d.r);
+  f(lv.f.inv); f(lv.f.wgt); f(lv.f.b); f(lv.f.x); f(lv.f.r);
+  lv = LevelDev();
+}
+
+// ------------------------------------------------------------------------------------
+// level operations (enqueue on stream s)
+// ------------------------------------------------------------------------------------
+template <typename T>
+static int op_apply(stmg_handle* h, int l, const T* x, const T* b, T* y, int mode, cudaStream_t s) {
+  LevelDev& lv = h->L[l];
+  CK(cudaMemsetAsync(y, 0, sizeof(T) * lv.H.size, s));
+  CK(launch_apply<T>(lv.H.dim, lv.H.np, lv.pd<T>().ap, x, b, y, mode, s));
+  h->launches += 1;
+  return STMG_OK;
+}
+
+template <typename T>
+static int op_sweep(stmg_handle* h, int l, const T* res, T* x, cudaStream_t s) {
+  LevelDev& lv = h->L[l];
+  PrecDev<T>& P = lv.pd<T>();
+  if (!P.has_inv) return STMG_ERR_ARG;
+  Prof pr(h, l == 0 ? STMG_PROF_FINE_SWEEP : STMG_PROF_SMOOTHER, s, prec_of<T>());
+  CK(launch_vanka_sweep<T>(lv.dofs, P.inv, res, P.wgt, x, lv.H.n_patches, lv.H.B, lv.H.Bc, lv.ppb, lv.streaming, s));
+  h->launches += 1;
+  return STMG_OK;
+}
+
+template <typename T>
+static int op_restrict(stmg_handle* h, int l, const T* rf, T* bc, cudaStream_t s) {
+  LevelDev& lc = h->L[l + 1];
+  CK(cudaMemsetAsync(bc, 0, sizeof(T) * lc.H.size, s));
+  CK(launch_restrict<T>(h->L[l].pd<T>().tp, rf, bc, s));
+  h->launches += 1;
+  return STMG_OK;
+}
+
+template <typename T>
+static int op_prolongate_add(stmg_handle* h, int l, const T* yc, T* xf, cudaStream_t s) {
+  CK(launch_prolongate<T>(h->L[l].pd<T>().tp, yc, xf, s));
+  h->launches += 1;
+  return STMG_OK;
+}
+
+template <typename T>
+static int op_coarse(stmg_handle* h, const T* b, T* x, cudaStream_t s) {
+  LevelDev& lv = h->L.back();
+  CK(launch_coarse<T>((int)lv.H.size, lv.G, b, x, s));
+  h->launches += 1;
+  return STMG_OK;
+}
+
+// V-cycle on level l: input L[l].b, output L[l].x (zero initial guess), Alg. 1.
+template <typename T>
+static int vcycle_level(stmg_handle* h, int l, cudaStream_t s) {
+  LevelDev& lv = h->L[l];
+  PrecDev<T>& P = lv.pd<T>();
+  const size_t bytes = sizeof(T) * lv.H.size;
+  if (l == (int)h->L.size() - 1) return op_coarse<T>(h, P.b, P.x, s);
+  CK(cudaMemsetAsync(P.x, 0, bytes, s));
+  for (int it = 0; it < h->cfg.nu1; ++it) {          // presmoothing (Eq. Alg:VGMGPre)
+    if (it == 0) {
+      CKS(op_sweep<T>(h, l, P.b, P.x, s));           // x = 0: the residual is b
+    } else {
+      CKS(op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, s));
+      CKS(op_sweep<T>(h, l, P.r, P.x, s));
+    }
+  }
+  const T* res = P.b;
+  if (h->cfg.nu1 > 0) {                              // step 1 of Alg. 4 / 5
+    CKS(op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, s));
+    res = P.r;
+  }
+  PrecDev<T>& C = h->L[l + 1].pd<T>();
+  CKS(op_restrict<T>(h, l, res, C.b, s));            // step 2/3 of Alg. 4 / 5
+  CKS(vcycle_level<T>(h, l + 1, s));
+  CKS(op_prolongate_add<T>(h, l, C.x, P.x, s));      // Alg. 6 / 7
+  for (int it = 0; it < h->cfg.nu2; ++it) {          // postsmoothing (Eq. Alg:VGMGPost)
+    CKS(op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, s));
+    CKS(op_sweep<T>(h, l, P.r, P.x, s));
+  }
+  return STMG_OK;
+}
+
+// Run the V-cycle on the finest level's fixed buffers, through a CUDA graph if enabled.
+template <typename T>
+static int run_vcycle(stmg_handle* h) {
+  const int w = prec_of<T>();
+  if (!h->cfg.use_graphs) return vcycle_level<T>(h, 0, h->st);
+  if (!h->graph[w]) {
+    // warm-up run (sets kernel attributes outside capture), then capture on gst
+    CK(cudaEventRecord(h->ev_fork, h->st));
+    CK(cudaStreamWaitEvent(h->gst, h->ev_fork, 0));
+    CKS(vcycle_level<T>(h, 0, h->gst));
+    CK(cudaStreamSynchronize(h->gst));
+    harvest(h, h->pending, false);
+    const long long before = h->launches;
+    CK(cudaStreamBeginCapture(h->gst, cudaStreamCaptureModeRelaxed));
+    h->capturing = true;
+    int s = vcycle_level<T>(h, 0, h->gst);
+    h->capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->gst, &g);
+    if (s != STMG_OK) { if (g) cudaGraphDestroy(g); return s; }
+    if (e != cudaSuccess) return STMG_ERR_CUDA;
+    e = cudaGraphInstantiate(&h->graph[w], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { h->graph[w] = nullptr; return STMG_ERR_CUDA; }
+    h->graph_kernels[w] = h->launches - before;
+    h->launches = before;
+    CK(cudaEventRecord(h->ev_join, h->gst));
+    CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+    return STMG_OK;   // the warm-up run already produced this V-cycle's output
+  }
+  CK(cudaEventRecord(h->ev_fork, h->st));
+  CK(cudaStreamWaitEvent(h->gst, h->ev_fork, 0));
+  CK(cudaGraphLaunch(h->graph[w], h->gst));
+  h->launches += h->graph_kernels[w];
+  CK(cudaEventRecord(h->ev_join, h->gst));
+  CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+  if (h->prof && !h->graph_pairs[w].empty()) h->graph_pending[w] = true;
+  return STMG_OK;
+}
+
+// z = M v (FP64 in and out) with the V-cycle in precision prec
+static int precondition(stmg_handle* h, int prec, const double* v, double* z) {
+  LevelDev& l0 = h->L[0];
+  const long long D = l0.H.size;
+  Prof pr(h, PROF_VCYCLE, h->st);
+  if (prec == STMG_FP64) {
+    if (!l0.d.b) return STMG_ERR_ARG;
+    CK(cudaMemcpyAsync(l0.d.b, v, sizeof(double) * D, cudaMemcpyDeviceToDevice, h->st));
+    CKS(run_vcycle<double>(h));
+    CK(cudaMemcpyAsync(z, l0.d.x, sizeof(double) * D, cudaMemcpyDeviceToDevice, h->st));
+  } else {
+    if (!l0.f.b) return STMG_ERR_ARG;
+    CK((launch_convert<double, float>(D, v, l0.f.b, h->st)));
+    CKS(run_vcycle<float>(h));
+    CK((launch_convert<float, double>(D, l0.f.x, z, h->st)));
+    h->launches += 2;
+  }
+  return STMG_OK;
+}
+
+// ||x||_2 into dev_out[0] (device), via the multidot reduction
+static int dev_norm(stmg_handle* h, const double* x, long long n, double* dev_out) {
+  const int nb = multidot_blocks(n);
+  CK(launch_multidot(n, 1, x, n, x, h->partial, nb, h->st));
+  CK(launch_reduce_partials(1, nb, h->partial, dev_out, 0, h->st));
+  CK(launch_sqrt_inplace(dev_out, h->st));
+  h->launches += 3;
+  return STMG_OK;
+}
+
+static int ensure_krylov(stmg_handle* h, int m) {
+  if (h->m_alloc >= m) return STMG_OK;
+  auto f = [](void* p) { if (p) cudaFree(p); };
+  f(h->V); f(h->Z); f(h->w); f(h->hcol); f(h->tmp); f(h->partial); f(h->bnorm);
+  h->V = h->Z = h->w = h->hcol = h->tmp = h->partial = h->bnorm = nullptr;
+  const long long D = h->L[0].H.size;
+  CKS(dalloc(&h->V, (size_t)(m + 1) * D));
+  CKS(dalloc(&h->Z, (size_t)m * D));
+  CKS(dalloc(&h->w, D));
+  CKS(dalloc(&h->hcol, m + 2));
+  CKS(dalloc(&h->tmp, m + 2));
+  CKS(dalloc(&h->partial, (size_t)304 * (m + 2)));
+  CKS(dalloc(&h->bnorm, 4));
+  h->m_alloc = m;
+  return STMG_OK;
+}
+
+static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_info* info) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int m = h->cfg.gmres_max_iter;
+  const double tol = h->cfg.rel_tol;
+  const int prec = h->cfg.precond_precision;
+  CKS(ensure_krylov(h, m));
+  LevelDev& l0 = h->L[0];
+  const long long D = l0.H.size;
+  cudaStream_t s = h->st;
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), hc(m + 2);
+  double hv[2];
+  info->iterations = 0; info->rel_residual = 0.0; info->status = STMG_OK; info->seconds = 0.0;
+  CKS(dev_norm(h, b, D, h->bnorm));
+  {
+    Prof pr(h, STMG_PROF_OPERATOR, s);
+    CKS(op_apply<double>(h, 0, x, b, h->V, RESIDUAL, s));
+  }
+  CKS(dev_norm(h, h->V, D, h->bnorm + 1));
+  CK(cudaMemcpyAsync(hv, h->bnorm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  harvest_all(h);
+  const double bn = hv[0], beta = hv[1];
+  if (!std::isfinite(bn) || !std::isfinite(beta)) { info->status = STMG_ERR_NONFINITE; return info->status; }
+  if (bn == 0.0) {
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * D, s));
+    CK(cudaStreamSynchronize(s));
+    return STMG_OK;
+  }
+  if (beta <= tol * bn) {
+    info->rel_residual = beta / bn;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return STMG_OK;
+  }
+  CK(launch_scale(D, 1.0 / beta, h->V, h->V, s));
+  h->launches += 1;
+  g[0] = beta;
+  int j = 0, status = STMG_ERR_NOT_CONVERGED;
+  for (j = 0; j < m; ++j) {
+    double* vj = h->V + (size_t)j * D;
+    double* zj = h->Z + (size_t)j * D;
+    CKS(precondition(h, prec, vj, zj));
+    {
+      Prof pr(h, STMG_PROF_OPERATOR, s);
+      CKS(op_apply<double>(h, 0, zj, nullptr, h->w, APPLY, s));
+    }
+    {
+      Prof pr(h, STMG_PROF_OTHER, s);
+      const int nb = multidot_blocks(D);
+      // CGS2: h = V^T w, w -= V h, twice; h accumulated in hcol
+      CK(launch_multidot(D, j + 1, h->V, D, h->w, h->partial, nb, s));
+      CK(launch_reduce_partials(j + 1, nb, h->partial, h->hcol, 0, s));
+      CK(launch_multiaxpy(D, j + 1, h->V, D, h->hcol, -1.0, h->w, s));
+      CK(launch_multidot(D, j + 1, h->V, D, h->w, h->partial, nb, s));
+      CK(launch_reduce_partials(j + 1, nb, h->partial, h->tmp, 0, s));
+      CK(launch_multiaxpy(D, j + 1, h->V, D, h->tmp, -1.0, h->w, s));
+      CK(launch_reduce_partials(j + 1, nb, h->partial, h->hcol, 1, s));
+      CKS(dev_norm(h, h->w, D, h->hcol + j + 1));
+      CK(launch_scale_by_inverse(D, h->hcol + j + 1, h->w, h->V + (size_t)(j + 1) * D, s));
+      h->launches += 8;
+    }
+    CK(cudaMemcpyAsync(hc.data(), h->hcol, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    harvest_all(h);
+    for (int i = 0; i <= j + 1; ++i) {
+      if (!std::isfinite(hc[i])) { info->status = STMG_ERR_NONFINITE; info->iterations = j + 1; return info->status; }
+      H[(size_t)i * m + j] = hc[i];
+    }
+    for (int i = 0; i < j; ++i) {     // previous Givens rotations
+      const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+      H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+      H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+    }
+    const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+    const double den = std::hypot(a, c);
+    if (den == 0.0) { status = STMG_ERR_BREAKDOWN; break; }
+    cs[j] = a / den; sn[j] = c / den;
+    H[(size_t)j * m + j] = den;
+    H[(size_t)(j + 1) * m + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    if (std::fabs(g[j + 1]) <= tol * bn) { status = STMG_OK; ++j; break; }
+    if (c == 0.0) { status = STMG_OK; ++j; break; }   // lucky breakdown: exact solution
+  }
+  const int kdim = j < m ? j : m;
+  // back substitution H y = g, then x += Z y
+  std::vector<double> y(kdim, 0.0);
+  for (int i = kdim - 1; i >= 0; --i) {
+    double t = g[i];
+    for (int q = i + 1; q < kdim; ++q) t -= H[(size_t)i * m + q] * y[q];
+    y[i] = t / H[(size_t)i * m + i];
+  }
+  CK(cudaMemcpyAsync(h->tmp, y.data(), sizeof(double) * kdim, cudaMemcpyHostToDevice, s));
+  CK(launch_multiaxpy(D, kdim, h->Z, D, h->tmp, 1.0, x, s));
+  h->launches += 1;
+  {
+    Prof pr(h, STMG_PROF_OPERATOR, s);
+    CKS(op_apply<double>(h, 0, x, b, h->w, RESIDUAL, s));
+  }
+  CKS(dev_norm(h, h->w, D, h->bnorm + 2));
+  CK(cudaMemcpyAsync(hv, h->bnorm + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  harvest_all(h);
+  info->iterations = kdim;
+  info->rel_residual = hv[0] / bn;
+  if (!std::isfinite(info->rel_residual)) status = STMG_ERR_NONFINITE;
+  else if (info->rel_residual <= tol * (1.0 + 1e-3)) status = STMG_OK;
+  else if (status == STMG_OK) status = STMG_ERR_NOT_CONVERGED;
+  info->status = status;
+  info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return status;
+}
+
+template <typename T>
+static int smooth_t(stmg_handle* h, int lvl, const T* b, T* x, int steps) {
+  PrecDev<T>& P = h->L[lvl].pd<T>();
+  for (int s = 0; s < steps; ++s) {
+    CKS(op_apply<T>(h, lvl, x, b, P.r, RESIDUAL, h->st));
+    CKS(op_sweep<T>(h, lvl, P.r, x, h->st));
+  }
+  return STMG_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------
+extern "C" {
+
+const char* stmg_status_string(int s) {
+  switch (s) {
+    case STMG_OK: return "ok";
+    case STMG_ERR_ARG: return "invalid argument";
+    case STMG_ERR_OOM: return "out of memory";
+    case STMG_ERR_NOT_CONVERGED: return "not converged";
+    case STMG_ERR_BREAKDOWN: return "Arnoldi breakdown";
+    case STMG_ERR_NONFINITE: return "non-finite value";
+    case STMG_ERR_CUDA: return "CUDA error";
+    case STMG_ERR_UNIMPLEMENTED: return "not implemented for these parameters";
+    case STMG_ERR_SINGULAR: return "singular patch or coarse matrix";
+    default: return "unknown status";
+  }
+}
+
+int stmg_default_config(stmg_config* c) {
+  if (!c) return STMG_ERR_ARG;
+  std::memset(c, 0, sizeof(*c));
+  c->dim = 2; c->n_cells = 8; c->r = 1; c->k = 1;
+  c->nu = 1.0; c->T = 1.0; c->n_slabs = 4;
+  c->n_levels = 0;
+  for (int i = 0; i < STMG_MAX_LEVELS; ++i) c->smoother[i] = STMG_CELL;
+  c->omega = 0.7; c->nu1 = 1; c->nu2 = 1;
+  c->precond_precision = STMG_FP64;
+  c->precisions = 3;
+  c->gmres_max_iter = 200;
+  c->rel_tol = 1e-8;
+  c->use_graphs = 1;
+  return STMG_OK;
+}
+
+static int create_impl(const stmg_config* cfg, stmg_handle* h) {
+  h->cfg = *cfg;
+  const stmg_config& c = h->cfg;
+  if (c.dim != 2 && c.dim != 3) return STMG_ERR_ARG;
+  if (c.n_cells < 1 || c.r < 1 || c.k < 0 || c.n_slabs < 1 || !(c.T > 0) || !(c.nu > 0)) return STMG_ERR_ARG;
+  if (c.r > 4 || c.k > 3) return STMG_ERR_UNIMPLEMENTED;
+  if (c.gmres_max_iter < 1 || !(c.rel_tol > 0) || c.nu1 < 0 || c.nu2 < 0) return STMG_ERR_ARG;
+  if ((c.precisions & 3) == 0) return STMG_ERR_ARG;
+  if (c.precond_precision != STMG_FP64 && c.precond_precision != STMG_FP32) return STMG_ERR_ARG;
+  if (!(c.precisions & (1 << c.precond_precision))) return STMG_ERR_ARG;
+  h->tau = c.T / c.n_slabs;
+  std::vector<std::array<int, 3>> lv;
+  if (c.n_levels == 0) {
+    if (c.n_cells & (c.n_cells - 1)) return STMG_ERR_ARG;   // default rule needs n = 2^c
+    lv = default_hierarchy(c.n_cells, c.r, c.k);
+  } else {
+    if (c.n_levels > STMG_MAX_LEVELS) return STMG_ERR_ARG;
+    for (int i = 0; i < c.n_levels; ++i) lv.push_back({c.level_n[i], c.level_r[i], c.level_k[i]});
+    if (lv[0][0] != c.n_cells || lv[0][1] != c.r || lv[0][2] != c.k) return STMG_ERR_ARG;
+  }
+  if (lv.size() > STMG_MAX_LEVELS) return STMG_ERR_ARG;
+  for (size_t i = 0; i < lv.size(); ++i) {
+    if (lv[i][1] < 1 || lv[i][1] > 4 || lv[i][2] < 0 || lv[i][2] > 3 || lv[i][0] < 1) return STMG_ERR_ARG;
+    if (i + 1 < lv.size()) {
+      const auto &f = lv[i], &cc = lv[i + 1];
+      const bool hstep = f[0] == 2 * cc[0], same = f[0] == cc[0];
+      if (!(hstep || same) || cc[1] > f[1] || cc[2] > f[2]) return STMG_ERR_ARG;
+    }
+  }
+  h->L.resize(lv.size());
+  try {
+    for (size_t i = 0; i < lv.size(); ++i) {
+      LevelDev& L = h->L[i];
+      init_level_geometry(&L.H, c.dim, lv[i][0], lv[i][1], lv[i][2], h->tau, c.nu);
+    }
+  } catch (const std::exception&) {
+    return STMG_ERR_ARG;
+  }
+  CK(cudaStreamCreateWithFlags(&h->gst, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  for (size_t i = 0; i < h->L.size(); ++i) {
+    LevelDev& L = h->L[i];
+    LevelHost& H = L.H;
+    const bool coarsest = i + 1 == h->L.size();
+    double* d_cls = nullptr;
+    int* d_cls_of = nullptr;
+    if (!coarsest) {
+      const int kind = c.smoother[i] == STMG_VSP ? STMG_VSP : STMG_CELL;
+      build_patches(&H, kind);
+      if (!build_class_inverses(&H)) return STMG_ERR_SINGULAR;
+      CKS(dalloc(&L.dofs, H.dofs.size()));
+      CK(cudaMemcpy(L.dofs, H.dofs.data(), sizeof(int) * H.dofs.size(), cudaMemcpyHostToDevice));
+      CKS(dalloc(&d_cls, H.class_inv.size()));
+      CK(cudaMemcpy(d_cls, H.class_inv.data(), sizeof(double) * H.class_inv.size(), cudaMemcpyHostToDevice));
+      CKS(dalloc(&d_cls_of, H.patch_class.size()));
+      CK(cudaMemcpy(d_cls_of, H.patch_class.data(), sizeof(int) * H.patch_class.size(), cudaMemcpyHostToDevice));
+      const double inv_bytes = (double)H.n_patches * H.B * H.Bc * 4.0;
+      L.streaming = inv_bytes > 48e6 ? 1 : 0;
+      L.ppb = std::max(1, std::min(8, 1024 / H.B));
+    } else {
+      std::vector<double> Gcm;
+      if (!build_coarse_inverse(&H, &Gcm)) return STMG_ERR_SINGULAR;
+      CKS(dalloc(&L.G, Gcm.size()));
+      CK(cudaMemcpy(L.G, Gcm.data(), sizeof(double) * Gcm.size(), cudaMemcpyHostToDevice));
+    }
+    int st = STMG_OK;
+    if (c.precisions & 1) st = setup_precision<double>(h, L, d_cls, d_cls_of);
+    if (st == STMG_OK && (c.precisions & 2)) st = setup_precision<float>(h, L, d_cls, d_cls_of);
+    cudaStreamSynchronize(h->st);
+    if (d_cls) cudaFree(d_cls);
+    if (d_cls_of) cudaFree(d_cls_of);
+    // keep the host copies small: drop the per-class index lists and dense inverses
+    H.class_idx.clear(); H.class_idx.shrink_to_fit();
+    H.class_dir.clear(); H.class_dir.shrink_to_fit();
+    H.class_inv.clear(); H.class_inv.shrink_to_fit();
+    if (st != STMG_OK) return st;
+  }
+  for (size_t i = 0; i + 1 < h->L.size(); ++i) {
+    fill_transfer_params<double>(h->L[i].H, h->L[i + 1].H, &h->L[i].d.tp);
+    fill_transfer_params<float>(h->L[i].H, h->L[i + 1].H, &h->L[i].f.tp);
+  }
+  // finest-level helpers: slab coupling and forcing
+  const LevelHost& F = h->L[0].H;
+  MassParams& mp = h->mp;
+  std::memset(&mp, 0, sizeof(mp));
+  mp.dim = F.dim; mp.n = F.n; mp.G = F.G; mp.np = F.np; mp.kt = F.kt;
+  mp.n_nodes = F.n_nodes; mp.n_vel = F.n_vel;
+  for (int i = 0; i < F.np * F.np; ++i) mp.M1[i] = F.t1.M1[i];
+  mp.hd = std::pow(F.h, F.dim);
+  for (int a = 0; a < F.kt; ++a) mp.phi_left[a] = F.tt.phi_left[a];
+  ForcingParams& fp = h->fp;
+  std::memset(&fp, 0, sizeof(fp));
+  fp.dim = F.dim; fp.n = F.n; fp.G = F.G; fp.np = F.np; fp.nq = F.r + 4; fp.kt = F.kt;
+  fp.n_nodes = F.n_nodes; fp.n_vel = F.n_vel;
+  double gx[16], gw[16];
+  gauss_legendre(fp.nq, gx, gw);
+  for (int q = 0; q < fp.nq; ++q) {
+    const double xq = 0.5 * (gx[q] + 1.0);
+    fp.wq[q] = 0.5 * gw[q] * F.h;
+    for (int p = 0; p < F.np; ++p) fp.phiq[p * fp.nq + q] = lagrange_eval(F.t1.xi, F.np, p, xq);
+  }
+  for (int a = 0; a < F.kt; ++a) fp.scale[a] = 0.5 * h->tau * F.tt.weights[a];
+  CK(cudaDeviceSynchronize());
+  return STMG_OK;
+}
+
+int stmg_create(const stmg_config* cfg, stmg_handle** out) {
+  if (!cfg || !out) return STMG_ERR_ARG;
+  *out = nullptr;
+  stmg_handle* h = new (std::nothrow) stmg_handle();
+  if (!h) return STMG_ERR_OOM;
+  int s;
+  try {
+    s = create_impl(cfg, h);
+  } catch (const std::bad_alloc&) {
+    s = STMG_ERR_OOM;
+  } catch (...) {
+    s = STMG_ERR_ARG;
+  }
+  if (s != STMG_OK) { stmg_destroy(h); return s; }
+  *out = h;
+  return STMG_OK;
+}
+
+void stmg_destroy(stmg_handle* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
+  if (h->gst) cudaStreamSynchronize(h->gst);
+  for (auto& g : h->graph) if (g) cudaGraphExecDestroy(g);
+  for (auto& L : h->L) free_level(L);
+  auto f = [](void* p) { if (p) cudaFree(p); };
+  f(h->V); f(h->Z); f(h->w); f(h->hcol); f(h->tmp); f(h->partial); f(h->bnorm);
+  f(h->xhost_b); f(h->xhost_x);
+  for (auto e : h->all_events) cudaEventDestroy(e);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->gst) cudaStreamDestroy(h->gst);
+  delete h;
+}
+
+int stmg_set_stream(stmg_handle* h, void* stream) {
+  if (!h) return STMG_ERR_ARG;
+  h->st = reinterpret_cast<cudaStream_t>(stream);
+  return STMG_OK;
+}
+
+int stmg_num_levels(const stmg_handle* h, int* n) {
+  if (!h || !n) return STMG_ERR_ARG;
+  *n = (int)h->L.size();
+  return STMG_OK;
+}
+
+int stmg_level_info(const stmg_handle* h, int lvl, stmg_level_info_t* info) {
+  if (!h || !info || lvl < 0 || lvl >= (int)h->L.size()) return STMG_ERR_ARG;
+  const LevelDev& L = h->L[lvl];
+  const LevelHost& H = L.H;
+  std::memset(info, 0, sizeof(*info));
+  info->n = H.n; info->r = H.r; info->k = H.k;
+  info->size = H.size; info->n_vel = H.n_vel; info->n_pres = H.n_pres;
+  info->smoother = H.smoother;
+  info->patch_size = H.B;
+  info->n_patches = H.n_patches;
+  info->n_patch_classes = (int)H.class_rep.size();
+  if (L.d.has_inv) info->inverse_bytes[0] = (long long)H.n_patches * H.B * H.Bc * 8;
+  if (L.f.has_inv) info->inverse_bytes[1] = (long long)H.n_patches * H.B * H.Bc * 4;
+  return STMG_OK;
+}
+
+static bool prec_ok(const stmg_handle* h, int lvl, int prec) {
+  if (!h || lvl < 0 || lvl >= (int)h->L.size()) return false;
+  if (prec == STMG_FP64) return h->L[lvl].d.b != nullptr;
+  if (prec == STMG_FP32) return h->L[lvl].f.b != nullptr;
+  return false;
+}
+
+int stmg_apply(stmg_handle* h, int lvl, int prec, const void* x, void* y) {
+  if (!prec_ok(h, lvl, prec) || !x || !y) return STMG_ERR_ARG;
+  if (prec == STMG_FP64) return op_apply<double>(h, lvl, (const double*)x, nullptr, (double*)y, APPLY, h->st);
+  return op_apply<float>(h, lvl, (const float*)x, nullptr, (float*)y, APPLY, h->st);
+}
+
+int stmg_residual(stmg_handle* h, int lvl, int prec, const void* b, const void* x, void* r) {
+  if (!prec_ok(h, lvl, prec) || !x || !b || !r) return STMG_ERR_ARG;
+  if (prec == STMG_FP64)
+    return op_apply<double>(h, lvl, (const double*)x, (const double*)b, (double*)r, RESIDUAL, h->st);
+  return op_apply<float>(h, lvl, (const float*)x, (const float*)b, (float*)r, RESIDUAL, h->st);
+}
+
+int stmg_smooth(stmg_handle* h, int lvl, int prec, const void* b, void* x, int steps) {
+  if (!prec_ok(h, lvl, prec) || !b || !x || steps < 0 || lvl == (int)h->L.size() - 1) return STMG_ERR_ARG;
+  if (prec == STMG_FP64) return smooth_t<double>(h, lvl, (const double*)b, (double*)x, steps);
+  return smooth_t<float>(h, lvl, (const float*)b, (float*)x, steps);
+}
+
+int stmg_vanka_sweep(stmg_handle* h, int lvl, int prec, const void* res, void* x) {
+  if (!prec_ok(h, lvl, prec) || !res || !x || lvl == (int)h->L.size() - 1) return STMG_ERR_ARG;
+  if (prec == STMG_FP64) return op_sweep<double>(h, lvl, (const double*)res, (double*)x, h->st);
+  return op_sweep<float>(h, lvl, (const float*)res, (float*)x, h->st);
+}
+
+int stmg_restrict(stmg_handle* h, int lvl, int prec, const void* rf, void* bc) {
+  if (!prec_ok(h, lvl, prec) || lvl + 1 >= (int)h->L.size() || !rf || !bc) return STMG_ERR_ARG;
+  if (prec == STMG_FP64) return op_restrict<double>(h, lvl, (const double*)rf, (double*)bc, h->st);
+  return op_restrict<float>(h, lvl, (const float*)rf, (float*)bc, h->st);
+}
+
+int stmg_prolongate_add(stmg_handle* h, int lvl, int prec, const void* yc, void* xf) {
+  if (!prec_ok(h, lvl, prec) || lvl + 1 >= (int)h->L.size() || !yc || !xf) return STMG_ERR_ARG;
+  if (prec == STMG_FP64) return op_prolongate_add<double>(h, lvl, (const double*)yc, (double*)xf, h->st);
+  return op_prolongate_add<float>(h, lvl, (const float*)yc, (float*)xf, h->st);
+}
+
+int stmg_coarse_solve(stmg_handle* h, int prec, const void* b, void* x) {
+  if (!h || !b || !x || !prec_ok(h, (int)h->L.size() - 1, prec)) return STMG_ERR_ARG;
+  if (prec == STMG_FP64) return op_coarse<double>(h, (const double*)b, (double*)x, h->st);
+  return op_coarse<float>(h, (const float*)b, (float*)x, h->st);
+}
+
+int stmg_vcycle(stmg_handle* h, int prec, const double* b, double* x) {
+  if (!h || !b || !x || !prec_ok(h, 0, prec)) return STMG_ERR_ARG;
+  return precondition(h, prec, b, x);
+}
+
+int stmg_slab_rhs(stmg_handle* h, const double* F, const double* x_prev, double* b) {
+  if (!h || !F || !b) return STMG_ERR_ARG;
+  const LevelHost& H = h->L[0].H;
+  CK(cudaMemcpyAsync(b, F, sizeof(double) * H.size, cudaMemcpyDeviceToDevice, h->st));
+  if (x_prev) {
+    CK(launch_mass_coupling(h->mp, x_prev + (size_t)(H.kt - 1) * H.n_vel, b, h->st));
+    h->launches += 1;
+  }
+  return STMG_OK;
+}
+
+int stmg_solve_slab(stmg_handle* h, const double* b, double* x, stmg_solve_info* info) {
+  if (!h || !b || !x || !info) return STMG_ERR_ARG;
+  return solve_impl(h, b, x, info);
+}
+
+int stmg_solve_slab_host(stmg_handle* h, const double* bh, double* xh, stmg_solve_info* info) {
+  if (!h || !bh || !xh || !info) return STMG_ERR_ARG;
+  const long long D = h->L[0].H.size;
+  if (!h->xhost_b) {
+    CKS(dalloc(&h->xhost_b, D));
+    CKS(dalloc(&h->xhost_x, D));
+  }
+  CK(cudaMemcpyAsync(h->xhost_b, bh, sizeof(double) * D, cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->xhost_x, xh, sizeof(double) * D, cudaMemcpyHostToDevice, h->st));
+  int s = solve_impl(h, h->xhost_b, h->xhost_x, info);
+  CK(cudaMemcpyAsync(xh, h->xhost_x, sizeof(double) * D, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return s;
+}
+
+int stmg_forcing_npoints(const stmg_handle* h, int* nq) {
+  if (!h || !nq) return STMG_ERR_ARG;
+  *nq = ipow(h->fp.nq, h->fp.dim);
+  return STMG_OK;
+}
+
+int stmg_forcing_points(stmg_handle* h, double* xq) {
+  if (!h || !xq) return STMG_ERR_ARG;
+  const LevelHost& F = h->L[0].H;
+  const int nq = h->fp.nq, dim = F.dim, nqc = ipow(nq, dim);
+  double gx[16], gw[16];
+  gauss_legendre(nq, gx, gw);
+  std::vector<double> pts((size_t)F.n_cells * nqc * dim);
+  for (long long c = 0; c < F.n_cells; ++c) {
+    const int cc[3] = {(int)(c % F.n), (int)((c / F.n) % F.n), dim == 3 ? (int)(c / ((long long)F.n * F.n)) : 0};
+    for (int q = 0; q < nqc; ++q) {
+      const int qi[3] = {q % nq, (q / nq) % nq, q / (nq * nq)};
+      for (int d = 0; d < dim; ++d)
+        pts[((size_t)c * nqc + q) * dim + d] = (cc[d] + 0.5 * (gx[qi[d]] + 1.0)) * F.h;
+    }
+  }
+  CK(cudaMemcpy(xq, pts.data(), sizeof(double) * pts.size(), cudaMemcpyHostToDevice));
+  return STMG_OK;
+}
+
+int stmg_slab_times(const stmg_handle* h, int slab, double* t) {
+  if (!h || !t || slab < 0) return STMG_ERR_ARG;
+  const LevelHost& F = h->L[0].H;
+  for (int a = 0; a < F.kt; ++a) t[a] = slab * h->tau + 0.5 * h->tau * (F.tt.nodes[a] + 1.0);
+  return STMG_OK;
+}
+
+int stmg_assemble_forcing(stmg_handle* h, const double* fq, double* F) {
+  if (!h || !fq || !F) return STMG_ERR_ARG;
+  CK(cudaMemsetAsync(F, 0, sizeof(double) * h->L[0].H.size, h->st));
+  CK(launch_forcing(h->fp, fq, F, h->st));
+  h->launches += 1;
+  return STMG_OK;
+}
+
+int stmg_set_profiling(stmg_handle* h, int on) {
+  if (!h || on < 0 || on > 2) return STMG_ERR_ARG;
+  if (on != h->prof) {
+    for (auto& g : h->graph) if (g) { cudaGraphExecDestroy(g); g = nullptr; }   // recapture with/without events
+    h->graph_pairs[0].clear(); h->graph_pairs[1].clear();
+  }
+  h->prof = on;
+  return STMG_OK;
+}
+
+int stmg_get_profile(stmg_handle* h, double* ms, long long* n, int reset) {
+  if (!h) return STMG_ERR_ARG;
+  if (h->st) CK(cudaStreamSynchronize(h->st)); else CK(cudaDeviceSynchronize());
+  CK(cudaStreamSynchronize(h->gst));
+  harvest_all(h);
+  for (int i = 0; i < STMG_PROF_N; ++i) {
+    if (ms) ms[i] = h->prof_ms[i];
+    if (n) n[i] = h->prof_n[i];
+  }
+  if (ms) ms[STMG_PROF_MG_OTHER] = h->prof_ms[PROF_VCYCLE] - h->prof_ms[STMG_PROF_SMOOTHER];
+  if (n) n[STMG_PROF_MG_OTHER] = h->prof_n[PROF_VCYCLE];
+  if (reset) {
+    std::memset(h->prof_ms, 0, sizeof(h->prof_ms));
+    std::memset(h->prof_n, 0, sizeof(h->prof_n));
+  }
+  return STMG_OK;
+}
+
+long long stmg_kernel_launches(const stmg_handle* h) { return h ? h->launches : 0; }
+
+int stmg_sweep_bytes(const stmg_handle* h, int lvl, int prec, double* bytes) {
+  if (!h || !bytes || lvl < 0 || lvl + 1 >= (int)h->L.size()) return STMG_ERR_ARG;
+  const LevelHost& H = h->L[lvl].H;
+  const double s = prec == STMG_FP64 ? 8.0 : 4.0;
+  // inverses + patch index table + gathered residual + weights + read-modify-write of x
+  *bytes = (double)H.n_patches * H.B * H.Bc * s + (double)H.n_patches * H.B * 4.0 + 4.0 * H.size * s;
+  return STMG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+// Internal declarations of libstmg: level data, kernel parameter blocks and launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <array>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "stmg.h"
+
+namespace stmg {
+
+constexpr int MAXNP = 6;    // velocity nodes per direction per cell (r <= 4)
+constexpr int MAXKT = 4;    // temporal dofs per slab (k <= 3)
+constexpr int MAXPM = 35;   // pressure modes per cell, C(4+3, 3)
+constexpr int MAXNS = 2 * (MAXNP - 1) + 1;  // fine nodes per direction under one coarse cell
+
+// ------------------------------------------------------------------------------------
+// host-side numerics (setup.cpp)
+// ------------------------------------------------------------------------------------
+struct Tables1D {                 // one spatial degree on the reference interval [0,1]
+  int np = 0;                     // r + 2 velocity nodes
+  int r = 0;
+  double xi[MAXNP];               // Gauss-Lobatto nodes
+  double M1[MAXNP * MAXNP];       // int ell_i ell_j
+  double K1[MAXNP * MAXNP];       // int ell_i' ell_j'
+  double G1[MAXNP * MAXNP];       // [i * np + p] = int L_i ell_p'   (i <= r)
+  double N1[MAXNP * MAXNP];       // [i * np + p] = int L_i ell_p
+};
+
+struct TimeTables {               // DG(k) with the right Radau Lagrange basis
+  int kt = 0;
+  double nodes[MAXKT], weights[MAXKT];
+  double K[MAXKT * MAXKT];        // [a * kt + b]
+  double M[MAXKT];                // diagonal of the temporal mass, includes tau/2
+  double phi_left[MAXKT];         // phi_a(t_{n-1}^+)
+};
+
+Tables1D make_tables_1d(int r);
+TimeTables make_time_tables(int k, double tau);
+void pressure_modes(int dim, int r, std::vector<std::array<int, 3>>* out);
+void gauss_legendre(int n, double* x, double* w);            // on [-1, 1]
+double lagrange_eval(const double* nodes, int n, int j, double t);
+double legendre_unit(int i, double xi);                       // sqrt(2i+1) P_i(2 xi - 1)
+
+// ------------------------------------------------------------------------------------
+// kernel parameter blocks (passed by value; tables converted to the kernel type)
+// ------------------------------------------------------------------------------------
+template <typename T>
+struct ApplyParams {
+  int n, G, kt, npm, cpb;
+  long long n_nodes, n_vel, n_pres;
+  T M1[MAXNP * MAXNP], K1[MAXNP * MAXNP], G1[MAXNP * MAXNP], N1[MAXNP * MAXNP];
+  T Kt[MAXKT * MAXKT];
+  T hd;                           // h^d (mass scaling)
+  T beta[MAXKT];                  // M_tau[a] nu h^(d-2) (Laplacian scaling)
+  T bscale[MAXKT];                // -M_tau[a] h^(d-1)   (divergence scaling)
+  signed char modes[MAXPM][3];
+};
+
+template <typename T>
+struct TransferParams {
+  int dim, h_type;                // h_type: 1 = n -> 2n in space, 0 = same mesh
+  int nc, nf, npc, npf, ns;       // coarse / fine cells per dir, nodes per cell, span nodes
+  int Gc, Gf, ktc, ktf, npmc, npmf, cpb;
+  long long nnc, nnf, nvc, nvf, npc_tot, npf_tot;   // nodes, velocity dofs, pressure dofs
+  T P1[MAXNS * MAXNP];            // [s * npc + j] = ell_j^coarse(position of fine node s)
+  T Pt[MAXKT * MAXKT];            // [af * ktc + ac] = phi_ac^coarse(t_af^fine)
+  T E[2][MAXNP * MAXNP];          // h-type pressure: E[o][i' * (rc+1) + i]
+  signed char modes_c[MAXPM][3], modes_f[MAXPM][3];
+  int rc;                         // coarse pressure degree
+};
+
+struct ForcingParams {
+  int dim, n, G, np, nq, kt, cpb;
+  long long n_nodes, n_vel;
+  double phiq[MAXNP * 10];        // [p * nq + q] = ell_p(xq)
+  double wq[10];                  // Gauss weights on [0,1] times h
+  double scale[MAXKT];            // tau/2 w_a
+};
+
+struct MassParams {
+  int dim, n, G, np, kt, cpb;
+  long long n_nodes, n_vel;
+  double M1[MAXNP * MAXNP];
+  double hd;
+  double phi_left[MAXKT];
+};
+
+// ------------------------------------------------------------------------------------
+// launchers (return cudaError_t of the launch); all asynchronous on `st`
+// ------------------------------------------------------------------------------------
+enum ApplyMode { APPLY = 0, RESIDUAL = 1 };
+
+template <typename T>
+cudaError_t launch_apply(int dim, int np, const ApplyParams<T>& p, const T* x, const T* b, T* y,
+                         int mode, cudaStream_t st);
+template <typename T>
+size_t apply_smem_bytes(int dim, int np, int kt, int npm, int cpb);
+
+template <typename T>
+cudaError_t launch_vanka_sweep(const int* dofs, const T* inv, const T* res, const T* wgt, T* x,
+                               long long n_patches, int B, int Bc, int ppb, int streaming,
+                               cudaStream_t st);
+template <typename T>
+cudaError_t launch_replicate_inverses(const double* cls, const int* cls_of_patch, T* inv,
+                                      long long n_patches, int B, int Bc, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_prolongate(const TransferParams<T>& p, const T* yc, T* xf, cudaStream_t st);
+template <typename T>
+cudaError_t launch_restrict(const TransferParams<T>& p, const T* rf, T* bc, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_coarse(int D, const double* Gcm, const T* b, T* x, cudaStream_t st);
+
+cudaError_t launch_mass_coupling(const MassParams& p, const double* vprev, double* b, cudaStream_t st);
+cudaError_t launch_forcing(const ForcingParams& p, const double* fq, double* F, cudaStream_t st);
+
+// vector kernels
+template <typename Ti, typename To>
+cudaError_t launch_convert(long long n, const Ti* in, To* out, cudaStream_t st);
+cudaError_t launch_scale(long long n, double a, const double* x, double* y, cudaStream_t st);
+cudaError_t launch_multidot(long long n, int nvec, const double* V, long long ld, const double* w,
+                            double* partial, int nblocks, cudaStream_t st);
+cudaError_t launch_reduce_partials(int nvec, int nblocks, const double* partial, double* out,
+                                   int accumulate, cudaStream_t st);
+// y += sign * sum_i coef[i] V[i], coef on the device
+cudaError_t launch_multiaxpy(long long n, int nvec, const double* V, long long ld,
+                             const double* coef, double sign, double* y, cudaStream_t st);
+// y = a * x where a = 1 / dev_scalar[0] (normalisation without a host round trip)
+cudaError_t launch_scale_by_inverse(long long n, const double* dev_scalar, const double* x,
+                                    double* y, cudaStream_t st);
+cudaError_t launch_sqrt_inplace(double* v, cudaStream_t st);
+
+int multidot_blocks(long long n);
+
+}  // namespace stmg

@@ -1,0 +1,180 @@
+// Vector kernels of the FGMRES driver (FP64) and the coarse-level direct solve.
+//
+// The Arnoldi step uses classical Gram-Schmidt applied twice (CGS2): the projections
+// h = V^T w of all previous basis vectors are computed in one pass over V (multidot:
+// per block partial sums for every basis vector, then a deterministic tree over the
+// blocks), and w -= V h is one more pass (multiaxpy).  Scalars stay on the device.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace stmg {
+
+namespace {
+constexpr int RED_THREADS = 256;
+constexpr int MD_VEC = 8;   // basis vectors handled per multidot pass
+}
+
+template <typename Ti, typename To>
+__global__ void k_convert(long long n, const Ti* __restrict__ in, To* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (To)in[i];
+}
+
+static unsigned grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  const long long cap = 152LL * 16;
+  return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+template <typename Ti, typename To>
+cudaError_t launch_convert(long long n, const Ti* in, To* out, cudaStream_t st) {
+  k_convert<Ti, To><<<grid_for(n), 256, 0, st>>>(n, in, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_convert<double, float>(long long, const double*, float*, cudaStream_t);
+template cudaError_t launch_convert<float, double>(long long, const float*, double*, cudaStream_t);
+
+__global__ void k_scale(long long n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+cudaError_t launch_scale(long long n, double a, const double* x, double* y, cudaStream_t st) {
+  k_scale<<<grid_for(n), 256, 0, st>>>(n, a, x, y);
+  return cudaGetLastError();
+}
+
+__global__ void k_scale_by_inverse(long long n, const double* __restrict__ s, const double* __restrict__ x,
+                                   double* __restrict__ y) {
+  const double a = 1.0 / s[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+cudaError_t launch_scale_by_inverse(long long n, const double* s, const double* x, double* y, cudaStream_t st) {
+  k_scale_by_inverse<<<grid_for(n), 256, 0, st>>>(n, s, x, y);
+  return cudaGetLastError();
+}
+
+__global__ void k_sqrt(double* v) { v[0] = sqrt(v[0]); }
+cudaError_t launch_sqrt_inplace(double* v, cudaStream_t st) {
+  k_sqrt<<<1, 1, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+int multidot_blocks(long long n) {
+  long long b = (n + RED_THREADS * 8 - 1) / (RED_THREADS * 8);
+  if (b > 304) b = 304;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// partial[blk * nvec + i] = sum over this block's rows of V[i][row] * w[row]
+__global__ void __launch_bounds__(RED_THREADS) k_multidot(long long n, int nvec, const double* __restrict__ V,
+                                                          long long ld, const double* __restrict__ w,
+                                                          double* __restrict__ partial) {
+  __shared__ double red[RED_THREADS / 32][MD_VEC];
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const long long lo = blockIdx.x * chunk;
+  const long long hi = lo + chunk < n ? lo + chunk : n;
+  for (int v0 = 0; v0 < nvec; v0 += MD_VEC) {
+    const int nv = nvec - v0 < MD_VEC ? nvec - v0 : MD_VEC;
+    double acc[MD_VEC];
+#pragma unroll
+    for (int i = 0; i < MD_VEC; ++i) acc[i] = 0.0;
+    for (long long r = lo + threadIdx.x; r < hi; r += blockDim.x) {
+      const double wr = w[r];
+#pragma unroll
+      for (int i = 0; i < MD_VEC; ++i)
+        if (i < nv) acc[i] += V[(size_t)(v0 + i) * ld + r] * wr;
+    }
+#pragma unroll
+    for (int i = 0; i < MD_VEC; ++i) {
+      double a = acc[i];
+      for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][i] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+      double s = 0.0;
+      for (int wv = 0; wv < RED_THREADS / 32; ++wv) s += red[wv][threadIdx.x];
+      partial[(size_t)blockIdx.x * nvec + v0 + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_multidot(long long n, int nvec, const double* V, long long ld, const double* w, double* partial,
+                            int nblocks, cudaStream_t st) {
+  k_multidot<<<nblocks, RED_THREADS, 0, st>>>(n, nvec, V, ld, w, partial);
+  return cudaGetLastError();
+}
+
+// out[i] (+)= sum_blk partial[blk * nvec + i], fixed order (deterministic)
+__global__ void k_reduce_partials(int nvec, int nblocks, const double* __restrict__ partial, double* __restrict__ out,
+                                  int accumulate) {
+  const int i = blockIdx.x;
+  __shared__ double red[RED_THREADS];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(size_t)b * nvec + i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = RED_THREADS / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[i] = accumulate ? out[i] + red[0] : red[0];
+}
+
+cudaError_t launch_reduce_partials(int nvec, int nblocks, const double* partial, double* out, int accumulate,
+                                   cudaStream_t st) {
+  k_reduce_partials<<<nvec, RED_THREADS, 0, st>>>(nvec, nblocks, partial, out, accumulate);
+  return cudaGetLastError();
+}
+
+// y[r] += sign * sum_i coef[i] V[i][r]
+__global__ void k_multiaxpy(long long n, int nvec, const double* __restrict__ V, long long ld,
+                            const double* __restrict__ coef, double sign, double* __restrict__ y) {
+  extern __shared__ double cs[];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = sign * coef[i];
+  __syncthreads();
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < nvec; ++i) s += cs[i] * V[(size_t)i * ld + r];
+    y[r] += s;
+  }
+}
+
+cudaError_t launch_multiaxpy(long long n, int nvec, const double* V, long long ld, const double* coef, double sign,
+                             double* y, cudaStream_t st) {
+  k_multiaxpy<<<grid_for(n), 256, sizeof(double) * (nvec > 0 ? nvec : 1), st>>>(n, nvec, V, ld, coef, sign, y);
+  return cudaGetLastError();
+}
+
+// Coarse direct solve: x = G b, G column-major D x D in FP64; vectors of type T.
+template <typename T>
+__global__ void k_coarse(int D, const double* __restrict__ Gcm, const T* __restrict__ b, T* __restrict__ x) {
+  extern __shared__ double bs[];
+  for (int i = threadIdx.x; i < D; i += blockDim.x) bs[i] = (double)b[i];
+  __syncthreads();
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < D; row += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < D; ++c) s += Gcm[(size_t)c * D + row] * bs[c];
+    x[row] = (T)s;
+  }
+}
+
+template <typename T>
+cudaError_t launch_coarse(int D, const double* Gcm, const T* b, T* x, cudaStream_t st) {
+  const int blocks = (D + 255) / 256;
+  const size_t smem = sizeof(double) * (size_t)D;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_coarse<T><<<blocks, 256, smem, st>>>(D, Gcm, b, x);
+  return cudaGetLastError();
+}
+template cudaError_t launch_coarse<double>(int, const double*, const double*, double*, cudaStream_t);
+template cudaError_t launch_coarse<float>(int, const double*, const float*, float*, cudaStream_t);
+
+}  // namespace stmg

@@ -1,0 +1,378 @@
+// Host setup of the multigrid levels: hierarchy (Alg. 2/3), patch index sets (cell and
+// vertex-star patches, remark after Eq. vanka), patch matrices R_T S R_T^T assembled
+// from element contributions, their inversion (Gauss-Jordan, partial pivoting, FP64),
+// and the bordered coarsest-level inverse.
+#include "levels.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+#include <thread>
+#include <unordered_map>
+
+namespace stmg {
+
+static int ipow(int b, int e) { int r = 1; while (e-- > 0) r *= b; return r; }
+static int binom(int n, int k) { long long r = 1; for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i; return (int)r; }
+
+std::vector<std::array<int, 3>> default_hierarchy(int n, int r, int k) {
+  // space: (n, r), (n, r/2), ..., (n, 1), then (n/2, 1), ..., (1, 1)
+  std::vector<std::array<int, 2>> space;
+  for (int rr = r; rr >= 1; rr /= 2) space.push_back({n, rr});
+  for (int nn = n / 2; nn >= 1; nn /= 2) space.push_back({nn, 1});
+  // time: k, k/2, ..., 1, then 1 again (the geometric loop of Alg. 2 re-adds the last
+  // pair); k = 0 stays 0.  Both lists are aligned at the coarse end, the shorter one is
+  // padded at the fine end with its finest entry (Alg. 3, P4).
+  std::vector<int> time;
+  if (k == 0) time.push_back(0);
+  else { for (int kk = k; kk >= 1; kk /= 2) time.push_back(kk); time.push_back(1); }
+  const size_t L = std::max(space.size(), time.size());
+  while (space.size() < L) space.insert(space.begin(), space.front());
+  while (time.size() < L) time.insert(time.begin(), time.front());
+  std::vector<std::array<int, 3>> out;
+  for (size_t i = 0; i < L; ++i) out.push_back({space[i][0], space[i][1], time[i]});
+  return out;
+}
+
+void init_level_geometry(LevelHost* L, int dim, int n, int r, int k, double tau, double nu) {
+  L->dim = dim; L->n = n; L->r = r; L->k = k; L->kt = k + 1;
+  L->np = r + 2; L->G = (r + 1) * n + 1;
+  L->nq = ipow(L->np, dim);
+  L->h = 1.0 / n; L->tau = tau; L->nu = nu;
+  pressure_modes(dim, r, &L->modes);
+  L->npm = (int)L->modes.size();
+  if (L->npm != binom(r + dim, dim)) throw std::runtime_error("pressure modes");
+  L->n_cells = ipow(n, dim);
+  L->n_nodes = 1; for (int d = 0; d < dim; ++d) L->n_nodes *= L->G;
+  L->n_vel = (long long)dim * L->n_nodes;
+  L->n_pres = (long long)L->n_cells * L->npm;
+  L->size = (long long)L->kt * (L->n_vel + L->n_pres);
+  L->t1 = make_tables_1d(r);
+  L->tt = make_time_tables(k, tau);
+  // element matrices on a cell of size h (Kronecker products of the 1D tables)
+  const int np = L->np, nq = L->nq;
+  L->Me.assign((size_t)nq * nq, 0.0);
+  L->Ae.assign((size_t)nq * nq, 0.0);
+  L->Be.assign((size_t)dim * L->npm * nq, 0.0);
+  std::vector<std::array<int, 3>> loc(nq);
+  for (int p = 0; p < nq; ++p) loc[p] = {p % np, (p / np) % np, dim == 3 ? p / (np * np) : 0};
+  const double h = L->h;
+  for (int p = 0; p < nq; ++p)
+    for (int q = 0; q < nq; ++q) {
+      double m = std::pow(h, dim), a = 0.0;
+      for (int d = 0; d < dim; ++d) m *= L->t1.M1[loc[p][d] * np + loc[q][d]];
+      for (int dd = 0; dd < dim; ++dd) {
+        double t = std::pow(h, dim - 2);
+        for (int d = 0; d < dim; ++d)
+          t *= (d == dd ? L->t1.K1 : L->t1.M1)[loc[p][d] * np + loc[q][d]];
+        a += t;
+      }
+      L->Me[(size_t)p * nq + q] = m;
+      L->Ae[(size_t)p * nq + q] = a;
+    }
+  for (int c = 0; c < dim; ++c)
+    for (int m = 0; m < L->npm; ++m)
+      for (int p = 0; p < nq; ++p) {
+        double v = std::pow(h, dim - 1);
+        for (int d = 0; d < dim; ++d) v *= (d == c ? L->t1.G1 : L->t1.N1)[L->modes[m][d] * np + loc[p][d]];
+        L->Be[((size_t)c * L->npm + m) * nq + p] = v;
+      }
+}
+
+// ------------------------------------------------------------------------------------
+// patches
+// ------------------------------------------------------------------------------------
+static bool node_dirichlet(const LevelHost& L, const int* g) {
+  for (int d = 0; d < L.dim; ++d)
+    if (g[d] == 0 || g[d] == L.G - 1) return true;
+  return false;
+}
+
+static long long node_index(const LevelHost& L, const int* g) {
+  long long idx = 0, s = 1;
+  for (int d = 0; d < L.dim; ++d) { idx += g[d] * s; s *= L.G; }
+  return idx;
+}
+
+// Fill the patch of cells [clo, chi] (per dim, inclusive) with velocity nodes of the
+// closure box and all pressure modes of the cells; returns global slab indices, with
+// a parallel Dirichlet flag.
+static void box_patch(const LevelHost& L, const int* clo, const int* chi, std::vector<long long>* idx,
+                      std::vector<char>* dir) {
+  const int dim = L.dim, R1 = L.r + 1;
+  int nlo[3] = {0, 0, 0}, nhi[3] = {0, 0, 0};
+  for (int d = 0; d < dim; ++d) { nlo[d] = clo[d] * R1; nhi[d] = (chi[d] + 1) * R1; }
+  idx->clear();
+  dir->clear();
+  for (int a = 0; a < L.kt; ++a)
+    for (int comp = 0; comp < dim; ++comp)
+      for (int gz = nlo[2]; gz <= nhi[2]; ++gz)
+        for (int gy = nlo[1]; gy <= nhi[1]; ++gy)
+          for (int gx = nlo[0]; gx <= nhi[0]; ++gx) {
+            int g[3] = {gx, gy, gz};
+            idx->push_back(a * L.n_vel + comp * L.n_nodes + node_index(L, g));
+            dir->push_back(node_dirichlet(L, g) ? 1 : 0);
+          }
+  const long long poff = (long long)L.kt * L.n_vel;
+  for (int a = 0; a < L.kt; ++a)
+    for (int cz = clo[2]; cz <= chi[2]; ++cz)
+      for (int cy = clo[1]; cy <= chi[1]; ++cy)
+        for (int cx = clo[0]; cx <= chi[0]; ++cx) {
+          const long long cell = cx + (long long)L.n * (cy + (long long)L.n * cz);
+          for (int m = 0; m < L.npm; ++m) {
+            idx->push_back(poff + a * L.n_pres + cell * L.npm + m);
+            dir->push_back(0);
+          }
+        }
+}
+
+void build_patches(LevelHost* L, int kind) {
+  const int dim = L->dim, n = L->n;
+  L->smoother = kind;
+  std::vector<long long> idx;
+  std::vector<char> dir;
+  std::map<long long, int> class_of_key;
+  int per[3] = {1, 1, 1};
+  for (int d = 0; d < dim; ++d) per[d] = kind == STMG_CELL ? n : n + 1;
+  L->n_patches = (long long)per[0] * per[1] * per[2];
+  // first pass: B_max
+  int Bmax = 0;
+  if (kind == STMG_CELL) {
+    Bmax = L->kt * (dim * L->nq + L->npm);
+  } else {
+    const int side = 2 * (L->r + 1) + 1;
+    int nside = n >= 2 ? side : L->np;
+    Bmax = L->kt * (dim * ipow(nside, dim) + ipow(n >= 2 ? 2 : 1, dim) * L->npm);
+  }
+  L->B = Bmax;
+  L->Bc = (Bmax + 3) / 4 * 4;
+  L->dofs.assign((size_t)L->n_patches * Bmax, -2);
+  L->patch_class.assign(L->n_patches, 0);
+  L->class_rep.clear();
+  L->class_B.clear();
+  for (long long p = 0; p < L->n_patches; ++p) {
+    int c[3] = {(int)(p % per[0]), (int)((p / per[0]) % per[1]), (int)(p / ((long long)per[0] * per[1]))};
+    int clo[3] = {0, 0, 0}, chi[3] = {0, 0, 0};
+    long long key = 0;
+    for (int d = 0; d < dim; ++d) {
+      if (kind == STMG_CELL) {
+        clo[d] = chi[d] = c[d];
+        // which neighbours exist: c-1, c+1
+        key |= (long long)((c[d] > 0) | ((c[d] < n - 1) << 1)) << (4 * d);
+      } else {
+        clo[d] = std::max(c[d] - 1, 0);
+        chi[d] = std::min(c[d], n - 1);
+        int bits = 0;
+        for (int o = -2; o <= 1; ++o) if (c[d] + o >= 0 && c[d] + o <= n - 1) bits |= 1 << (o + 2);
+        key |= (long long)bits << (4 * d);
+      }
+    }
+    box_patch(*L, clo, chi, &idx, &dir);
+    if ((int)idx.size() > Bmax) throw std::runtime_error("patch larger than B_max");
+    for (size_t i = 0; i < idx.size(); ++i) L->dofs[(size_t)p * Bmax + i] = dir[i] ? -1 : (int)idx[i];
+    auto it = class_of_key.find(key);
+    if (it == class_of_key.end()) {
+      const int cid = (int)L->class_rep.size();
+      class_of_key[key] = cid;
+      L->class_rep.push_back(p);
+      L->class_B.push_back((int)idx.size());
+      L->class_idx.push_back(idx);
+      L->class_dir.push_back(dir);
+      L->patch_class[p] = cid;
+    } else {
+      L->patch_class[p] = it->second;
+    }
+  }
+  // valence of every slab dof (number of patches containing it)
+  L->valence.assign(L->size, 0);
+  for (size_t e = 0; e < L->dofs.size(); ++e)
+    if (L->dofs[e] >= 0) L->valence[L->dofs[e]]++;
+}
+
+// S restricted to the index set idx (global slab indices), boundary rows/cols identity.
+void assemble_submatrix(const LevelHost& L, const std::vector<long long>& idx, const std::vector<char>& dir,
+                        std::vector<double>* S) {
+  const int B = (int)idx.size(), dim = L.dim, np = L.np, nq = L.nq, kt = L.kt, npm = L.npm, n = L.n;
+  S->assign((size_t)B * B, 0.0);
+  std::unordered_map<long long, int> pos;
+  pos.reserve(B * 2);
+  for (int i = 0; i < B; ++i) pos[idx[i]] = i;
+  // node bounding box of the set
+  int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+  bool any_vel = false;
+  std::vector<long long> cells_with_p;
+  const long long poff = (long long)kt * L.n_vel;
+  for (int i = 0; i < B; ++i) {
+    if (idx[i] < poff) {
+      long long g = idx[i] % L.n_vel % L.n_nodes;
+      for (int d = 0; d < dim; ++d) { int gd = (int)(g % L.G); g /= L.G; lo[d] = std::min(lo[d], gd); hi[d] = std::max(hi[d], gd); }
+      any_vel = true;
+    }
+  }
+  int clo[3] = {0, 0, 0}, chi[3] = {0, 0, 0};
+  for (int d = 0; d < dim; ++d) {
+    if (any_vel) { clo[d] = std::max(0, lo[d] / (L.r + 1) - 1); chi[d] = std::min(n - 1, hi[d] / (L.r + 1)); }
+    else { clo[d] = 0; chi[d] = n - 1; }
+  }
+  std::vector<int> vpos((size_t)kt * dim * nq), ppos((size_t)kt * npm);
+  const double* Kt = L.tt.K;
+  for (int cz = clo[2]; cz <= chi[2]; ++cz)
+    for (int cy = clo[1]; cy <= chi[1]; ++cy)
+      for (int cx = clo[0]; cx <= chi[0]; ++cx) {
+        const int cc[3] = {cx, cy, cz};
+        const long long cell = cx + (long long)n * (cy + (long long)n * cz);
+        bool any = false;
+        for (int p = 0; p < nq; ++p) {
+          int g[3] = {cc[0] * (np - 1) + p % np, cc[1] * (np - 1) + (p / np) % np,
+                      dim == 3 ? cc[2] * (np - 1) + p / (np * np) : 0};
+          const long long gn = node_index(L, g);
+          for (int a = 0; a < kt; ++a)
+            for (int comp = 0; comp < dim; ++comp) {
+              auto it = pos.find(a * L.n_vel + comp * L.n_nodes + gn);
+              const int v = it == pos.end() ? -1 : it->second;
+              vpos[((size_t)a * dim + comp) * nq + p] = v;
+              any = any || v >= 0;
+            }
+        }
+        bool anyp = false;
+        for (int a = 0; a < kt; ++a)
+          for (int m = 0; m < npm; ++m) {
+            auto it = pos.find(poff + a * L.n_pres + cell * npm + m);
+            ppos[a * npm + m] = it == pos.end() ? -1 : it->second;
+            anyp = anyp || ppos[a * npm + m] >= 0;
+          }
+        if (!any && !anyp) continue;
+        for (int comp = 0; comp < dim; ++comp)
+          for (int p = 0; p < nq; ++p)
+            for (int q = 0; q < nq; ++q) {
+              const double me = L.Me[(size_t)p * nq + q], ae = L.Ae[(size_t)p * nq + q];
+              for (int a = 0; a < kt; ++a) {
+                const int ip = vpos[((size_t)a * dim + comp) * nq + p];
+                if (ip < 0) continue;
+                for (int b = 0; b < kt; ++b) {
+                  const int iq = vpos[((size_t)b * dim + comp) * nq + q];
+                  if (iq < 0) continue;
+                  double v = Kt[a * kt + b] * me;
+                  if (a == b) v += L.tt.M[a] * L.nu * ae;
+                  (*S)[(size_t)ip * B + iq] += v;
+                }
+              }
+            }
+        for (int a = 0; a < kt; ++a)
+          for (int m = 0; m < npm; ++m) {
+            const int im = ppos[a * npm + m];
+            if (im < 0) continue;
+            for (int comp = 0; comp < dim; ++comp)
+              for (int p = 0; p < nq; ++p) {
+                const int ip = vpos[((size_t)a * dim + comp) * nq + p];
+                if (ip < 0) continue;
+                const double v = -L.tt.M[a] * L.Be[((size_t)comp * npm + m) * nq + p];
+                (*S)[(size_t)ip * B + im] += v;
+                (*S)[(size_t)im * B + ip] += v;
+              }
+          }
+      }
+  for (int i = 0; i < B; ++i)
+    if (dir[i]) {
+      for (int j = 0; j < B; ++j) { (*S)[(size_t)i * B + j] = 0.0; (*S)[(size_t)j * B + i] = 0.0; }
+      (*S)[(size_t)i * B + i] = 1.0;
+    }
+}
+
+// In-place inverse of the row-major n x n matrix A (Gauss-Jordan, partial pivoting).
+bool invert_gauss_jordan(double* A, int n) {
+  std::vector<int> piv(n);
+  std::vector<double> row(n);
+  double amax = 0.0;
+  for (size_t i = 0; i < (size_t)n * n; ++i) amax = std::max(amax, std::fabs(A[i]));
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    double best = std::fabs(A[(size_t)c * n + c]);
+    for (int i = c + 1; i < n; ++i) {
+      const double v = std::fabs(A[(size_t)i * n + c]);
+      if (v > best) { best = v; p = i; }
+    }
+    if (!(best > 1e-14 * amax)) return false;
+    piv[c] = p;
+    if (p != c)
+      for (int j = 0; j < n; ++j) std::swap(A[(size_t)c * n + j], A[(size_t)p * n + j]);
+    const double inv = 1.0 / A[(size_t)c * n + c];
+    A[(size_t)c * n + c] = 1.0;
+    double* rc = A + (size_t)c * n;
+    for (int j = 0; j < n; ++j) rc[j] *= inv;
+    for (int i = 0; i < n; ++i) {
+      if (i == c) continue;
+      double* ri = A + (size_t)i * n;
+      const double f = ri[c];
+      if (f == 0.0) continue;
+      ri[c] = 0.0;
+      for (int j = 0; j < n; ++j) ri[j] -= f * rc[j];
+    }
+  }
+  // undo the row interchanges as column interchanges, last first
+  for (int c = n - 1; c >= 0; --c)
+    if (piv[c] != c)
+      for (int i = 0; i < n; ++i) std::swap(A[(size_t)i * n + c], A[(size_t)i * n + piv[c]]);
+  return true;
+}
+
+bool build_class_inverses(LevelHost* L) {
+  const int nc = (int)L->class_rep.size(), B = L->B;
+  L->class_inv.assign((size_t)nc * B * B, 0.0);
+  std::vector<int> ok(nc, 1);
+  auto work = [&](int c) {
+    std::vector<double> S;
+    assemble_submatrix(*L, L->class_idx[c], L->class_dir[c], &S);
+    const int b = L->class_B[c];
+    if (!invert_gauss_jordan(S.data(), b)) { ok[c] = 0; return; }
+    for (int i = 0; i < b; ++i)
+      std::memcpy(&L->class_inv[((size_t)c * B + i) * B], &S[(size_t)i * b], sizeof(double) * b);
+  };
+  unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (nc <= 1 || nth <= 1) {
+    for (int c = 0; c < nc; ++c) work(c);
+  } else {
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nth; ++t)
+      th.emplace_back([&, t]() { for (int c = (int)t; c < nc; c += (int)nth) work(c); });
+    for (auto& t : th) t.join();
+  }
+  for (int c = 0; c < nc; ++c) if (!ok[c]) return false;
+  return true;
+}
+
+bool build_coarse_inverse(LevelHost* L, std::vector<double>* Gcm) {
+  // all dofs of the level, in slab order
+  std::vector<long long> idx(L->size);
+  std::vector<char> dir(L->size, 0);
+  for (long long i = 0; i < L->size; ++i) idx[i] = i;
+  for (int a = 0; a < L->kt; ++a)
+    for (int comp = 0; comp < L->dim; ++comp)
+      for (long long g = 0; g < L->n_nodes; ++g) {
+        int gg[3] = {0, 0, 0};
+        long long t = g;
+        for (int d = 0; d < L->dim; ++d) { gg[d] = (int)(t % L->G); t /= L->G; }
+        if (node_dirichlet(*L, gg)) dir[a * L->n_vel + comp * L->n_nodes + g] = 1;
+      }
+  std::vector<double> S;
+  assemble_submatrix(*L, idx, dir, &S);
+  const int D = (int)L->size, kt = L->kt, Db = D + kt;
+  std::vector<double> A((size_t)Db * Db, 0.0);
+  for (int i = 0; i < D; ++i) std::memcpy(&A[(size_t)i * Db], &S[(size_t)i * D], sizeof(double) * D);
+  const long long poff = (long long)kt * L->n_vel;
+  for (int a = 0; a < kt; ++a)
+    for (long long c = 0; c < L->n_cells; ++c) {
+      const long long i = poff + a * L->n_pres + c * L->npm;   // mode 0 = the constant
+      A[(size_t)i * Db + D + a] = 1.0;
+      A[(size_t)(D + a) * Db + i] = 1.0;
+    }
+  if (!invert_gauss_jordan(A.data(), Db)) return false;
+  Gcm->assign((size_t)D * D, 0.0);
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) (*Gcm)[(size_t)j * D + i] = A[(size_t)i * Db + j];   // column-major
+  return true;
+}
+
+}  // namespace stmg

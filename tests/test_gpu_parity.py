@@ -1,0 +1,259 @@
+"""GPU parity: every hot-path call of libstmg (through the C ABI) against the FP64 oracle
+on the same seeded inputs.
+
+Tolerances (relative, max-norm over max-norm of the reference):
+  FP64 apply / residual / sweep / smoothing step / transfers / coarse solve: 1e-12
+  FP64 V-cycle: 1e-11;  solves to 1e-12 agree to 1e-9 (pressure mean removed)
+  FP32: apply / transfers 2e-6, sweep 1e-5, V-cycle 1e-4 (single-precision rounding
+  of O(B) and O(levels) operations).
+"""
+import numpy as np
+import pytest
+
+from oracle.stokes import MGConfig, Multigrid, Slab, march, slab_prolongation
+from workloads import fourier_forcing_2d, manufactured_2d, random_vector, taylor_green_3d
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_2502_09159_gb300 as stmg  # noqa: E402
+
+stmg.build()
+
+NU, TAU = 0.9, 0.2
+
+
+def rel(a, b):
+    a = a.detach().cpu().numpy() if hasattr(a, "detach") else np.asarray(a)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def dev(v, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(v)).to("cuda", dtype)
+
+
+# (dim, n, r, k, explicit levels or None)
+CASES = [
+    (2, 4, 1, 1, None),
+    (2, 3, 2, 2, [(3, 2, 2), (3, 1, 1)]),          # ragged: 9 cells
+    (2, 4, 3, 0, None),                             # DG(0)
+    (2, 2, 4, 3, None),                             # largest degrees
+    (2, 5, 1, 1, [(5, 1, 1)]),                      # single level, odd n
+    (3, 2, 1, 1, None),
+    (3, 2, 2, 1, None),
+]
+IDS = ["2d-n4-r1k1", "2d-n3-r2k2", "2d-n4-r3k0", "2d-n2-r4k3", "2d-n5-single", "3d-n2-r1k1", "3d-n2-r2k1"]
+
+_cache = {}
+
+
+def setup_case(case, smoother="cell"):
+    key = (case[:4], smoother)
+    if key in _cache:
+        return _cache[key]
+    dim, n, r, k, levels = case
+    levels = levels or stmg.host_default_hierarchy(n, r, k)
+    og = Multigrid(dim, levels, NU, TAU, MGConfig(smoother=smoother))
+    sm = [stmg.VSP if smoother == "vsp" else stmg.CELL] * len(levels)
+    g = stmg.SpaceTimeMG(dim=dim, n_cells=n, r=r, k=k, nu=NU, T=TAU * 5, n_slabs=5, levels=levels,
+                         smoothers=sm, use_graphs=False)
+    _cache[key] = (og, g)
+    return og, g
+
+
+def free_vec(slab, seed):
+    v = random_vector(slab.size, seed)
+    v[slab.dirichlet] = 0.0
+    return v
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_apply_and_residual(case):
+    og, g = setup_case(case)
+    for l, s in enumerate(og.slabs):
+        x = random_vector(s.size, 3 + l)
+        b = random_vector(s.size, 40 + l)
+        ref = s.S @ x
+        assert rel(g.apply(dev(x), l), ref) < 1e-12
+        assert rel(g.residual(dev(b), dev(x), l), b - ref) < 1e-12
+        assert rel(g.apply(dev(x, torch.float32), l).double(), ref) < 2e-6
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_vanka_sweep_and_smoothing_step(case):
+    og, g = setup_case(case)
+    for l, (s, W) in enumerate(zip(og.slabs[:-1], og.smoothers)):
+        res = free_vec(s, 7 + l)
+        ref = W.omega * W.correction(res)
+        x = torch.zeros(s.size, dtype=torch.float64, device="cuda")
+        assert rel(g.vanka_sweep(dev(res), x, l), ref) < 1e-12
+        x32 = torch.zeros(s.size, dtype=torch.float32, device="cuda")
+        assert rel(g.vanka_sweep(dev(res, torch.float32), x32, l).double(), ref) < 1e-5
+        b, x0 = free_vec(s, 11 + l), free_vec(s, 13 + l)
+        assert rel(g.smooth(dev(b), dev(x0), l, steps=1), W.step(b, x0)) < 1e-12
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c[4] != [(5, 1, 1)]],
+                         ids=[i for c, i in zip(CASES, IDS) if c[4] != [(5, 1, 1)]])
+def test_transfers(case):
+    og, g = setup_case(case)
+    for l in range(len(og.slabs) - 1):
+        P = og.P[l]
+        fine, coarse = og.slabs[l], og.slabs[l + 1]
+        r_f = random_vector(fine.size, 17 + l)
+        assert rel(g.restrict(dev(r_f), l), P.T @ r_f) < 1e-12
+        y_c = random_vector(coarse.size, 19 + l)
+        x_f = free_vec(fine, 23 + l)
+        assert rel(g.prolongate_add(dev(y_c), dev(x_f), l), x_f + P @ y_c) < 1e-12
+        assert rel(g.restrict(dev(r_f, torch.float32), l).double(), P.T @ r_f) < 2e-6
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_coarse_solve_and_vcycle(case):
+    og, g = setup_case(case)
+    cs = og.slabs[-1]
+    bc = free_vec(cs, 29)
+    assert rel(g.coarse_solve(dev(bc)), og.coarse_inv @ bc) < 1e-12
+    s0 = og.slabs[0]
+    b = free_vec(s0, 31)
+    ref = og.vcycle(b)
+    assert rel(g.vcycle(dev(b), "fp64"), ref) < 1e-11
+    assert rel(g.vcycle(dev(b), "fp32"), ref) < 1e-4
+
+
+def test_vcycle_graph_equals_eager():
+    case = CASES[0]
+    dim, n, r, k, _ = case
+    og, ge = setup_case(case)
+    gg = stmg.SpaceTimeMG(dim=dim, n_cells=n, r=r, k=k, nu=NU, T=TAU * 5, n_slabs=5, use_graphs=True)
+    b = dev(free_vec(og.slabs[0], 37))
+    for prec in ("fp64", "fp32"):
+        x1 = ge.vcycle(b, prec)
+        for _ in range(3):                               # capture, then replays
+            x2 = gg.vcycle(b, prec)
+            assert rel(x2, x1.cpu().numpy()) < (1e-13 if prec == "fp64" else 1e-6)
+    assert gg.kernel_launches > 0
+
+
+@pytest.mark.parametrize("smoother", ["vsp"])
+def test_vertex_star_smoother(smoother):
+    case = (2, 4, 1, 1, None)
+    og, g = setup_case(case, smoother)
+    for l, (s, W) in enumerate(zip(og.slabs[:-1], og.smoothers)):
+        res = free_vec(s, 41 + l)
+        x = torch.zeros(s.size, dtype=torch.float64, device="cuda")
+        assert rel(g.vanka_sweep(dev(res), x, l), W.omega * W.correction(res)) < 1e-12
+    b = free_vec(og.slabs[0], 43)
+    assert rel(g.vcycle(dev(b), "fp64"), og.vcycle(b)) < 1e-11
+
+
+def test_solve_slab_matches_direct_solve():
+    dim, n, r, k = 2, 8, 2, 1
+    pb = manufactured_2d(nu=1.0)
+    slab = Slab(dim, n, r, k, 1.0, 0.25)
+    F = slab.rhs_forcing(pb.forcing, 0.0)
+    xd = slab.direct_solve(F)
+    g = stmg.SpaceTimeMG(dim=dim, n_cells=n, r=r, k=k, nu=1.0, T=1.0, n_slabs=4, rel_tol=1e-12)
+    x, info = g.solve_slab(dev(F))
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-12
+    xs = slab.remove_pressure_mean(x.cpu().numpy())
+    assert rel(xs, slab.remove_pressure_mean(xd)) < 1e-9
+    for a in range(slab.kt):
+        assert np.abs(slab.B @ slab.vel(x.cpu().numpy(), a)).max() < 1e-10
+
+
+def test_forcing_and_slab_rhs():
+    dim, n, r, k = 2, 4, 2, 2
+    pb = fourier_forcing_2d(nu=1.0)
+    slab = Slab(dim, n, r, k, 1.0, 1.0 / 16)
+    g = stmg.SpaceTimeMG(dim=dim, n_cells=n, r=r, k=k, nu=1.0, T=1.0, n_slabs=16)
+    F = g.forcing(pb.forcing, slab=3)
+    Fo = slab.rhs_forcing(pb.forcing, 3 / 16)
+    assert rel(F, Fo) < 1e-12
+    x_prev = random_vector(slab.size, 47)
+    b = g.slab_rhs(F, dev(x_prev))
+    ref = Fo + slab.coupling(slab.vel(x_prev, slab.kt - 1))
+    assert rel(b, ref) < 1e-12
+    assert rel(g.slab_rhs(F), Fo) == 0.0
+
+
+def test_forcing_3d():
+    pb = taylor_green_3d(nu=1e-2)
+    slab = Slab(3, 2, 2, 1, 1e-2, 1.0 / 8)
+    g = stmg.SpaceTimeMG(dim=3, n_cells=2, r=2, k=1, nu=1e-2, T=1.0, n_slabs=8)
+    assert rel(g.forcing(pb.forcing, slab=2), slab.rhs_forcing(pb.forcing, 2 / 8)) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_time_marching_config1(prec):
+    """Config 1 (8x8, Q2/P1/DG(1), 4 slabs, nu = 1, manufactured field x sin(pi t)):
+    GPU time marching against the oracle's, and the manufactured-solution error."""
+    pb = manufactured_2d(nu=1.0, time="sin_pi")
+    sols_o, infos_o, slab, _ = march(pb, 8, 1, 1, 4, tol=1e-12)
+    g = stmg.SpaceTimeMG(dim=2, n_cells=8, r=1, k=1, nu=1.0, T=1.0, n_slabs=4, precond_precision=prec,
+                         rel_tol=1e-12)
+    x = None
+    for s in range(4):
+        F = g.forcing(pb.forcing, s)
+        b = g.slab_rhs(F, x)
+        x, info = g.solve_slab(b)
+        assert info["status"] == 0 and info["rel_residual"] <= 1e-12
+        d = slab.remove_pressure_mean(x.cpu().numpy())
+        assert rel(d, slab.remove_pressure_mean(sols_o[s])) < 1e-9
+        assert info["iterations"] <= infos_o[s].iterations + (1 if prec == "fp64" else 4)
+
+
+def test_fp32_preconditioner_reaches_fp64_tolerance():
+    dim, n, r, k = 2, 16, 2, 2
+    pb = fourier_forcing_2d(nu=1.0)
+    g = stmg.SpaceTimeMG(dim=dim, n_cells=n, r=r, k=k, nu=1.0, T=1.0, n_slabs=16, precond_precision="fp32")
+    F = g.forcing(pb.forcing, 0)
+    x, info = g.solve_slab(g.slab_rhs(F))
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-8
+    r_ = g.residual(g.slab_rhs(F), x)
+    b = g.slab_rhs(F)
+    assert (torch.linalg.norm(r_) / torch.linalg.norm(b)).item() <= 1.001e-8
+
+
+def test_host_buffers_solve():
+    g = stmg.SpaceTimeMG(dim=2, n_cells=8, r=1, k=1)
+    pb = manufactured_2d()
+    b = g.slab_rhs(g.forcing(pb.forcing, 0))
+    xd, info_d = g.solve_slab(b)
+    bh = b.cpu().numpy().copy()
+    xh = np.zeros_like(bh)
+    info = g.solve_slab_host(bh, xh)
+    assert info["status"] == 0 and info["iterations"] == info_d["iterations"]
+    assert rel(xh, xd.cpu().numpy()) < 1e-12
+
+
+def test_error_statuses():
+    with pytest.raises(stmg.StmgError):
+        stmg.SpaceTimeMG(dim=2, n_cells=4, r=5, k=1)                 # not built: r > 4
+    with pytest.raises(stmg.StmgError):
+        stmg.SpaceTimeMG(dim=2, n_cells=6, r=1, k=1)                 # default rule needs 2^c
+    with pytest.raises(stmg.StmgError):
+        stmg.SpaceTimeMG(dim=2, n_cells=4, r=1, k=1, levels=[(4, 1, 1), (1, 1, 1)])   # 4 -> 1 invalid
+    g = stmg.SpaceTimeMG(dim=2, n_cells=8, r=1, k=1, gmres_max_iter=1)
+    b = g.slab_rhs(g.forcing(manufactured_2d().forcing, 0))
+    _, info = g.solve_slab(b)
+    assert info["status"] == stmg._lib.ERR_NOT_CONVERGED
+    bn = b.clone()
+    bn[5] = float("nan")
+    with pytest.raises(stmg.StmgError):
+        g.solve_slab(bn)
+    with pytest.raises(ValueError):
+        g.apply(torch.zeros(3, dtype=torch.float64, device="cuda"))
+
+
+def test_profiling_counters():
+    g = stmg.SpaceTimeMG(dim=2, n_cells=8, r=2, k=1, precond_precision="fp32")
+    g.set_profiling(2)
+    b = g.slab_rhs(g.forcing(manufactured_2d().forcing, 0))
+    _, info = g.solve_slab(b)
+    p = g.profile(reset=True)
+    assert p["fine_sweep"]["launches"] == 2 * info["iterations"]
+    assert p["fine_sweep"]["ms"] > 0 and p["operator"]["launches"] >= info["iterations"]

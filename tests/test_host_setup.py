@@ -1,0 +1,120 @@
+"""CPU checks of libstmg's host side: the library loads, exports every symbol that
+include/stmg.h declares, and its setup numerics agree with the FP64 oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.fe import SpaceFE, TimeFE
+from oracle.stokes import MGConfig, Multigrid, Slab, cell_patches, default_hierarchy, vertex_star_patches
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2502_09159_gb300 as p
+    p.build()
+    return p
+
+
+def test_library_exports_every_declared_symbol(pkg):
+    import ctypes
+    from paper_2502_09159_gb300 import _lib
+    lib = _lib.load()
+    with open(os.path.join(ROOT, "include", "stmg.h")) as f:
+        text = f.read()
+    names = set(re.findall(r"\b(stmg_[a-z0-9_]+)\s*\(", text))
+    assert len(names) >= 30
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    assert set(_lib._SIGS) == names          # the binding covers exactly the header
+    assert lib.stmg_status_string(0) == b"ok"
+    assert lib.stmg_status_string(7).startswith(b"not implemented")
+
+
+def test_create_without_gpu_fails_cleanly(pkg):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(RuntimeError):
+        pkg.SpaceTimeMG(dim=2, n_cells=2)
+
+
+@pytest.mark.parametrize("n,r,k", [(8, 1, 1), (64, 2, 2), (32, 2, 1), (16, 3, 3), (4, 4, 2), (2, 1, 0),
+                                   (1, 1, 1), (128, 2, 1), (4, 1, 3)])
+def test_hierarchy_matches_oracle(pkg, n, r, k):
+    assert pkg.host_default_hierarchy(n, r, k) == default_hierarchy(n, r, k)
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+def test_tables_1d_match_oracle_element_matrices(pkg, r):
+    t = pkg.host_tables_1d(r)
+    s = SpaceFE(2, 1, r)                     # h = 1: element matrices are the 1D tables
+    assert np.allclose(t["xi"], s.xi, atol=1e-15)
+    assert np.abs(np.kron(t["M1"], t["M1"]) - s.Me).max() < 1e-14
+    assert np.abs(np.kron(t["M1"], t["K1"]) + np.kron(t["K1"], t["M1"]) - s.Ae).max() < 1e-12
+    loc = s.local_nodes()
+    for comp in range(2):
+        ref = np.array([[(t["G1"] if comp == 0 else t["N1"])[e[0], p[0]] *
+                         (t["G1"] if comp == 1 else t["N1"])[e[1], p[1]] for p in loc] for e in s.modes])
+        assert np.abs(ref - s.Be[comp]).max() < 1e-13
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_time_tables_match_oracle(pkg, k):
+    tau = 0.37
+    t = pkg.host_time_tables(k, tau)
+    o = TimeFE(k, tau)
+    assert np.abs(t["nodes"] - o.nodes).max() < 1e-14
+    assert np.abs(t["weights"] - o.weights).max() < 1e-14
+    assert np.abs(t["K"] - o.K).max() < 1e-13
+    assert np.abs(t["M"] - np.diag(o.M)).max() < 1e-15
+    assert np.abs(t["phi_left"] - o.phi_left).max() < 1e-13
+
+
+def _oracle_dofs(slab, pat):
+    d = np.array(pat, dtype=np.int64)
+    return np.where(slab.dirichlet[d], -1, d)
+
+
+@pytest.mark.parametrize("dim,n,r,k", [(2, 3, 1, 1), (2, 3, 2, 2), (2, 4, 1, 0), (2, 2, 3, 1), (3, 2, 1, 1)])
+def test_cell_patch_inverses_match_oracle(pkg, dim, n, r, k):
+    nu, tau = 0.8, 0.25
+    levels = [(n, r, k), (1, 1, min(k, 1))] if n > 1 else [(n, r, k)]
+    mg = Multigrid(dim, levels, nu, tau, MGConfig())
+    slab, W = mg.slabs[0], mg.smoothers[0]
+    pats = cell_patches(slab)
+    check = sorted(set([0, len(pats) // 2, len(pats) - 1, 1 % len(pats)]))
+    for p in check:
+        hp = pkg.host_patch(dim, n, r, k, nu, tau, pkg.CELL, p)
+        assert np.array_equal(hp["dofs"], _oracle_dofs(slab, pats[p]))
+        A = W.inv[p]
+        assert np.abs(hp["inverse"] - A).max() <= 1e-10 * np.abs(A).max()
+    v = pkg.host_valence(dim, n, r, k, pkg.CELL)
+    free = ~slab.dirichlet
+    assert np.allclose(1.0 / v[free], W.weight[free])
+
+
+def test_vsp_patch_inverses_match_oracle(pkg):
+    dim, n, r, k, nu, tau = 2, 3, 1, 1, 1.0, 0.5
+    mg = Multigrid(dim, [(n, r, k), (1, 1, 1)], nu, tau, MGConfig(smoother="vsp"))
+    slab, W = mg.slabs[0], mg.smoothers[0]
+    pats = vertex_star_patches(slab)
+    for p in [0, 1, 5, len(pats) - 1]:
+        hp = pkg.host_patch(dim, n, r, k, nu, tau, pkg.VSP, p)
+        b = len(pats[p])
+        assert np.array_equal(hp["dofs"][:b], _oracle_dofs(slab, pats[p]))
+        assert np.all(hp["dofs"][b:] == -2)
+        A = W.inv[p]
+        assert np.abs(hp["inverse"][:b, :b] - A).max() <= 1e-10 * np.abs(A).max()
+        assert np.all(hp["inverse"][b:, :] == 0) and np.all(hp["inverse"][:, b:] == 0)
+
+
+@pytest.mark.parametrize("dim,n,r,k", [(2, 1, 1, 1), (3, 1, 1, 1), (2, 2, 1, 0)])
+def test_coarse_inverse_matches_oracle(pkg, dim, n, r, k):
+    nu, tau = 1.3, 0.2
+    mg = Multigrid(dim, [(n, r, k)], nu, tau, MGConfig())
+    G = pkg.host_coarse_inverse(dim, n, r, k, nu, tau)
+    assert np.abs(G - mg.coarse_inv).max() <= 1e-10 * np.abs(mg.coarse_inv).max()
