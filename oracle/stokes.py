@@ -300,11 +300,24 @@ class Vanka:
     def __init__(self, slab: Slab, patches, omega):
         self.slab, self.patches, self.omega = slab, patches, omega
         S = slab.S
-        self.inv = [np.linalg.inv(S[p][:, p].toarray()) for p in patches]
+        self.inv = [self._local_inverse(S[p][:, p].toarray(), p) for p in patches]
         cnt = np.zeros(slab.size)
         for p in patches:
             cnt[p] += 1
         self.weight = 1.0 / cnt
+
+    def _local_inverse(self, A, p):
+        """[R_T S R_T^T]^{-1}.  A patch that contains every cell of the mesh (the centre
+        vertex star of a 2x2 mesh) has only boundary velocity dofs around it, so its
+        matrix is singular in the pressure constant of each temporal dof; it is inverted
+        with the same bordering as the coarsest level (zero-mean pressure correction)."""
+        s = self.slab
+        N = s.pressure_nullspace()[p]
+        if np.count_nonzero(N) < s.kt * s.space.n_cells:
+            return np.linalg.inv(A)
+        kt = s.kt
+        Bd = np.block([[A, N], [N.T, np.zeros((kt, kt))]])
+        return np.linalg.inv(Bd)[:len(p), :len(p)]
 
     def correction(self, res):
         """D_w sum_T R_T^T A_T R_T res (Eq. vanka0 with valence weights)."""

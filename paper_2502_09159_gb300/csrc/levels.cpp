@@ -322,10 +322,32 @@ bool build_class_inverses(LevelHost* L) {
   const int nc = (int)L->class_rep.size(), B = L->B;
   L->class_inv.assign((size_t)nc * B * B, 0.0);
   std::vector<int> ok(nc, 1);
+  const long long poff = (long long)L->kt * L->n_vel;
   auto work = [&](int c) {
     std::vector<double> S;
-    assemble_submatrix(*L, L->class_idx[c], L->class_dir[c], &S);
+    const std::vector<long long>& idx = L->class_idx[c];
+    assemble_submatrix(*L, idx, L->class_dir[c], &S);
     const int b = L->class_B[c];
+    // a patch holding every cell's pressure (the centre vertex star of a 2x2 mesh) is
+    // surrounded by boundary dofs only: singular in the pressure constant of every
+    // temporal dof; invert it bordered like the coarsest level (zero-mean correction)
+    std::vector<int> mode0;
+    for (int i = 0; i < b; ++i)
+      if (idx[i] >= poff && (idx[i] - poff) % L->n_pres % L->npm == 0) mode0.push_back(i);
+    if ((long long)mode0.size() == (long long)L->kt * L->n_cells) {
+      const int kt = L->kt, bb = b + kt;
+      std::vector<double> A((size_t)bb * bb, 0.0);
+      for (int i = 0; i < b; ++i) std::memcpy(&A[(size_t)i * bb], &S[(size_t)i * b], sizeof(double) * b);
+      for (int i : mode0) {
+        const int a = (int)((idx[i] - poff) / L->n_pres);
+        A[(size_t)i * bb + b + a] = 1.0;
+        A[(size_t)(b + a) * bb + i] = 1.0;
+      }
+      if (!invert_gauss_jordan(A.data(), bb)) { ok[c] = 0; return; }
+      for (int i = 0; i < b; ++i)
+        std::memcpy(&L->class_inv[((size_t)c * B + i) * B], &A[(size_t)i * bb], sizeof(double) * b);
+      return;
+    }
     if (!invert_gauss_jordan(S.data(), b)) { ok[c] = 0; return; }
     for (int i = 0; i < b; ++i)
       std::memcpy(&L->class_inv[((size_t)c * B + i) * B], &S[(size_t)i * b], sizeof(double) * b);
