@@ -1,0 +1,402 @@
+"""Benchmark: space-time dofs/s of the hp space-time multigrid solve on one GB300.
+
+Workload (default, the 2D configuration the headline metric is quoted on): unit square
+x [0,1], 64x64 cells, Q3/P2disc (r=2) in space, DG(2) in time, 16 slabs, nu = 1,
+forcing = seeded random Fourier modes (8 modes per potential, c ~ N(0,1), a,b ~ U{1..4},
+theta ~ U[0,2pi), numpy PCG64 seeds 1 and 2), hp hierarchy r:2->1, k kept to the two
+coarsest levels, cell Vanka with omega = 0.7, FGMRES to ||b - S x|| <= 1e-8 ||b||.
+One step = one time march over all 16 slabs (slab right-hand side with the coupling to
+the previous slab, FGMRES + one V-cycle per iteration).  value = 16 * D / step time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The headline runs the V-cycle in FP32 (FGMRES, true residual and coarse solve in FP64);
+the FP64-preconditioner solve, the apply / sweep / V-cycle rates and the roofline of the
+dominant kernel (the finest-level Vanka sweep) are reported beside it.  --impl reference
+times the FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(dim=2, n_cells=64, r=2, k=2, nu=1.0, T=1.0, n_slabs=16)
+WORKLOAD_NAME = "2D 64x64 Q3/P2disc DG(2), 16 slabs, Fourier forcing (seeds 1,2), cell Vanka"
+METRIC = "space-time DoFs/s (apply, Vanka sweep, V-cycle); time-to-1e-8 mixed vs FP64"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-micro", action="store_true", help="skip the per-kernel rate measurements")
+    p.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline (profiler runs)")
+    p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def slab_dofs(w):
+    d, n, r, k = w["dim"], w["n_cells"], w["r"], w["k"]
+    return (k + 1) * (d * ((r + 1) * n + 1) ** d + math.comb(r + d, d) * n ** d)
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.path = index, None, None
+
+    def start(self):
+        try:
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic(kernel_file, key):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, or None
+    when the kernel source changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        with open(os.path.join(ROOT, "paper_2502_09159_gb300", "csrc", kernel_file), "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        e = tr.get(key)
+        if e and e.get("source_sha256_16") == h:
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2502_09159_gb300 as stmg
+    from workloads import fourier_forcing_2d
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    stmg.build()
+    w = WORKLOAD
+    D = slab_dofs(w)
+    N = w["n_slabs"]
+    # replicas: every rank solves its own problem (different forcing seeds), no data-path collective
+    pb = fourier_forcing_2d(nu=w["nu"], seed_psi=1 + 10 * rank, seed_phi=2 + 10 * rank)
+
+    def make(prec):
+        return stmg.SpaceTimeMG(**w, precond_precision=prec)
+
+    mg = make("fp32")
+    pts = mg.forcing_points()
+    F = [mg.forcing(pb.forcing, s, pts) for s in range(N)]        # resident inputs
+    x_bufs = [mg.zeros() for _ in range(N)]
+    b_buf = mg.empty()
+    launches0 = mg.kernel_launches
+
+    def step(g, iters):
+        x_prev = None
+        for s in range(N):
+            g.slab_rhs(F[s], x_prev, out=b_buf)
+            x_bufs[s].zero_()
+            _, info = g.solve_slab(b_buf, out=x_bufs[s])
+            if info["status"] != 0:
+                raise RuntimeError(f"slab {s}: {info}")
+            iters.append(info["iterations"])
+            x_prev = x_bufs[s]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    its = []
+    for _ in range(args.warmup):
+        step(mg, its)
+    mg.set_profiling(1)                     # events around the finest-level sweeps only
+    mg.profile(reset=True)
+    clocks = Clocks(local)
+    its = []
+    barrier()
+    clocks.start()
+    launches_before = mg.kernel_launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        step(mg, its)
+    ev1.record()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = mg.kernel_launches - launches_before
+    clk = clocks.stop()
+    prof = mg.profile(reset=True)
+    mg.set_profiling(0)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    ms_step = ms / args.steps
+    value = world * N * D / (ms_step / 1e3)
+
+    # ---- roofline of the dominant kernel: finest-level FP32 Vanka sweep
+    sweep_ms = prof["fine_sweep"]["ms"] / max(prof["fine_sweep"]["launches"], 1)
+    sweep_bytes = mg.sweep_bytes(0, "fp32")
+    peaks, peak_kind = measured_peaks()
+    achieved = sweep_bytes / (sweep_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_kind": peak_kind,
+                "traffic": ncu_traffic("k_vanka.cu", "vanka_sweep_fp32_finest"),
+                "kernel": "k_vanka_sweep<float>, finest level", "bytes_per_launch": sweep_bytes,
+                "avg_launch_ms": round(sweep_ms, 5), "launches_timed": prof["fine_sweep"]["launches"]}
+
+    # ---- end to end through the public API: pinned host F in, host solution out, every slab
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(mg, F, x_bufs, b_buf, N, D, world, args, barrier)
+
+    # ---- per-kernel rates and FP64 vs mixed time-to-1e-8 (not part of the timed step)
+    extra = {}
+    if not args.no_micro and rank == 0:
+        extra = micro(mg, make, F, N, D, step)
+    line = {"metric": METRIC, "value": value, "unit": "space-time DoFs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 FGMRES + f32 V-cycle", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "dofs_per_slab": D, "slabs_per_step": N,
+                       "levels": [(l["n"], l["r"], l["k"]) for l in mg.levels],
+                       "precond": "fp32", "rel_tol": 1e-8, "parallelism": f"replicas x{world}",
+                       "l2_policy": "inputs larger than L2 (finest FP32 patch inverses "
+                                    f"{mg.levels[0]['inverse_bytes'][1] / 1e6:.0f} MB > 129 MB)",
+                       "mean_gmres_iterations": statistics.mean(its) if its else None},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    line.update(extra)
+    if rank == 0:
+        if not args.no_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(mg, F, x_bufs, b_buf, N, D, world, args, barrier):
+    import torch
+    Fh = [f.cpu().pin_memory() for f in F]
+    Xh = [torch.empty(D, dtype=torch.float64).pin_memory() for _ in range(N)]
+    Fd = mg.empty()
+
+    def e2e_step():
+        x_prev = None
+        for s in range(N):
+            Fd.copy_(Fh[s], non_blocking=True)
+            mg.slab_rhs(Fd, x_prev, out=b_buf)
+            x_bufs[s].zero_()
+            mg.solve_slab(b_buf, out=x_bufs[s])
+            Xh[s].copy_(x_bufs[s], non_blocking=True)
+            x_prev = x_bufs[s]
+    e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    return {"value": world * N * D / (e2e_ms / 1e3), "unit": "space-time DoFs/s",
+            "h2d_bytes_per_step": N * D * 8, "d2h_bytes_per_step": N * D * 8}
+
+
+def micro(mg, make, F, N, D, step_fn):
+    import torch
+    out = {}
+
+    def timeit(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    x64 = torch.randn(D, dtype=torch.float64, device="cuda")
+    x32 = x64.float()
+    y64, y32 = torch.empty_like(x64), torch.empty_like(x32)
+    rates = {}
+    for tag, x, y in (("fp64", x64, y64), ("fp32", x32, y32)):
+        t = timeit(lambda: mg.apply(x, 0, out=y))
+        rates[f"apply_{tag}"] = D / (t / 1e3)
+        t = timeit(lambda: mg.vanka_sweep(x, y, 0))
+        rates[f"vanka_sweep_{tag}"] = D / (t / 1e3)
+        sb = mg.sweep_bytes(0, tag)
+        rates[f"vanka_sweep_{tag}_GBs"] = sb / (t / 1e3) / 1e9
+        t = timeit(lambda: (mg.residual(x, y, 0, out=y), mg.vanka_sweep(y, x, 0)))
+        rates[f"smoothing_step_{tag}"] = D / (t / 1e3)
+        b = x64.clone()
+        z = torch.empty_like(b)
+        t = timeit(lambda: mg.vcycle(b, tag, out=z))
+        rates[f"vcycle_{tag}"] = D / (t / 1e3)
+    out["rates_dofs_per_s"] = {k: float(f"{v:.4g}") for k, v in rates.items()}
+    # time-to-1e-8: FP64 preconditioner vs FP32 preconditioner, same march
+    tt = {}
+    for prec in ("fp64", "fp32"):
+        g = mg if prec == "fp32" else make("fp64")
+        its = []
+        step_fn(g, its)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        its = []
+        e0.record()
+        step_fn(g, its)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        tt[prec] = {"ms_per_slab": ms / N, "mean_iterations": statistics.mean(its), "theta_dofs_per_s": N * D / (ms / 1e3)}
+        if g is not mg:
+            g.close()
+    out["time_to_1e-8"] = tt
+    return out
+
+
+# ----------------------------------------------------------------------------- oracle
+_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle.stokes import MGConfig, march, Multigrid, default_hierarchy, fgmres
+from workloads import fourier_forcing_2d
+w = {w!r}
+pb = fourier_forcing_2d(nu=w["nu"])
+tau = w["T"] / w["n_slabs"]
+t0 = time.time()
+mg = Multigrid(w["dim"], default_hierarchy(w["n_cells"], w["r"], w["k"]), w["nu"], tau, MGConfig())
+t_setup = time.time() - t0
+slab = mg.slabs[0]
+b = slab.rhs_forcing(pb.forcing, 0.0)
+times = []
+for rep in range({reps}):
+    t0 = time.time()
+    x, info = fgmres(lambda z: slab.S @ z, mg.vcycle, b, tol=1e-8)
+    times.append(time.time() - t0)
+print(json.dumps({{"setup_s": t_setup, "solve_s": times, "iterations": info.iterations, "D": slab.size}}))
+"""
+
+
+def oracle_sample(reps):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = _ORACLE_SNIPPET.format(root=ROOT, w=WORKLOAD, reps=reps)
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if p.returncode != 0:
+        raise RuntimeError(p.stderr[-2000:])
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(reps=1):
+    try:
+        r = oracle_sample(reps)
+        t = min(r["solve_s"])
+        return {"value": r["D"] / t, "unit": "space-time DoFs/s", "cores": 1, "kind": "oracle",
+                "sample": f"slab 1 of 16 solved by the FP64 oracle (FGMRES + V-cycle to 1e-8, "
+                          f"{r['iterations']} iterations, {t:.1f} s; setup {r['setup_s']:.1f} s not timed)"}
+    except Exception as e:  # the baseline is reported, not required
+        return {"value": None, "unit": "space-time DoFs/s", "cores": 1, "kind": "oracle", "error": str(e)[:300]}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    r = oracle_sample(args.warmup + args.steps)
+    times = r["solve_s"][args.warmup:]
+    t = sum(times) / len(times)
+    value = r["D"] / t
+    sample = (f"per step: slab 1 of 16 of the same workload solved by the FP64 oracle (FGMRES + V-cycle "
+              f"to 1e-8, {r['iterations']} iterations); setup {r['setup_s']:.1f} s not timed")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "space-time DoFs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "dofs_per_slab": r["D"]},
+            "cpu_baseline": {"value": value, "unit": "space-time DoFs/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "space-time DoFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -196,7 +196,8 @@ int  stmg_vcycle(stmg_handle* h, int prec, const double* b, double* x);
 
 /* b = F + (C_tau (x) M_h) V_prev (right-hand side of Eq. AlgSysTMS): velocity rows of
    temporal dof a get phi_a(t_{n-1}^+) M_h v_prev, v_prev = the last temporal velocity
-   V^{k+1} of x_prev (a full previous-slab vector); x_prev = NULL means v_prev = 0.
+   V^{k+1} of x_prev (a full previous-slab vector; its boundary entries are ignored, the
+   boundary data being homogeneous); x_prev = NULL means v_prev = 0.
    F: the forcing part (Eq. DefFn), FP64, length D_0; b must not alias F or x_prev. */
 int  stmg_slab_rhs(stmg_handle* h, const double* F, const double* x_prev, double* b);
 

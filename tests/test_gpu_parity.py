@@ -173,10 +173,12 @@ def test_forcing_and_slab_rhs():
     F = g.forcing(pb.forcing, slab=3)
     Fo = slab.rhs_forcing(pb.forcing, 3 / 16)
     assert rel(F, Fo) < 1e-12
-    x_prev = random_vector(slab.size, 47)
+    x_prev = free_vec(slab, 47)                         # a previous solution: zero on the boundary
     b = g.slab_rhs(F, dev(x_prev))
     ref = Fo + slab.coupling(slab.vel(x_prev, slab.kt - 1))
     assert rel(b, ref) < 1e-12
+    x_bad = random_vector(slab.size, 47)                # boundary entries of x_prev are ignored
+    assert rel(g.slab_rhs(F, dev(x_bad)), ref) < 1e-12
     assert rel(g.slab_rhs(F), Fo) == 0.0
 
 
