@@ -28,7 +28,7 @@ _PREC = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _b
+    from .builder import build as _b
     return _b(force=force)
 
 

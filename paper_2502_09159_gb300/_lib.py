@@ -90,7 +90,7 @@ def load():
         return _lib
     if not os.path.exists(LIB_PATH):
         raise RuntimeError(f"libstmg.so is missing ({LIB_PATH}): build it with "
-                           "`python -m paper_2502_09159_gb300.build` (there is no CPU fallback)")
+                           "`python -m paper_2502_09159_gb300.builder` (there is no CPU fallback)")
     lib = C.CDLL(LIB_PATH)
     for name, (res, args) in _SIGS.items():
         fn = getattr(lib, name)

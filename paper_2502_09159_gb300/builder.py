@@ -1,7 +1,7 @@
 """Build libstmg.so in-tree for sm_103a (nvcc for the kernels, g++ for the host setup).
 
-    python -m paper_2502_09159_gb300.build          # build if sources changed
-    python -m paper_2502_09159_gb300.build --force  # rebuild
+    python -m paper_2502_09159_gb300.builder          # build if sources changed
+    python -m paper_2502_09159_gb300.builder --force  # rebuild
 
 Objects go to paper_2502_09159_gb300/_build/, the library to
 paper_2502_09159_gb300/libstmg.so.  Translation units compile in parallel; a stamp
