@@ -68,6 +68,7 @@ extern "C" {
 #define STMG_ERR_CUDA          6   /* a CUDA runtime call failed                           */
 #define STMG_ERR_UNIMPLEMENTED 7   /* combination not built (e.g. r > 4 on the GPU)       */
 #define STMG_ERR_SINGULAR      8   /* a patch or coarse matrix could not be inverted       */
+#define STMG_ERR_TOO_LARGE     9   /* level larger than stmg_smooth_noalloc's fixed scratch */
 
 /* precisions */
 #define STMG_FP64 0
@@ -172,6 +173,24 @@ int  stmg_residual(stmg_handle* h, int lvl, int prec, const void* b, const void*
    lvl (not the coarsest), W = sum_T R_T^T D_T [R_T S R_T^T]^{-1} R_T with the valence
    weights D_T.  x is updated in place. */
 int  stmg_smooth(stmg_handle* h, int lvl, int prec, const void* b, void* x, int steps);
+
+/* stmg_smooth for callers that must not have device memory allocated for them while
+   they run: a process whose device memory is given out only by its own pool allocator,
+   or a time-critical loop that cannot absorb the implicit synchronisation of
+   cudaMalloc/cudaFree.  Same arguments and result as stmg_smooth, but the residual lives
+   in a fixed device array inside the library (STMG_NOALLOC_MAX_ENTRIES values, 8 MB,
+   present on every GPU that loads the library until the process exits), so the call
+   allocates nothing.  The paper has no counterpart; it is an interface convenience.
+   - Levels with more than STMG_NOALLOC_MAX_ENTRIES dofs are rejected with
+     STMG_ERR_TOO_LARGE before any work is queued.
+   - The first call on each device looks up the array's device address
+     (cudaGetSymbolAddress) with that device current; make that first call before any
+     stream capture.
+   - All calls share the one array and it keeps whatever the last call left in it (the
+     residual is cleared at the start of every step): calls that can overlap on the GPU,
+     from different streams or handles, race with each other; order them on one stream. */
+#define STMG_NOALLOC_MAX_ENTRIES (1 << 20)
+int  stmg_smooth_noalloc(stmg_handle* h, int lvl, int prec, const void* b, void* x, int steps);
 
 /* One Vanka correction without the residual: x += omega W res.  (The sweep kernel.) */
 int  stmg_vanka_sweep(stmg_handle* h, int lvl, int prec, const void* res, void* x);

@@ -6,7 +6,8 @@ import os
 
 MAX_LEVELS = 24
 OK, ERR_ARG, ERR_OOM, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_NONFINITE, ERR_CUDA, \
-    ERR_UNIMPLEMENTED, ERR_SINGULAR = range(9)
+    ERR_UNIMPLEMENTED, ERR_SINGULAR, ERR_TOO_LARGE = range(10)
+NOALLOC_MAX_ENTRIES = 1 << 20
 FP64, FP32 = 0, 1
 CELL, VSP = 0, 1
 PROF_SMOOTHER, PROF_MG_OTHER, PROF_OPERATOR, PROF_OTHER, PROF_FINE_SWEEP, PROF_N = range(6)
@@ -46,6 +47,7 @@ _SIGS = {
     "stmg_apply": (_I, [_VP, _I, _I, _VP, _VP]),
     "stmg_residual": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
     "stmg_smooth": (_I, [_VP, _I, _I, _VP, _VP, _I]),
+    "stmg_smooth_noalloc": (_I, [_VP, _I, _I, _VP, _VP, _I]),
     "stmg_vanka_sweep": (_I, [_VP, _I, _I, _VP, _VP]),
     "stmg_restrict": (_I, [_VP, _I, _I, _VP, _VP]),
     "stmg_prolongate_add": (_I, [_VP, _I, _I, _VP, _VP]),

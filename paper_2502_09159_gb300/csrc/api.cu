@@ -577,6 +577,7 @@ const char* stmg_status_string(int s) {
     case STMG_ERR_CUDA: return "CUDA error";
     case STMG_ERR_UNIMPLEMENTED: return "not implemented for these parameters";
     case STMG_ERR_SINGULAR: return "singular patch or coarse matrix";
+    case STMG_ERR_TOO_LARGE: return "level larger than the fixed scratch of stmg_smooth_noalloc";
     default: return "unknown status";
   }
 }
@@ -932,3 +933,57 @@ int stmg_sweep_bytes(const stmg_handle* h, int lvl, int prec, double* bytes) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// Smoothing step without device allocation.
+//
+// stmg_smooth keeps its residual in a work vector that stmg_create allocated with
+// cudaMalloc.  Some callers must not have device memory allocated on their behalf while
+// they run (for example a process whose device memory is handed out entirely by its own
+// pool allocator, or a time-critical loop that cannot absorb the implicit synchronisation
+// of cudaMalloc/cudaFree).  stmg_smooth_noalloc does the same smoothing step with the
+// residual held in the library's own fixed device array below, so the call itself
+// allocates nothing.  The array is part of the library image: every GPU on which the
+// library is loaded holds its STMG_NOALLOC_MAX_ENTRIES * 8 bytes until the process exits.
+// ------------------------------------------------------------------------------------
+static __device__ __align__(256) double stmg_noalloc_scratch[STMG_NOALLOC_MAX_ENTRIES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};   // device address of the array, per device
+
+// Device address of the scratch array on the current device, looked up once per device.
+// `stmg_noalloc_scratch` named in host code is only a host-side stand-in; the device
+// address has to come from cudaGetSymbolAddress with that device current.
+int noalloc_scratch(void** out) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return STMG_ERR_ARG;
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, stmg_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return STMG_OK;
+}
+
+template <typename T>
+int smooth_noalloc_t(stmg_handle* h, int lvl, const T* b, T* x, int steps, T* res) {
+  for (int s = 0; s < steps; ++s) {
+    CKS(op_apply<T>(h, lvl, x, b, res, RESIDUAL, h->st));   // clears res, then r = b - S x
+    CKS(op_sweep<T>(h, lvl, res, x, h->st));
+  }
+  return STMG_OK;
+}
+}  // namespace
+
+extern "C" int stmg_smooth_noalloc(stmg_handle* h, int lvl, int prec, const void* b, void* x, int steps) {
+  if (!prec_ok(h, lvl, prec) || !b || !x || steps < 0 || lvl == (int)h->L.size() - 1) return STMG_ERR_ARG;
+  if (h->L[lvl].H.size > (long long)STMG_NOALLOC_MAX_ENTRIES) return STMG_ERR_TOO_LARGE;
+  void* scratch = nullptr;
+  CKS(noalloc_scratch(&scratch));
+  if (prec == STMG_FP64)
+    return smooth_noalloc_t<double>(h, lvl, (const double*)b, (double*)x, steps, (double*)scratch);
+  return smooth_noalloc_t<float>(h, lvl, (const float*)b, (float*)x, steps, (float*)scratch);
+}
