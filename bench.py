@@ -44,6 +44,9 @@ def parse():
     p.add_argument("--no-micro", action="store_true", help="skip the per-kernel rate measurements")
     p.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline (profiler runs)")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
+    p.add_argument("--coarse-n", type=int, default=8, help="coarsest mesh of the hierarchy (Alg. 2's 1/h_0)")
+    p.add_argument("--k-min", type=int, default=2, help="lowest temporal degree of the hierarchy")
+    p.add_argument("--levels", default="", help="explicit level list n:r:k,... fine -> coarse")
     return p.parse_args()
 
 
@@ -152,8 +155,10 @@ def run_ours(args):
     # replicas: every rank solves its own problem (different forcing seeds), no data-path collective
     pb = fourier_forcing_2d(nu=w["nu"], seed_psi=1 + 10 * rank, seed_phi=2 + 10 * rank)
 
-    def make(prec):
-        return stmg.SpaceTimeMG(**w, precond_precision=prec)
+    levels = [tuple(int(v) for v in t.split(":")) for t in args.levels.split(",")] if args.levels else None
+
+    def make(prec, coarse_n=args.coarse_n, k_min=args.k_min):
+        return stmg.SpaceTimeMG(**w, precond_precision=prec, coarse_n=coarse_n, k_min=k_min, levels=levels)
 
     mg = make("fp32")
     pts = mg.forcing_points()
@@ -228,12 +233,16 @@ def run_ours(args):
     extra = {}
     if not args.no_micro and rank == 0:
         extra = micro(mg, make, F, N, D, step)
+        extra["time_split"] = time_split(mg, step)
+        extra["paper_hierarchy"] = paper_rule(make, step, N, D)
     line = {"metric": METRIC, "value": value, "unit": "space-time DoFs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 FGMRES + f32 V-cycle", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "dofs_per_slab": D, "slabs_per_step": N,
                        "levels": [(l["n"], l["r"], l["k"]) for l in mg.levels],
                        "precond": "fp32", "rel_tol": 1e-8, "parallelism": f"replicas x{world}",
+                       "hierarchy": f"Alg. 2/3 with h_0 = 1/{args.coarse_n}, lowest temporal degree "
+                                    f"{args.k_min}" if not levels else "explicit",
                        "l2_policy": "inputs larger than L2 (finest FP32 patch inverses "
                                     f"{mg.levels[0]['inverse_bytes'][1] / 1e6:.0f} MB > 129 MB)",
                        "mean_gmres_iterations": statistics.mean(its) if its else None},
@@ -241,7 +250,7 @@ def run_ours(args):
     line.update(extra)
     if rank == 0:
         if not args.no_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(coarse_n=args.coarse_n, k_min=args.k_min)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -274,6 +283,45 @@ def run_e2e(mg, F, x_bufs, b_buf, N, D, world, args, barrier):
     e2e_ms = e0.elapsed_time(e1) / args.steps
     return {"value": world * N * D / (e2e_ms / 1e3), "unit": "space-time DoFs/s",
             "h2d_bytes_per_step": N * D * 8, "d2h_bytes_per_step": N * D * 8}
+
+
+def time_split(mg, step_fn):
+    """One more march with events around every category (the split of the paper's
+    lid-cavity breakdown): smoother, MG without smoother, operator outside MG, other."""
+    import torch
+    mg.set_profiling(2)
+    mg.profile(reset=True)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    step_fn(mg, [])
+    torch.cuda.synchronize()
+    wall = (time.time() - t0) * 1e3
+    p = mg.profile(reset=True)
+    mg.set_profiling(0)
+    out = {k: round(v["ms"], 3) for k, v in p.items()}
+    out["wall_ms"] = round(wall, 3)
+    return out
+
+
+def paper_rule(make, step_fn, N, D):
+    """The hierarchy pinned by Table 2(b) (coarsest mesh 1x1, DG(1) on the two coarsest
+    levels), same workload, FP32 V-cycle."""
+    import torch
+    g = make("fp32", coarse_n=1, k_min=1)
+    its = []
+    step_fn(g, its)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its = []
+    e0.record()
+    step_fn(g, its)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {"value": N * D / (ms / 1e3), "ms_per_step": ms, "mean_iterations": statistics.mean(its),
+           "levels": [(l["n"], l["r"], l["k"]) for l in g.levels]}
+    g.close()
+    return out
 
 
 def micro(mg, make, F, N, D, step_fn):
@@ -341,7 +389,8 @@ w = {w!r}
 pb = fourier_forcing_2d(nu=w["nu"])
 tau = w["T"] / w["n_slabs"]
 t0 = time.time()
-mg = Multigrid(w["dim"], default_hierarchy(w["n_cells"], w["r"], w["k"]), w["nu"], tau, MGConfig())
+mg = Multigrid(w["dim"], default_hierarchy(w["n_cells"], w["r"], w["k"], {coarse_n}, {k_min}), w["nu"], tau,
+               MGConfig())
 t_setup = time.time() - t0
 slab = mg.slabs[0]
 b = slab.rhs_forcing(pb.forcing, 0.0)
@@ -354,18 +403,18 @@ print(json.dumps({{"setup_s": t_setup, "solve_s": times, "iterations": info.iter
 """
 
 
-def oracle_sample(reps):
+def oracle_sample(reps, coarse_n=8, k_min=2):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = _ORACLE_SNIPPET.format(root=ROOT, w=WORKLOAD, reps=reps)
+    code = _ORACLE_SNIPPET.format(root=ROOT, w=WORKLOAD, reps=reps, coarse_n=coarse_n, k_min=k_min)
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if p.returncode != 0:
         raise RuntimeError(p.stderr[-2000:])
     return json.loads(p.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline(reps=1):
+def cpu_baseline(reps=1, coarse_n=8, k_min=2):
     try:
-        r = oracle_sample(reps)
+        r = oracle_sample(reps, coarse_n, k_min)
         t = min(r["solve_s"])
         return {"value": r["D"] / t, "unit": "space-time DoFs/s", "cores": 1, "kind": "oracle",
                 "sample": f"slab 1 of 16 solved by the FP64 oracle (FGMRES + V-cycle to 1e-8, "
@@ -378,7 +427,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    r = oracle_sample(args.warmup + args.steps)
+    r = oracle_sample(args.warmup + args.steps, args.coarse_n, args.k_min)
     times = r["solve_s"][args.warmup:]
     t = sum(times) / len(times)
     value = r["D"] / t

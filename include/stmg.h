@@ -69,6 +69,7 @@ extern "C" {
 #define STMG_ERR_UNIMPLEMENTED 7   /* combination not built (e.g. r > 4 on the GPU)       */
 #define STMG_ERR_SINGULAR      8   /* a patch or coarse matrix could not be inverted       */
 #define STMG_ERR_TOO_LARGE     9   /* level larger than stmg_smooth_noalloc's fixed scratch */
+#define STMG_ERR_TIMEOUT      10   /* a bounded wait inside a kernel expired (device flag)  */
 
 /* precisions */
 #define STMG_FP64 0
@@ -105,6 +106,19 @@ typedef struct {
   int    gmres_max_iter;   /* Krylov basis size; no restarts (default 200)               */
   double rel_tol;          /* stop when ||b - S x||_2 <= rel_tol ||b||_2 (default 1e-8) */
   int    use_graphs;       /* capture each V-cycle in a CUDA graph (default 1)           */
+  int    sweep_variant;    /* Vanka sweep kernel: 0 = chosen by the tuner (default),
+                              1 = one thread block per group of patches,
+                              2 = persistent TMA-pipelined (one CTA per SM,
+                              cp.async.bulk + mbarrier; patches with B <= 512)          */
+  int    autotune;         /* 1 (default): stmg_create times the candidate launch shapes
+                              of every level (see stmg_autotune) and keeps the fastest  */
+  int    coarse_n;         /* coarsest mesh of the default hierarchy (Alg. 2's h_0 =
+                              1/coarse_n, a power of 2 <= n_cells; default 1, the rule
+                              Table 2(b) pins); the coarsest level is solved directly    */
+  int    k_min;            /* lowest temporal degree of the default hierarchy's
+                              polynomial coarsening in time (Alg. 2's r_0 for k; default
+                              1 as in the paper's runs; k_min >= k keeps DG(k) on every
+                              level)                                                     */
 } stmg_config;
 
 typedef struct {
@@ -117,6 +131,10 @@ typedef struct {
   long long n_patches;
   int       n_patch_classes;/* distinct patch matrices inverted at setup                 */
   long long inverse_bytes[2]; /* stored patch-inverse bytes for FP64 / FP32 (0: none)    */
+  int       sweep_variant[2];            /* per precision: 1 block sweep, 2 TMA sweep      */
+  int       patches_per_block[2];        /* block sweep launch shape, per precision          */
+  int       apply_cells_per_block[2];    /* apply / residual launch shape, per precision     */
+  int       transfer_cells_per_block[2]; /* transfers to the next coarser level              */
 } stmg_level_info_t;
 
 typedef struct {
@@ -258,6 +276,18 @@ int  stmg_set_profiling(stmg_handle* h, int on);
    synchronises.  reset != 0 zeroes the counters afterwards. */
 int  stmg_get_profile(stmg_handle* h, double* ms, long long* launches, int reset);
 
+/* Launch-parameter tuner: for every level and set-up precision, times the candidate
+   launch shapes (sweep: 1/2/4/8 patches per block or the TMA-pipelined variant; apply and
+   transfers: 1..32 cells per block) with CUDA events on the handle's own work vectors and
+   keeps the fastest; cached V-cycle graphs are recaptured.  Synchronous.  stmg_create
+   calls it when cfg.autotune = 1. */
+int  stmg_autotune(stmg_handle* h);
+
+/* Synchronise and report device-side failures: STMG_ERR_TIMEOUT if a bounded wait in a
+   kernel (the TMA sweep's mbarrier waits) expired since the last check; clears the flag.
+   stmg_solve_slab checks the same flag itself. */
+int  stmg_device_status(stmg_handle* h);
+
 /* Total number of this library's kernel launches since the handle was created. */
 long long stmg_kernel_launches(const stmg_handle* h);
 
@@ -271,9 +301,12 @@ const char* stmg_status_string(int status);
  * The setup numerics that stmg_create runs on the host before uploading, callable from
  * a CPU-only process.  Host pointers; sizes as stated; no allocation is returned. */
 
-/* Default level list (Alg. 2/3, the rule pinned by Table 2(b)): levels[3*i..3*i+2] =
-   (n, r, k) fine -> coarse, *count levels (<= STMG_MAX_LEVELS). */
-int  stmg_host_default_hierarchy(int n, int r, int k, int* levels, int* count);
+/* Default level list (Alg. 2/3, the rule pinned by Table 2(b)) with coarsest mesh
+   coarse_n and lowest temporal degree k_min (both 1 in the paper's runs):
+   levels[3*i..3*i+2] = (n, r, k) fine -> coarse,
+   *count levels (<= STMG_MAX_LEVELS). */
+int  stmg_host_default_hierarchy(int n, int r, int k, int coarse_n, int k_min, int* levels,
+                                 int* count);
 
 /* 1D tables on [0,1] for degree r: Gauss-Lobatto nodes xi[r+2], M1/K1 [(r+2)^2] (mass,
    stiffness of the Lagrange basis), G1/N1 [(r+1)(r+2)] (int L_i ell_p', int L_i ell_p).

@@ -207,32 +207,34 @@ def slab_prolongation(coarse: Slab, fine: Slab):
 # ---------------------------------------------------------------------------
 # Hierarchy (Alg. 2 ConstructHierarchy, Alg. 3 CombineHierarchies)
 # ---------------------------------------------------------------------------
-def default_hierarchy(n, r, k):
+def default_hierarchy(n, r, k, coarse_n=1, k_min=1):
     """Level list fine -> coarse as (n, r, k), the rule decoded from Table 2(b).
 
     Space (Alg. 2 on (h, r)): (n, r), (n, r//2), ..., (n, 1), then (n/2, 1), ..., (1, 1).
     Time (Alg. 2 on (tau, k), no geometric coarsening in time when marching): k, k//2,
     ..., 1, then 1 once more (the geometric loop re-adds the last pair).  Alg. 3 aligns
     both lists at the coarse end and pads the shorter one at the fine end with its
-    finest entry (P4).  k = 0 gives k = 0 on every level."""
+    finest entry (P4).  k = 0 gives k = 0 on every level.  coarse_n is the coarsest mesh
+    (Alg. 2's h_0 = 1 / coarse_n) and k_min the lowest temporal degree; the paper's runs
+    use coarse_n = k_min = 1."""
     space = []
     rr = r
     while rr >= 1:
         space.append((n, rr))
         rr //= 2
     nn = n // 2
-    while nn >= 1:
+    while nn >= max(coarse_n, 1):
         space.append((nn, 1))
         nn //= 2
     if k == 0:
         time = [0]
     else:
-        time = []
-        kk = k
-        while kk >= 1:
-            time.append(kk)
-            kk //= 2
-        time.append(1)
+        # polynomial loop down to k_min (Alg. 2's r_0 in time; 1 in the paper's runs), then
+        # the last degree once more
+        time = [k]
+        while time[-1] // 2 >= max(k_min, 1):
+            time.append(time[-1] // 2)
+        time.append(time[-1])
     L = max(len(space), len(time))
     space = [space[0]] * (L - len(space)) + space
     time = [time[0]] * (L - len(time)) + time

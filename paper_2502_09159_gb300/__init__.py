@@ -48,7 +48,8 @@ class SpaceTimeMG:
                  T: float = 1.0, n_slabs: int = 4, levels: Optional[Sequence[Sequence[int]]] = None,
                  smoothers: Optional[Sequence[int]] = None, omega: float = 0.7, nu1: int = 1,
                  nu2: int = 1, precond_precision="fp64", precisions=("fp64", "fp32"),
-                 gmres_max_iter: int = 200, rel_tol: float = 1e-8, use_graphs: bool = True):
+                 gmres_max_iter: int = 200, rel_tol: float = 1e-8, use_graphs: bool = True,
+                 sweep_variant: int = 0, autotune: bool = True, coarse_n: int = 1, k_min: int = 1):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("SpaceTimeMG needs a CUDA device (no CPU fallback)")
@@ -69,6 +70,10 @@ class SpaceTimeMG:
         cfg.precisions = sum(1 << _PREC[p] for p in precisions)
         cfg.gmres_max_iter, cfg.rel_tol = gmres_max_iter, rel_tol
         cfg.use_graphs = int(use_graphs)
+        cfg.sweep_variant = int(sweep_variant)
+        cfg.autotune = int(autotune)
+        cfg.coarse_n = int(coarse_n)
+        cfg.k_min = int(k_min)
         self.cfg = cfg
         self.dim, self.r, self.k = dim, r, k
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -85,7 +90,11 @@ class SpaceTimeMG:
             self.levels.append({"n": li.n, "r": li.r, "k": li.k, "size": li.size, "n_vel": li.n_vel,
                                 "n_pres": li.n_pres, "smoother": li.smoother, "patch_size": li.patch_size,
                                 "n_patches": li.n_patches, "n_patch_classes": li.n_patch_classes,
-                                "inverse_bytes": tuple(li.inverse_bytes)})
+                                "inverse_bytes": tuple(li.inverse_bytes),
+                                "sweep_variant": tuple(li.sweep_variant),
+                                "patches_per_block": tuple(li.patches_per_block),
+                                "apply_cells_per_block": tuple(li.apply_cells_per_block),
+                                "transfer_cells_per_block": tuple(li.transfer_cells_per_block)})
 
     # ---------------------------------------------------------------- plumbing
     def close(self):
@@ -279,6 +288,10 @@ class SpaceTimeMG:
         names = ["smoother", "mg_other", "operator", "other", "fine_sweep"]
         return {nm: {"ms": ms[i], "launches": n[i]} for i, nm in enumerate(names)}
 
+    def device_status(self):
+        """Synchronise; raise StmgError if a bounded device-side wait expired."""
+        check("stmg_device_status", self._lib.stmg_device_status(self._h))
+
     @property
     def kernel_launches(self) -> int:
         return int(self._lib.stmg_kernel_launches(self._h))
@@ -290,11 +303,12 @@ class SpaceTimeMG:
 
 
 # -------------------------------------------------------------------- host introspection
-def host_default_hierarchy(n: int, r: int, k: int):
+def host_default_hierarchy(n: int, r: int, k: int, coarse_n: int = 1, k_min: int = 1):
     lib = load()
     buf = (C.c_int * (3 * _lib.MAX_LEVELS))()
     cnt = C.c_int()
-    check("stmg_host_default_hierarchy", lib.stmg_host_default_hierarchy(n, r, k, buf, C.byref(cnt)))
+    check("stmg_host_default_hierarchy", lib.stmg_host_default_hierarchy(n, r, k, coarse_n, k_min, buf,
+                                                                                   C.byref(cnt)))
     return [tuple(buf[3 * i:3 * i + 3]) for i in range(cnt.value)]
 
 

@@ -6,7 +6,7 @@ import os
 
 MAX_LEVELS = 24
 OK, ERR_ARG, ERR_OOM, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_NONFINITE, ERR_CUDA, \
-    ERR_UNIMPLEMENTED, ERR_SINGULAR, ERR_TOO_LARGE = range(10)
+    ERR_UNIMPLEMENTED, ERR_SINGULAR, ERR_TOO_LARGE, ERR_TIMEOUT = range(11)
 NOALLOC_MAX_ENTRIES = 1 << 20
 FP64, FP32 = 0, 1
 CELL, VSP = 0, 1
@@ -21,14 +21,18 @@ class Config(C.Structure):
                 ("level_k", C.c_int * MAX_LEVELS), ("smoother", C.c_int * MAX_LEVELS),
                 ("omega", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("precond_precision", C.c_int), ("precisions", C.c_int),
-                ("gmres_max_iter", C.c_int), ("rel_tol", C.c_double), ("use_graphs", C.c_int)]
+                ("gmres_max_iter", C.c_int), ("rel_tol", C.c_double), ("use_graphs", C.c_int),
+                ("sweep_variant", C.c_int), ("autotune", C.c_int), ("coarse_n", C.c_int),
+                ("k_min", C.c_int)]
 
 
 class LevelInfo(C.Structure):
     _fields_ = [("n", C.c_int), ("r", C.c_int), ("k", C.c_int),
                 ("size", C.c_longlong), ("n_vel", C.c_longlong), ("n_pres", C.c_longlong),
                 ("smoother", C.c_int), ("patch_size", C.c_int), ("n_patches", C.c_longlong),
-                ("n_patch_classes", C.c_int), ("inverse_bytes", C.c_longlong * 2)]
+                ("n_patch_classes", C.c_int), ("inverse_bytes", C.c_longlong * 2),
+                ("sweep_variant", C.c_int * 2), ("patches_per_block", C.c_int * 2),
+                ("apply_cells_per_block", C.c_int * 2), ("transfer_cells_per_block", C.c_int * 2)]
 
 
 class SolveInfo(C.Structure):
@@ -63,9 +67,11 @@ _SIGS = {
     "stmg_set_profiling": (_I, [_VP, _I]),
     "stmg_get_profile": (_I, [_VP, C.POINTER(_D), C.POINTER(_LL), _I]),
     "stmg_kernel_launches": (_LL, [_VP]),
+    "stmg_device_status": (_I, [_VP]),
+    "stmg_autotune": (_I, [_VP]),
     "stmg_sweep_bytes": (_I, [_VP, _I, _I, C.POINTER(_D)]),
     "stmg_status_string": (C.c_char_p, [_I]),
-    "stmg_host_default_hierarchy": (_I, [_I, _I, _I, C.POINTER(_I), C.POINTER(_I)]),
+    "stmg_host_default_hierarchy": (_I, [_I, _I, _I, _I, _I, C.POINTER(_I), C.POINTER(_I)]),
     "stmg_host_tables_1d": (_I, [_I] + [C.POINTER(_D)] * 5),
     "stmg_host_time_tables": (_I, [_I, _D] + [C.POINTER(_D)] * 5),
     "stmg_host_patch": (_I, [_I, _I, _I, _I, _D, _D, _I, _LL, C.POINTER(_I), C.POINTER(_D),

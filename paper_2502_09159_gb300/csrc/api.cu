@@ -20,7 +20,6 @@ namespace {
 template <typename T>
 struct PrecDev {
   T* inv = nullptr;   // per-patch inverses, interleaved layout
-  T* wgt = nullptr;   // omega / valence per slab dof
   T* b = nullptr;     // V-cycle right-hand side of this level
   T* x = nullptr;     // V-cycle iterate of this level
   T* r = nullptr;     // residual work vector
@@ -35,8 +34,10 @@ struct LevelDev {
   PrecDev<double> d;
   PrecDev<float> f;
   double* G = nullptr;      // coarsest level: bordered inverse, column-major
+  double* Gacc = nullptr;   // coarsest level with D > 1024: FP64 accumulator of the tiled GEMV
   int streaming = 0;        // read the inverses with evict-first loads
-  int ppb = 1;              // patches per block of the sweep kernel
+  int sweep_var[2] = {1, 1};  // per precision: 1 = block per patch group, 2 = TMA-pipelined
+  int ppb[2] = {1, 1};        // per precision: patches per block of the block sweep
   template <typename T> PrecDev<T>& pd();
 };
 template <> PrecDev<double>& LevelDev::pd<double>() { return d; }
@@ -58,6 +59,8 @@ struct stmg_handle {
   double *V = nullptr, *Z = nullptr, *w = nullptr, *hcol = nullptr, *tmp = nullptr, *partial = nullptr;
   double *bnorm = nullptr, *xhost_b = nullptr, *xhost_x = nullptr;
   int m_alloc = 0;
+  int* d_err = nullptr;           // device flag raised by bounded waits that expired
+  int n_sm = 1;
   ForcingParams fp{};
   MassParams mp{};
   // instrumentation
@@ -230,6 +233,11 @@ static void fill_transfer_params(const LevelHost& F, const LevelHost& C, Transfe
       }
   for (int m = 0; m < C.npm; ++m) for (int d = 0; d < 3; ++d) p->modes_c[m][d] = (signed char)C.modes[m][d];
   for (int m = 0; m < F.npm; ++m) for (int d = 0; d < 3; ++d) p->modes_f[m][d] = (signed char)F.modes[m][d];
+  p->cpb = 1;
+  while (p->cpb < 8 && transfer_smem<T>(*p, 0) * 2 <= 48 * 1024 && transfer_smem<T>(*p, 1) * 2 <= 48 * 1024)
+    p->cpb *= 2;
+  const int ncd = F.dim == 2 ? C.n * C.n : C.n * C.n * C.n;
+  if (p->cpb > ncd) p->cpb = ncd;
 }
 
 template <typename T>
@@ -244,22 +252,32 @@ static int dalloc(T** p, size_t count) {
   return STMG_OK;
 }
 
+// with_inverses = false sets up only the operator and the work vectors (the finest level
+// always has FP64 operator data: FGMRES applies S in FP64 whatever the V-cycle precision)
 template <typename T>
-static int setup_precision(stmg_handle* h, LevelDev& lv, const double* d_cls, const int* d_cls_of) {
+static int setup_precision(stmg_handle* h, LevelDev& lv, const double* d_cls, const int* d_cls_of,
+                           bool with_inverses = true) {
   PrecDev<T>& P = lv.pd<T>();
   const LevelHost& H = lv.H;
   fill_apply_params<T>(H, &P.ap);
   CKS(dalloc(&P.b, H.size));
   CKS(dalloc(&P.x, H.size));
   CKS(dalloc(&P.r, H.size));
-  if (H.smoother >= 0) {
-    CKS(dalloc(&P.inv, (size_t)H.n_patches * H.B * H.Bc));
-    CK(launch_replicate_inverses<T>(d_cls, d_cls_of, P.inv, H.n_patches, H.B, H.Bc, h->st));
-    std::vector<T> w(H.size, T(0));
+  if (H.smoother >= 0 && with_inverses) {
+    // omega / valence per dof (FP64), folded into the rows of every stored inverse
+    std::vector<double> w(H.size, 0.0);
     for (long long i = 0; i < H.size; ++i)
-      if (H.valence[i] > 0) w[i] = (T)(h->cfg.omega / H.valence[i]);
-    CKS(dalloc(&P.wgt, H.size));
-    CK(cudaMemcpy(P.wgt, w.data(), sizeof(T) * H.size, cudaMemcpyHostToDevice));
+      if (H.valence[i] > 0) w[i] = h->cfg.omega / H.valence[i];
+    double* d_w = nullptr;
+    CKS(dalloc(&d_w, H.size));
+    CK(cudaMemcpy(d_w, w.data(), sizeof(double) * H.size, cudaMemcpyHostToDevice));
+    int s = dalloc(&P.inv, (size_t)H.n_patches * H.B * H.Bc);
+    if (s == STMG_OK && launch_replicate_inverses<T>(d_cls, d_cls_of, lv.dofs, d_w, P.inv, H.n_patches, H.B,
+                                                     H.Bc, h->st) != cudaSuccess)
+      s = STMG_ERR_CUDA;
+    cudaStreamSynchronize(h->st);
+    cudaFree(d_w);
+    if (s != STMG_OK) return s;
     P.has_inv = true;
   }
   return STMG_OK;
@@ -267,9 +285,9 @@ static int setup_precision(stmg_handle* h, LevelDev& lv, const double* d_cls, co
 
 static void free_level(LevelDev& lv) {
   auto f = [](void* p) { if (p) cudaFree(p); };
-  f(lv.dofs); f(lv.G);
-  f(lv.d.inv); f(lv.d.wgt); f(lv.d.b); f(lv.d.x); f(lv.d.r);
-  f(lv.f.inv); f(lv.f.wgt); f(lv.f.b); f(lv.f.x); f(lv.f.r);
+  f(lv.dofs); f(lv.G); f(lv.Gacc);
+  f(lv.d.inv); f(lv.d.b); f(lv.d.x); f(lv.d.r);
+  f(lv.f.inv); f(lv.f.b); f(lv.f.x); f(lv.f.r);
   lv = LevelDev();
 }
 
@@ -291,7 +309,13 @@ static int op_sweep(stmg_handle* h, int l, const T* res, T* x, cudaStream_t s) {
   PrecDev<T>& P = lv.pd<T>();
   if (!P.has_inv) return STMG_ERR_ARG;
   Prof pr(h, l == 0 ? STMG_PROF_FINE_SWEEP : STMG_PROF_SMOOTHER, s, prec_of<T>());
-  CK(launch_vanka_sweep<T>(lv.dofs, P.inv, res, P.wgt, x, lv.H.n_patches, lv.H.B, lv.H.Bc, lv.ppb, lv.streaming, s));
+  const int w = prec_of<T>();
+  if (lv.sweep_var[w] == 2 && tma_sweep_supported<T>(lv.H.B))
+    CK(launch_vanka_sweep_tma<T>(lv.dofs, P.inv, res, x, lv.H.n_patches, lv.H.B, lv.H.Bc, h->n_sm,
+                                 lv.streaming, h->d_err, s));
+  else
+    CK(launch_vanka_sweep<T>(lv.dofs, P.inv, res, x, lv.H.n_patches, lv.H.B, lv.H.Bc, lv.ppb[w],
+                             lv.streaming, s));
   h->launches += 1;
   return STMG_OK;
 }
@@ -315,8 +339,109 @@ static int op_prolongate_add(stmg_handle* h, int l, const T* yc, T* xf, cudaStre
 template <typename T>
 static int op_coarse(stmg_handle* h, const T* b, T* x, cudaStream_t s) {
   LevelDev& lv = h->L.back();
-  CK(launch_coarse<T>((int)lv.H.size, lv.G, b, x, s));
-  h->launches += 1;
+  if (lv.Gacc) {
+    CK(launch_coarse_tiled<T>((int)lv.H.size, lv.G, b, x, lv.Gacc, s));
+    h->launches += 2;
+  } else {
+    CK(launch_coarse<T>((int)lv.H.size, lv.G, b, x, s));
+    h->launches += 1;
+  }
+  return STMG_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Launch-parameter tuner: per level and precision, time each candidate launch shape with
+// CUDA events (3 warm-up, 5 timed launches, on the level's own work vectors, whose
+// contents are irrelevant to the timing) and keep the fastest:
+//   sweep      block sweep with 1, 2, 4, 8 patches per block, or the TMA-pipelined sweep
+//   apply      1 ... 32 cells per block (shared memory <= 100 KB)
+//   transfers  1 ... 32 coarse cells per block for restriction + prolongation
+// ------------------------------------------------------------------------------------
+template <typename F>
+static int time_it(stmg_handle* h, F&& fn, float* ms) {
+  cudaEvent_t a = new_event(h), b = new_event(h);
+  if (!a || !b) return STMG_ERR_CUDA;
+  for (int i = 0; i < 3; ++i) CKS(fn());
+  CK(cudaEventRecord(a, h->st));
+  for (int i = 0; i < 5; ++i) CKS(fn());
+  CK(cudaEventRecord(b, h->st));
+  CK(cudaEventSynchronize(b));
+  CK(cudaEventElapsedTime(ms, a, b));
+  h->free_events.push_back(a);
+  h->free_events.push_back(b);
+  return STMG_OK;
+}
+
+template <typename T>
+static int autotune_level(stmg_handle* h, int l) {
+  LevelDev& lv = h->L[l];
+  PrecDev<T>& P = lv.pd<T>();
+  if (!P.b) return STMG_OK;
+  const int w = prec_of<T>();
+  const size_t bytes = sizeof(T) * lv.H.size;
+  CK(cudaMemsetAsync(P.b, 0, bytes, h->st));
+  CK(cudaMemsetAsync(P.x, 0, bytes, h->st));
+  CK(cudaMemsetAsync(P.r, 0, bytes, h->st));
+  const long long saved = h->launches;
+  const bool last = l + 1 == (int)h->L.size();
+  float best = 1e30f, ms = 0.f;
+  if (!last && P.has_inv) {
+    int best_var = 1, best_ppb = lv.ppb[w];
+    const int only = h->cfg.sweep_variant;             // 0: free choice, 1 / 2: fixed variant
+    for (int ppb = 1; ppb <= 8 && only != 2; ppb *= 2) {
+      if (ppb * lv.H.B > 1024) break;
+      lv.sweep_var[w] = 1;
+      lv.ppb[w] = ppb;
+      CKS(time_it(h, [&]() { return op_sweep<T>(h, l, P.r, P.x, h->st); }, &ms));
+      if (ms < best) { best = ms; best_var = 1; best_ppb = ppb; }
+    }
+    if (only != 1 && tma_sweep_supported<T>(lv.H.B)) {
+      lv.sweep_var[w] = 2;
+      CKS(time_it(h, [&]() { return op_sweep<T>(h, l, P.r, P.x, h->st); }, &ms));
+      if (ms < best) { best = ms; best_var = 2; }
+    }
+    lv.sweep_var[w] = best_var;
+    lv.ppb[w] = best_ppb;
+  }
+  {
+    best = 1e30f;
+    int best_cpb = P.ap.cpb;
+    for (int cpb = 1; cpb <= 32 && cpb <= lv.H.n_cells; cpb *= 2) {
+      if (apply_smem_bytes<T>(lv.H.dim, lv.H.np, lv.H.kt, lv.H.npm, cpb) > 100 * 1024) break;
+      P.ap.cpb = cpb;
+      CKS(time_it(h, [&]() { return op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, h->st); }, &ms));
+      if (ms < best) { best = ms; best_cpb = cpb; }
+    }
+    P.ap.cpb = best_cpb;
+  }
+  if (!last && h->L[l + 1].pd<T>().b) {
+    PrecDev<T>& C = h->L[l + 1].pd<T>();
+    const int ncd = lv.H.dim == 2 ? h->L[l + 1].H.n * h->L[l + 1].H.n : h->L[l + 1].H.n * h->L[l + 1].H.n * h->L[l + 1].H.n;
+    best = 1e30f;
+    int best_cpb = P.tp.cpb;
+    for (int cpb = 1; cpb <= 32 && cpb <= ncd; cpb *= 2) {
+      P.tp.cpb = cpb;
+      if (transfer_smem<T>(P.tp, 0) > 100 * 1024 || transfer_smem<T>(P.tp, 1) > 100 * 1024) break;
+      CKS(time_it(h, [&]() {
+        CKS(op_restrict<T>(h, l, P.r, C.b, h->st));
+        return op_prolongate_add<T>(h, l, C.x, P.x, h->st);
+      }, &ms));
+      if (ms < best) { best = ms; best_cpb = cpb; }
+    }
+    P.tp.cpb = best_cpb;
+  }
+  h->launches = saved;
+  return STMG_OK;
+}
+
+static int autotune_impl(stmg_handle* h) {
+  for (size_t l = 0; l < h->L.size(); ++l) {
+    CKS(autotune_level<double>(h, (int)l));
+    CKS(autotune_level<float>(h, (int)l));
+  }
+  for (auto& g : h->graph) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  h->graph_pairs[0].clear(); h->graph_pairs[1].clear();
+  if (h->st) CK(cudaStreamSynchronize(h->st)); else CK(cudaDeviceSynchronize());
   return STMG_OK;
 }
 
@@ -539,8 +664,15 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
   }
   CKS(dev_norm(h, h->w, D, h->bnorm + 2));
   CK(cudaMemcpyAsync(hv, h->bnorm + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  int derr = 0;
+  CK(cudaMemcpyAsync(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   harvest_all(h);
+  if (derr) {
+    CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    info->status = STMG_ERR_TIMEOUT;
+    return STMG_ERR_TIMEOUT;
+  }
   info->iterations = kdim;
   info->rel_residual = hv[0] / bn;
   if (!std::isfinite(info->rel_residual)) status = STMG_ERR_NONFINITE;
@@ -578,6 +710,7 @@ const char* stmg_status_string(int s) {
     case STMG_ERR_UNIMPLEMENTED: return "not implemented for these parameters";
     case STMG_ERR_SINGULAR: return "singular patch or coarse matrix";
     case STMG_ERR_TOO_LARGE: return "level larger than the fixed scratch of stmg_smooth_noalloc";
+    case STMG_ERR_TIMEOUT: return "a bounded device-side wait expired";
     default: return "unknown status";
   }
 }
@@ -595,6 +728,10 @@ int stmg_default_config(stmg_config* c) {
   c->gmres_max_iter = 200;
   c->rel_tol = 1e-8;
   c->use_graphs = 1;
+  c->sweep_variant = 0;
+  c->autotune = 1;
+  c->coarse_n = 1;
+  c->k_min = 1;
   return STMG_OK;
 }
 
@@ -606,13 +743,16 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
   if (c.r > 4 || c.k > 3) return STMG_ERR_UNIMPLEMENTED;
   if (c.gmres_max_iter < 1 || !(c.rel_tol > 0) || c.nu1 < 0 || c.nu2 < 0) return STMG_ERR_ARG;
   if ((c.precisions & 3) == 0) return STMG_ERR_ARG;
+  if (c.sweep_variant < 0 || c.sweep_variant > 2) return STMG_ERR_ARG;
   if (c.precond_precision != STMG_FP64 && c.precond_precision != STMG_FP32) return STMG_ERR_ARG;
   if (!(c.precisions & (1 << c.precond_precision))) return STMG_ERR_ARG;
   h->tau = c.T / c.n_slabs;
   std::vector<std::array<int, 3>> lv;
   if (c.n_levels == 0) {
     if (c.n_cells & (c.n_cells - 1)) return STMG_ERR_ARG;   // default rule needs n = 2^c
-    lv = default_hierarchy(c.n_cells, c.r, c.k);
+    if (c.coarse_n < 1 || c.coarse_n > c.n_cells || (c.coarse_n & (c.coarse_n - 1))) return STMG_ERR_ARG;
+    if (c.k_min < 1) return STMG_ERR_ARG;
+    lv = default_hierarchy(c.n_cells, c.r, c.k, c.coarse_n, c.k_min);
   } else {
     if (c.n_levels > STMG_MAX_LEVELS) return STMG_ERR_ARG;
     for (int i = 0; i < c.n_levels; ++i) lv.push_back({c.level_n[i], c.level_r[i], c.level_k[i]});
@@ -637,6 +777,13 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
     return STMG_ERR_ARG;
   }
   CK(cudaStreamCreateWithFlags(&h->gst, cudaStreamNonBlocking));
+  {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
+    CKS(dalloc(&h->d_err, 1));
+    CK(cudaMemset(h->d_err, 0, sizeof(int)));
+  }
   CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   for (size_t i = 0; i < h->L.size(); ++i) {
@@ -657,15 +804,20 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
       CK(cudaMemcpy(d_cls_of, H.patch_class.data(), sizeof(int) * H.patch_class.size(), cudaMemcpyHostToDevice));
       const double inv_bytes = (double)H.n_patches * H.B * H.Bc * 4.0;
       L.streaming = inv_bytes > 48e6 ? 1 : 0;
-      L.ppb = std::max(1, std::min(8, 1024 / H.B));
+      for (int w = 0; w < 2; ++w) {
+        L.ppb[w] = std::max(1, std::min(8, 1024 / H.B));
+        L.sweep_var[w] = c.sweep_variant == 2 ? 2 : 1;
+      }
     } else {
       std::vector<double> Gcm;
       if (!build_coarse_inverse(&H, &Gcm)) return STMG_ERR_SINGULAR;
       CKS(dalloc(&L.G, Gcm.size()));
       CK(cudaMemcpy(L.G, Gcm.data(), sizeof(double) * Gcm.size(), cudaMemcpyHostToDevice));
+      if (H.size > 1024) CKS(dalloc(&L.Gacc, H.size));
     }
     int st = STMG_OK;
     if (c.precisions & 1) st = setup_precision<double>(h, L, d_cls, d_cls_of);
+    else if (i == 0) st = setup_precision<double>(h, L, d_cls, d_cls_of, false);
     if (st == STMG_OK && (c.precisions & 2)) st = setup_precision<float>(h, L, d_cls, d_cls_of);
     cudaStreamSynchronize(h->st);
     if (d_cls) cudaFree(d_cls);
@@ -680,6 +832,7 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
     fill_transfer_params<double>(h->L[i].H, h->L[i + 1].H, &h->L[i].d.tp);
     fill_transfer_params<float>(h->L[i].H, h->L[i + 1].H, &h->L[i].f.tp);
   }
+  if (c.autotune) CKS(autotune_impl(h));
   // finest-level helpers: slab coupling and forcing
   const LevelHost& F = h->L[0].H;
   MassParams& mp = h->mp;
@@ -731,7 +884,7 @@ void stmg_destroy(stmg_handle* h) {
   for (auto& L : h->L) free_level(L);
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(h->V); f(h->Z); f(h->w); f(h->hcol); f(h->tmp); f(h->partial); f(h->bnorm);
-  f(h->xhost_b); f(h->xhost_x);
+  f(h->xhost_b); f(h->xhost_x); f(h->d_err);
   for (auto e : h->all_events) cudaEventDestroy(e);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -764,6 +917,14 @@ int stmg_level_info(const stmg_handle* h, int lvl, stmg_level_info_t* info) {
   info->n_patch_classes = (int)H.class_rep.size();
   if (L.d.has_inv) info->inverse_bytes[0] = (long long)H.n_patches * H.B * H.Bc * 8;
   if (L.f.has_inv) info->inverse_bytes[1] = (long long)H.n_patches * H.B * H.Bc * 4;
+  for (int w = 0; w < 2; ++w) {
+    info->sweep_variant[w] = L.sweep_var[w];
+    info->patches_per_block[w] = L.ppb[w];
+  }
+  info->apply_cells_per_block[0] = L.d.ap.cpb;
+  info->apply_cells_per_block[1] = L.f.ap.cpb;
+  info->transfer_cells_per_block[0] = L.d.tp.cpb;
+  info->transfer_cells_per_block[1] = L.f.tp.cpb;
   return STMG_OK;
 }
 
@@ -819,6 +980,7 @@ int stmg_coarse_solve(stmg_handle* h, int prec, const void* b, void* x) {
 
 int stmg_vcycle(stmg_handle* h, int prec, const double* b, double* x) {
   if (!h || !b || !x || !prec_ok(h, 0, prec)) return STMG_ERR_ARG;
+  if (!(h->cfg.precisions & (1 << prec))) return STMG_ERR_ARG;   // that V-cycle was not set up
   return precondition(h, prec, b, x);
 }
 
@@ -923,12 +1085,31 @@ int stmg_get_profile(stmg_handle* h, double* ms, long long* n, int reset) {
 
 long long stmg_kernel_launches(const stmg_handle* h) { return h ? h->launches : 0; }
 
+int stmg_autotune(stmg_handle* h) {
+  if (!h) return STMG_ERR_ARG;
+  return autotune_impl(h);
+}
+
+int stmg_device_status(stmg_handle* h) {
+  if (!h) return STMG_ERR_ARG;
+  if (h->st) CK(cudaStreamSynchronize(h->st)); else CK(cudaDeviceSynchronize());
+  CK(cudaStreamSynchronize(h->gst));
+  int derr = 0;
+  CK(cudaMemcpy(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (derr) {
+    CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    return STMG_ERR_TIMEOUT;
+  }
+  return STMG_OK;
+}
+
 int stmg_sweep_bytes(const stmg_handle* h, int lvl, int prec, double* bytes) {
   if (!h || !bytes || lvl < 0 || lvl + 1 >= (int)h->L.size()) return STMG_ERR_ARG;
   const LevelHost& H = h->L[lvl].H;
   const double s = prec == STMG_FP64 ? 8.0 : 4.0;
-  // inverses + patch index table + gathered residual + weights + read-modify-write of x
-  *bytes = (double)H.n_patches * H.B * H.Bc * s + (double)H.n_patches * H.B * 4.0 + 4.0 * H.size * s;
+  // inverses (valence weights folded in) + patch index table + gathered residual +
+  // read-modify-write of x
+  *bytes = (double)H.n_patches * H.B * H.Bc * s + (double)H.n_patches * H.B * 4.0 + 3.0 * H.size * s;
   return STMG_OK;
 }
 

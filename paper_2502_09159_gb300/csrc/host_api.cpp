@@ -13,9 +13,9 @@ using namespace stmg;
 
 extern "C" {
 
-int stmg_host_default_hierarchy(int n, int r, int k, int* levels, int* count) {
-  if (!levels || !count || n < 1 || r < 1 || k < 0) return STMG_ERR_ARG;
-  auto lv = default_hierarchy(n, r, k);
+int stmg_host_default_hierarchy(int n, int r, int k, int coarse_n, int k_min, int* levels, int* count) {
+  if (!levels || !count || n < 1 || r < 1 || k < 0 || coarse_n < 1 || k_min < 1) return STMG_ERR_ARG;
+  auto lv = default_hierarchy(n, r, k, coarse_n, k_min);
   if ((int)lv.size() > STMG_MAX_LEVELS) return STMG_ERR_ARG;
   for (size_t i = 0; i < lv.size(); ++i)
     for (int j = 0; j < 3; ++j) levels[3 * i + j] = lv[i][j];

@@ -102,20 +102,30 @@ template <typename T>
 size_t apply_smem_bytes(int dim, int np, int kt, int npm, int cpb);
 
 template <typename T>
-cudaError_t launch_vanka_sweep(const int* dofs, const T* inv, const T* res, const T* wgt, T* x,
-                               long long n_patches, int B, int Bc, int ppb, int streaming,
-                               cudaStream_t st);
+cudaError_t launch_vanka_sweep(const int* dofs, const T* inv, const T* res, T* x, long long n_patches, int B,
+                               int Bc, int ppb, int streaming, cudaStream_t st);
+constexpr int TMA_NCW = 4;   // consumer warps of the TMA-pipelined sweep (+1 producer warp)
 template <typename T>
-cudaError_t launch_replicate_inverses(const double* cls, const int* cls_of_patch, T* inv,
-                                      long long n_patches, int B, int Bc, cudaStream_t st);
+cudaError_t launch_vanka_sweep_tma(const int* dofs, const T* inv, const T* res, T* x, long long n_patches, int B,
+                                   int Bc, int n_sm, int streaming, int* err, cudaStream_t st);
+template <typename T>
+bool tma_sweep_supported(int B);
+template <typename T>
+cudaError_t launch_replicate_inverses(const double* cls, const int* cls_of_patch, const int* dofs,
+                                      const double* w, T* inv, long long n_patches, int B, int Bc,
+                                      cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_prolongate(const TransferParams<T>& p, const T* yc, T* xf, cudaStream_t st);
 template <typename T>
 cudaError_t launch_restrict(const TransferParams<T>& p, const T* rf, T* bc, cudaStream_t st);
+template <typename T>
+size_t transfer_smem(const TransferParams<T>& p, int restrict_);
 
 template <typename T>
 cudaError_t launch_coarse(int D, const double* Gcm, const T* b, T* x, cudaStream_t st);
+template <typename T>
+cudaError_t launch_coarse_tiled(int D, const double* Gcm, const T* b, T* x, double* acc, cudaStream_t st);
 
 cudaError_t launch_mass_coupling(const MassParams& p, const double* vprev, double* b, cudaStream_t st);
 cudaError_t launch_forcing(const ForcingParams& p, const double* fq, double* F, cudaStream_t st);

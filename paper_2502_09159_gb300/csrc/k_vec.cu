@@ -163,6 +163,51 @@ __global__ void k_coarse(int D, const double* __restrict__ Gcm, const T* __restr
   }
 }
 
+// Large coarse levels (D > 1024): tiles of 256 rows x 64 columns of G, four independent
+// FP64 accumulators per row, partial products accumulated in FP64 (acc, zeroed first),
+// then rounded to the vector type.  Enough tiles to cover every SM.
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_tiled(int D, const double* __restrict__ Gcm,
+                                                      const T* __restrict__ b, double* __restrict__ acc) {
+  constexpr int CT = 64;
+  __shared__ double bs[CT];
+  const int c0 = blockIdx.y * CT;
+  const int cn = min(CT, D - c0);
+  if (threadIdx.x < CT) bs[threadIdx.x] = threadIdx.x < cn ? (double)b[c0 + threadIdx.x] : 0.0;
+  __syncthreads();
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= D) return;
+  const double* g = Gcm + (size_t)c0 * D + row;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int c = 0;
+  for (; c + 4 <= cn; c += 4) {
+    s0 += g[(size_t)c * D] * bs[c];
+    s1 += g[(size_t)(c + 1) * D] * bs[c + 1];
+    s2 += g[(size_t)(c + 2) * D] * bs[c + 2];
+    s3 += g[(size_t)(c + 3) * D] * bs[c + 3];
+  }
+  for (; c < cn; ++c) s0 += g[(size_t)c * D] * bs[c];
+  atomicAdd(acc + row, (s0 + s1) + (s2 + s3));
+}
+
+template <typename T>
+__global__ void k_coarse_finish(int D, const double* __restrict__ acc, T* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < D) x[i] = (T)acc[i];
+}
+
+template <typename T>
+cudaError_t launch_coarse_tiled(int D, const double* Gcm, const T* b, T* x, double* acc, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * D, st);
+  if (e != cudaSuccess) return e;
+  const int nr = (D + 255) / 256, nc = (D + 63) / 64;
+  k_coarse_tiled<T><<<dim3(nr, nc), 256, 0, st>>>(D, Gcm, b, acc);
+  k_coarse_finish<T><<<nr, 256, 0, st>>>(D, acc, x);
+  return cudaGetLastError();
+}
+template cudaError_t launch_coarse_tiled<double>(int, const double*, const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_coarse_tiled<float>(int, const double*, const float*, float*, double*, cudaStream_t);
+
 template <typename T>
 cudaError_t launch_coarse(int D, const double* Gcm, const T* b, T* x, cudaStream_t st) {
   const int blocks = (D + 255) / 256;

@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <condition_variable>
+#include <mutex>
 #include <cstring>
 #include <map>
 #include <stdexcept>
@@ -17,17 +19,26 @@ namespace stmg {
 static int ipow(int b, int e) { int r = 1; while (e-- > 0) r *= b; return r; }
 static int binom(int n, int k) { long long r = 1; for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i; return (int)r; }
 
-std::vector<std::array<int, 3>> default_hierarchy(int n, int r, int k) {
-  // space: (n, r), (n, r/2), ..., (n, 1), then (n/2, 1), ..., (1, 1)
+std::vector<std::array<int, 3>> default_hierarchy(int n, int r, int k, int coarse_n, int k_min) {
+  // space: (n, r), (n, r/2), ..., (n, 1), then (n/2, 1), ..., (coarse_n, 1); coarse_n is the
+  // coarsest mesh of Alg. 2 (its h_0 = 1 / coarse_n)
   std::vector<std::array<int, 2>> space;
   for (int rr = r; rr >= 1; rr /= 2) space.push_back({n, rr});
-  for (int nn = n / 2; nn >= 1; nn /= 2) space.push_back({nn, 1});
+  for (int nn = n / 2; nn >= coarse_n && nn >= 1; nn /= 2) space.push_back({nn, 1});
   // time: k, k/2, ..., 1, then 1 again (the geometric loop of Alg. 2 re-adds the last
   // pair); k = 0 stays 0.  Both lists are aligned at the coarse end, the shorter one is
   // padded at the fine end with its finest entry (Alg. 3, P4).
+  // k_min: lowest temporal degree of the polynomial loop (Alg. 2's r_0 applied in time; the
+  // paper's runs use 1); k_min >= k keeps DG(k) on every level.
   std::vector<int> time;
+  const int kmin = k_min < 1 ? 1 : k_min;
   if (k == 0) time.push_back(0);
-  else { for (int kk = k; kk >= 1; kk /= 2) time.push_back(kk); time.push_back(1); }
+  else {
+    int kk = k;
+    time.push_back(kk);
+    while (kk / 2 >= kmin) { kk /= 2; time.push_back(kk); }
+    time.push_back(kk);
+  }
   const size_t L = std::max(space.size(), time.size());
   while (space.size() < L) space.insert(space.begin(), space.front());
   while (time.size() < L) time.insert(time.begin(), time.front());
@@ -281,8 +292,74 @@ void assemble_submatrix(const LevelHost& L, const std::vector<long long>& idx, c
     }
 }
 
+// Multithreaded in-place Gauss-Jordan (same arithmetic, rows of each elimination step
+// split over threads) for the large dense matrices of coarse levels.
+static bool invert_gauss_jordan_mt(double* A, int n, int nth) {
+  std::vector<int> piv(n);
+  double amax = 0.0;
+  for (size_t i = 0; i < (size_t)n * n; ++i) amax = std::max(amax, std::fabs(A[i]));
+  std::mutex mu;
+  std::condition_variable cv;
+  int arrived = 0;
+  long long gen = 0;
+  auto barrier = [&]() {
+    std::unique_lock<std::mutex> lk(mu);
+    const long long g = gen;
+    if (++arrived == nth) { arrived = 0; ++gen; cv.notify_all(); }
+    else cv.wait(lk, [&] { return gen != g; });
+  };
+  bool ok = true;
+  auto worker = [&](int t) {
+    for (int c = 0; c < n; ++c) {
+      if (t == 0) {
+        int p = c;
+        double best = std::fabs(A[(size_t)c * n + c]);
+        for (int i = c + 1; i < n; ++i) {
+          const double v = std::fabs(A[(size_t)i * n + c]);
+          if (v > best) { best = v; p = i; }
+        }
+        if (!(best > 1e-14 * amax)) ok = false;
+        piv[c] = p;
+        if (ok) {
+          if (p != c)
+            for (int j = 0; j < n; ++j) std::swap(A[(size_t)c * n + j], A[(size_t)p * n + j]);
+          const double inv = 1.0 / A[(size_t)c * n + c];
+          A[(size_t)c * n + c] = 1.0;
+          double* rc = A + (size_t)c * n;
+          for (int j = 0; j < n; ++j) rc[j] *= inv;
+        }
+      }
+      barrier();
+      if (!ok) return;
+      const double* rc = A + (size_t)c * n;
+      for (int i = t; i < n; i += nth) {
+        if (i == c) continue;
+        double* ri = A + (size_t)i * n;
+        const double f = ri[c];
+        if (f == 0.0) continue;
+        ri[c] = 0.0;
+        for (int j = 0; j < n; ++j) ri[j] -= f * rc[j];
+      }
+      barrier();
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nth; ++t) th.emplace_back(worker, t);
+  worker(0);
+  for (auto& x : th) x.join();
+  if (!ok) return false;
+  for (int c = n - 1; c >= 0; --c)
+    if (piv[c] != c)
+      for (int i = 0; i < n; ++i) std::swap(A[(size_t)i * n + c], A[(size_t)i * n + piv[c]]);
+  return true;
+}
+
 // In-place inverse of the row-major n x n matrix A (Gauss-Jordan, partial pivoting).
 bool invert_gauss_jordan(double* A, int n) {
+  if (n >= 768) {
+    const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    if (nth > 1) return invert_gauss_jordan_mt(A, n, nth);
+  }
   std::vector<int> piv(n);
   std::vector<double> row(n);
   double amax = 0.0;

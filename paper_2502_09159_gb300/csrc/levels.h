@@ -29,7 +29,7 @@ struct LevelHost {
   std::vector<int> valence;                // [size]
 };
 
-std::vector<std::array<int, 3>> default_hierarchy(int n, int r, int k);
+std::vector<std::array<int, 3>> default_hierarchy(int n, int r, int k, int coarse_n = 1, int k_min = 1);
 void init_level_geometry(LevelHost* L, int dim, int n, int r, int k, double tau, double nu);
 void build_patches(LevelHost* L, int kind);
 void assemble_submatrix(const LevelHost& L, const std::vector<long long>& idx, const std::vector<char>& dir,

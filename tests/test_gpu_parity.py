@@ -94,6 +94,7 @@ def test_vanka_sweep_and_smoothing_step(case):
         assert rel(g.vanka_sweep(dev(res, torch.float32), x32, l).double(), ref) < 1e-5
         b, x0 = free_vec(s, 11 + l), free_vec(s, 13 + l)
         assert rel(g.smooth(dev(b), dev(x0), l, steps=1), W.step(b, x0)) < 1e-12
+    g.device_status()
 
 
 @pytest.mark.parametrize("case", [c for c in CASES if c[4] != [(5, 1, 1)]],
@@ -119,6 +120,49 @@ def test_coarse_solve_and_vcycle(case):
     assert rel(g.coarse_solve(dev(bc)), og.coarse_inv @ bc) < 1e-12
     s0 = og.slabs[0]
     b = free_vec(s0, 31)
+    ref = og.vcycle(b)
+    assert rel(g.vcycle(dev(b), "fp64"), ref) < 1e-11
+    assert rel(g.vcycle(dev(b), "fp32"), ref) < 1e-4
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_sweep_variants_agree_full_size(dtype):
+    """The bench workload's levels (64x64, Q3/P2, DG(2)): the persistent TMA-pipelined
+    sweep and the tuner's choice equal the one-block-per-patch-group sweep."""
+    gs = [stmg.SpaceTimeMG(dim=2, n_cells=64, r=2, k=2, n_slabs=16, sweep_variant=v, use_graphs=False,
+                           precisions=("fp64",) if dtype == torch.float64 else ("fp32",),
+                           precond_precision="fp64" if dtype == torch.float64 else "fp32") for v in (2, 1, 0)]
+    assert all(v == 2 for v in gs[0].levels[0]["sweep_variant"][1 if dtype == torch.float32 else 0:][:1])
+    for l in range(len(gs[0].levels) - 1):
+        res = torch.from_numpy(random_vector(gs[0].size(l), 50 + l)).to("cuda", dtype)
+        out = []
+        for g in gs:
+            x = torch.zeros_like(res)
+            for _ in range(2):
+                g.vanka_sweep(res, x, l)
+            out.append(x)
+        tol = 1e-13 if dtype == torch.float64 else 2e-6
+        for o in (out[0], out[2]):                      # TMA and tuned against the block sweep
+            assert ((o - out[1]).abs().max() / out[1].abs().max()).item() < tol
+    for g in gs:
+        g.device_status()
+        g.close()
+
+
+@pytest.mark.parametrize("coarse_n", [4, 8])
+def test_vcycle_with_coarser_mesh_stop(coarse_n):
+    """Alg. 2 with h_0 = 1/coarse_n: the coarsest level is an 8x8 (D = 1540, tiled FP64
+    coarse product) or 4x4 mesh solved directly."""
+    dim, n, r, k = 2, 16, 1, 1
+    levels = stmg.host_default_hierarchy(n, r, k, coarse_n)
+    og = Multigrid(dim, levels, NU, TAU, MGConfig())
+    g = stmg.SpaceTimeMG(dim=dim, n_cells=n, r=r, k=k, nu=NU, T=TAU * 5, n_slabs=5, coarse_n=coarse_n)
+    assert [(l["n"], l["r"], l["k"]) for l in g.levels] == [tuple(x) for x in levels]
+    cs = og.slabs[-1]
+    bc = free_vec(cs, 51)
+    for dt, tol in ((torch.float64, 1e-12), (torch.float32, 2e-6)):
+        assert rel(g.coarse_solve(dev(bc, dt)).double(), og.coarse_inv @ bc) < tol
+    b = free_vec(og.slabs[0], 53)
     ref = og.vcycle(b)
     assert rel(g.vcycle(dev(b), "fp64"), ref) < 1e-11
     assert rel(g.vcycle(dev(b), "fp32"), ref) < 1e-4

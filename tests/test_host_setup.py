@@ -46,6 +46,10 @@ def test_create_without_gpu_fails_cleanly(pkg):
                                    (1, 1, 1), (128, 2, 1), (4, 1, 3)])
 def test_hierarchy_matches_oracle(pkg, n, r, k):
     assert pkg.host_default_hierarchy(n, r, k) == default_hierarchy(n, r, k)
+    for cn in (1, 2, 8):
+        for km in (1, 2, 4):
+            if cn <= n:
+                assert pkg.host_default_hierarchy(n, r, k, cn, km) == default_hierarchy(n, r, k, cn, km)
 
 
 @pytest.mark.parametrize("r", [1, 2, 3, 4])
