@@ -30,8 +30,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(dim=2, n_cells=64, r=2, k=2, nu=1.0, T=1.0, n_slabs=16)
-WORKLOAD_NAME = "2D 64x64 Q3/P2disc DG(2), 16 slabs, Fourier forcing (seeds 1,2), cell Vanka"
+WORKLOADS = {
+    "c2": (dict(dim=2, n_cells=64, r=2, k=2, nu=1.0, T=1.0, n_slabs=16),
+           "2D 64x64 Q3/P2disc DG(2), 16 slabs, Fourier forcing (seeds 1,2), cell Vanka", "fourier"),
+    "c3": (dict(dim=3, n_cells=32, r=2, k=1, nu=1e-2, T=1.0, n_slabs=8),
+           "3D 32^3 Q3/P2disc DG(1), 8 slabs, Taylor-Green-like field, nu = 1e-2, cell Vanka", "taylor_green"),
+}
+WORKLOAD, WORKLOAD_NAME, _ = WORKLOADS["c2"]
 METRIC = "space-time DoFs/s (apply, Vanka sweep, V-cycle); time-to-1e-8 mixed vs FP64"
 
 
@@ -44,9 +49,12 @@ def parse():
     p.add_argument("--no-micro", action="store_true", help="skip the per-kernel rate measurements")
     p.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline (profiler runs)")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
-    p.add_argument("--coarse-n", type=int, default=8, help="coarsest mesh of the hierarchy (Alg. 2's 1/h_0)")
-    p.add_argument("--k-min", type=int, default=2, help="lowest temporal degree of the hierarchy")
+    p.add_argument("--coarse-n", type=int, default=0,
+                   help="coarsest mesh of the hierarchy (Alg. 2's 1/h_0); 0: 8 in 2D, 1 in 3D")
+    p.add_argument("--k-min", type=int, default=0, help="lowest temporal degree of the hierarchy; 0: k in 2D, 1 in 3D")
     p.add_argument("--levels", default="", help="explicit level list n:r:k,... fine -> coarse")
+    p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
+                   help="c2: the 2D headline configuration; c3: the 3D 32^3 configuration")
     return p.parse_args()
 
 
@@ -139,7 +147,13 @@ def run_ours(args):
     import torch
 
     import paper_2502_09159_gb300 as stmg
-    from workloads import fourier_forcing_2d
+    from workloads import fourier_forcing_2d, taylor_green_3d
+    global WORKLOAD, WORKLOAD_NAME
+    WORKLOAD, WORKLOAD_NAME, forcing_kind = WORKLOADS[args.workload]
+    if args.coarse_n == 0:
+        args.coarse_n = 8 if WORKLOAD["dim"] == 2 else 1
+    if args.k_min == 0:
+        args.k_min = WORKLOAD["k"] if WORKLOAD["dim"] == 2 else 1
 
     rank, world, local = dist_env()
     if world > 1:
@@ -153,12 +167,18 @@ def run_ours(args):
     D = slab_dofs(w)
     N = w["n_slabs"]
     # replicas: every rank solves its own problem (different forcing seeds), no data-path collective
-    pb = fourier_forcing_2d(nu=w["nu"], seed_psi=1 + 10 * rank, seed_phi=2 + 10 * rank)
+    if forcing_kind == "fourier":
+        pb = fourier_forcing_2d(nu=w["nu"], seed_psi=1 + 10 * rank, seed_phi=2 + 10 * rank)
+    else:
+        pb = taylor_green_3d(nu=w["nu"])
+    precisions = ("fp64", "fp32") if w["dim"] == 2 else ("fp32",)
 
     levels = [tuple(int(v) for v in t.split(":")) for t in args.levels.split(",")] if args.levels else None
 
     def make(prec, coarse_n=args.coarse_n, k_min=args.k_min):
-        return stmg.SpaceTimeMG(**w, precond_precision=prec, coarse_n=coarse_n, k_min=k_min, levels=levels)
+        return stmg.SpaceTimeMG(**w, precond_precision=prec, coarse_n=min(coarse_n, w["n_cells"]),
+                                k_min=k_min, levels=levels, precisions=precisions if prec == "fp32" else (prec,),
+                                gmres_max_iter=200 if w["dim"] == 2 else 80)
 
     mg = make("fp32")
     pts = mg.forcing_points()
@@ -344,7 +364,8 @@ def micro(mg, make, F, N, D, step_fn):
     x32 = x64.float()
     y64, y32 = torch.empty_like(x64), torch.empty_like(x32)
     rates = {}
-    for tag, x, y in (("fp64", x64, y64), ("fp32", x32, y32)):
+    have = [("fp64", x64, y64)] if mg.levels[0]["inverse_bytes"][0] else []
+    for tag, x, y in have + [("fp32", x32, y32)]:
         t = timeit(lambda: mg.apply(x, 0, out=y))
         rates[f"apply_{tag}"] = D / (t / 1e3)
         t = timeit(lambda: mg.vanka_sweep(x, y, 0))
@@ -361,7 +382,7 @@ def micro(mg, make, F, N, D, step_fn):
     # time-to-1e-8: FP64 preconditioner vs FP32 preconditioner, same march
     tt = {}
     for prec in ("fp64", "fp32"):
-        g = mg if prec == "fp32" else make("fp64")
+        g = mg if prec == "fp32" else make("fp64")     # FP64 V-cycle (FP64 inverses)
         its = []
         step_fn(g, its)
         torch.cuda.synchronize()
@@ -384,9 +405,9 @@ _ORACLE_SNIPPET = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
 from oracle.stokes import MGConfig, march, Multigrid, default_hierarchy, fgmres
-from workloads import fourier_forcing_2d
+from workloads import fourier_forcing_2d, taylor_green_3d
 w = {w!r}
-pb = fourier_forcing_2d(nu=w["nu"])
+pb = fourier_forcing_2d(nu=w["nu"]) if w["dim"] == 2 else taylor_green_3d(nu=w["nu"])
 tau = w["T"] / w["n_slabs"]
 t0 = time.time()
 mg = Multigrid(w["dim"], default_hierarchy(w["n_cells"], w["r"], w["k"], {coarse_n}, {k_min}), w["nu"], tau,
@@ -403,9 +424,19 @@ print(json.dumps({{"setup_s": t_setup, "solve_s": times, "iterations": info.iter
 """
 
 
+def oracle_workload():
+    """The oracle's bounded sample: the workload itself in 2D; in 3D the same discretisation
+    on an 8^3 mesh (the assembled 32^3 system does not fit the oracle)."""
+    w = dict(WORKLOAD)
+    if w["dim"] == 3:
+        w["n_cells"] = min(w["n_cells"], 8)
+    return w
+
+
 def oracle_sample(reps, coarse_n=8, k_min=2):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = _ORACLE_SNIPPET.format(root=ROOT, w=WORKLOAD, reps=reps, coarse_n=coarse_n, k_min=k_min)
+    w = oracle_workload()
+    code = _ORACLE_SNIPPET.format(root=ROOT, w=w, reps=reps, coarse_n=min(coarse_n, w["n_cells"]), k_min=k_min)
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if p.returncode != 0:
         raise RuntimeError(p.stderr[-2000:])
@@ -417,16 +448,23 @@ def cpu_baseline(reps=1, coarse_n=8, k_min=2):
         r = oracle_sample(reps, coarse_n, k_min)
         t = min(r["solve_s"])
         return {"value": r["D"] / t, "unit": "space-time DoFs/s", "cores": 1, "kind": "oracle",
-                "sample": f"slab 1 of 16 solved by the FP64 oracle (FGMRES + V-cycle to 1e-8, "
+                "sample": f"slab 1 of {WORKLOAD['n_slabs']} ({oracle_workload()['n_cells']}^{WORKLOAD['dim']} "
+                          f"cells) solved by the FP64 oracle (FGMRES + V-cycle to 1e-8, "
                           f"{r['iterations']} iterations, {t:.1f} s; setup {r['setup_s']:.1f} s not timed)"}
     except Exception as e:  # the baseline is reported, not required
         return {"value": None, "unit": "space-time DoFs/s", "cores": 1, "kind": "oracle", "error": str(e)[:300]}
 
 
 def run_reference(args):
+    global WORKLOAD, WORKLOAD_NAME
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    WORKLOAD, WORKLOAD_NAME, _ = WORKLOADS[args.workload]
+    if args.coarse_n == 0:
+        args.coarse_n = 8 if WORKLOAD["dim"] == 2 else 1
+    if args.k_min == 0:
+        args.k_min = WORKLOAD["k"] if WORKLOAD["dim"] == 2 else 1
     r = oracle_sample(args.warmup + args.steps, args.coarse_n, args.k_min)
     times = r["solve_s"][args.warmup:]
     t = sum(times) / len(times)

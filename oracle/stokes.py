@@ -39,36 +39,21 @@ from .fe import SpaceFE, TimeFE, gauss_legendre, lagrange_values, legendre_unit,
 # ---------------------------------------------------------------------------
 # Slab operator and right-hand side (Problem LocAlg, Eq. InAlg, DefDtauh)
 # ---------------------------------------------------------------------------
-class Slab:
-    """Space-time slab system of one level: spaces, matrices and the Dirichlet mask."""
+class SlabGeometry:
+    """Spaces, layout and Dirichlet mask of one slab system, without assembled matrices
+    (enough for right-hand sides, error norms and row-wise evaluation at any size)."""
 
     def __init__(self, dim, n, r, k, nu, tau):
         self.space = SpaceFE(dim, n, r)
         self.time = TimeFE(k, tau)
         self.dim, self.n, self.r, self.k, self.nu, self.tau = dim, n, r, k, nu, tau
         sp_ = self.space
-        self.Mv = sp_.mass()
-        self.Av = sp_.laplace()
-        self.B = sp_.divergence()
         self.nv, self.npr = sp_.n_vel, sp_.n_pres
         self.kt = k + 1
         self.size = self.kt * (self.nv + self.npr)
         assert self.size == slab_size(dim, n, r, k)
         dir_v = sp_.vel_dirichlet()
         self.dirichlet = np.concatenate([np.tile(dir_v, self.kt), np.zeros(self.kt * self.npr, bool)])
-        self.S = self._assemble()
-
-    def _assemble(self):
-        t = self.time
-        Mt = sp.csr_matrix(t.M)
-        vel = sp.kron(sp.csr_matrix(t.K), self.Mv) + sp.kron(Mt, self.nu * self.Av)
-        vp = -sp.kron(Mt, self.B.T)
-        pv = -sp.kron(Mt, self.B)
-        pp = sp.csr_matrix((self.kt * self.npr, self.kt * self.npr))
-        S = sp.bmat([[vel, vp], [pv, pp]], format="csr")
-        free = sp.diags((~self.dirichlet).astype(float))
-        fix = sp.diags(self.dirichlet.astype(float))
-        return (free @ S @ free + fix).tocsr()
 
     # layout helpers ---------------------------------------------------------
     def vel(self, X, a):
@@ -89,6 +74,77 @@ class Slab:
             F[a * self.nv:(a + 1) * self.nv] = self.tau / 2 * t.weights[a] * load
         F[self.dirichlet] = 0.0
         return F
+
+
+def slab_rows(geo: SlabGeometry, x, rows):
+    """Rows `rows` of S x (Eq. InAlg / DefDtauh with the identity on Dirichlet rows and
+    columns), evaluated one by one from the element matrices of the cells that touch each
+    row's dof: for any mesh size, without assembling S."""
+    sp_, t = geo.space, geo.time
+    kt, dim, nv, npr = geo.kt, geo.dim, geo.nv, geo.npr
+    poff = kt * nv
+    G, R1, n = sp_.G, sp_.r + 1, sp_.n
+    vdir = sp_.dirichlet
+    out = np.zeros(len(rows))
+
+    def xv(a, comp, nodes):                       # velocity entries, Dirichlet columns removed
+        v = x[a * nv + comp * sp_.n_nodes + nodes]
+        return np.where(vdir[nodes], 0.0, v)
+
+    for q, i in enumerate(rows):
+        if i < poff:                              # velocity row (a, comp, node)
+            a, rest = divmod(i, nv)
+            comp, node = divmod(rest, sp_.n_nodes)
+            if vdir[node]:
+                out[q] = x[i]
+                continue
+            g = np.array([(node // G ** d) % G for d in range(dim)])
+            cands = [sorted({min(gd // R1, n - 1), max(gd - 1, 0) // R1}) for gd in g]
+            s = 0.0
+            for cell in np.array(np.meshgrid(*cands, indexing="ij")).reshape(dim, -1).T:
+                c = int((cell * n ** np.arange(dim)).sum())
+                loc = g - cell * R1
+                if np.any(loc < 0) or np.any(loc > R1):
+                    continue
+                p = int((loc * sp_.np1 ** np.arange(dim)).sum())
+                nodes = sp_.cell_nodes[c]
+                for b in range(kt):
+                    ub = xv(b, comp, nodes)
+                    s += t.K[a, b] * (sp_.Me[p] @ ub)
+                s += t.M[a, a] * geo.nu * (sp_.Ae[p] @ xv(a, comp, nodes))
+                pc = x[poff + a * npr + c * sp_.n_pm + np.arange(sp_.n_pm)]
+                s -= t.M[a, a] * (sp_.Be[comp][:, p] @ pc)
+            out[q] = s
+        else:                                     # pressure row (a, cell, mode)
+            a, rest = divmod(i - poff, npr)
+            c, m = divmod(rest, sp_.n_pm)
+            nodes = sp_.cell_nodes[c]
+            out[q] = -t.M[a, a] * sum(sp_.Be[comp][m] @ xv(a, comp, nodes) for comp in range(dim))
+    return out
+
+
+class Slab(SlabGeometry):
+    """Space-time slab system of one level: spaces, matrices and the Dirichlet mask."""
+
+    def __init__(self, dim, n, r, k, nu, tau):
+        super().__init__(dim, n, r, k, nu, tau)
+        sp_ = self.space
+        self.Mv = sp_.mass()
+        self.Av = sp_.laplace()
+        self.B = sp_.divergence()
+        self.S = self._assemble()
+
+    def _assemble(self):
+        t = self.time
+        Mt = sp.csr_matrix(t.M)
+        vel = sp.kron(sp.csr_matrix(t.K), self.Mv) + sp.kron(Mt, self.nu * self.Av)
+        vp = -sp.kron(Mt, self.B.T)
+        pv = -sp.kron(Mt, self.B)
+        pp = sp.csr_matrix((self.kt * self.npr, self.kt * self.npr))
+        S = sp.bmat([[vel, vp], [pv, pp]], format="csr")
+        free = sp.diags((~self.dirichlet).astype(float))
+        fix = sp.diags(self.dirichlet.astype(float))
+        return (free @ S @ free + fix).tocsr()
 
     def coupling(self, v_prev):
         """(C_tau (x) M_h) V_{n-1} of Eq. InAlg: velocity row a gets phi_a(t_{n-1}^+) M_h v_{n-1}."""

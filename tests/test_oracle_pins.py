@@ -360,3 +360,16 @@ def test_mg_iterations_bounded_in_h():
         _, infos, _, _ = march(pb, n, 1, 1, n, tol=1e-8, slabs_to_run=2)
         its.append(max(i.iterations for i in infos))
     assert max(its) <= 15 and its[-1] <= its[1] + 3
+
+
+@pytest.mark.parametrize("dim,n,r,k", [(2, 3, 2, 2), (3, 2, 1, 1), (2, 4, 1, 0), (3, 2, 2, 1)])
+def test_slab_rows_equal_assembled_rows(dim, n, r, k):
+    """Row-wise evaluation of S x from element matrices (used for full-size sampled parity)
+    equals the assembled operator."""
+    from oracle.stokes import slab_rows
+    from workloads import random_vector
+    s = Slab(dim, n, r, k, 0.7, 0.3)
+    x = random_vector(s.size, 5)
+    rows = np.random.default_rng(1).choice(s.size, 80, replace=False)
+    ref = (s.S @ x)[rows]
+    assert np.abs(slab_rows(s, x, rows) - ref).max() <= 1e-13 * np.abs(ref).max()
