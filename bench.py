@@ -65,6 +65,27 @@ def dist_env():
     return rank, world, local
 
 
+def replica_seeds(rank):
+    """Forcing seeds of the problem rank `rank` solves: replicas run independent problems."""
+    return 1 + 10 * rank, 2 + 10 * rank
+
+
+def max_over_ranks(ms, world, device=None):
+    """The slowest rank's time (the job's time) via an all-reduce; identity on one rank."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def aggregate_value(world, slabs, dofs_per_slab, ms_per_step):
+    """Whole-job throughput: all ranks' space-time dofs per step over the slowest rank's time."""
+    return world * slabs * dofs_per_slab / (ms_per_step / 1e3)
+
+
 def slab_dofs(w):
     d, n, r, k = w["dim"], w["n_cells"], w["r"], w["k"]
     return (k + 1) * (d * ((r + 1) * n + 1) ** d + math.comb(r + d, d) * n ** d)
@@ -168,7 +189,8 @@ def run_ours(args):
     N = w["n_slabs"]
     # replicas: every rank solves its own problem (different forcing seeds), no data-path collective
     if forcing_kind == "fourier":
-        pb = fourier_forcing_2d(nu=w["nu"], seed_psi=1 + 10 * rank, seed_phi=2 + 10 * rank)
+        sp, sf = replica_seeds(rank)
+        pb = fourier_forcing_2d(nu=w["nu"], seed_psi=sp, seed_phi=sf)
     else:
         pb = taylor_green_3d(nu=w["nu"])
     precisions = ("fp64", "fp32") if w["dim"] == 2 else ("fp32",)
@@ -225,13 +247,9 @@ def run_ours(args):
     clk = clocks.stop()
     prof = mg.profile(reset=True)
     mg.set_profiling(0)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(ms, world, device="cuda")
     ms_step = ms / args.steps
-    value = world * N * D / (ms_step / 1e3)
+    value = aggregate_value(world, N, D, ms_step)
 
     # ---- roofline of the dominant kernel: finest-level FP32 Vanka sweep
     sweep_ms = prof["fine_sweep"]["ms"] / max(prof["fine_sweep"]["launches"], 1)
