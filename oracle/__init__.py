@@ -15,6 +15,9 @@ from the paper's definitions:
                slab coupling (Eq. AlgSysTMS), transfer operators (App. A),
                hierarchy (Alg. 2/3), Vanka smoothers (Eq. vanka0, vanka), the
                V-cycle (Alg. 1, App. B), FGMRES, time marching, error norms.
+* warmstart.py - cell tensors of slab vectors, temporal extrapolation of the DG(k)
+               polynomial, and the convolutional network of the learned initial
+               guess (forward, backward, loss, Adam); no counterpart in the paper.
 
 Everything is float64 (numpy / scipy.sparse).  Functions whose result has no pin
 independent of the oracle itself say "parity unpinned" in their docstring.

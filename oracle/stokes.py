@@ -63,6 +63,17 @@ class SlabGeometry:
         o = self.kt * self.nv
         return X[o + a * self.npr:o + (a + 1) * self.npr]
 
+    def remove_pressure_mean(self, X):
+        """Copy of X with the mean of each temporal pressure removed (means are mode-0
+        coefficients weighted equally on the uniform mesh)."""
+        Y = X.copy()
+        o = self.kt * self.nv
+        mode0 = np.arange(self.space.n_cells) * self.space.n_pm
+        for a in range(self.kt):
+            idx = o + a * self.npr + mode0
+            Y[idx] -= Y[idx].mean()
+        return Y
+
     def rhs_forcing(self, f, t0):
         """F_n of Eq. DefFn: (F_n^a)_i = Q_n(<f, phi_a chi_i>) = tau/2 w_a <f(t_n^a), chi_i>,
         spatial integral with (r+4)^d Gauss points; zero on Dirichlet dofs."""
@@ -164,17 +175,6 @@ class Slab(SlabGeometry):
         for a in range(self.kt):
             N[o + a * self.npr + mode0, a] = 1.0
         return N
-
-    def remove_pressure_mean(self, X):
-        """Copy of X with the mean of each temporal pressure removed (means are mode-0
-        coefficients weighted equally on the uniform mesh)."""
-        Y = X.copy()
-        o = self.kt * self.nv
-        mode0 = np.arange(self.space.n_cells) * self.space.n_pm
-        for a in range(self.kt):
-            idx = o + a * self.npr + mode0
-            Y[idx] -= Y[idx].mean()
-        return Y
 
     def direct_solve(self, b):
         """Bordered sparse LU solve of S x = b with zero-mean pressure per temporal dof."""
