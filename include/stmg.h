@@ -45,8 +45,9 @@
  * Slab operator (Eq. InAlg, DefDtauh, with the viscosity of Problem DVP):
  *     S = [ K_tau (x) M_h + M_tau (x) nu A_h    -M_tau (x) B_h^T ]
  *         [ -M_tau (x) B_h                       0               ]
- *   with the boundary velocity rows and columns replaced by the identity (homogeneous
- *   Dirichlet data).  The continuity rows carry a minus sign (the spatial part is
+ *   with the boundary velocity rows and columns replaced by the identity (Dirichlet
+ *   data; non-homogeneous data enter the right-hand side through stmg_dirichlet_lift).
+ *   The continuity rows carry a minus sign (the spatial part is
  *   symmetric); solutions and smoother corrections are unaffected by that choice.
  *   The pressure is determined up to one constant per temporal dof; solutions from
  *   stmg_solve_slab are returned as computed (compare them after removing the mean).
@@ -231,12 +232,21 @@ int  stmg_coarse_solve(stmg_handle* h, int prec, const void* b, void* x);
    FP64).  b, x: FP64, length D_0. */
 int  stmg_vcycle(stmg_handle* h, int prec, const double* b, double* x);
 
-/* b = F + (C_tau (x) M_h) V_prev (right-hand side of Eq. AlgSysTMS): velocity rows of
-   temporal dof a get phi_a(t_{n-1}^+) M_h v_prev, v_prev = the last temporal velocity
-   V^{k+1} of x_prev (a full previous-slab vector; its boundary entries are ignored, the
-   boundary data being homogeneous); x_prev = NULL means v_prev = 0.
+/* b = F + (C_tau (x) M_h) V_prev (right-hand side of Eq. AlgSysTMS): interior velocity
+   rows of temporal dof a get phi_a(t_{n-1}^+) M_h v_prev, v_prev = the last temporal
+   velocity V^{k+1} of x_prev (a full previous-slab vector, boundary values included: the
+   jump term couples the whole finite-element function); x_prev = NULL means v_prev = 0.
+   Boundary rows of b are copied from F.
    F: the forcing part (Eq. DefFn), FP64, length D_0; b must not alias F or x_prev. */
 int  stmg_slab_rhs(stmg_handle* h, const double* F, const double* x_prev, double* b);
+
+/* Non-homogeneous Dirichlet data: y = b - S_{.,D} g on the interior rows (S's columns of
+   the boundary velocity dofs applied to the boundary values of g; the interior entries of
+   g are not read) and y = g on the boundary rows.  Solving S x = y then gives the
+   solution with x = g on the boundary (Eq. InAlg with the boundary values moved to the
+   right-hand side).  g, b, y: device FP64, length D_0; y must not alias g or b.  Needs
+   the FP64 operator (precisions bit STMG_FP64). */
+int  stmg_dirichlet_lift(stmg_handle* h, const double* g, const double* b, double* y);
 
 /* Solve S x = b on the finest level with FGMRES (right preconditioning by one V-cycle
    in cfg.precond_precision, CGS2 orthogonalisation in FP64, no restart).  x: initial
@@ -265,6 +275,40 @@ int  stmg_slab_times(const stmg_handle* h, int slab, double* t_host);
    [a][cell][q][dim] samples of f at the points and times above.  F (device FP64,
    length D_0) is overwritten; boundary and pressure entries are 0. */
 int  stmg_assemble_forcing(stmg_handle* h, const double* fq, double* F);
+
+/* ---- cell tensors and temporal extrapolation (learned initial guess, stmg_net.h) ---- */
+
+/* Channels of a cell tensor on level lvl: C = (k+1) (d (r+2)^d + C(r+d, d)). */
+int  stmg_cells_channels(const stmg_handle* h, int lvl, int* C);
+
+/* cells[c][ch] = (float)((x - base)[map(c, ch)] * inv_scale[ch]), computed in FP64: one
+   row of C channels per cell (cells lexicographic, x fastest).  Channels: the velocity
+   values (temporal dof a, component, local node (r+2)^d with x fastest), then the
+   pressure modes (temporal dof a, mode), i.e. every slab entry that belongs to the cell;
+   a velocity node shared by several cells is copied into each.  x, base: device FP64
+   slab vectors of level lvl (base may be NULL = 0); inv_scale: device FP32 [C] (NULL =
+   1); cells: device FP32 [n^d][C]. */
+int  stmg_cells_gather(stmg_handle* h, int lvl, const double* x, const double* base, const float* inv_scale,
+                       float* cells);
+
+/* x += the average over the copies of each entry of scale[ch] * cells[c][ch] (the
+   inverse of the gather on consistent tensors), on every non-boundary entry; boundary
+   velocity entries of x are left unchanged.  Sums run in FP64 in increasing cell order.
+   scale: device FP32 [C] (NULL = 1).  x: device FP64, length D_lvl. */
+int  stmg_cells_scatter_add(stmg_handle* h, int lvl, const float* cells, const float* scale, double* x);
+
+/* x_next = the DG(k) polynomial of x_prev (Lagrange basis at the right Radau points,
+   Eq. BasYk) evaluated at the next slab's Radau points, for every velocity and pressure
+   entry: x_next^a = sum_b phi_b(s_a + 2) x_prev^b on the reference interval.  Exact for
+   data that is polynomial of degree <= k in time.  x_prev, x_next: device FP64, length
+   D_lvl, must not alias. */
+int  stmg_extrapolate(stmg_handle* h, int lvl, const double* x_prev, double* x_next);
+
+/* Remove the mean pressure of every temporal dof in place (the mode-0 coefficients of
+   all cells are shifted by their average; the uniform mesh weights cells equally).  The
+   pressure of the slab system is determined up to these constants, so b - S x is
+   unchanged.  x: device FP64, length D_lvl. */
+int  stmg_remove_pressure_mean(stmg_handle* h, int lvl, double* x);
 
 /* ---- instrumentation ------------------------------------------------------------- */
 

@@ -74,6 +74,20 @@ class SlabGeometry:
             Y[idx] -= Y[idx].mean()
         return Y
 
+    def boundary_vector(self, fn, t0):
+        """Slab vector with fn(x, t_n^a) (a tuple of dim velocity arrays) on the boundary
+        velocity dofs of every temporal dof, zero elsewhere."""
+        sp_ = self.space
+        g = np.zeros(self.size)
+        bnodes = np.nonzero(sp_.dirichlet)[0]
+        X = tuple(sp_.node_coords[bnodes, d] for d in range(self.dim))
+        for a in range(self.kt):
+            ta = t0 + self.tau / 2 * (self.time.nodes[a] + 1.0)
+            vals = fn(X, ta)
+            for comp in range(self.dim):
+                g[a * self.nv + comp * sp_.n_nodes + bnodes] = np.broadcast_to(vals[comp], bnodes.shape)
+        return g
+
     def rhs_forcing(self, f, t0):
         """F_n of Eq. DefFn: (F_n^a)_i = Q_n(<f, phi_a chi_i>) = tau/2 w_a <f(t_n^a), chi_i>,
         spatial integral with (r+4)^d Gauss points; zero on Dirichlet dofs."""
@@ -143,19 +157,29 @@ class Slab(SlabGeometry):
         self.Mv = sp_.mass()
         self.Av = sp_.laplace()
         self.B = sp_.divergence()
-        self.S = self._assemble()
+        self.S_raw = self._assemble_raw()
+        free = sp.diags((~self.dirichlet).astype(float))
+        fix = sp.diags(self.dirichlet.astype(float))
+        self.S = (free @ self.S_raw @ free + fix).tocsr()
 
-    def _assemble(self):
+    def _assemble_raw(self):
+        """S of Eq. InAlg before any boundary condition is imposed."""
         t = self.time
         Mt = sp.csr_matrix(t.M)
         vel = sp.kron(sp.csr_matrix(t.K), self.Mv) + sp.kron(Mt, self.nu * self.Av)
         vp = -sp.kron(Mt, self.B.T)
         pv = -sp.kron(Mt, self.B)
         pp = sp.csr_matrix((self.kt * self.npr, self.kt * self.npr))
-        S = sp.bmat([[vel, vp], [pv, pp]], format="csr")
-        free = sp.diags((~self.dirichlet).astype(float))
-        fix = sp.diags(self.dirichlet.astype(float))
-        return (free @ S @ free + fix).tocsr()
+        return sp.bmat([[vel, vp], [pv, pp]], format="csr")
+
+    def lift(self, g, b):
+        """Right-hand side with non-homogeneous Dirichlet values g (entries on the boundary
+        dofs): interior rows b - S_raw[:, D] g_D, boundary rows g.  The solution of S x = lift
+        then satisfies x_D = g_D and the interior rows of S_raw x = b."""
+        gd = np.where(self.dirichlet, g, 0.0)
+        y = b - self.S_raw @ gd
+        y[self.dirichlet] = g[self.dirichlet]
+        return y
 
     def coupling(self, v_prev):
         """(C_tau (x) M_h) V_{n-1} of Eq. InAlg: velocity row a gets phi_a(t_{n-1}^+) M_h v_{n-1}."""
@@ -502,7 +526,8 @@ def fgmres(apply, precond, b, x0=None, tol=1e-8, maxit=200):
 # ---------------------------------------------------------------------------
 def march(problem, n, r, k, n_slabs, cfg: MGConfig = MGConfig(), tol=1e-8, levels=None,
           solver="mg", slabs_to_run=None):
-    """Solve slab by slab: D X_n = B_n + (C_tau (x) M_h) V_{n-1}, V_0 = 0.
+    """Solve slab by slab: D X_n = B_n + (C_tau (x) M_h) V_{n-1}, V_0 = 0; with
+    problem.boundary set, its values are imposed on the boundary dofs (Slab.lift).
 
     solver = "mg": FGMRES preconditioned by one V-cycle; "direct": bordered sparse LU.
     Returns (list of slab solutions, list of SolveInfo, the finest Slab, Multigrid)."""
@@ -512,9 +537,12 @@ def march(problem, n, r, k, n_slabs, cfg: MGConfig = MGConfig(), tol=1e-8, level
     slab = mg.slabs[0] if mg else Slab(problem.dim, n, r, k, problem.nu, tau)
     v_prev = np.zeros(slab.nv)
     sols, infos = [], []
+    bnd = getattr(problem, "boundary", None)
     for s in range(slabs_to_run or n_slabs):
         t0 = s * tau
         b = slab.rhs_forcing(problem.forcing, t0) + slab.coupling(v_prev)
+        if bnd is not None:
+            b = slab.lift(slab.boundary_vector(bnd, t0), b)
         if solver == "mg":
             x, info = fgmres(lambda z: slab.S @ z, mg.vcycle, b, tol=tol)
         else:

@@ -211,6 +211,40 @@ class SpaceTimeMG:
             self._h, _ptr(F), _ptr(x_prev) if x_prev is not None else None, _ptr(b)))
         return b
 
+    def dirichlet_lift(self, g, b, out=None):
+        """y = b - S_{.,D} g on interior rows, y = g on boundary rows (non-homogeneous
+        Dirichlet data g moved to the right-hand side)."""
+        self._vec(g, 0, "g")
+        self._vec(b, 0, "b")
+        y = out if out is not None else self.empty(0)
+        self._stream()
+        check("stmg_dirichlet_lift", self._lib.stmg_dirichlet_lift(self._h, _ptr(g), _ptr(b), _ptr(y)))
+        return y
+
+    def boundary_vector(self, fn: Callable, slab: int):
+        """Slab vector (device FP64) holding fn(x, t) -> tuple of dim velocity arrays at the
+        boundary velocity nodes for the slab's Radau times t_n^a, zero elsewhere (input
+        preparation on the host: node coordinates from the Gauss-Lobatto nodes)."""
+        torch = _torch()
+        n, r, dim = self.levels[0]["n"], self.r, self.dim
+        xi = host_tables_1d(r)["xi"]
+        G = (r + 1) * n + 1
+        i = np.arange(G)
+        cell = np.minimum(i // (r + 1), n - 1)
+        coord = (cell + xi[i - cell * (r + 1)]) / n
+        idx = np.indices((G,) * dim).reshape(dim, -1)[::-1]          # x fastest
+        on_b = np.any((idx == 0) | (idx == G - 1), axis=0)
+        nodes = np.nonzero(on_b)[0]
+        X = tuple(coord[idx[d, nodes]] for d in range(dim))
+        nn = G ** dim
+        nv = dim * nn
+        out = np.zeros(self.size(0))
+        for a, t in enumerate(self.slab_times(slab)):
+            vals = fn(X, t)
+            for comp in range(dim):
+                out[a * nv + comp * nn + nodes] = np.broadcast_to(vals[comp], nodes.shape)
+        return torch.from_numpy(out).to(self.device)
+
     def solve_slab(self, b, x0=None, out=None):
         """FGMRES + V-cycle solve of S x = b; returns (x, info dict)."""
         self._vec(b, 0, "b")
@@ -239,6 +273,64 @@ class SpaceTimeMG:
             raise StmgError("stmg_solve_slab_host", st)
         return {"iterations": info.iterations, "rel_residual": info.rel_residual, "status": info.status,
                 "seconds": info.seconds}
+
+    # ---------------------------------------------------------------- cell tensors
+    def n_channels(self, lvl: int = 0) -> int:
+        c = C.c_int()
+        check("stmg_cells_channels", self._lib.stmg_cells_channels(self._h, lvl, C.byref(c)))
+        return c.value
+
+    def _f32(self, t, n, name):
+        torch = _torch()
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() \
+                or t.numel() != n:
+            raise ValueError(f"{name}: need a contiguous float32 CUDA tensor of {n} entries")
+
+    def cells_gather(self, x, base=None, inv_scale=None, out=None, lvl: int = 0):
+        """Cell tensor [n^d, C] (FP32) of (x - base) * inv_scale."""
+        torch = _torch()
+        if x.dtype != torch.float64:
+            raise ValueError("x: float64")
+        self._vec(x, lvl, "x")
+        if base is not None:
+            self._vec(base, lvl, "base")
+        Cn = self.n_channels(lvl)
+        if inv_scale is not None:
+            self._f32(inv_scale, Cn, "inv_scale")
+        ncell = self.levels[lvl]["n"] ** self.dim
+        cells = out if out is not None else torch.empty((ncell, Cn), dtype=torch.float32, device=self.device)
+        self._f32(cells, ncell * Cn, "out")
+        self._stream()
+        check("stmg_cells_gather", self._lib.stmg_cells_gather(
+            self._h, lvl, _ptr(x), _ptr(base) if base is not None else None,
+            _ptr(inv_scale) if inv_scale is not None else None, _ptr(cells)))
+        return cells
+
+    def cells_scatter_add(self, cells, x, scale=None, lvl: int = 0):
+        """x += average over copies of scale * cells (boundary entries untouched)."""
+        self._vec(x, lvl, "x")
+        Cn = self.n_channels(lvl)
+        self._f32(cells, self.levels[lvl]["n"] ** self.dim * Cn, "cells")
+        if scale is not None:
+            self._f32(scale, Cn, "scale")
+        self._stream()
+        check("stmg_cells_scatter_add", self._lib.stmg_cells_scatter_add(
+            self._h, lvl, _ptr(cells), _ptr(scale) if scale is not None else None, _ptr(x)))
+        return x
+
+    def extrapolate(self, x_prev, out=None, lvl: int = 0):
+        """The previous slab's DG(k) polynomial at the next slab's Radau points."""
+        self._vec(x_prev, lvl, "x_prev")
+        x = out if out is not None else self.empty(lvl)
+        self._stream()
+        check("stmg_extrapolate", self._lib.stmg_extrapolate(self._h, lvl, _ptr(x_prev), _ptr(x)))
+        return x
+
+    def remove_pressure_mean(self, x, lvl: int = 0):
+        self._vec(x, lvl, "x")
+        self._stream()
+        check("stmg_remove_pressure_mean", self._lib.stmg_remove_pressure_mean(self._h, lvl, _ptr(x)))
+        return x
 
     # ---------------------------------------------------------------- forcing
     def forcing_points(self):

@@ -1,4 +1,4 @@
-"""ctypes declarations of libstmg (include/stmg.h).  Argument marshalling only."""
+"""ctypes declarations of libstmg (include/stmg.h, include/stmg_net.h).  Argument marshalling only."""
 from __future__ import annotations
 
 import ctypes as C
@@ -58,6 +58,7 @@ _SIGS = {
     "stmg_coarse_solve": (_I, [_VP, _I, _VP, _VP]),
     "stmg_vcycle": (_I, [_VP, _I, _VP, _VP]),
     "stmg_slab_rhs": (_I, [_VP, _VP, _VP, _VP]),
+    "stmg_dirichlet_lift": (_I, [_VP, _VP, _VP, _VP]),
     "stmg_solve_slab": (_I, [_VP, _VP, _VP, C.POINTER(SolveInfo)]),
     "stmg_solve_slab_host": (_I, [_VP, _VP, _VP, C.POINTER(SolveInfo)]),
     "stmg_forcing_npoints": (_I, [_VP, C.POINTER(_I)]),
@@ -71,6 +72,26 @@ _SIGS = {
     "stmg_autotune": (_I, [_VP]),
     "stmg_sweep_bytes": (_I, [_VP, _I, _I, C.POINTER(_D)]),
     "stmg_status_string": (C.c_char_p, [_I]),
+    "stmg_cells_channels": (_I, [_VP, _I, C.POINTER(_I)]),
+    "stmg_cells_gather": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
+    "stmg_cells_scatter_add": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "stmg_extrapolate": (_I, [_VP, _I, _VP, _VP]),
+    "stmg_remove_pressure_mean": (_I, [_VP, _I, _VP]),
+    "stmg_net_create": (_I, [_I, _I, _I, _I, _I, _I, _I, C.c_ulonglong, C.POINTER(_VP)]),
+    "stmg_net_destroy": (None, [_VP]),
+    "stmg_net_set_stream": (_I, [_VP, _VP]),
+    "stmg_net_num_params": (_I, [_VP, C.POINTER(_LL)]),
+    "stmg_net_set_params": (_I, [_VP, _VP]),
+    "stmg_net_get_params": (_I, [_VP, _VP]),
+    "stmg_net_get_grads": (_I, [_VP, _VP]),
+    "stmg_net_forward": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "stmg_net_backward": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "stmg_net_mse": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP]),
+    "stmg_net_adam": (_I, [_VP, C.c_float, C.c_float, C.c_float, C.c_float, _I]),
+    "stmg_net_train_step": (_I, [_VP, _I, _VP, _VP, _VP, C.c_float, C.c_float, C.c_float, C.c_float, _I,
+                                 _VP]),
+    "stmg_channel_rms": (_I, [_LL, _I, _VP, _VP, _VP, _VP]),
+    "stmg_scale_channels": (_I, [_LL, _I, _VP, _VP, _VP]),
     "stmg_host_default_hierarchy": (_I, [_I, _I, _I, _I, _I, C.POINTER(_I), C.POINTER(_I)]),
     "stmg_host_tables_1d": (_I, [_I] + [C.POINTER(_D)] * 5),
     "stmg_host_time_tables": (_I, [_I, _D] + [C.POINTER(_D)] * 5),

@@ -23,8 +23,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libstmg.so")
 
-SOURCES = ["setup.cpp", "levels.cpp", "host_api.cpp",
-           "k_apply.cu", "k_vanka.cu", "k_transfer.cu", "k_vec.cu", "api.cu"]
+SOURCES = ["setup.cpp", "levels.cpp", "host_api.cpp", "net_api.cpp",
+           "k_apply.cu", "k_vanka.cu", "k_transfer.cu", "k_vec.cu", "k_cells.cu", "k_net.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -51,8 +51,9 @@ def _stamp(nv, cxx):
     for f in sorted(os.listdir(CSRC)):
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(f.encode() + fh.read())
-    with open(os.path.join(INCLUDE, "stmg.h"), "rb") as fh:
-        h.update(fh.read())
+    for f in sorted(os.listdir(INCLUDE)):
+        with open(os.path.join(INCLUDE, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
     h.update(" ".join(nv + cxx).encode())
     return h.hexdigest()
 

@@ -389,7 +389,7 @@ static int autotune_level(stmg_handle* h, int l) {
     int best_var = 1, best_ppb = lv.ppb[w];
     const int only = h->cfg.sweep_variant;             // 0: free choice, 1 / 2: fixed variant
     for (int ppb = 1; ppb <= 8 && only != 2; ppb *= 2) {
-      if (ppb * lv.H.B > 1024) break;
+      if (ppb > 1 && ppb * lv.H.B > 1024) break;
       lv.sweep_var[w] = 1;
       lv.ppb[w] = ppb;
       CKS(time_it(h, [&]() { return op_sweep<T>(h, l, P.r, P.x, h->st); }, &ms));
@@ -984,6 +984,11 @@ int stmg_vcycle(stmg_handle* h, int prec, const double* b, double* x) {
   return precondition(h, prec, b, x);
 }
 
+int stmg_dirichlet_lift(stmg_handle* h, const double* g, const double* b, double* y) {
+  if (!h || !g || !b || !y || y == g || y == b || !(h->cfg.precisions & 1)) return STMG_ERR_ARG;
+  return op_apply<double>(h, 0, g, b, y, LIFT, h->st);
+}
+
 int stmg_slab_rhs(stmg_handle* h, const double* F, const double* x_prev, double* b) {
   if (!h || !F || !b) return STMG_ERR_ARG;
   const LevelHost& H = h->L[0].H;
@@ -1100,6 +1105,56 @@ int stmg_device_status(stmg_handle* h) {
     CK(cudaMemset(h->d_err, 0, sizeof(int)));
     return STMG_ERR_TIMEOUT;
   }
+  return STMG_OK;
+}
+
+// ---- cell tensors and temporal extrapolation ---------------------------------------
+
+static CellsParams cells_params(const LevelHost& H) {
+  CellsParams p{};
+  p.dim = H.dim; p.n = H.n; p.r1 = H.r + 1; p.np = H.np; p.G = H.G; p.kt = H.kt; p.npm = H.npm;
+  p.Pn = H.dim == 2 ? H.np * H.np : H.np * H.np * H.np;
+  p.C = H.kt * (H.dim * p.Pn + H.npm);
+  p.n_nodes = H.n_nodes; p.nv = H.n_vel; p.npr = H.n_pres; p.size = H.size; p.n_cells = H.n_cells;
+  // phi_b at the next slab's Radau points: s_a + 2 on the previous slab's reference interval
+  for (int a = 0; a < H.kt; ++a)
+    for (int bb = 0; bb < H.kt; ++bb)
+      p.E[a * H.kt + bb] = lagrange_eval(H.tt.nodes, H.kt, bb, H.tt.nodes[a] + 2.0);
+  return p;
+}
+
+int stmg_cells_channels(const stmg_handle* h, int lvl, int* C) {
+  if (!h || !C || lvl < 0 || lvl >= (int)h->L.size()) return STMG_ERR_ARG;
+  *C = cells_params(h->L[lvl].H).C;
+  return STMG_OK;
+}
+
+int stmg_cells_gather(stmg_handle* h, int lvl, const double* x, const double* base, const float* inv_scale,
+                      float* cells) {
+  if (!h || !x || !cells || lvl < 0 || lvl >= (int)h->L.size()) return STMG_ERR_ARG;
+  CK(launch_cells_gather(cells_params(h->L[lvl].H), x, base, inv_scale, cells, h->st));
+  h->launches += 1;
+  return STMG_OK;
+}
+
+int stmg_cells_scatter_add(stmg_handle* h, int lvl, const float* cells, const float* scale, double* x) {
+  if (!h || !x || !cells || lvl < 0 || lvl >= (int)h->L.size()) return STMG_ERR_ARG;
+  CK(launch_cells_scatter_add(cells_params(h->L[lvl].H), cells, scale, x, h->st));
+  h->launches += 1;
+  return STMG_OK;
+}
+
+int stmg_extrapolate(stmg_handle* h, int lvl, const double* x_prev, double* x_next) {
+  if (!h || !x_prev || !x_next || x_prev == x_next || lvl < 0 || lvl >= (int)h->L.size()) return STMG_ERR_ARG;
+  CK(launch_extrapolate(cells_params(h->L[lvl].H), x_prev, x_next, h->st));
+  h->launches += 1;
+  return STMG_OK;
+}
+
+int stmg_remove_pressure_mean(stmg_handle* h, int lvl, double* x) {
+  if (!h || !x || lvl < 0 || lvl >= (int)h->L.size()) return STMG_ERR_ARG;
+  CK(launch_remove_pressure_mean(cells_params(h->L[lvl].H), x, h->st));
+  h->launches += 1;
   return STMG_OK;
 }
 

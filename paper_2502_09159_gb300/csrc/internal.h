@@ -90,10 +90,16 @@ struct MassParams {
   double phi_left[MAXKT];
 };
 
+struct CellsParams {              // level geometry for the cell-tensor maps
+  int dim, n, r1, np, G, kt, npm, C, Pn;   // r1 = r + 1, Pn = np^dim nodes per cell
+  long long n_nodes, nv, npr, size, n_cells;
+  double E[MAXKT * MAXKT];        // [a * kt + b] = phi_b(s_a + 2): temporal extrapolation
+};
+
 // ------------------------------------------------------------------------------------
 // launchers (return cudaError_t of the launch); all asynchronous on `st`
 // ------------------------------------------------------------------------------------
-enum ApplyMode { APPLY = 0, RESIDUAL = 1 };
+enum ApplyMode { APPLY = 0, RESIDUAL = 1, LIFT = 2 };
 
 template <typename T>
 cudaError_t launch_apply(int dim, int np, const ApplyParams<T>& p, const T* x, const T* b, T* y,
@@ -147,5 +153,13 @@ cudaError_t launch_scale_by_inverse(long long n, const double* dev_scalar, const
 cudaError_t launch_sqrt_inplace(double* v, cudaStream_t st);
 
 int multidot_blocks(long long n);
+
+// cell tensors (k_cells.cu)
+cudaError_t launch_cells_gather(const CellsParams& p, const double* x, const double* base, const float* inv_scale,
+                                float* cells, cudaStream_t st);
+cudaError_t launch_cells_scatter_add(const CellsParams& p, const float* cells, const float* scale, double* x,
+                                     cudaStream_t st);
+cudaError_t launch_extrapolate(const CellsParams& p, const double* xp, double* xn, cudaStream_t st);
+cudaError_t launch_remove_pressure_mean(const CellsParams& p, double* x, cudaStream_t st);
 
 }  // namespace stmg

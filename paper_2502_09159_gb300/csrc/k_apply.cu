@@ -11,7 +11,9 @@
 //   * scatter-adds the velocity rows (atomics; cells share nodes) and stores the
 //     cell-local pressure rows.
 // Boundary rows are the identity: the owner cell of each boundary node adds +x (apply)
-// or b - x (residual).  On axis-aligned uniform cells every element operator is a sum
+// or b - x (residual).  The LIFT mode moves non-homogeneous boundary data to the right-
+// hand side: y = b - S_{.,D} g on the interior rows (only the boundary values of g are
+// read) and y = g on the boundary rows.  On axis-aligned uniform cells every element operator is a sum
 // of Kronecker products of the 1D matrices M1 = int ell ell, K1 = int ell' ell',
 // G1 = int L ell', N1 = int L ell on [0,1]; the kernel applies those factors directly.
 #include <cuda_runtime.h>
@@ -82,12 +84,15 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams<T> P, const T* 
       if (DIM == 3) dir = dir || gz == 0 || gz == G - 1;
       const long long g = gx + (long long)G * (gy + (long long)G * gz);
       const int node = ix + NP * (iy + NP * iz);
-      U[cl * VS + (a * DIM + comp) * NQ + node] = dir ? T(0) : x[a * nvel + comp * nnod + g];
+      // LIFT reads only the boundary values (the columns S_{.,D}); the other modes only
+      // the interior ones (boundary columns are identity columns)
+      const bool take = mode == LIFT ? dir : !dir;
+      U[cl * VS + (a * DIM + comp) * NQ + node] = take ? x[a * nvel + comp * nnod + g] : T(0);
     }
     const int totp = nc * kt * npm;
     for (int w = threadIdx.x; w < totp; w += blockDim.x) {
       const int m = w % npm, t = w / npm, a = t % kt, cl = t / kt;
-      PIN[(cl * kt + a) * npm + m] = x[poff + a * P.n_pres + (long long)(c0 + cl) * npm + m];
+      PIN[(cl * kt + a) * npm + m] = mode == LIFT ? T(0) : x[poff + a * P.n_pres + (long long)(c0 + cl) * npm + m];
     }
   }
   __syncthreads();
@@ -262,7 +267,7 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams<T> P, const T* 
   // ---- scatter -----------------------------------------------------------------------
   {
     const int tot = nc * VS;
-    const bool res = mode == RESIDUAL;
+    const bool res = mode != APPLY;
     for (int w = threadIdx.x; w < tot; w += blockDim.x) {
       int t = w;
       const int ix = t % NP; t /= NP;
@@ -288,8 +293,8 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams<T> P, const T* 
         add = res ? -v : v;
       }
       if (own) {
-        if (res) add += b[gi];
-        if (dir) add += res ? -x[gi] : x[gi];
+        if (dir) add += mode == LIFT ? x[gi] : (res ? b[gi] - x[gi] : x[gi]);
+        else if (res) add += b[gi];
       } else if (dir) {
         continue;
       }
@@ -366,9 +371,8 @@ __global__ void k_mass_coupling(const MassParams P, const double* __restrict__ v
     const int node = w % nq, comp = w / nq;
     const int ix = node % np, iy = (node / np) % np, iz = dim == 3 ? node / (np * np) : 0;
     const int gx = cc[0] * (np - 1) + ix, gy = cc[1] * (np - 1) + iy, gz = cc[2] * (np - 1) + iz;
-    bool dir = gx == 0 || gx == G - 1 || gy == 0 || gy == G - 1 || (dim == 3 && (gz == 0 || gz == G - 1));
     const long long g = gx + (long long)G * (gy + (long long)G * gz);
-    U[w] = dir ? 0.0 : v[comp * P.n_nodes + g];
+    U[w] = v[comp * P.n_nodes + g];              // boundary values included (Eq. InAlg: full M_h)
   }
   __syncthreads();
   // W = h^d (M1 (x) M1 (x) M1) U, direct tensor contraction (small, setup-like cost)

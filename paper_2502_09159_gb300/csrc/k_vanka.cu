@@ -69,36 +69,40 @@ __global__ void __launch_bounds__(1024) k_vanka_sweep(const int* __restrict__ do
     rs[t] = v;
   }
   __syncthreads();
-  const int pl = threadIdx.x / B, j = threadIdx.x % B;
-  const long long p = p0 + pl;
-  if (pl >= ppb || p >= n_patches) return;
   const int nch = Bc / VW;
-  const V* A = reinterpret_cast<const V*>(inv + (size_t)p * B * Bc) + j;
-  const T* r = rs + pl * Bc;
-  T acc0 = 0, acc1 = 0;
   const bool st = streaming != 0;
-  int c = 0;
-  for (; c + 8 <= nch; c += 8) {
-    V a[8];
+  // one row per thread; blocks of fewer threads than ppb * B rows (B > 1024) loop
+  for (int t = threadIdx.x; t < ppb * B; t += blockDim.x) {
+    const int pl = t / B, j = t % B;
+    const long long p = p0 + pl;
+    if (p >= n_patches) break;
+    const V* A = reinterpret_cast<const V*>(inv + (size_t)p * B * Bc) + j;
+    const T* r = rs + pl * Bc;
+    T acc0 = 0, acc1 = 0;
+    int c = 0;
+    for (; c + 8 <= nch; c += 8) {
+      V a[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) a[u] = load_vec(A + (size_t)(c + u) * B, st);
+      for (int u = 0; u < 8; ++u) a[u] = load_vec(A + (size_t)(c + u) * B, st);
 #pragma unroll
-    for (int u = 0; u < 8; u += 2) {
-      acc0 += dotv(a[u], r + (c + u) * VW);
-      acc1 += dotv(a[u + 1], r + (c + u + 1) * VW);
+      for (int u = 0; u < 8; u += 2) {
+        acc0 += dotv(a[u], r + (c + u) * VW);
+        acc1 += dotv(a[u + 1], r + (c + u + 1) * VW);
+      }
     }
+    for (; c < nch; ++c) acc0 += dotv(load_vec(A + (size_t)c * B, st), r + c * VW);
+    const int g = dofs[p * B + j];
+    if (g >= 0) atomicAdd(x + g, acc0 + acc1);   // rows carry omega / valence
   }
-  for (; c < nch; ++c) acc0 += dotv(load_vec(A + (size_t)c * B, st), r + c * VW);
-  const int g = dofs[p * B + j];
-  if (g >= 0) atomicAdd(x + g, acc0 + acc1);   // rows carry omega / valence
 }
 
 template <typename T>
 cudaError_t launch_vanka_sweep(const int* dofs, const T* inv, const T* res, T* x, long long n_patches, int B,
                                int Bc, int ppb, int streaming, cudaStream_t st) {
   if (ppb * B > 1024) ppb = 1024 / B;
-  if (ppb < 1) return cudaErrorInvalidValue;
-  const int threads = ((ppb * B + 31) / 32) * 32;
+  if (ppb < 1) ppb = 1;
+  if (B < 1) return cudaErrorInvalidValue;
+  const int threads = ppb * B > 1024 ? 1024 : ((ppb * B + 31) / 32) * 32;
   const long long blocks = (n_patches + ppb - 1) / ppb;
   const size_t smem = sizeof(T) * (size_t)ppb * Bc;
   if (smem > 48 * 1024) {

@@ -44,8 +44,11 @@ CASES = [
     (2, 5, 1, 1, [(5, 1, 1)]),                      # single level, odd n
     (3, 2, 1, 1, None),
     (3, 2, 2, 1, None),
+    (3, 2, 3, 2, None),                             # 3D Q4/P3, DG(2)
+    (3, 2, 4, 1, None),                             # 3D Q5/P4: largest spatial degree
 ]
-IDS = ["2d-n4-r1k1", "2d-n3-r2k2", "2d-n4-r3k0", "2d-n2-r4k3", "2d-n5-single", "3d-n2-r1k1", "3d-n2-r2k1"]
+IDS = ["2d-n4-r1k1", "2d-n3-r2k2", "2d-n4-r3k0", "2d-n2-r4k3", "2d-n5-single", "3d-n2-r1k1", "3d-n2-r2k1",
+       "3d-n2-r3k2", "3d-n2-r4k1"]
 
 _cache = {}
 
@@ -221,8 +224,9 @@ def test_forcing_and_slab_rhs():
     b = g.slab_rhs(F, dev(x_prev))
     ref = Fo + slab.coupling(slab.vel(x_prev, slab.kt - 1))
     assert rel(b, ref) < 1e-12
-    x_bad = random_vector(slab.size, 47)                # boundary entries of x_prev are ignored
-    assert rel(g.slab_rhs(F, dev(x_bad)), ref) < 1e-12
+    x_any = random_vector(slab.size, 47)                # boundary values enter the jump term too
+    ref_any = Fo + slab.coupling(slab.vel(x_any, slab.kt - 1))
+    assert rel(g.slab_rhs(F, dev(x_any)), ref_any) < 1e-12
     assert torch.equal(g.slab_rhs(F), F)                # no previous slab: b is F itself
 
 
