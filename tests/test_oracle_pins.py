@@ -16,7 +16,7 @@ from oracle.fe import (SpaceFE, TimeFE, gauss_legendre, gauss_lobatto, legendre_
 from oracle.stokes import (MGConfig, Multigrid, Slab, cell_patches, default_hierarchy, errors,
                            fgmres, march, slab_prolongation, vanka_patch_entries,
                            vertex_star_patches)
-from workloads import manufactured_2d, polynomial_2d, taylor_green_3d
+from workloads import lid_driven_3d, manufactured_2d, polynomial_2d, polynomial_boundary, taylor_green_3d
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -265,6 +265,39 @@ def test_exact_reproduction_polynomial_solution():
     sols, _, slab, _ = march(pb, 2, 3, 1, 3, solver="direct")
     e = errors(pb, slab, sols)
     assert e["v_L2L2"] < 1e-11 and e["v_L2H1"] < 1e-10 and e["p_L2L2"] < 1e-10
+
+
+@pytest.mark.parametrize("dim,n,r,k", [(2, 2, 1, 1), (2, 3, 2, 2), (3, 2, 1, 1)])
+def test_exact_reproduction_with_boundary_data(dim, n, r, k):
+    """Non-homogeneous Dirichlet data: v = t (y^2, x^2[, ...]) (Q2, nonzero on the boundary),
+    p = t (x - 1/2) (P1) are reproduced exactly over three slabs, which needs the boundary
+    values on the boundary rows, their columns moved to the right-hand side, and the
+    previous slab's boundary values in the jump term."""
+    pb = polynomial_boundary(dim, nu=0.6)
+    sols, _, slab, _ = march(pb, n, r, k, 3, solver="direct")
+    e = errors(pb, slab, sols)
+    assert e["v_L2L2"] < 1e-11 and e["v_L2H1"] < 1e-10 and e["p_L2L2"] < 1e-10
+    assert np.abs(sols[-1][slab.dirichlet] - slab.boundary_vector(pb.boundary, 2 * slab.tau)[slab.dirichlet]).max() \
+        < 1e-13
+
+
+def test_lift_leaves_homogeneous_problems_unchanged_and_is_linear():
+    slab = Slab(2, 3, 1, 1, 1.0, 0.1)
+    b = np.where(slab.dirichlet, 0.0, np.arange(slab.size, dtype=float))
+    assert np.array_equal(slab.lift(np.zeros(slab.size), b), b)
+    g1, g2 = np.sin(np.arange(slab.size)), np.cos(np.arange(slab.size))
+    z = np.zeros(slab.size)
+    lin = slab.lift(g1 + 2 * g2, z) - slab.lift(g1, z) - 2 * slab.lift(g2, z)
+    assert np.abs(lin).max() < 1e-12
+
+
+def test_lid_boundary_data():
+    """The lid moves with sin(pi t / 4) in x on z = 1 and nowhere else."""
+    pb = lid_driven_3d()
+    X = (np.array([0.3, 0.3, 0.0]), np.array([0.6, 0.6, 0.5]), np.array([1.0, 0.0, 1.0]))
+    u, v, w = pb.boundary(X, 2.0)
+    assert np.allclose(u, [1.0, 0.0, 1.0]) and np.all(v == 0) and np.all(w == 0)
+    assert np.allclose(pb.boundary(X, 8.0)[0], 0.0, atol=1e-15)
 
 
 def test_table1_errors_golden():

@@ -62,6 +62,7 @@ class Problem:
     pressure: Callable | None    # p(x, t) -> array
     velocity_grad: Callable | None = None  # grad v(x,t) -> [dim][dim] arrays, [i][j] = d_j v_i
     name: str = ""
+    boundary: Callable | None = None       # Dirichlet velocity data g(x, t) on the boundary (None: 0)
 
 
 def _time_factor(kind: str):
@@ -233,6 +234,56 @@ def polynomial_2d(m: int = 1, nu: float = 1.0, T: float = 1.0) -> Problem:
     return Problem(2, nu, T, forcing, velocity, pressure, velocity_grad, f"polynomial_2d[m={m}]")
 
 
+def polynomial_boundary(dim: int = 2, nu: float = 1.0, T: float = 1.0) -> Problem:
+    """Divergence-free quadratic velocity that does not vanish on the boundary, for checks
+    of non-homogeneous Dirichlet data: v = t (y^2, x^2) in 2D, v = t (y^2, z^2, x^2) in 3D
+    (each component independent of its own coordinate), p = t (x - 1/2).  v lies in Q_2 and
+    p in P_1, both linear in t: reproduced exactly by Q_{r+1}/P_r, DG(k) for r, k >= 1."""
+    def velocity(x, t):
+        if dim == 2:
+            X, Y = x
+            return (t * Y ** 2, t * X ** 2)
+        X, Y, Z = x
+        return (t * Y ** 2, t * Z ** 2, t * X ** 2)
+
+    def velocity_grad(x, t):
+        zero = np.zeros(np.broadcast(*x).shape)
+        if dim == 2:
+            X, Y = x
+            return [[zero, 2 * t * Y + zero], [2 * t * X + zero, zero]]
+        X, Y, Z = x
+        return [[zero, 2 * t * Y + zero, zero], [zero, zero, 2 * t * Z + zero], [2 * t * X + zero, zero, zero]]
+
+    def pressure(x, t):
+        return t * (x[0] - 0.5)
+
+    def forcing(x, t):
+        # d_t v - nu Lap v + grad p: Lap of each quadratic component is 2 t
+        v = velocity(x, 1.0)
+        out = [vi - 2.0 * nu * t for vi in v]
+        out[0] = out[0] + t
+        return tuple(out)
+
+    return Problem(dim, nu, T, forcing, velocity, pressure, velocity_grad, f"polynomial_boundary_{dim}d",
+                   boundary=velocity)
+
+
+def lid_driven_3d(nu: float = 1.0, T: float = 8.0) -> Problem:
+    """Lid-driven cavity of Sec. 5.3: no forcing, no-slip walls, and on the lid z = 1 the
+    velocity sin(pi t / 4) in the x direction (the paper gives the profile as a scalar; the
+    x component is this reading), imposed on every node of the closed lid face."""
+    def zero(x, t):
+        z = np.zeros(np.broadcast(*x).shape)
+        return (z, z.copy(), z.copy())
+
+    def boundary(x, t):
+        X, Y, Z = x
+        lid = np.isclose(Z, 1.0).astype(float)
+        return (math.sin(PI * t / 4.0) * lid, 0.0 * lid, 0.0 * lid)
+
+    return Problem(3, nu, T, zero, None, None, None, "lid_driven_3d", boundary=boundary)
+
+
 def random_vector(n: int, seed: int = 3, dtype=np.float64) -> np.ndarray:
     """Seeded U[-1, 1] vector of length n (numpy PCG64)."""
     rng = np.random.default_rng(seed)
@@ -241,4 +292,5 @@ def random_vector(n: int, seed: int = 3, dtype=np.float64) -> np.ndarray:
 
 def problem_by_name(name: str, **kw) -> Problem:
     return {"manufactured_2d": manufactured_2d, "taylor_green_3d": taylor_green_3d,
-            "fourier_2d": fourier_forcing_2d, "polynomial_2d": polynomial_2d}[name](**kw)
+            "fourier_2d": fourier_forcing_2d, "polynomial_2d": polynomial_2d,
+            "polynomial_boundary": polynomial_boundary, "lid_driven_3d": lid_driven_3d}[name](**kw)
