@@ -35,7 +35,13 @@ WORKLOADS = {
            "2D 64x64 Q3/P2disc DG(2), 16 slabs, Fourier forcing (seeds 1,2), cell Vanka", "fourier"),
     "c3": (dict(dim=3, n_cells=32, r=2, k=1, nu=1e-2, T=1.0, n_slabs=8),
            "3D 32^3 Q3/P2disc DG(1), 8 slabs, Taylor-Green-like field, nu = 1e-2, cell Vanka", "taylor_green"),
+    "lid": (dict(dim=3, n_cells=16, r=2, k=2, nu=1.0, T=8.0, n_slabs=256),
+            "3D lid-driven cavity (Sec. 5.3, c = 4): 16^3 Q3/P2disc DG(2), 256 slabs on [0, 8], lid velocity "
+            "sin(pi t / 4) in x on z = 1, no-slip walls, nu = 1, cell Vanka, n_sm = 1", "lid"),
 }
+WORKLOADS_KIND = {name: kind for _, name, kind in WORKLOADS.values()}
+# the paper's throughput on the same workload (Table 3, c = 4, r = 2, n_sm = 1; 13,824 CPU ranks)
+PAPER_THETA = {"lid": 302520576 / 149.4}
 WORKLOAD, WORKLOAD_NAME, _ = WORKLOADS["c2"]
 METRIC = "space-time DoFs/s (apply, Vanka sweep, V-cycle); time-to-1e-8 mixed vs FP64"
 
@@ -54,7 +60,8 @@ def parse():
     p.add_argument("--k-min", type=int, default=0, help="lowest temporal degree of the hierarchy; 0: k in 2D, 1 in 3D")
     p.add_argument("--levels", default="", help="explicit level list n:r:k,... fine -> coarse")
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
-                   help="c2: the 2D headline configuration; c3: the 3D 32^3 configuration")
+                   help="c2: the 2D headline configuration; c3: the 3D 32^3 configuration; "
+                        "lid: the lid-driven cavity at c = 4")
     return p.parse_args()
 
 
@@ -168,7 +175,7 @@ def run_ours(args):
     import torch
 
     import paper_2502_09159_gb300 as stmg
-    from workloads import fourier_forcing_2d, taylor_green_3d
+    from workloads import fourier_forcing_2d, lid_driven_3d, taylor_green_3d
     global WORKLOAD, WORKLOAD_NAME
     WORKLOAD, WORKLOAD_NAME, forcing_kind = WORKLOADS[args.workload]
     if args.coarse_n == 0:
@@ -191,6 +198,8 @@ def run_ours(args):
     if forcing_kind == "fourier":
         sp, sf = replica_seeds(rank)
         pb = fourier_forcing_2d(nu=w["nu"], seed_psi=sp, seed_phi=sf)
+    elif forcing_kind == "lid":
+        pb = lid_driven_3d(nu=w["nu"], T=w["T"])
     else:
         pb = taylor_green_3d(nu=w["nu"])
     precisions = ("fp64", "fp32") if w["dim"] == 2 else ("fp32",)
@@ -203,16 +212,31 @@ def run_ours(args):
                                 gmres_max_iter=200 if w["dim"] == 2 else 80)
 
     mg = make("fp32")
-    pts = mg.forcing_points()
-    F = [mg.forcing(pb.forcing, s, pts) for s in range(N)]        # resident inputs
+    # resident per-slab inputs: the assembled forcing, or for the lid-driven cavity (no
+    # forcing) the slab's boundary values
+    if forcing_kind == "lid":
+        F0 = mg.zeros()
+        F = [mg.boundary_vector(pb.boundary, s) for s in range(N)]
+    else:
+        F0 = None
+        pts = mg.forcing_points()
+        F = [mg.forcing(pb.forcing, s, pts) for s in range(N)]
     x_bufs = [mg.zeros() for _ in range(N)]
     b_buf = mg.empty()
+    b_tmp = mg.empty()
     launches0 = mg.kernel_launches
+
+    def build_b(g, inp, x_prev):
+        if F0 is None:
+            g.slab_rhs(inp, x_prev, out=b_buf)
+        else:
+            g.slab_rhs(F0, x_prev, out=b_tmp)
+            g.dirichlet_lift(inp, b_tmp, out=b_buf)
 
     def step(g, iters):
         x_prev = None
         for s in range(N):
-            g.slab_rhs(F[s], x_prev, out=b_buf)
+            build_b(g, F[s], x_prev)
             x_bufs[s].zero_()
             _, info = g.solve_slab(b_buf, out=x_bufs[s])
             if info["status"] != 0:
@@ -265,7 +289,7 @@ def run_ours(args):
     # ---- end to end through the public API: pinned host F in, host solution out, every slab
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(mg, F, x_bufs, b_buf, N, D, world, args, barrier)
+        e2e = run_e2e(mg, F, x_bufs, b_buf, N, D, world, args, barrier, build_b)
 
     # ---- per-kernel rates and FP64 vs mixed time-to-1e-8 (not part of the timed step)
     extra = {}
@@ -273,9 +297,14 @@ def run_ours(args):
         extra = micro(mg, make, F, N, D, step)
         extra["time_split"] = time_split(mg, step)
         extra["paper_hierarchy"] = paper_rule(make, step, N, D)
+        if args.workload == "c2":
+            mg.close()
+            torch.cuda.empty_cache()
+            extra["warm_start"] = warm_start_bench()
     line = {"metric": METRIC, "value": value, "unit": "space-time DoFs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 FGMRES + f32 V-cycle", "data": "synthetic",
+            "vs_baseline": (value / PAPER_THETA[args.workload]) if args.workload in PAPER_THETA else None,
+            "dtype": "f64 FGMRES + f32 V-cycle", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "dofs_per_slab": D, "slabs_per_step": N,
                        "levels": [(l["n"], l["r"], l["k"]) for l in mg.levels],
                        "precond": "fp32", "rel_tol": 1e-8, "parallelism": f"replicas x{world}",
@@ -295,7 +324,89 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(mg, F, x_bufs, b_buf, N, D, world, args, barrier):
+def warm_start_bench():
+    """The learned initial guess on its workload: 2D 128^2 Q3/P2disc DG(1), 256 slabs on
+    [0, 1], Fourier forcing (seeds 4, 5) whose phases drift by 0.05 * 2 pi per unit time.
+    Slabs 0-127 are solved from the extrapolated guess; pairs of slabs 16-127 (after the
+    start-up transient) train the network on the initial-residual ratio; slabs 128-255 are
+    then marched three times, from the zero, the extrapolated and the learned guess, each
+    timed with CUDA events including the guess itself."""
+    import numpy as np
+    import torch
+
+    import paper_2502_09159_gb300 as stmg
+    from paper_2502_09159_gb300.warmstart import WarmStart
+    from workloads import fourier_forcing_2d
+    n, N = 128, 256
+    pb = fourier_forcing_2d(nu=1.0, seed_psi=4, seed_phi=5, drift=0.05 * 2 * math.pi)
+    g = stmg.SpaceTimeMG(dim=2, n_cells=n, r=2, k=1, nu=1.0, T=1.0, n_slabs=N, precond_precision="fp32",
+                         coarse_n=8, k_min=1)
+    D = g.size(0)
+    pts = g.forcing_points()
+    F = [g.forcing(pb.forcing, s, pts) for s in range(N)]
+    ws = WarmStart(g, hidden=64, layers=4, capacity=N // 2, seed=1)
+    b = g.empty()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    x_prev = g.zeros()
+    for s in range(N // 2):
+        g.slab_rhs(F[s], x_prev if s else None, out=b)
+        x, info = g.solve_slab(b, ws.guess(x_prev, "extrapolate") if s else None)
+        g.remove_pressure_mean(x)
+        if s >= 16:
+            ws.add_pair(x_prev, x)
+        x_prev = x
+    e1.record()
+    torch.cuda.synchronize()
+    collect_ms = e0.elapsed_time(e1)
+    start = x_prev
+    e0.record()
+    losses = ws.fit_residual(steps=800, batch=4, lr=1e-4, warmup=100)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    ratio = ws.residual_ratio()
+    modes = {}
+    guess_buf = g.empty()
+    for m in WarmStart.MODES:
+        its = []
+        xp = start
+        sols = [g.empty() for _ in range(2)]
+        torch.cuda.synchronize()
+        e0.record()
+        for s in range(N // 2, N):
+            g.slab_rhs(F[s], xp, out=b)
+            ws.guess(xp, m, out=guess_buf)
+            x = sols[s % 2]
+            x.copy_(guess_buf)
+            _, info = g.solve_slab(b, out=x)
+            if info["status"] != 0:
+                raise RuntimeError(f"warm start {m}: slab {s}: {info}")
+            its.append(info["iterations"])
+            xp = x
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        modes[m] = {"ms_per_slab": round(ms / (N // 2), 3), "mean_iterations": round(statistics.mean(its), 3),
+                    "theta_dofs_per_s": (N // 2) * D / (ms / 1e3)}
+    # the guess alone (gather, network, scatter, extrapolation) per slab
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(20):
+        ws.guess(start, "net", out=guess_buf)
+    e1.record()
+    torch.cuda.synchronize()
+    out = {"workload": "2D 128x128 Q3/P2disc DG(1), 256 slabs, drifting Fourier forcing (seeds 4, 5); "
+                       "train on slabs 16-127, evaluate on 128-255",
+           "dofs_per_slab": D, "network": "4 conv3x3 layers, 64 channels, linear 3x3 bypass, FP32",
+           "train_pairs": ws.count, "collect_ms": round(collect_ms, 1), "train_ms": round(train_ms, 1),
+           "train_steps": len(losses), "residual_ratio_sq_train": round(ratio, 4),
+           "net_guess_ms": round(e0.elapsed_time(e1) / 20, 3), "modes": modes}
+    g.close()
+    return out
+
+
+def run_e2e(mg, F, x_bufs, b_buf, N, D, world, args, barrier, build_b):
     import torch
     Fh = [f.cpu().pin_memory() for f in F]
     Xh = [torch.empty(D, dtype=torch.float64).pin_memory() for _ in range(N)]
@@ -305,7 +416,7 @@ def run_e2e(mg, F, x_bufs, b_buf, N, D, world, args, barrier):
         x_prev = None
         for s in range(N):
             Fd.copy_(Fh[s], non_blocking=True)
-            mg.slab_rhs(Fd, x_prev, out=b_buf)
+            build_b(mg, Fd, x_prev)
             x_bufs[s].zero_()
             mg.solve_slab(b_buf, out=x_bufs[s])
             Xh[s].copy_(x_bufs[s], non_blocking=True)
@@ -423,9 +534,11 @@ _ORACLE_SNIPPET = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
 from oracle.stokes import MGConfig, march, Multigrid, default_hierarchy, fgmres
-from workloads import fourier_forcing_2d, taylor_green_3d
+from workloads import fourier_forcing_2d, lid_driven_3d, taylor_green_3d
 w = {w!r}
-pb = fourier_forcing_2d(nu=w["nu"]) if w["dim"] == 2 else taylor_green_3d(nu=w["nu"])
+kind = {kind!r}
+pb = (fourier_forcing_2d(nu=w["nu"]) if kind == "fourier" else
+      lid_driven_3d(nu=w["nu"], T=w["T"]) if kind == "lid" else taylor_green_3d(nu=w["nu"]))
 tau = w["T"] / w["n_slabs"]
 t0 = time.time()
 mg = Multigrid(w["dim"], default_hierarchy(w["n_cells"], w["r"], w["k"], {coarse_n}, {k_min}), w["nu"], tau,
@@ -433,6 +546,8 @@ mg = Multigrid(w["dim"], default_hierarchy(w["n_cells"], w["r"], w["k"], {coarse
 t_setup = time.time() - t0
 slab = mg.slabs[0]
 b = slab.rhs_forcing(pb.forcing, 0.0)
+if pb.boundary is not None:
+    b = slab.lift(slab.boundary_vector(pb.boundary, 0.0), b)
 times = []
 for rep in range({reps}):
     t0 = time.time()
@@ -454,7 +569,9 @@ def oracle_workload():
 def oracle_sample(reps, coarse_n=8, k_min=2):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     w = oracle_workload()
-    code = _ORACLE_SNIPPET.format(root=ROOT, w=w, reps=reps, coarse_n=min(coarse_n, w["n_cells"]), k_min=k_min)
+    kind = WORKLOADS_KIND.get(WORKLOAD_NAME, "fourier")
+    code = _ORACLE_SNIPPET.format(root=ROOT, w=w, kind=kind, reps=reps, coarse_n=min(coarse_n, w["n_cells"]),
+                                  k_min=k_min)
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if p.returncode != 0:
         raise RuntimeError(p.stderr[-2000:])
@@ -487,8 +604,10 @@ def run_reference(args):
     times = r["solve_s"][args.warmup:]
     t = sum(times) / len(times)
     value = r["D"] / t
-    sample = (f"per step: slab 1 of 16 of the same workload solved by the FP64 oracle (FGMRES + V-cycle "
-              f"to 1e-8, {r['iterations']} iterations); setup {r['setup_s']:.1f} s not timed")
+    ow = oracle_workload()
+    sample = (f"per step: slab 1 of {WORKLOAD['n_slabs']} of the same workload on {ow['n_cells']}^{ow['dim']} cells "
+              f"solved by the FP64 oracle (FGMRES + V-cycle to 1e-8, {r['iterations']} iterations); "
+              f"setup {r['setup_s']:.1f} s not timed")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "space-time DoFs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -185,6 +185,12 @@ int  stmg_level_info(const stmg_handle* h, int lvl, stmg_level_info_t* info);
    x, y: length D_lvl, precision prec; must not alias. */
 int  stmg_apply(stmg_handle* h, int lvl, int prec, const void* x, void* y);
 
+/* y = S_lvl^T x.  M_h, A_h and M_tau are symmetric and the two B blocks of Eq. InAlg are
+   each other's transposes, so S^T is S with K_tau transposed; the boundary identity rows
+   and columns are unchanged.  For adjoint (gradient) computations, e.g. training the
+   learned initial guess on the residual norm.  x, y must not alias. */
+int  stmg_apply_transpose(stmg_handle* h, int lvl, int prec, const void* x, void* y);
+
 /* r = b - S_lvl x (App. B, step 1 of Alg. 4/5).  r must not alias b or x. */
 int  stmg_residual(stmg_handle* h, int lvl, int prec, const void* b, const void* x, void* r);
 
@@ -296,6 +302,16 @@ int  stmg_cells_gather(stmg_handle* h, int lvl, const double* x, const double* b
    velocity entries of x are left unchanged.  Sums run in FP64 in increasing cell order.
    scale: device FP32 [C] (NULL = 1).  x: device FP64, length D_lvl. */
 int  stmg_cells_scatter_add(stmg_handle* h, int lvl, const float* cells, const float* scale, double* x);
+
+/* The adjoint of stmg_cells_scatter_add: every copy of a non-boundary velocity dof g
+   receives scale[ch] x[g] / (number of cells holding g); copies of boundary dofs get 0;
+   pressure modes get scale[ch] x[g].  Computed in FP64, rounded to FP32.  x: device FP64
+   slab vector of level lvl; scale: device FP32 [C] (NULL = 1); cells: device FP32 [n^d][C]. */
+int  stmg_cells_gather_adjoint(stmg_handle* h, int lvl, const double* x, const float* scale, float* cells);
+
+/* out[0] = sum_i x_i y_i over n FP64 entries (device pointers), deterministic (fixed-order
+   per-block partial sums); asynchronous on the handle's stream. */
+int  stmg_dot(stmg_handle* h, long long n, const double* x, const double* y, double* out);
 
 /* x_next = the DG(k) polynomial of x_prev (Lagrange basis at the right Radau points,
    Eq. BasYk) evaluated at the next slab's Radau points, for every velocity and pressure

@@ -20,10 +20,15 @@
  * c_in -> hidden -> ... -> hidden -> c_out, a bias per output channel and ReLU after every
  * layer except the last:
  *     y[b, i, j, o] = bias[o] + sum_{ky, kx, c} W[o, ky, kx, c] x[b, i + ky - 1, j + kx - 1, c]
+ * With skip != 0 a linear bypass, one more 3x3 convolution (c_in -> c_out, no bias), maps
+ * the input straight to the output and is added to the last layer's result: the hidden
+ * layers are narrower than the cell tensors, and the bypass carries the part of the map
+ * that is linear.
  * Parameters: one flat FP32 vector, layer after layer, each layer W[o][ky][kx][c] followed
- * by bias[o]; stmg_net_num_params gives its length.  Initialisation: He-uniform weights
- * (bound sqrt(6 / (9 c))) from a seeded splitmix64 stream, zero biases, and a zero last
- * layer so that a fresh network returns 0 (the guess is then the extrapolation).
+ * by bias[o], then the bypass W[o][ky][kx][c]; stmg_net_num_params gives its length.
+ * Initialisation: He-uniform weights (bound sqrt(6 / (9 c))) from a seeded splitmix64
+ * stream, zero biases, and a zero last layer and bypass so that a fresh network returns 0
+ * (the guess is then the extrapolation).
  * Loss: mean of (pred - target)^2 over all elements.  Optimiser: Adam (Kingma and Ba, 2015)
  * with bias correction.  All reductions run in a fixed order: results are deterministic.
  *
@@ -47,7 +52,7 @@ typedef struct stmg_net stmg_net;
 
 /* Create a network for H x W grids.  1 <= n_layers <= 16, channels in 1..1024,
    max_batch >= 1.  STMG_ERR_ARG on bad sizes, STMG_ERR_OOM if memory runs out. */
-int  stmg_net_create(int H, int W, int c_in, int hidden, int c_out, int n_layers, int max_batch,
+int  stmg_net_create(int H, int W, int c_in, int hidden, int c_out, int n_layers, int skip, int max_batch,
                      unsigned long long seed, stmg_net** out);
 void stmg_net_destroy(stmg_net* net);
 int  stmg_net_set_stream(stmg_net* net, void* cuda_stream);
@@ -88,6 +93,10 @@ int  stmg_net_train_step(stmg_net* net, int batch, const float* inputs, const fl
 /* Per-channel statistics of data[rows][C] (FP32): rms[c] = sqrt(mean_rows data^2) and
    inv_rms[c] = 1 / rms[c] (0 where rms[c] is 0).  Either output may be NULL. */
 int  stmg_channel_rms(long long rows, int C, const float* data, float* rms, float* inv_rms, void* cuda_stream);
+
+/* Root mean square of all n entries of data (FP32) and its inverse (0 if the RMS is 0),
+   written to rms[0] / inv_rms[0] (device; either may be NULL). */
+int  stmg_tensor_rms(long long n, const float* data, float* rms, float* inv_rms, void* cuda_stream);
 
 /* data[rows][C] *= s[c] in place. */
 int  stmg_scale_channels(long long rows, int C, float* data, const float* s, void* cuda_stream);

@@ -18,16 +18,19 @@ checked element by element.  Definitions:
   interval the next slab's node s_a lies at s_a + 2.
 * Network: L convolutions of size 3x3 with zero padding on the H x W grid of cells,
   channels c_in -> hidden -> ... -> hidden -> c_out, bias, ReLU after every layer except
-  the last.  Tensors are NHWC; weights W[o, ky, kx, c], then the bias; layer after layer
-  in one flat parameter vector.
+  the last; optionally a linear bypass, one more 3x3 convolution (no bias) from the input
+  straight to the output, added to the last layer's result.  Tensors are NHWC; weights
+  W[o, ky, kx, c], then the bias; layer after layer in one flat parameter vector, the
+  bypass weights last.
       y[b, i, j, o] = bias[o] + sum_{ky, kx, c} W[o, ky, kx, c] x[b, i + ky - 1, j + kx - 1, c]
 * Loss: the mean of (pred - target)^2 over all elements.
 * Adam (Kingma and Ba, 2015) with bias correction.
 
 Pins (tests/test_oracle_warmstart.py): the convolution against scipy.signal.correlate2d,
 the backward pass and the loss gradient against central finite differences, Adam's first
-step against its closed form, scatter(gather(x)) = x, the extrapolation matrix of DG(1)
-against the hand-derived values and exactness on polynomials of degree <= k.
+step against its closed form, scatter(gather(x)) = x, the adjoint identity
+<scatter(c), x> = <c, adjoint(x)>, the extrapolation matrix of DG(1) against the
+hand-derived values and exactness on polynomials of degree <= k.
 """
 from __future__ import annotations
 
@@ -89,6 +92,18 @@ def cells_scatter_add(geo, cells, x, scale=None):
     return out
 
 
+def cells_gather_adjoint(geo, x, scale=None):
+    """The adjoint of cells_scatter_add (x -> cells): each copy of a non-Dirichlet entry g
+    receives scale[ch] x[g] / (number of copies of g); copies of Dirichlet entries get 0."""
+    idx = cell_index_map(geo)
+    cnt = np.bincount(idx.ravel(), minlength=geo.size).astype(float)
+    w = np.where(geo.dirichlet, 0.0, x / cnt)
+    v = w[idx]
+    if scale is not None:
+        v = v * np.asarray(scale, dtype=np.float64)[None, :]
+    return v
+
+
 def channel_rms(data):
     """Root mean square of every channel (last axis) over all other axes."""
     d = np.asarray(data, dtype=np.float64)
@@ -121,12 +136,13 @@ def layer_shapes(c_in, hidden, c_out, n_layers):
     return [(chans[l + 1], chans[l]) for l in range(n_layers)]
 
 
-def n_params(c_in, hidden, c_out, n_layers):
-    return sum(o * 9 * c + o for o, c in layer_shapes(c_in, hidden, c_out, n_layers))
+def n_params(c_in, hidden, c_out, n_layers, skip=False):
+    return sum(o * 9 * c + o for o, c in layer_shapes(c_in, hidden, c_out, n_layers)) + \
+        (c_out * 9 * c_in if skip else 0)
 
 
-def unpack(theta, c_in, hidden, c_out, n_layers):
-    """Flat parameter vector -> [(W[o, 3, 3, c], bias[o])] per layer."""
+def unpack(theta, c_in, hidden, c_out, n_layers, skip=False):
+    """Flat parameter vector -> ([(W[o, 3, 3, c], bias[o])] per layer, bypass W or None)."""
     out, p = [], 0
     for o, c in layer_shapes(c_in, hidden, c_out, n_layers):
         W = theta[p:p + o * 9 * c].reshape(o, 3, 3, c)
@@ -134,8 +150,12 @@ def unpack(theta, c_in, hidden, c_out, n_layers):
         b = theta[p:p + o]
         p += o
         out.append((W, b))
+    Ws = None
+    if skip:
+        Ws = theta[p:p + c_out * 9 * c_in].reshape(c_out, 3, 3, c_in)
+        p += c_out * 9 * c_in
     assert p == len(theta)
-    return out
+    return out, Ws
 
 
 def conv3x3(x, W, b):
@@ -170,9 +190,9 @@ def conv3x3_grad_weights(x, g):
     return dW, g.sum(axis=(0, 1, 2))
 
 
-def forward(theta, x, c_in, hidden, c_out, n_layers):
+def forward(theta, x, c_in, hidden, c_out, n_layers, skip=False):
     """Network output and the input of every layer (for the backward pass)."""
-    layers = unpack(theta, c_in, hidden, c_out, n_layers)
+    layers, Ws = unpack(theta, c_in, hidden, c_out, n_layers, skip)
     acts = [x]
     h = x
     for l, (W, b) in enumerate(layers):
@@ -180,12 +200,14 @@ def forward(theta, x, c_in, hidden, c_out, n_layers):
         if l < n_layers - 1:
             h = np.maximum(h, 0.0)
             acts.append(h)
+    if skip:
+        h = h + conv3x3(x, Ws, np.zeros(c_out))
     return h, acts
 
 
-def backward(theta, acts, g_out, c_in, hidden, c_out, n_layers):
+def backward(theta, acts, g_out, c_in, hidden, c_out, n_layers, skip=False):
     """Gradient of sum(g_out * network(x)) with respect to the flat parameters."""
-    layers = unpack(theta, c_in, hidden, c_out, n_layers)
+    layers, _ = unpack(theta, c_in, hidden, c_out, n_layers, skip)
     grads = [None] * n_layers
     g = g_out
     for l in range(n_layers - 1, -1, -1):
@@ -193,7 +215,10 @@ def backward(theta, acts, g_out, c_in, hidden, c_out, n_layers):
         grads[l] = conv3x3_grad_weights(acts[l], g)
         if l > 0:
             g = conv3x3_grad_input(g, W) * (acts[l] > 0.0)
-    return np.concatenate([np.concatenate([dW.ravel(), db]) for dW, db in grads])
+    flat = [np.concatenate([dW.ravel(), db]) for dW, db in grads]
+    if skip:
+        flat.append(conv3x3_grad_weights(acts[0], g_out)[0].ravel())
+    return np.concatenate(flat)
 
 
 def mse(pred, target):

@@ -142,6 +142,14 @@ class SpaceTimeMG:
         check("stmg_apply", self._lib.stmg_apply(self._h, lvl, p, _ptr(x), _ptr(y)))
         return y
 
+    def apply_transpose(self, x, lvl: int = 0, out=None):
+        """y = S_lvl^T x (matrix-free)."""
+        p = self._vec(x, lvl, "x")
+        y = out if out is not None else self.empty(lvl, x.dtype)
+        self._stream()
+        check("stmg_apply_transpose", self._lib.stmg_apply_transpose(self._h, lvl, p, _ptr(x), _ptr(y)))
+        return y
+
     def residual(self, b, x, lvl: int = 0, out=None):
         """r = b - S_lvl x."""
         p = self._vec(x, lvl, "x")
@@ -317,6 +325,33 @@ class SpaceTimeMG:
         check("stmg_cells_scatter_add", self._lib.stmg_cells_scatter_add(
             self._h, lvl, _ptr(cells), _ptr(scale) if scale is not None else None, _ptr(x)))
         return x
+
+    def cells_gather_adjoint(self, x, scale=None, out=None, lvl: int = 0):
+        """Adjoint of cells_scatter_add: copies of x divided by their multiplicity."""
+        torch = _torch()
+        if x.dtype != torch.float64:
+            raise ValueError("x: float64")
+        self._vec(x, lvl, "x")
+        Cn = self.n_channels(lvl)
+        if scale is not None:
+            self._f32(scale, Cn, "scale")
+        ncell = self.levels[lvl]["n"] ** self.dim
+        cells = out if out is not None else torch.empty((ncell, Cn), dtype=torch.float32, device=self.device)
+        self._f32(cells, ncell * Cn, "out")
+        self._stream()
+        check("stmg_cells_gather_adjoint", self._lib.stmg_cells_gather_adjoint(
+            self._h, lvl, _ptr(x), _ptr(scale) if scale is not None else None, _ptr(cells)))
+        return cells
+
+    def dot(self, x, y, out=None):
+        """Deterministic FP64 dot product into a 1-element device tensor."""
+        torch = _torch()
+        if x.dtype != torch.float64 or y.dtype != torch.float64 or x.numel() != y.numel():
+            raise ValueError("dot: two float64 tensors of one length")
+        o = out if out is not None else torch.empty(1, dtype=torch.float64, device=self.device)
+        self._stream()
+        check("stmg_dot", self._lib.stmg_dot(self._h, x.numel(), _ptr(x), _ptr(y), _ptr(o)))
+        return o
 
     def extrapolate(self, x_prev, out=None, lvl: int = 0):
         """The previous slab's DG(k) polynomial at the next slab's Radau points."""

@@ -50,6 +50,7 @@ _SIGS = {
     "stmg_level_info": (_I, [_VP, _I, C.POINTER(LevelInfo)]),
     "stmg_apply": (_I, [_VP, _I, _I, _VP, _VP]),
     "stmg_residual": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
+    "stmg_apply_transpose": (_I, [_VP, _I, _I, _VP, _VP]),
     "stmg_smooth": (_I, [_VP, _I, _I, _VP, _VP, _I]),
     "stmg_smooth_noalloc": (_I, [_VP, _I, _I, _VP, _VP, _I]),
     "stmg_vanka_sweep": (_I, [_VP, _I, _I, _VP, _VP]),
@@ -75,9 +76,11 @@ _SIGS = {
     "stmg_cells_channels": (_I, [_VP, _I, C.POINTER(_I)]),
     "stmg_cells_gather": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "stmg_cells_scatter_add": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "stmg_cells_gather_adjoint": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "stmg_dot": (_I, [_VP, _LL, _VP, _VP, _VP]),
     "stmg_extrapolate": (_I, [_VP, _I, _VP, _VP]),
     "stmg_remove_pressure_mean": (_I, [_VP, _I, _VP]),
-    "stmg_net_create": (_I, [_I, _I, _I, _I, _I, _I, _I, C.c_ulonglong, C.POINTER(_VP)]),
+    "stmg_net_create": (_I, [_I, _I, _I, _I, _I, _I, _I, _I, C.c_ulonglong, C.POINTER(_VP)]),
     "stmg_net_destroy": (None, [_VP]),
     "stmg_net_set_stream": (_I, [_VP, _VP]),
     "stmg_net_num_params": (_I, [_VP, C.POINTER(_LL)]),
@@ -91,6 +94,7 @@ _SIGS = {
     "stmg_net_train_step": (_I, [_VP, _I, _VP, _VP, _VP, C.c_float, C.c_float, C.c_float, C.c_float, _I,
                                  _VP]),
     "stmg_channel_rms": (_I, [_LL, _I, _VP, _VP, _VP, _VP]),
+    "stmg_tensor_rms": (_I, [_LL, _VP, _VP, _VP, _VP]),
     "stmg_scale_channels": (_I, [_LL, _I, _VP, _VP, _VP]),
     "stmg_host_default_hierarchy": (_I, [_I, _I, _I, _I, _I, C.POINTER(_I), C.POINTER(_I)]),
     "stmg_host_tables_1d": (_I, [_I] + [C.POINTER(_D)] * 5),

@@ -60,6 +60,7 @@ struct stmg_handle {
   double *bnorm = nullptr, *xhost_b = nullptr, *xhost_x = nullptr;
   int m_alloc = 0;
   int* d_err = nullptr;           // device flag raised by bounded waits that expired
+  double* dot_part = nullptr;     // per-block partial sums of stmg_dot (allocated on first use)
   int n_sm = 1;
   ForcingParams fp{};
   MassParams mp{};
@@ -884,7 +885,7 @@ void stmg_destroy(stmg_handle* h) {
   for (auto& L : h->L) free_level(L);
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(h->V); f(h->Z); f(h->w); f(h->hcol); f(h->tmp); f(h->partial); f(h->bnorm);
-  f(h->xhost_b); f(h->xhost_x); f(h->d_err);
+  f(h->xhost_b); f(h->xhost_x); f(h->d_err); f(h->dot_part);
   for (auto e : h->all_events) cudaEventDestroy(e);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -939,6 +940,12 @@ int stmg_apply(stmg_handle* h, int lvl, int prec, const void* x, void* y) {
   if (!prec_ok(h, lvl, prec) || !x || !y) return STMG_ERR_ARG;
   if (prec == STMG_FP64) return op_apply<double>(h, lvl, (const double*)x, nullptr, (double*)y, APPLY, h->st);
   return op_apply<float>(h, lvl, (const float*)x, nullptr, (float*)y, APPLY, h->st);
+}
+
+int stmg_apply_transpose(stmg_handle* h, int lvl, int prec, const void* x, void* y) {
+  if (!prec_ok(h, lvl, prec) || !x || !y || x == y) return STMG_ERR_ARG;
+  if (prec == STMG_FP64) return op_apply<double>(h, lvl, (const double*)x, nullptr, (double*)y, APPLY_T, h->st);
+  return op_apply<float>(h, lvl, (const float*)x, nullptr, (float*)y, APPLY_T, h->st);
 }
 
 int stmg_residual(stmg_handle* h, int lvl, int prec, const void* b, const void* x, void* r) {
@@ -1141,6 +1148,21 @@ int stmg_cells_scatter_add(stmg_handle* h, int lvl, const float* cells, const fl
   if (!h || !x || !cells || lvl < 0 || lvl >= (int)h->L.size()) return STMG_ERR_ARG;
   CK(launch_cells_scatter_add(cells_params(h->L[lvl].H), cells, scale, x, h->st));
   h->launches += 1;
+  return STMG_OK;
+}
+
+int stmg_cells_gather_adjoint(stmg_handle* h, int lvl, const double* x, const float* scale, float* cells) {
+  if (!h || !x || !cells || lvl < 0 || lvl >= (int)h->L.size()) return STMG_ERR_ARG;
+  CK(launch_cells_gather_adjoint(cells_params(h->L[lvl].H), x, scale, cells, h->st));
+  h->launches += 1;
+  return STMG_OK;
+}
+
+int stmg_dot(stmg_handle* h, long long n, const double* x, const double* y, double* out) {
+  if (!h || !x || !y || !out || n < 1) return STMG_ERR_ARG;
+  if (!h->dot_part) CKS(dalloc(&h->dot_part, (size_t)dot_blocks()));
+  CK(launch_dot(n, x, y, h->dot_part, out, h->st));
+  h->launches += 2;
   return STMG_OK;
 }
 

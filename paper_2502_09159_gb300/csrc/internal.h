@@ -99,7 +99,7 @@ struct CellsParams {              // level geometry for the cell-tensor maps
 // ------------------------------------------------------------------------------------
 // launchers (return cudaError_t of the launch); all asynchronous on `st`
 // ------------------------------------------------------------------------------------
-enum ApplyMode { APPLY = 0, RESIDUAL = 1, LIFT = 2 };
+enum ApplyMode { APPLY = 0, RESIDUAL = 1, LIFT = 2, APPLY_T = 3 };
 
 template <typename T>
 cudaError_t launch_apply(int dim, int np, const ApplyParams<T>& p, const T* x, const T* b, T* y,
@@ -159,7 +159,13 @@ cudaError_t launch_cells_gather(const CellsParams& p, const double* x, const dou
                                 float* cells, cudaStream_t st);
 cudaError_t launch_cells_scatter_add(const CellsParams& p, const float* cells, const float* scale, double* x,
                                      cudaStream_t st);
+cudaError_t launch_cells_gather_adjoint(const CellsParams& p, const double* x, const float* scale, float* cells,
+                                        cudaStream_t st);
 cudaError_t launch_extrapolate(const CellsParams& p, const double* xp, double* xn, cudaStream_t st);
+// out[0] = sum x_i y_i (deterministic: per-block partials, then a fixed-order sum); partial:
+// scratch of at least dot_blocks() doubles
+cudaError_t launch_dot(long long n, const double* x, const double* y, double* partial, double* out, cudaStream_t st);
+int dot_blocks();
 cudaError_t launch_remove_pressure_mean(const CellsParams& p, double* x, cudaStream_t st);
 
 }  // namespace stmg

@@ -13,7 +13,9 @@
 // Boundary rows are the identity: the owner cell of each boundary node adds +x (apply)
 // or b - x (residual).  The LIFT mode moves non-homogeneous boundary data to the right-
 // hand side: y = b - S_{.,D} g on the interior rows (only the boundary values of g are
-// read) and y = g on the boundary rows.  On axis-aligned uniform cells every element operator is a sum
+// read) and y = g on the boundary rows.  APPLY_T applies S^T: M_h, A_h and M_tau are
+// symmetric and the two B blocks are each other's transposes, so S^T is S with the
+// temporal matrix K_tau transposed.  On axis-aligned uniform cells every element operator is a sum
 // of Kronecker products of the 1D matrices M1 = int ell ell, K1 = int ell' ell',
 // G1 = int L ell', N1 = int L ell on [0,1]; the kernel applies those factors directly.
 #include <cuda_runtime.h>
@@ -106,7 +108,8 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams<T> P, const T* 
       const int a = t % kt, cl = t / kt;
       const T* u = U + cl * VS + node_comp;
       T s = 0;
-      for (int bb = 0; bb < kt; ++bb) s += P.Kt[a * MAXKT + bb] * u[bb * DIM * NQ];
+      const bool tr = mode == APPLY_T;         // S^T: the temporal matrix transposed
+      for (int bb = 0; bb < kt; ++bb) s += P.Kt[tr ? bb * MAXKT + a : a * MAXKT + bb] * u[bb * DIM * NQ];
       UT[cl * VS + a * DIM * NQ + node_comp] = s;
     }
     const int totp = nc * kt * npm;
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams<T> P, const T* 
   // ---- scatter -----------------------------------------------------------------------
   {
     const int tot = nc * VS;
-    const bool res = mode != APPLY;
+    const bool res = mode == RESIDUAL || mode == LIFT;
     for (int w = threadIdx.x; w < tot; w += blockDim.x) {
       int t = w;
       const int ix = t % NP; t /= NP;

@@ -112,6 +112,83 @@ cudaError_t launch_cells_scatter_add(const CellsParams& p, const float* cells, c
   return cudaGetLastError();
 }
 
+// Adjoint of the averaging scatter: every copy of a velocity dof g receives
+// scale[ch] x[g] / (number of copies of g); boundary dofs give 0 (the scatter leaves them).
+__global__ void k_cells_gather_adjoint(CellsParams p, const double* __restrict__ x, const float* __restrict__ scale,
+                                       float* __restrict__ cells) {
+  const long long total = p.n_cells * p.C;
+  const int nvch = p.kt * p.dim * p.Pn;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / p.C;
+    const int ch = (int)(e - c * p.C);
+    double v;
+    if (ch < nvch) {
+      const int a = ch / (p.dim * p.Pn);
+      const int rem = ch - a * p.dim * p.Pn;
+      const int comp = rem / p.Pn, node = rem - comp * p.Pn;
+      const int lx = node % p.np, ly = (node / p.np) % p.np, lz = node / (p.np * p.np);
+      const long long cx = c % p.n, cy = (c / p.n) % p.n, cz = c / ((long long)p.n * p.n);
+      const long long gx = cx * p.r1 + lx, gy = cy * p.r1 + ly, gz = cz * p.r1 + lz;
+      const long long last = p.G - 1;
+      const bool dir = gx == 0 || gx == last || gy == 0 || gy == last || (p.dim == 3 && (gz == 0 || gz == last));
+      // copies along one direction: 2 on an interior cell boundary, else 1
+      auto copies = [&](long long gi, int li) { return (li == 0 || li == p.np - 1) && gi > 0 && gi < last ? 2 : 1; };
+      int cnt = copies(gx, lx) * copies(gy, ly);
+      if (p.dim == 3) cnt *= copies(gz, lz);
+      const long long gi = p.dim == 2 ? gx + p.G * gy : gx + p.G * (gy + p.G * gz);
+      v = dir ? 0.0 : x[a * p.nv + comp * p.n_nodes + gi] / (double)cnt;
+    } else {
+      const int j = ch - nvch;
+      const int a = j / p.npm, m = j - a * p.npm;
+      v = x[p.kt * p.nv + a * p.npr + c * p.npm + m];
+    }
+    if (scale) v *= (double)scale[ch];
+    cells[e] = (float)v;
+  }
+}
+
+cudaError_t launch_cells_gather_adjoint(const CellsParams& p, const double* x, const float* scale, float* cells,
+                                        cudaStream_t st) {
+  k_cells_gather_adjoint<<<grid_of(p.n_cells * p.C, 256), 256, 0, st>>>(p, x, scale, cells);
+  return cudaGetLastError();
+}
+
+constexpr int DOT_BLOCKS = 304;
+
+__global__ void __launch_bounds__(256) k_dot(long long n, const double* __restrict__ x, const double* __restrict__ y,
+                                             double* __restrict__ partial) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += x[i] * y[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_dot_finish(const double* __restrict__ partial, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < DOT_BLOCKS; ++i) s += partial[i];
+    out[0] = s;
+  }
+}
+
+int dot_blocks() { return DOT_BLOCKS; }
+
+cudaError_t launch_dot(long long n, const double* x, const double* y, double* partial, double* out, cudaStream_t st) {
+  k_dot<<<DOT_BLOCKS, 256, 0, st>>>(n, x, y, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_dot_finish<<<1, 32, 0, st>>>(partial, out);
+  return cudaGetLastError();
+}
+
 __global__ void k_extrapolate(CellsParams p, const double* __restrict__ xp, double* __restrict__ xn) {
   const long long tot = p.nv + p.npr;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;

@@ -30,7 +30,7 @@ template <int TN>
 __global__ void __launch_bounds__(CT) k_conv3x3(const float* __restrict__ in, const int* __restrict__ index,
                                                 const float* __restrict__ Wm, const float* __restrict__ bias,
                                                 const float* __restrict__ mask, float* __restrict__ out, int B,
-                                                int H, int W, int Cin, int Cout, int relu) {
+                                                int H, int W, int Cin, int Cout, int relu, int accumulate) {
   constexpr int BN = 16 * TN;
   __shared__ __align__(16) float As[2][BK][BM + 4];
   __shared__ float Bs[2][BK][BN + 1];
@@ -133,24 +133,26 @@ __global__ void __launch_bounds__(CT) k_conv3x3(const float* __restrict__ in, co
       float v = acc[i][j] + (bias ? bias[o] : 0.f);
       if (relu) v = fmaxf(v, 0.f);
       if (mask && !(mask[m * Cout + o] > 0.f)) v = 0.f;
+      if (accumulate) v += out[m * Cout + o];
       out[m * Cout + o] = v;
     }
   }
 }
 
 cudaError_t launch_conv3x3(const float* in, const int* index, const float* Wm, const float* bias, const float* mask,
-                           float* out, int B, int H, int W, int Cin, int Cout, int relu, cudaStream_t st) {
+                           float* out, int B, int H, int W, int Cin, int Cout, int relu, int accumulate,
+                           cudaStream_t st) {
   const long long M = (long long)B * H * W;
   const unsigned gx = (unsigned)((M + BM - 1) / BM);
   if (Cout <= 32) {
-    k_conv3x3<2><<<dim3(gx, 1), CT, 0, st>>>(in, index, Wm, bias, mask, out, B, H, W, Cin, Cout, relu);
+    k_conv3x3<2><<<dim3(gx, 1), CT, 0, st>>>(in, index, Wm, bias, mask, out, B, H, W, Cin, Cout, relu, accumulate);
   } else if (Cout <= 64) {
-    k_conv3x3<4><<<dim3(gx, 1), CT, 0, st>>>(in, index, Wm, bias, mask, out, B, H, W, Cin, Cout, relu);
+    k_conv3x3<4><<<dim3(gx, 1), CT, 0, st>>>(in, index, Wm, bias, mask, out, B, H, W, Cin, Cout, relu, accumulate);
   } else if (Cout <= 80) {
-    k_conv3x3<5><<<dim3(gx, 1), CT, 0, st>>>(in, index, Wm, bias, mask, out, B, H, W, Cin, Cout, relu);
+    k_conv3x3<5><<<dim3(gx, 1), CT, 0, st>>>(in, index, Wm, bias, mask, out, B, H, W, Cin, Cout, relu, accumulate);
   } else {
     k_conv3x3<4><<<dim3(gx, (unsigned)((Cout + 63) / 64)), CT, 0, st>>>(in, index, Wm, bias, mask, out, B, H, W,
-                                                                         Cin, Cout, relu);
+                                                                         Cin, Cout, relu, accumulate);
   }
   return cudaGetLastError();
 }
@@ -292,7 +294,7 @@ cudaError_t launch_conv3x3_grads(const float* in, const int* index, const float*
   const long long nW = (long long)Cout * K;
   k_sum_rows<<<(unsigned)((nW + 255) / 256), 256, 0, st>>>((int)splits, nW, part, dW);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || !db) return e;
   // bias: pixel blocks of 512, partial sums reduced in order
   long long nb = (M + 511) / 512;
   if (nb * Cout > part_cap) nb = part_cap / Cout;
@@ -401,6 +403,33 @@ __global__ void __launch_bounds__(1024) k_channel_rms(long long rows, int C, con
 
 cudaError_t launch_channel_rms(long long rows, int C, const float* data, float* rms, float* inv, cudaStream_t st) {
   k_channel_rms<<<(C + 31) / 32, 1024, 0, st>>>(rows, C, data, rms, inv);
+  return cudaGetLastError();
+}
+
+// rms = sqrt(mean data^2) over the whole tensor: one block, fixed-order tree
+__global__ void __launch_bounds__(1024) k_tensor_rms(long long n, const float* __restrict__ data,
+                                                     float* __restrict__ rms, float* __restrict__ inv) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = (double)data[i];
+    s += v * v;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 512; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double q = n > 0 ? sqrt(red[0] / (double)n) : 0.0;
+    if (rms) rms[0] = (float)q;
+    if (inv) inv[0] = q > 0.0 ? (float)(1.0 / q) : 0.f;
+  }
+}
+
+cudaError_t launch_tensor_rms(long long n, const float* data, float* rms, float* inv, cudaStream_t st) {
+  k_tensor_rms<<<1, 1024, 0, st>>>(n, data, rms, inv);
   return cudaGetLastError();
 }
 

@@ -13,9 +13,10 @@
 using namespace stmg;
 
 struct stmg_net {
-  int H = 0, W = 0, cin = 0, hid = 0, cout = 0, L = 0, maxb = 0;
+  int H = 0, W = 0, cin = 0, hid = 0, cout = 0, L = 0, maxb = 0, skip = 0;
   std::vector<int> ci, co;                  // channels in / out per layer
   std::vector<long long> woff, boff;        // offsets of W and bias in the flat vector
+  long long soff = 0;                       // offset of the bypass weights (skip != 0)
   long long np = 0;
   float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
   float* wt = nullptr;                      // flipped, transposed weights of one layer
@@ -58,7 +59,7 @@ uint64_t splitmix64(uint64_t* s) {
 int init_params(stmg_net* n, uint64_t seed) {
   std::vector<float> h((size_t)n->np, 0.f);
   uint64_t s = seed;
-  for (int l = 0; l + 1 < n->L; ++l) {       // last layer stays zero: a fresh network returns 0
+  for (int l = 0; l + 1 < n->L; ++l) {       // last layer and bypass stay zero: a fresh network returns 0
     const double bound = std::sqrt(6.0 / (9.0 * n->ci[l]));
     const long long cnt = (long long)n->co[l] * 9 * n->ci[l];
     for (long long i = 0; i < cnt; ++i) {
@@ -80,14 +81,20 @@ int forward(stmg_net* n, int batch, const float* in, const int* index, float* ou
     const float* x = layer_in(n, l, in);
     float* y = l + 1 == n->L ? out : n->acts[l + 1];
     NCK(launch_conv3x3(x, l == 0 ? index : nullptr, n->params + n->woff[l], n->params + n->boff[l], nullptr, y,
-                       batch, n->H, n->W, n->ci[l], n->co[l], l + 1 < n->L, n->st));
+                       batch, n->H, n->W, n->ci[l], n->co[l], l + 1 < n->L, 0, n->st));
   }
+  if (n->skip)   // linear bypass from the input, added to the output
+    NCK(launch_conv3x3(in, index, n->params + n->soff, nullptr, nullptr, out, batch, n->H, n->W, n->cin, n->cout, 0,
+                       1, n->st));
   return STMG_OK;
 }
 
 int backward(stmg_net* n, int batch, const float* in, const int* index, const float* gout) {
   const float* G = gout;
   int cur = 0;
+  if (n->skip)
+    NCK(launch_conv3x3_grads(in, index, gout, n->grads + n->soff, nullptr, batch, n->H, n->W, n->cin, n->cout,
+                             n->part, n->part_cap, n->st));
   for (int l = n->L - 1; l >= 0; --l) {
     const float* x = layer_in(n, l, in);
     NCK(launch_conv3x3_grads(x, l == 0 ? index : nullptr, G, n->grads + n->woff[l], n->grads + n->boff[l], batch,
@@ -96,7 +103,7 @@ int backward(stmg_net* n, int batch, const float* in, const int* index, const fl
       // input gradient, masked by the ReLU that produced this layer's input
       NCK(launch_flip_transpose(n->params + n->woff[l], n->wt, n->ci[l], n->co[l], n->st));
       NCK(launch_conv3x3(G, nullptr, n->wt, nullptr, n->acts[l], n->g[cur], batch, n->H, n->W, n->co[l], n->ci[l], 0,
-                         n->st));
+                         0, n->st));
       G = n->g[cur];
       cur ^= 1;
     }
@@ -110,7 +117,7 @@ bool ok_batch(const stmg_net* n, int batch) { return n && batch >= 1 && batch <=
 
 extern "C" {
 
-int stmg_net_create(int H, int W, int c_in, int hidden, int c_out, int n_layers, int max_batch,
+int stmg_net_create(int H, int W, int c_in, int hidden, int c_out, int n_layers, int skip, int max_batch,
                     unsigned long long seed, stmg_net** out) {
   if (!out) return STMG_ERR_ARG;
   *out = nullptr;
@@ -119,6 +126,7 @@ int stmg_net_create(int H, int W, int c_in, int hidden, int c_out, int n_layers,
     return STMG_ERR_ARG;
   stmg_net* n = new stmg_net();
   n->H = H; n->W = W; n->cin = c_in; n->hid = hidden; n->cout = c_out; n->L = n_layers; n->maxb = max_batch;
+  n->skip = skip ? 1 : 0;
   int maxc = 0, maxk = 0;
   for (int l = 0; l < n_layers; ++l) {
     const int a = l == 0 ? c_in : hidden, b = l + 1 == n_layers ? c_out : hidden;
@@ -130,6 +138,11 @@ int stmg_net_create(int H, int W, int c_in, int hidden, int c_out, int n_layers,
     n->np += b;
     maxc = std::max(maxc, std::max(a, b));
     maxk = std::max(maxk, b * 9 * a);
+  }
+  if (n->skip) {
+    n->soff = n->np;
+    n->np += (long long)c_out * 9 * c_in;
+    maxk = std::max(maxk, c_out * 9 * c_in);
   }
   const long long pix = (long long)max_batch * H * W;
   n->part_cap = std::max((long long)64 * maxk, ((pix + 511) / 512) * (long long)maxc);
@@ -239,6 +252,12 @@ int stmg_net_train_step(stmg_net* n, int batch, const float* inputs, const float
 int stmg_channel_rms(long long rows, int C, const float* data, float* rms, float* inv_rms, void* stream) {
   if (rows < 1 || C < 1 || !data) return STMG_ERR_ARG;
   NCK(launch_channel_rms(rows, C, data, rms, inv_rms, (cudaStream_t)stream));
+  return STMG_OK;
+}
+
+int stmg_tensor_rms(long long n, const float* data, float* rms, float* inv_rms, void* stream) {
+  if (n < 1 || !data) return STMG_ERR_ARG;
+  NCK(launch_tensor_rms(n, data, rms, inv_rms, (cudaStream_t)stream));
   return STMG_OK;
 }
 

@@ -83,6 +83,8 @@ def test_apply_and_residual(case):
         assert rel(g.apply(dev(x), l), ref) < 1e-12
         assert rel(g.residual(dev(b), dev(x), l), b - ref) < 1e-12
         assert rel(g.apply(dev(x, torch.float32), l).double(), ref) < 2e-6
+        assert rel(g.apply_transpose(dev(x), l), s.S.T @ x) < 1e-12
+        assert rel(g.apply_transpose(dev(x, torch.float32), l).double(), s.S.T @ x) < 2e-6
 
 
 @pytest.mark.parametrize("case", CASES, ids=IDS)

@@ -10,12 +10,6 @@ from oracle.stokes import SlabGeometry
 from workloads import random_vector
 
 
-def small_net(seed=0, c_in=3, hidden=5, c_out=2, L=4):
-    rng = np.random.default_rng(seed)
-    theta = rng.standard_normal(ws.n_params(c_in, hidden, c_out, L)) * 0.4
-    return theta, (c_in, hidden, c_out, L)
-
-
 def test_conv_matches_library_correlation():
     rng = np.random.default_rng(1)
     x = rng.standard_normal((2, 5, 7, 3))
@@ -41,18 +35,20 @@ def test_conv_adjoint_identity():
     assert np.allclose(db, g.sum(axis=(0, 1, 2)))
 
 
-def test_backward_matches_finite_differences():
-    theta, dims = small_net()
+@pytest.mark.parametrize("skip", [False, True])
+def test_backward_matches_finite_differences(skip):
     rng = np.random.default_rng(3)
+    dims = (3, 5, 2, 4)
+    theta = rng.standard_normal(ws.n_params(*dims, skip=skip)) * 0.4
     x = rng.standard_normal((2, 4, 5, dims[0]))
     tgt = rng.standard_normal((2, 4, 5, dims[2]))
 
     def loss(th):
-        return ws.mse(ws.forward(th, x, *dims)[0], tgt)[0]
+        return ws.mse(ws.forward(th, x, *dims, skip=skip)[0], tgt)[0]
 
-    pred, acts = ws.forward(theta, x, *dims)
+    pred, acts = ws.forward(theta, x, *dims, skip=skip)
     _, g = ws.mse(pred, tgt)
-    grad = ws.backward(theta, acts, g, *dims)
+    grad = ws.backward(theta, acts, g, *dims, skip=skip)
     h = 1e-6
     for i in rng.choice(len(theta), 60, replace=False):
         e = np.zeros_like(theta)
@@ -142,6 +138,18 @@ def test_extrapolate_slab_vector_linear_in_time():
     assert np.allclose(ws.extrapolate(geo, slab(0.0)), slab(2.0), atol=1e-13)
 
 
+def test_bypass_is_a_linear_convolution_added_to_the_output():
+    """With every layer's weights and biases zero the network is its bypass alone."""
+    rng = np.random.default_rng(11)
+    dims = (3, 4, 2, 3)
+    n_layers_params = ws.n_params(*dims)
+    theta = np.zeros(ws.n_params(*dims, skip=True))
+    Ws = rng.standard_normal((2, 3, 3, 3))
+    theta[n_layers_params:] = Ws.ravel()
+    x = rng.standard_normal((1, 4, 4, 3))
+    assert np.allclose(ws.forward(theta, x, *dims, skip=True)[0], ws.conv3x3(x, Ws, np.zeros(2)))
+
+
 def test_channel_rms():
     d = np.array([[[3.0, 0.0], [4.0, 1.0]]])
     assert np.allclose(ws.channel_rms(d), [np.sqrt(12.5), np.sqrt(0.5)])
@@ -159,3 +167,15 @@ def test_scatter_averages_the_copies_of_a_shared_node():
     cells[tuple(copies[0])] = 4.0
     out = ws.cells_scatter_add(geo, cells, np.zeros(geo.size))
     assert out[centre] == 1.0 and np.count_nonzero(out) == 1
+
+
+@pytest.mark.parametrize("dim,n,r,k", [(2, 3, 2, 1), (3, 2, 1, 1)])
+def test_gather_adjoint_is_the_adjoint_of_the_scatter(dim, n, r, k):
+    geo = SlabGeometry(dim, n, r, k, 1.0, 0.1)
+    rng = np.random.default_rng(12)
+    c = rng.standard_normal((n ** dim, ws.n_channels(dim, r, k)))
+    x = rng.standard_normal(geo.size)
+    s = rng.uniform(0.5, 2.0, c.shape[1])
+    lhs = ws.cells_scatter_add(geo, c, np.zeros(geo.size), s) @ x
+    rhs = (c * ws.cells_gather_adjoint(geo, x, s)).sum()
+    assert np.isclose(lhs, rhs, rtol=1e-12)
