@@ -250,13 +250,15 @@ int  stmg_slab_rhs(stmg_handle* h, const double* F, const double* x_prev, double
    the boundary velocity dofs applied to the boundary values of g; the interior entries of
    g are not read) and y = g on the boundary rows.  Solving S x = y then gives the
    solution with x = g on the boundary (Eq. InAlg with the boundary values moved to the
-   right-hand side).  g, b, y: device FP64, length D_0; y must not alias g or b.  Needs
-   the FP64 operator (precisions bit STMG_FP64). */
+   right-hand side).  g, b, y: device FP64, length D_0; y must not alias g or b.  Uses the
+   finest level's FP64 operator, which every handle has (FGMRES runs in FP64). */
 int  stmg_dirichlet_lift(stmg_handle* h, const double* g, const double* b, double* y);
 
 /* Solve S x = b on the finest level with FGMRES (right preconditioning by one V-cycle
    in cfg.precond_precision, CGS2 orthogonalisation in FP64, no restart).  x: initial
-   guess in, solution out (FP64).  Synchronous.  Returns info->status. */
+   guess in, solution out (FP64); its boundary entries are first set to b's (the
+   boundary rows of S are the identity, and the V-cycle's corrections vanish there).
+   Synchronous.  Returns info->status. */
 int  stmg_solve_slab(stmg_handle* h, const double* b, double* x, stmg_solve_info* info);
 
 /* Same with HOST vectors (any host memory; pinned memory gives faster copies): copies b

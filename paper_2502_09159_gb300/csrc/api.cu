@@ -565,6 +565,19 @@ static int ensure_krylov(stmg_handle* h, int m) {
   return STMG_OK;
 }
 
+static CellsParams cells_params(const LevelHost& H) {
+  CellsParams p{};
+  p.dim = H.dim; p.n = H.n; p.r1 = H.r + 1; p.np = H.np; p.G = H.G; p.kt = H.kt; p.npm = H.npm;
+  p.Pn = H.dim == 2 ? H.np * H.np : H.np * H.np * H.np;
+  p.C = H.kt * (H.dim * p.Pn + H.npm);
+  p.n_nodes = H.n_nodes; p.nv = H.n_vel; p.npr = H.n_pres; p.size = H.size; p.n_cells = H.n_cells;
+  // phi_b at the next slab's Radau points: s_a + 2 on the previous slab's reference interval
+  for (int a = 0; a < H.kt; ++a)
+    for (int bb = 0; bb < H.kt; ++bb)
+      p.E[a * H.kt + bb] = lagrange_eval(H.tt.nodes, H.kt, bb, H.tt.nodes[a] + 2.0);
+  return p;
+}
+
 static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_info* info) {
   auto t0 = std::chrono::steady_clock::now();
   const int m = h->cfg.gmres_max_iter;
@@ -578,6 +591,10 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
   double hv[2];
   info->iterations = 0; info->rel_residual = 0.0; info->status = STMG_OK; info->seconds = 0.0;
   CKS(dev_norm(h, b, D, h->bnorm));
+  // the boundary rows of S are the identity: x_D = b_D exactly.  The V-cycle's corrections
+  // vanish on boundary dofs, so FGMRES keeps x_D where it starts; start it there.
+  CK(launch_copy_boundary(cells_params(l0.H), b, x, s));
+  h->launches += 1;
   {
     Prof pr(h, STMG_PROF_OPERATOR, s);
     CKS(op_apply<double>(h, 0, x, b, h->V, RESIDUAL, s));
@@ -992,7 +1009,7 @@ int stmg_vcycle(stmg_handle* h, int prec, const double* b, double* x) {
 }
 
 int stmg_dirichlet_lift(stmg_handle* h, const double* g, const double* b, double* y) {
-  if (!h || !g || !b || !y || y == g || y == b || !(h->cfg.precisions & 1)) return STMG_ERR_ARG;
+  if (!h || !g || !b || !y || y == g || y == b || !prec_ok(h, 0, STMG_FP64)) return STMG_ERR_ARG;
   return op_apply<double>(h, 0, g, b, y, LIFT, h->st);
 }
 
@@ -1117,18 +1134,6 @@ int stmg_device_status(stmg_handle* h) {
 
 // ---- cell tensors and temporal extrapolation ---------------------------------------
 
-static CellsParams cells_params(const LevelHost& H) {
-  CellsParams p{};
-  p.dim = H.dim; p.n = H.n; p.r1 = H.r + 1; p.np = H.np; p.G = H.G; p.kt = H.kt; p.npm = H.npm;
-  p.Pn = H.dim == 2 ? H.np * H.np : H.np * H.np * H.np;
-  p.C = H.kt * (H.dim * p.Pn + H.npm);
-  p.n_nodes = H.n_nodes; p.nv = H.n_vel; p.npr = H.n_pres; p.size = H.size; p.n_cells = H.n_cells;
-  // phi_b at the next slab's Radau points: s_a + 2 on the previous slab's reference interval
-  for (int a = 0; a < H.kt; ++a)
-    for (int bb = 0; bb < H.kt; ++bb)
-      p.E[a * H.kt + bb] = lagrange_eval(H.tt.nodes, H.kt, bb, H.tt.nodes[a] + 2.0);
-  return p;
-}
 
 int stmg_cells_channels(const stmg_handle* h, int lvl, int* C) {
   if (!h || !C || lvl < 0 || lvl >= (int)h->L.size()) return STMG_ERR_ARG;

@@ -162,6 +162,8 @@ cudaError_t launch_cells_scatter_add(const CellsParams& p, const float* cells, c
 cudaError_t launch_cells_gather_adjoint(const CellsParams& p, const double* x, const float* scale, float* cells,
                                         cudaStream_t st);
 cudaError_t launch_extrapolate(const CellsParams& p, const double* xp, double* xn, cudaStream_t st);
+// x[g] = b[g] on every boundary velocity dof g
+cudaError_t launch_copy_boundary(const CellsParams& p, const double* b, double* x, cudaStream_t st);
 // out[0] = sum x_i y_i (deterministic: per-block partials, then a fixed-order sum); partial:
 // scratch of at least dot_blocks() doubles
 cudaError_t launch_dot(long long n, const double* x, const double* y, double* partial, double* out, cudaStream_t st);

@@ -154,6 +154,22 @@ cudaError_t launch_cells_gather_adjoint(const CellsParams& p, const double* x, c
   return cudaGetLastError();
 }
 
+__global__ void k_copy_boundary(CellsParams p, const double* __restrict__ b, double* __restrict__ x) {
+  const long long vel = p.kt * p.nv;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < vel; g += (long long)gridDim.x * blockDim.x) {
+    const long long node = (g % p.nv) % p.n_nodes;
+    const int ix = (int)(node % p.G), iy = (int)((node / p.G) % p.G);
+    const int iz = p.dim == 3 ? (int)(node / ((long long)p.G * p.G)) : 0;
+    const int last = p.G - 1;
+    if (ix == 0 || ix == last || iy == 0 || iy == last || (p.dim == 3 && (iz == 0 || iz == last))) x[g] = b[g];
+  }
+}
+
+cudaError_t launch_copy_boundary(const CellsParams& p, const double* b, double* x, cudaStream_t st) {
+  k_copy_boundary<<<grid_of(p.kt * p.nv, 256), 256, 0, st>>>(p, b, x);
+  return cudaGetLastError();
+}
+
 constexpr int DOT_BLOCKS = 304;
 
 __global__ void __launch_bounds__(256) k_dot(long long n, const double* __restrict__ x, const double* __restrict__ y,

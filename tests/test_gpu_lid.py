@@ -23,11 +23,14 @@ def rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-@pytest.mark.parametrize("dim,n,r,k", [(2, 3, 2, 1), (2, 4, 1, 2), (3, 2, 2, 1)])
-def test_lift_matches_oracle(dim, n, r, k):
+@pytest.mark.parametrize("dim,n,r,k,precs", [(2, 3, 2, 1, ("fp64", "fp32")), (2, 4, 1, 2, ("fp32",)),
+                                             (3, 2, 2, 1, ("fp32",))])
+def test_lift_matches_oracle(dim, n, r, k, precs):
+    """Also on handles set up for the FP32 V-cycle only (their finest FP64 operator is the
+    one FGMRES uses)."""
     slab = Slab(dim, n, r, k, 0.8, 0.125)
     g = stmg.SpaceTimeMG(dim=dim, n_cells=n, r=r, k=k, nu=0.8, T=1.0, n_slabs=8, levels=[(n, r, k)],
-                         use_graphs=False, autotune=False)
+                         use_graphs=False, autotune=False, precisions=precs, precond_precision=precs[-1])
     gv, b = random_vector(slab.size, 1), random_vector(slab.size, 2)
     assert rel(g.dirichlet_lift(dev(gv), dev(b)), slab.lift(gv, b)) < 1e-12
     # homogeneous data: interior rows unchanged, boundary rows zero
