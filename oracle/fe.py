@@ -124,32 +124,65 @@ def pressure_modes(dim, r):
 # Temporal DG(k) element (Eq. GF, BasYk, DefKMC)
 # ---------------------------------------------------------------------------
 class TimeFE:
-    """DG(k) on one slab of length tau with the Lagrange basis at the right Radau points.
+    """DG(k) on a system of `nsub` consecutive subintervals of length tau (a macro time
+    step, Remark rem:GLSP; nsub = 1 is time marching, Eq. AlgSysTMS), Lagrange basis at the
+    right Radau points of every subinterval.
 
-    K[a,b] = int phi_b' phi_a dt + phi_b(t_{n-1}^+) phi_a(t_{n-1}^+)   (Eq. DefKMC)
-    M[a,b] = int phi_b phi_a dt                                       (Eq. DefKMC)
-    C[a,b] = delta_{b,k+1} phi_a(t_{n-1}^+)                           (Eq. DefKMC)
-    K does not depend on tau (the 2/tau of the derivative cancels the tau/2 of the
-    measure); M scales with tau.  Integrals use a Gauss rule exact for the integrand.
+    One subinterval (Eq. DefKMC):
+      K1[a,b] = int phi_b' phi_a dt + phi_b(t_{n-1}^+) phi_a(t_{n-1}^+)
+      M1[a,b] = int phi_b phi_a dt
+      C1[a,b] = delta_{b,k+1} phi_a(t_{n-1}^+)
+    K1 does not depend on tau (the 2/tau of the derivative cancels the tau/2 of the
+    measure); M1 scales with tau.  Integrals use a Gauss rule exact for the integrand.
+    The system of nsub subintervals (Eq. GloSys restricted to a macro step) has the
+    temporal matrices K = block-lower-bidiagonal(diagonal K1, subdiagonal -C1) and
+    M = blockdiag(M1); its temporal dofs are numbered subinterval by subinterval, and
+    its nodes are given as reference coordinates s + 2 j on [-1, 2 nsub - 1] (subinterval
+    j maps to [2j - 1, 2j + 1]).  Only the first subinterval couples to the previous
+    system: phi_left = (phi_a(t^+), 0, ..., 0).
     """
 
-    def __init__(self, k, tau):
-        self.k, self.tau = k, tau
-        self.nodes, self.weights = radau_right(k)
+    def __init__(self, k, tau, nsub=1):
+        self.k, self.tau, self.nsub = k, tau, nsub
+        s, w = radau_right(k)
+        self.nodes1, self.weights1 = s, w
         gx, gw = gauss_legendre(k + 2)
-        phi = lagrange_values(self.nodes, gx)           # [a, q]
-        dphi = lagrange_derivs(self.nodes, gx)          # d/dt_hat
-        phi_m1 = lagrange_values(self.nodes, [-1.0])[:, 0]
+        phi = lagrange_values(s, gx)                    # [a, q]
+        dphi = lagrange_derivs(s, gx)                   # d/dt_hat
+        phi_m1 = lagrange_values(s, [-1.0])[:, 0]
         # reference interval [-1,1]: dt = tau/2 dt_hat, d/dt = 2/tau d/dt_hat
-        self.K = (phi * gw) @ dphi.T + np.outer(phi_m1, phi_m1)
-        self.M = (tau / 2) * (phi * gw) @ phi.T
-        self.phi_left = phi_m1                          # phi_a(t_{n-1}^+)
-        self.C = np.zeros((k + 1, k + 1))
-        self.C[:, k] = phi_m1
+        K1 = (phi * gw) @ dphi.T + np.outer(phi_m1, phi_m1)
+        M1 = (tau / 2) * (phi * gw) @ phi.T
+        C1 = np.zeros((k + 1, k + 1))
+        C1[:, k] = phi_m1
+        k1 = k + 1
+        self.kt = nsub * k1
+        self.K = np.zeros((self.kt, self.kt))
+        self.M = np.zeros((self.kt, self.kt))
+        for j in range(nsub):
+            self.K[j * k1:(j + 1) * k1, j * k1:(j + 1) * k1] = K1
+            self.M[j * k1:(j + 1) * k1, j * k1:(j + 1) * k1] = M1
+            if j > 0:
+                self.K[j * k1:(j + 1) * k1, (j - 1) * k1:j * k1] = -C1
+        self.nodes = np.concatenate([s + 2.0 * j for j in range(nsub)])
+        self.weights = np.tile(w, nsub)
+        self.phi_left = np.concatenate([phi_m1, np.zeros((nsub - 1) * k1)])   # phi_a(t_{n-1}^+)
+        self.C = np.zeros((self.kt, self.kt))
+        self.C[:k1, self.kt - 1] = phi_m1
+        self.K1, self.M1, self.C1 = K1, M1, C1
 
     def basis_at(self, that):
-        """phi_a at reference times that in [-1,1]; shape (k+1, len(that))."""
-        return lagrange_values(self.nodes, that)
+        """phi_a at reference times that in [-1, 2 nsub - 1]; shape (kt, len(that)).  A
+        point on the border of two subintervals counts to the later one."""
+        that = np.atleast_1d(np.asarray(that, dtype=float))
+        out = np.zeros((self.kt, len(that)))
+        k1 = self.k + 1
+        j = np.clip(np.floor((that + 1.0) / 2.0).astype(int), 0, self.nsub - 1)
+        for jj in range(self.nsub):
+            m = j == jj
+            if m.any():
+                out[jj * k1:(jj + 1) * k1, m] = lagrange_values(self.nodes1, that[m] - 2.0 * jj)
+        return out
 
 
 # ---------------------------------------------------------------------------
@@ -318,6 +351,6 @@ class SpaceFE:
         return out
 
 
-def slab_size(dim, n, r, k):
-    """Dofs per slab D = (k+1)(d ((r+1)n+1)^d + C(r+d,d) n^d); boundary dofs counted."""
-    return (k + 1) * (dim * ((r + 1) * n + 1) ** dim + comb(r + dim, dim) * n ** dim)
+def slab_size(dim, n, r, k, nsub=1):
+    """Dofs per system D = nsub (k+1)(d ((r+1)n+1)^d + C(r+d,d) n^d); boundary dofs counted."""
+    return nsub * (k + 1) * (dim * ((r + 1) * n + 1) ** dim + comb(r + dim, dim) * n ** dim)

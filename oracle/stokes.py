@@ -43,15 +43,15 @@ class SlabGeometry:
     """Spaces, layout and Dirichlet mask of one slab system, without assembled matrices
     (enough for right-hand sides, error norms and row-wise evaluation at any size)."""
 
-    def __init__(self, dim, n, r, k, nu, tau):
+    def __init__(self, dim, n, r, k, nu, tau, nsub=1):
         self.space = SpaceFE(dim, n, r)
-        self.time = TimeFE(k, tau)
-        self.dim, self.n, self.r, self.k, self.nu, self.tau = dim, n, r, k, nu, tau
+        self.time = TimeFE(k, tau, nsub)
+        self.dim, self.n, self.r, self.k, self.nu, self.tau, self.nsub = dim, n, r, k, nu, tau, nsub
         sp_ = self.space
         self.nv, self.npr = sp_.n_vel, sp_.n_pres
-        self.kt = k + 1
+        self.kt = self.time.kt
         self.size = self.kt * (self.nv + self.npr)
-        assert self.size == slab_size(dim, n, r, k)
+        assert self.size == slab_size(dim, n, r, k, nsub)
         dir_v = sp_.vel_dirichlet()
         self.dirichlet = np.concatenate([np.tile(dir_v, self.kt), np.zeros(self.kt * self.npr, bool)])
 
@@ -151,8 +151,8 @@ def slab_rows(geo: SlabGeometry, x, rows):
 class Slab(SlabGeometry):
     """Space-time slab system of one level: spaces, matrices and the Dirichlet mask."""
 
-    def __init__(self, dim, n, r, k, nu, tau):
-        super().__init__(dim, n, r, k, nu, tau)
+    def __init__(self, dim, n, r, k, nu, tau, nsub=1):
+        super().__init__(dim, n, r, k, nu, tau, nsub)
         sp_ = self.space
         self.Mv = sp_.mass()
         self.Av = sp_.laplace()
@@ -268,8 +268,10 @@ def prolong_space(coarse: SpaceFE, fine: SpaceFE):
 
 
 def prolong_time(tc: TimeFE, tf: TimeFE):
-    """p-prolongation in time (Eq. DefPrRek): P[a, b] = phi_b^coarse(t_a^fine)."""
-    return lagrange_values(tc.nodes, tf.nodes).T
+    """p-prolongation in time (Eq. DefPrRek): P[a, b] = phi_b^coarse(t_a^fine) on each
+    subinterval of the system (block diagonal over the subintervals)."""
+    assert tc.nsub == tf.nsub
+    return np.kron(np.eye(tf.nsub), lagrange_values(tc.nodes1, tf.nodes1).T)
 
 
 def slab_prolongation(coarse: Slab, fine: Slab):
@@ -430,10 +432,10 @@ class Multigrid:
     Level operators are rediscretised on every level; between consecutive levels the
     transfer is whatever (n, r, k) change they have (h or p in space, p in time)."""
 
-    def __init__(self, dim, levels, nu, tau, cfg: MGConfig = MGConfig()):
+    def __init__(self, dim, levels, nu, tau, cfg: MGConfig = MGConfig(), nsub=1):
         self.cfg = cfg
         self.levels = list(levels)
-        self.slabs = [Slab(dim, n, r, k, nu, tau) for (n, r, k) in levels]
+        self.slabs = [Slab(dim, n, r, k, nu, tau, nsub) for (n, r, k) in levels]
         self.P = [slab_prolongation(self.slabs[i + 1], self.slabs[i]) for i in range(len(levels) - 1)]
         self.smoothers = []
         for s in self.slabs[:-1]:
@@ -525,21 +527,23 @@ def fgmres(apply, precond, b, x0=None, tol=1e-8, maxit=200):
 # Time marching (Eq. AlgSysTMS) and error norms
 # ---------------------------------------------------------------------------
 def march(problem, n, r, k, n_slabs, cfg: MGConfig = MGConfig(), tol=1e-8, levels=None,
-          solver="mg", slabs_to_run=None):
-    """Solve slab by slab: D X_n = B_n + (C_tau (x) M_h) V_{n-1}, V_0 = 0; with
-    problem.boundary set, its values are imposed on the boundary dofs (Slab.lift).
+          solver="mg", slabs_to_run=None, nsub=1):
+    """Solve system by system: D X_n = B_n + (C_tau (x) M_h) V_{n-1}, V_0 = 0, each system a
+    macro step of `nsub` subintervals (Remark rem:GLSP; nsub = 1 is Eq. AlgSysTMS), n_slabs
+    systems on (0, T]; with problem.boundary set, its values are imposed on the boundary
+    dofs (Slab.lift).
 
     solver = "mg": FGMRES preconditioned by one V-cycle; "direct": bordered sparse LU.
-    Returns (list of slab solutions, list of SolveInfo, the finest Slab, Multigrid)."""
-    tau = problem.T / n_slabs
+    Returns (list of system solutions, list of SolveInfo, the finest Slab, Multigrid)."""
+    tau = problem.T / (n_slabs * nsub)
     levels = levels or default_hierarchy(n, r, k)
-    mg = Multigrid(problem.dim, levels, problem.nu, tau, cfg) if solver == "mg" else None
-    slab = mg.slabs[0] if mg else Slab(problem.dim, n, r, k, problem.nu, tau)
+    mg = Multigrid(problem.dim, levels, problem.nu, tau, cfg, nsub) if solver == "mg" else None
+    slab = mg.slabs[0] if mg else Slab(problem.dim, n, r, k, problem.nu, tau, nsub)
     v_prev = np.zeros(slab.nv)
     sols, infos = [], []
     bnd = getattr(problem, "boundary", None)
     for s in range(slabs_to_run or n_slabs):
-        t0 = s * tau
+        t0 = s * nsub * tau
         b = slab.rhs_forcing(problem.forcing, t0) + slab.coupling(v_prev)
         if bnd is not None:
             b = slab.lift(slab.boundary_vector(bnd, t0), b)
@@ -573,27 +577,29 @@ def errors(problem, slab: Slab, sols, nq_v=None, nq_p=None, nq_t=None):
     xv, wv = rule(nq_v or slab.r + 4)
     xp, wp = rule(nq_p or slab.r + 4)
     tq, tw = gauss_legendre(nq_t or slab.k + 3)
-    phi_t = tf.basis_at(tq)                                   # [a, q]
+    phi_t = lagrange_values(tf.nodes1, tq)                    # [b, q] on one subinterval
+    k1 = slab.k + 1
     e_v = e_h1 = e_div = e_p = 0.0
     for s, X in enumerate(sols):
-        t0 = s * tau
-        for qi in range(len(tq)):
-            t = t0 + tau / 2 * (tq[qi] + 1)
-            V = sum(phi_t[a, qi] * slab.vel(X, a) for a in range(slab.kt))
-            P = sum(phi_t[a, qi] * slab.pres(X, a) for a in range(slab.kt))
-            wt = tau / 2 * tw[qi]
-            x, v, gv, _ = sp_.eval_cells(V, P, xv, grad=True)
-            ve = problem.velocity(tuple(x), t)
-            ge = problem.velocity_grad(tuple(x), t)
-            e_v += wt * sum(((v[c] - ve[c]) ** 2 * wv).sum() for c in range(slab.dim))
-            e_h1 += wt * sum(((gv[c][j] - ge[c][j]) ** 2 * wv).sum()
-                             for c in range(slab.dim) for j in range(slab.dim))
-            div = sum(gv[c][c] for c in range(slab.dim))
-            e_div += wt * ((div ** 2) * wv).sum()
-            x, _, _, p = sp_.eval_cells(V, P, xp)
-            pe = problem.pressure(tuple(x), t)
-            pm = (p * wp).sum() / wp.sum() / sp_.n_cells
-            pem = (pe * wp).sum() / wp.sum() / sp_.n_cells
-            e_p += wt * ((((p - pm) - (pe - pem)) ** 2) * wp).sum()
+        for jsub in range(tf.nsub):
+            t0 = (s * tf.nsub + jsub) * tau
+            for qi in range(len(tq)):
+                t = t0 + tau / 2 * (tq[qi] + 1)
+                V = sum(phi_t[b_, qi] * slab.vel(X, jsub * k1 + b_) for b_ in range(k1))
+                P = sum(phi_t[b_, qi] * slab.pres(X, jsub * k1 + b_) for b_ in range(k1))
+                wt = tau / 2 * tw[qi]
+                x, v, gv, _ = sp_.eval_cells(V, P, xv, grad=True)
+                ve = problem.velocity(tuple(x), t)
+                ge = problem.velocity_grad(tuple(x), t)
+                e_v += wt * sum(((v[c] - ve[c]) ** 2 * wv).sum() for c in range(slab.dim))
+                e_h1 += wt * sum(((gv[c][j] - ge[c][j]) ** 2 * wv).sum()
+                                 for c in range(slab.dim) for j in range(slab.dim))
+                div = sum(gv[c][c] for c in range(slab.dim))
+                e_div += wt * ((div ** 2) * wv).sum()
+                x, _, _, p = sp_.eval_cells(V, P, xp)
+                pe = problem.pressure(tuple(x), t)
+                pm = (p * wp).sum() / wp.sum() / sp_.n_cells
+                pem = (pe * wp).sum() / wp.sum() / sp_.n_cells
+                e_p += wt * ((((p - pm) - (pe - pem)) ** 2) * wp).sum()
     return {"v_L2L2": math.sqrt(e_v), "v_L2H1": math.sqrt(e_h1), "div_L2L2": math.sqrt(e_div),
             "p_L2L2": math.sqrt(e_p)}

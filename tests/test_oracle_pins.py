@@ -406,3 +406,56 @@ def test_slab_rows_equal_assembled_rows(dim, n, r, k):
     rows = np.random.default_rng(1).choice(s.size, 80, replace=False)
     ref = (s.S @ x)[rows]
     assert np.abs(slab_rows(s, x, rows) - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------
+# Macro time steps (Remark rem:GLSP): a system of nsub subintervals
+# ---------------------------------------------------------------------------
+def test_macro_time_fe_structure():
+    t1, t2 = TimeFE(1, 0.1), TimeFE(1, 0.1, nsub=2)
+    assert t2.kt == 4
+    assert np.allclose(t2.K[:2, :2], t1.K) and np.allclose(t2.K[2:, 2:], t1.K)
+    assert np.allclose(t2.K[2:, :2], -t1.C) and np.allclose(t2.K[:2, 2:], 0.0)
+    assert np.allclose(t2.M, np.kron(np.eye(2), t1.M))
+    assert np.allclose(t2.phi_left, [1.5, -0.5, 0.0, 0.0])
+    assert np.allclose(t2.nodes, [-1 / 3, 1.0, 5 / 3, 3.0])
+    # basis on the second subinterval is the first one's shifted by 2
+    that = np.array([1.5, 2.2])
+    assert np.allclose(t2.basis_at(that)[2:], t1.basis_at(that - 2.0)) and np.allclose(t2.basis_at(that)[:2], 0)
+
+
+@pytest.mark.parametrize("k,nsub", [(1, 2), (0, 3), (2, 2)])
+def test_macro_step_equals_time_marching(k, nsub):
+    """Solving nsub subintervals as one block-bidiagonal system (Eq. GloSys over a macro
+    step) gives exactly the time-marching solution (Eq. AlgSysTMS), subinterval by
+    subinterval."""
+    pb = manufactured_2d(nu=1.0, time="sin_pi")
+    n, r, N = 3, 1, 2
+    macro, _, sm, _ = march(pb, n, r, k, N, solver="direct", nsub=nsub)
+    single, _, s1, _ = march(pb, n, r, k, N * nsub, solver="direct")
+    k1 = k + 1
+    for m, X in enumerate(macro):
+        for j in range(nsub):
+            x1 = s1.remove_pressure_mean(single[m * nsub + j])
+            for b in range(k1):
+                a = j * k1 + b
+                assert np.abs(sm.vel(X, a) - s1.vel(x1, b)).max() < 1e-11
+                p_macro = sm.pres(sm.remove_pressure_mean(X), a)
+                assert np.abs(p_macro - s1.pres(x1, b)).max() < 1e-10
+
+
+def test_macro_step_exact_reproduction_and_multigrid():
+    """Q4/P3, DG(1), two subintervals per system: the polynomial field is reproduced
+    exactly, and FGMRES with the V-cycle (p-transfers in time per subinterval) solves the
+    macro system to its tolerance in a bounded number of iterations."""
+    pb = polynomial_2d(m=1, nu=0.7)
+    sols, _, slab, _ = march(pb, 2, 3, 1, 2, solver="direct", nsub=2)
+    e = errors(pb, slab, sols)
+    assert e["v_L2L2"] < 1e-11 and e["v_L2H1"] < 1e-10 and e["p_L2L2"] < 1e-10
+    pb2 = manufactured_2d(nu=1.0, time="sin_pi")
+    sols_mg, infos, slab2, _ = march(pb2, 4, 2, 2, 2, tol=1e-10, nsub=2)
+    sols_d, _, _, _ = march(pb2, 4, 2, 2, 2, solver="direct", nsub=2)
+    for xm, xd in zip(sols_mg, sols_d):
+        a, b = slab2.remove_pressure_mean(xm), slab2.remove_pressure_mean(xd)
+        assert np.abs(a - b).max() < 1e-7 * np.abs(b).max()
+    assert max(i.iterations for i in infos) <= 30
