@@ -31,6 +31,10 @@
  *
  * Slab vector layout (Eq. DefX / DefSubvec, per slab):
  *     [ V^1 ... V^{k+1} , P^1 ... P^{k+1} ]                      length D
+ *   With n_sub > 1 subintervals per system the temporal dofs are numbered subinterval by
+ *   subinterval, a = j (k+1) + b, and the vector is [V^1 .. V^{n_sub (k+1)}, P^1 .. ]
+ *   (all velocities, then all pressures; the paper's Eq. SubStrGloVec orders the same
+ *   unknowns subinterval-major, a permutation of this layout).
  *   V^a  velocity at temporal dof a (Lagrange basis at the right Gauss-Radau points,
  *        Eq. BasYk), component-major: v_x over all velocity nodes, then v_y (, v_z).
  *        Velocity nodes: the ((r+1) n + 1)^d grid of the Q_{r+1} Gauss-Lobatto nodes,
@@ -120,6 +124,12 @@ typedef struct {
                               polynomial coarsening in time (Alg. 2's r_0 for k; default
                               1 as in the paper's runs; k_min >= k keeps DG(k) on every
                               level)                                                     */
+  int    n_sub;            /* DG(k) subintervals per system (a macro time step, Remark
+                              rem:GLSP; default 1 = time marching, Eq. AlgSysTMS); the
+                              system of n_sub subintervals is solved at once and the
+                              temporal multigrid is p-coarsening per subinterval (no
+                              h-coarsening in time).  tau = T / (n_slabs n_sub);
+                              n_sub (k + 1) <= 8                                        */
 } stmg_config;
 
 typedef struct {
@@ -276,7 +286,8 @@ int  stmg_forcing_npoints(const stmg_handle* h, int* nq_per_cell);
    [cell][q][dim] (cells lexicographic, points x fastest). */
 int  stmg_forcing_points(stmg_handle* h, double* xq);
 
-/* Times t_n^a of the k+1 Radau points of slab `slab` (0-based), host FP64 array. */
+/* Times t_n^a of the n_sub (k+1) Radau points of system `slab` (0-based; subinterval by
+   subinterval), host FP64 array. */
 int  stmg_slab_times(const stmg_handle* h, int slab, double* t_host);
 
 /* F: (F^a)_i = tau/2 w_a <f(t_n^a), chi_i> by the Gauss rule above, from fq = device FP64

@@ -49,7 +49,8 @@ class SpaceTimeMG:
                  smoothers: Optional[Sequence[int]] = None, omega: float = 0.7, nu1: int = 1,
                  nu2: int = 1, precond_precision="fp64", precisions=("fp64", "fp32"),
                  gmres_max_iter: int = 200, rel_tol: float = 1e-8, use_graphs: bool = True,
-                 sweep_variant: int = 0, autotune: bool = True, coarse_n: int = 1, k_min: int = 1):
+                 sweep_variant: int = 0, autotune: bool = True, coarse_n: int = 1, k_min: int = 1,
+                 n_sub: int = 1):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("SpaceTimeMG needs a CUDA device (no CPU fallback)")
@@ -74,8 +75,10 @@ class SpaceTimeMG:
         cfg.autotune = int(autotune)
         cfg.coarse_n = int(coarse_n)
         cfg.k_min = int(k_min)
+        cfg.n_sub = int(n_sub)
         self.cfg = cfg
-        self.dim, self.r, self.k = dim, r, k
+        self.dim, self.r, self.k, self.n_sub = dim, r, k, int(n_sub)
+        self.kt = self.n_sub * (k + 1)
         self.device = torch.device("cuda", torch.cuda.current_device())
         h = C.c_void_p()
         check("stmg_create", lib.stmg_create(C.byref(cfg), C.byref(h)))
@@ -378,7 +381,7 @@ class SpaceTimeMG:
         return pts
 
     def slab_times(self, slab: int):
-        t = (C.c_double * (self.k + 1))()
+        t = (C.c_double * self.kt)()
         check("stmg_slab_times", self._lib.stmg_slab_times(self._h, slab, t))
         return list(t)
 

@@ -211,11 +211,17 @@ static void fill_transfer_params(const LevelHost& F, const LevelHost& C, Transfe
       p->P1[s * MAXNP + j] = (T)v;
     }
   }
+  // per subinterval (block diagonal): phi_ac^coarse at the fine Radau points
   for (int af = 0; af < F.kt; ++af)
     for (int ac = 0; ac < C.kt; ++ac) {
-      double v = lagrange_eval(C.tt.nodes, C.kt, ac, F.tt.nodes[af]);
-      for (int jj = 0; jj < C.kt; ++jj)
-        if (std::fabs(F.tt.nodes[af] - C.tt.nodes[jj]) < 1e-14) v = (jj == ac) ? 1.0 : 0.0;
+      const int jf = af / F.tt.k1, bf = af % F.tt.k1, jc = ac / C.tt.k1, bc = ac % C.tt.k1;
+      double v = 0.0;
+      if (jf == jc) {
+        const double s = F.tt.nodes1[bf];
+        v = lagrange_eval(C.tt.nodes1, C.tt.k1, bc, s);
+        for (int jj = 0; jj < C.tt.k1; ++jj)
+          if (std::fabs(s - C.tt.nodes1[jj]) < 1e-14) v = (jj == bc) ? 1.0 : 0.0;
+      }
       p->Pt[af * MAXKT + ac] = (T)v;
     }
   // E[o][i' * (rc+1) + i] = int_0^1 L_i((o + xi)/2) L_i'(xi) dxi
@@ -571,10 +577,15 @@ static CellsParams cells_params(const LevelHost& H) {
   p.Pn = H.dim == 2 ? H.np * H.np : H.np * H.np * H.np;
   p.C = H.kt * (H.dim * p.Pn + H.npm);
   p.n_nodes = H.n_nodes; p.nv = H.n_vel; p.npr = H.n_pres; p.size = H.size; p.n_cells = H.n_cells;
-  // phi_b at the next slab's Radau points: s_a + 2 on the previous slab's reference interval
+  // the previous system's last subinterval polynomial at the next system's Radau points:
+  // subinterval j of the next system lies at s + 2 (j + 1) on its reference interval
+  const int k1 = H.tt.k1, last = H.nsub - 1;
   for (int a = 0; a < H.kt; ++a)
-    for (int bb = 0; bb < H.kt; ++bb)
-      p.E[a * H.kt + bb] = lagrange_eval(H.tt.nodes, H.kt, bb, H.tt.nodes[a] + 2.0);
+    for (int bb = 0; bb < H.kt; ++bb) {
+      const int ja = a / k1, jb = bb / k1;
+      p.E[a * H.kt + bb] = jb == last ? lagrange_eval(H.tt.nodes1, k1, bb % k1, H.tt.nodes1[a % k1] + 2.0 * (ja + 1))
+                                      : 0.0;
+    }
   return p;
 }
 
@@ -750,6 +761,7 @@ int stmg_default_config(stmg_config* c) {
   c->autotune = 1;
   c->coarse_n = 1;
   c->k_min = 1;
+  c->n_sub = 1;
   return STMG_OK;
 }
 
@@ -759,12 +771,14 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
   if (c.dim != 2 && c.dim != 3) return STMG_ERR_ARG;
   if (c.n_cells < 1 || c.r < 1 || c.k < 0 || c.n_slabs < 1 || !(c.T > 0) || !(c.nu > 0)) return STMG_ERR_ARG;
   if (c.r > 4 || c.k > 3) return STMG_ERR_UNIMPLEMENTED;
+  if (c.n_sub < 1) return STMG_ERR_ARG;
+  if (c.n_sub * (c.k + 1) > MAXKT) return STMG_ERR_UNIMPLEMENTED;
   if (c.gmres_max_iter < 1 || !(c.rel_tol > 0) || c.nu1 < 0 || c.nu2 < 0) return STMG_ERR_ARG;
   if ((c.precisions & 3) == 0) return STMG_ERR_ARG;
   if (c.sweep_variant < 0 || c.sweep_variant > 2) return STMG_ERR_ARG;
   if (c.precond_precision != STMG_FP64 && c.precond_precision != STMG_FP32) return STMG_ERR_ARG;
   if (!(c.precisions & (1 << c.precond_precision))) return STMG_ERR_ARG;
-  h->tau = c.T / c.n_slabs;
+  h->tau = c.T / ((double)c.n_slabs * c.n_sub);
   std::vector<std::array<int, 3>> lv;
   if (c.n_levels == 0) {
     if (c.n_cells & (c.n_cells - 1)) return STMG_ERR_ARG;   // default rule needs n = 2^c
@@ -789,7 +803,7 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
   try {
     for (size_t i = 0; i < lv.size(); ++i) {
       LevelDev& L = h->L[i];
-      init_level_geometry(&L.H, c.dim, lv[i][0], lv[i][1], lv[i][2], h->tau, c.nu);
+      init_level_geometry(&L.H, c.dim, lv[i][0], lv[i][1], lv[i][2], h->tau, c.nu, c.n_sub);
     }
   } catch (const std::exception&) {
     return STMG_ERR_ARG;
@@ -1072,7 +1086,8 @@ int stmg_forcing_points(stmg_handle* h, double* xq) {
 int stmg_slab_times(const stmg_handle* h, int slab, double* t) {
   if (!h || !t || slab < 0) return STMG_ERR_ARG;
   const LevelHost& F = h->L[0].H;
-  for (int a = 0; a < F.kt; ++a) t[a] = slab * h->tau + 0.5 * h->tau * (F.tt.nodes[a] + 1.0);
+  for (int a = 0; a < F.kt; ++a)
+    t[a] = (double)slab * F.nsub * h->tau + 0.5 * h->tau * (F.tt.nodes[a] + 1.0);
   return STMG_OK;
 }
 

@@ -14,7 +14,7 @@
 namespace stmg {
 
 constexpr int MAXNP = 6;    // velocity nodes per direction per cell (r <= 4)
-constexpr int MAXKT = 4;    // temporal dofs per slab (k <= 3)
+constexpr int MAXKT = 8;    // temporal dofs per system: n_sub (k + 1) <= 8
 constexpr int MAXPM = 35;   // pressure modes per cell, C(4+3, 3)
 constexpr int MAXNS = 2 * (MAXNP - 1) + 1;  // fine nodes per direction under one coarse cell
 
@@ -31,16 +31,18 @@ struct Tables1D {                 // one spatial degree on the reference interva
   double N1[MAXNP * MAXNP];       // [i * np + p] = int L_i ell_p
 };
 
-struct TimeTables {               // DG(k) with the right Radau Lagrange basis
-  int kt = 0;
-  double nodes[MAXKT], weights[MAXKT];
-  double K[MAXKT * MAXKT];        // [a * kt + b]
+struct TimeTables {               // DG(k) with the right Radau Lagrange basis on n_sub subintervals
+  int kt = 0;                     // n_sub (k + 1) temporal dofs, subinterval by subinterval
+  int k1 = 0, nsub = 1;           // k + 1, subintervals per system
+  double nodes1[MAXKT];           // Radau points of one subinterval on [-1, 1]
+  double nodes[MAXKT], weights[MAXKT];   // nodes of subinterval j shifted by 2 j
+  double K[MAXKT * MAXKT];        // [a * kt + b]: block-bidiagonal (K1 on, -C1 below the diagonal)
   double M[MAXKT];                // diagonal of the temporal mass, includes tau/2
-  double phi_left[MAXKT];         // phi_a(t_{n-1}^+)
+  double phi_left[MAXKT];         // phi_a(t_{n-1}^+) on the first subinterval, 0 on the others
 };
 
 Tables1D make_tables_1d(int r);
-TimeTables make_time_tables(int k, double tau);
+TimeTables make_time_tables(int k, double tau, int nsub = 1);
 void pressure_modes(int dim, int r, std::vector<std::array<int, 3>>* out);
 void gauss_legendre(int n, double* x, double* w);            // on [-1, 1]
 double lagrange_eval(const double* nodes, int n, int j, double t);

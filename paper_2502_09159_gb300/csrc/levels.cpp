@@ -47,8 +47,8 @@ std::vector<std::array<int, 3>> default_hierarchy(int n, int r, int k, int coars
   return out;
 }
 
-void init_level_geometry(LevelHost* L, int dim, int n, int r, int k, double tau, double nu) {
-  L->dim = dim; L->n = n; L->r = r; L->k = k; L->kt = k + 1;
+void init_level_geometry(LevelHost* L, int dim, int n, int r, int k, double tau, double nu, int nsub) {
+  L->dim = dim; L->n = n; L->r = r; L->k = k; L->kt = nsub * (k + 1); L->nsub = nsub;
   L->np = r + 2; L->G = (r + 1) * n + 1;
   L->nq = ipow(L->np, dim);
   L->h = 1.0 / n; L->tau = tau; L->nu = nu;
@@ -61,7 +61,7 @@ void init_level_geometry(LevelHost* L, int dim, int n, int r, int k, double tau,
   L->n_pres = (long long)L->n_cells * L->npm;
   L->size = (long long)L->kt * (L->n_vel + L->n_pres);
   L->t1 = make_tables_1d(r);
-  L->tt = make_time_tables(k, tau);
+  L->tt = make_time_tables(k, tau, nsub);
   // element matrices on a cell of size h (Kronecker products of the 1D tables)
   const int np = L->np, nq = L->nq;
   L->Me.assign((size_t)nq * nq, 0.0);

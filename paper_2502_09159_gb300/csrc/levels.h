@@ -9,7 +9,7 @@
 namespace stmg {
 
 struct LevelHost {
-  int dim = 2, n = 1, r = 1, k = 0, kt = 1, np = 3, nq = 9, G = 3, npm = 3, n_cells = 1;
+  int dim = 2, n = 1, r = 1, k = 0, kt = 1, nsub = 1, np = 3, nq = 9, G = 3, npm = 3, n_cells = 1;
   long long n_nodes = 0, n_vel = 0, n_pres = 0, size = 0;
   double h = 1.0, tau = 1.0, nu = 1.0;
   Tables1D t1;
@@ -30,7 +30,7 @@ struct LevelHost {
 };
 
 std::vector<std::array<int, 3>> default_hierarchy(int n, int r, int k, int coarse_n = 1, int k_min = 1);
-void init_level_geometry(LevelHost* L, int dim, int n, int r, int k, double tau, double nu);
+void init_level_geometry(LevelHost* L, int dim, int n, int r, int k, double tau, double nu, int nsub = 1);
 void build_patches(LevelHost* L, int kind);
 void assemble_submatrix(const LevelHost& L, const std::vector<long long>& idx, const std::vector<char>& dir,
                         std::vector<double>* S);

@@ -150,7 +150,12 @@ Tables1D make_tables_1d(int r) {
   return t;
 }
 
-TimeTables make_time_tables(int k, double tau) {
+// One DG(k) subinterval (Eq. DefKMC), then the system of nsub subintervals (Eq. GloSys
+// over a macro step, Remark rem:GLSP): K block-bidiagonal with K1 on the diagonal and
+// -C1 below it (C1[a][b] = delta_{b,k} phi_a(-1)), M block diagonal, nodes of subinterval
+// j shifted by 2 j, the coupling to the previous system only on the first subinterval.
+TimeTables make_time_tables(int k, double tau, int nsub) {
+  if (nsub < 1 || nsub * (k + 1) > MAXKT) throw std::runtime_error("time tables: too many temporal dofs");
   TimeTables t;
   const int kt = k + 1;
   t.kt = kt;
@@ -181,7 +186,26 @@ TimeTables make_time_tables(int k, double tau) {
   }
   for (int a = 0; a < kt; ++a)
     for (int b = 0; b < kt; ++b) t.K[a * kt + b] += t.phi_left[a] * t.phi_left[b];
-  return t;
+  t.k1 = kt;
+  t.nsub = 1;
+  for (int a = 0; a < kt; ++a) t.nodes1[a] = t.nodes[a];
+  if (nsub == 1) return t;
+  TimeTables m = t;
+  const int KT = nsub * kt;
+  m.kt = KT;
+  m.nsub = nsub;
+  for (int i = 0; i < MAXKT * MAXKT; ++i) m.K[i] = 0.0;
+  for (int j = 0; j < nsub; ++j)
+    for (int a = 0; a < kt; ++a) {
+      const int A = j * kt + a;
+      m.nodes[A] = t.nodes[a] + 2.0 * j;
+      m.weights[A] = t.weights[a];
+      m.M[A] = t.M[a];
+      m.phi_left[A] = j == 0 ? t.phi_left[a] : 0.0;
+      for (int b = 0; b < kt; ++b) m.K[A * KT + j * kt + b] = t.K[a * kt + b];
+      if (j > 0) m.K[A * KT + (j - 1) * kt + (kt - 1)] = -t.phi_left[a];
+    }
+  return m;
 }
 
 }  // namespace stmg
