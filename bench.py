@@ -59,6 +59,8 @@ def parse():
                    help="coarsest mesh of the hierarchy (Alg. 2's 1/h_0); 0: 8 in 2D, 1 in 3D")
     p.add_argument("--k-min", type=int, default=0, help="lowest temporal degree of the hierarchy; 0: k in 2D, 1 in 3D")
     p.add_argument("--levels", default="", help="explicit level list n:r:k,... fine -> coarse")
+    p.add_argument("--profile-range", action="store_true",
+                   help="wrap the timed steps in cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
                    help="c2: the 2D headline configuration; c3: the 3D 32^3 configuration; "
                         "lid: the lid-driven cavity at c = 4")
@@ -261,11 +263,15 @@ def run_ours(args):
     clocks.start()
     launches_before = mg.kernel_launches
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.profile_range:
+        torch.cuda.profiler.start()
     ev0.record()
     for _ in range(args.steps):
         step(mg, its)
     ev1.record()
     barrier()
+    if args.profile_range:
+        torch.cuda.profiler.stop()
     ms = ev0.elapsed_time(ev1)
     launches = mg.kernel_launches - launches_before
     clk = clocks.stop()

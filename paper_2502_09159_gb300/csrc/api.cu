@@ -61,6 +61,9 @@ struct stmg_handle {
   int m_alloc = 0;
   int* d_err = nullptr;           // device flag raised by bounded waits that expired
   double* dot_part = nullptr;     // per-block partial sums of stmg_dot (allocated on first use)
+  unsigned* cgs_bar = nullptr;    // grid barrier of the cooperative CGS2 step (count, generation)
+  double* cgs_part = nullptr;     // its partial sums
+  int cgs_blocks = 0;             // co-resident blocks of that launch (0: use the split kernels)
   int n_sm = 1;
   ForcingParams fp{};
   MassParams mp{};
@@ -566,6 +569,11 @@ static int ensure_krylov(stmg_handle* h, int m) {
   CKS(dalloc(&h->hcol, m + 2));
   CKS(dalloc(&h->tmp, m + 2));
   CKS(dalloc(&h->partial, (size_t)304 * (m + 2)));
+  if (h->cgs_blocks > 0) {
+    if (h->cgs_part) cudaFree(h->cgs_part);
+    h->cgs_part = nullptr;
+    CKS(dalloc(&h->cgs_part, (size_t)cgs2_scratch(h->cgs_blocks)));
+  }
   CKS(dalloc(&h->bnorm, 4));
   h->m_alloc = m;
   return STMG_OK;
@@ -601,6 +609,7 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), hc(m + 2);
   double hv[2];
   info->iterations = 0; info->rel_residual = 0.0; info->status = STMG_OK; info->seconds = 0.0;
+  if (h->cgs_bar) CK(cudaMemsetAsync(h->cgs_bar, 0, 2 * sizeof(unsigned), s));
   CKS(dev_norm(h, b, D, h->bnorm));
   // the boundary rows of S are the identity: x_D = b_D exactly.  The V-cycle's corrections
   // vanish on boundary dofs, so FGMRES keeps x_D where it starts; start it there.
@@ -638,7 +647,13 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
       Prof pr(h, STMG_PROF_OPERATOR, s);
       CKS(op_apply<double>(h, 0, zj, nullptr, h->w, APPLY, s));
     }
-    {
+    if (h->cgs_blocks > 0 && j + 1 <= cgs2_max_vectors()) {
+      Prof pr(h, STMG_PROF_OTHER, s);
+      // CGS2 and the normalisation of the next basis vector in one cooperative launch
+      CK(launch_cgs2(D, j + 1, h->V, D, h->w, h->cgs_part, h->hcol, h->V + (size_t)(j + 1) * D, h->cgs_bar, h->d_err,
+                     h->cgs_blocks, s));
+      h->launches += 1;
+    } else {
       Prof pr(h, STMG_PROF_OTHER, s);
       const int nb = multidot_blocks(D);
       // CGS2: h = V^T w, w -= V h, twice; h accumulated in hcol
@@ -654,8 +669,17 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
       h->launches += 8;
     }
     CK(cudaMemcpyAsync(hc.data(), h->hcol, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+    int ierr = 0;
+    CK(cudaMemcpyAsync(&ierr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     harvest_all(h);
+    if (ierr) {                       // a bounded wait expired (grid barrier or TMA pipeline)
+      CK(cudaMemset(h->d_err, 0, sizeof(int)));
+      if (h->cgs_bar) CK(cudaMemset(h->cgs_bar, 0, 2 * sizeof(unsigned)));
+      info->status = STMG_ERR_TIMEOUT;
+      info->iterations = j + 1;
+      return STMG_ERR_TIMEOUT;
+    }
     for (int i = 0; i <= j + 1; ++i) {
       if (!std::isfinite(hc[i])) { info->status = STMG_ERR_NONFINITE; info->iterations = j + 1; return info->status; }
       H[(size_t)i * m + j] = hc[i];
@@ -699,6 +723,7 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
   harvest_all(h);
   if (derr) {
     CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    if (h->cgs_bar) CK(cudaMemset(h->cgs_bar, 0, 2 * sizeof(unsigned)));
     info->status = STMG_ERR_TIMEOUT;
     return STMG_ERR_TIMEOUT;
   }
@@ -815,6 +840,11 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
     CK(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
     CKS(dalloc(&h->d_err, 1));
     CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    h->cgs_blocks = cgs2_blocks(h->n_sm);
+    if (h->cgs_blocks > 0) {
+      CKS(dalloc(&h->cgs_bar, 2));
+      CK(cudaMemset(h->cgs_bar, 0, 2 * sizeof(unsigned)));
+    }
   }
   CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
@@ -916,7 +946,7 @@ void stmg_destroy(stmg_handle* h) {
   for (auto& L : h->L) free_level(L);
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(h->V); f(h->Z); f(h->w); f(h->hcol); f(h->tmp); f(h->partial); f(h->bnorm);
-  f(h->xhost_b); f(h->xhost_x); f(h->d_err); f(h->dot_part);
+  f(h->xhost_b); f(h->xhost_x); f(h->d_err); f(h->dot_part); f(h->cgs_bar); f(h->cgs_part);
   for (auto e : h->all_events) cudaEventDestroy(e);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);

@@ -155,6 +155,12 @@ cudaError_t launch_scale_by_inverse(long long n, const double* dev_scalar, const
 cudaError_t launch_sqrt_inplace(double* v, cudaStream_t st);
 
 int multidot_blocks(long long n);
+// one CGS2 Arnoldi step in a cooperative launch (see k_vec.cu); bar: 2 zeroed unsigned
+cudaError_t launch_cgs2(long long n, int nv, const double* V, long long ld, double* w, double* partial, double* hcol,
+                        double* vnext, unsigned* bar, int* err, int nblocks, cudaStream_t st);
+int cgs2_blocks(int n_sm);       // co-resident blocks to launch (0: not available)
+int cgs2_max_vectors();
+int cgs2_scratch(int nblocks);   // doubles of partial-sum scratch for nblocks
 
 // cell tensors (k_cells.cu)
 cudaError_t launch_cells_gather(const CellsParams& p, const double* x, const double* base, const float* inv_scale,

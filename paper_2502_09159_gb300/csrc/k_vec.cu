@@ -150,6 +150,150 @@ cudaError_t launch_multiaxpy(long long n, int nvec, const double* V, long long l
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------
+// One Arnoldi step of FGMRES in a single cooperative launch (CGS2):
+//   h  = V^T w,  w -= V h,  h2 = V^T w,  w -= V h2,  hcol[0..nv) = h + h2,
+//   hcol[nv] = ||w||,  vnext = w / ||w||.
+// Every block owns a contiguous range of rows, so the axpys and the next pass's partial
+// dot products touch only the block's own rows; grid-wide barriers are needed only after
+// partial sums are written (three per step).  Each block sums all blocks' partials itself,
+// in block order (deterministic).  The barriers are bounded: a wait that exceeds its
+// iteration limit raises *err and the kernel returns (the host reports STMG_ERR_TIMEOUT).
+// The launch is cooperative, so all blocks are resident and every barrier completes.
+// ------------------------------------------------------------------------------------
+namespace {
+constexpr int CGS_THREADS = 256;
+constexpr int CGS_MAXV = 256;          // basis vectors per step (gmres_max_iter + 1)
+constexpr long long BARRIER_SPINS = 1LL << 22;
+
+// sense-free generation barrier over all blocks; returns false if the wait timed out
+__device__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks, int* err,
+                             int* sh_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned my = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(count, 1u);
+    bool ok = true;
+    if (arrived == nblocks - 1) {
+      *count = 0;
+      __threadfence();
+      atomicAdd((unsigned*)gen, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == my) {
+        if (++it > BARRIER_SPINS) { atomicExch(err, 2); ok = false; break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *sh_ok = ok ? 1 : 0;
+  }
+  __syncthreads();
+  return *sh_ok != 0;
+}
+
+// partial[blk * nv + i] = sum over rows [lo, hi) of V_i w, eight vectors per sweep over w
+__device__ void block_partials(long long lo, long long hi, int nv, const double* __restrict__ V, long long ld,
+                               const double* __restrict__ w, double* __restrict__ out, double (*red)[8]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int v0 = 0; v0 < nv; v0 += 8) {
+    const int cnt = nv - v0 < 8 ? nv - v0 : 8;
+    double acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = 0.0;
+    for (long long r = lo + threadIdx.x; r < hi; r += CGS_THREADS) {
+      const double wr = w[r];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i < cnt) acc[i] += V[(size_t)(v0 + i) * ld + r] * wr;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      double a = acc[i];
+      for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+      if (lane == 0) red[wid][i] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      double t = 0.0;
+      for (int q = 0; q < CGS_THREADS / 32; ++q) t += red[q][threadIdx.x];
+      out[v0 + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+}  // namespace
+
+// part: 3 regions of gridDim.x * CGS_MAXV doubles (first pass, second pass, norm), so that
+// no region is overwritten while another block may still read it.
+__global__ void __launch_bounds__(CGS_THREADS) k_cgs2(long long n, int nv, const double* __restrict__ V, long long ld,
+                                                    double* __restrict__ w, double* __restrict__ part,
+                                                    double* __restrict__ hcol, double* __restrict__ vnext,
+                                                    unsigned* bar, int* err) {
+  __shared__ double h[CGS_MAXV], h2[CGS_MAXV], red[CGS_THREADS / 32][8];
+  __shared__ int sh_ok;
+  __shared__ double nrm;
+  const unsigned G = gridDim.x;
+  const long long chunk = (n + G - 1) / G;
+  const long long lo = (long long)blockIdx.x * chunk;
+  const long long hi = lo + chunk < n ? lo + chunk : n;
+  unsigned* count = bar;
+  volatile unsigned* gen = bar + 1;
+  const size_t region = (size_t)G * CGS_MAXV;
+  for (int pass = 0; pass < 2; ++pass) {
+    double* pp = part + pass * region;
+    block_partials(lo, hi, nv, V, ld, w, pp + (size_t)blockIdx.x * nv, red);
+    if (!grid_barrier(count, gen, G, err, &sh_ok)) return;
+    double* hh = pass == 0 ? h : h2;
+    for (int i = threadIdx.x; i < nv; i += CGS_THREADS) {
+      double s = 0.0;
+      for (unsigned bb = 0; bb < G; ++bb) s += pp[(size_t)bb * nv + i];
+      hh[i] = s;
+    }
+    __syncthreads();
+    for (long long r = lo + threadIdx.x; r < hi; r += CGS_THREADS) {
+      double s = 0.0;
+      for (int i = 0; i < nv; ++i) s += hh[i] * V[(size_t)i * ld + r];
+      w[r] -= s;
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < nv; i += CGS_THREADS) hcol[i] = h[i] + h2[i];
+  double* pn = part + 2 * region;
+  block_partials(lo, hi, 1, w, 0, w, pn + blockIdx.x, red);
+  if (!grid_barrier(count, gen, G, err, &sh_ok)) return;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (unsigned bb = 0; bb < G; ++bb) t += pn[bb];
+    nrm = sqrt(t);
+    if (blockIdx.x == 0) hcol[nv] = nrm;
+  }
+  __syncthreads();
+  const double inv = 1.0 / nrm;
+  for (long long r = lo + threadIdx.x; r < hi; r += CGS_THREADS) vnext[r] = w[r] * inv;
+}
+
+int cgs2_scratch(int nblocks) { return 3 * nblocks * CGS_MAXV; }
+
+int cgs2_max_vectors() { return CGS_MAXV; }
+
+cudaError_t launch_cgs2(long long n, int nv, const double* V, long long ld, double* w, double* partial, double* hcol,
+                        double* vnext, unsigned* bar, int* err, int nblocks, cudaStream_t st) {
+  if (nv < 1 || nv > CGS_MAXV || nblocks < 1) return cudaErrorInvalidValue;
+  void* args[] = {&n, &nv, &V, &ld, &w, &partial, &hcol, &vnext, &bar, &err};
+  return cudaLaunchCooperativeKernel((const void*)k_cgs2, dim3(nblocks), dim3(CGS_THREADS), args, 0, st);
+}
+
+int cgs2_blocks(int n_sm) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs2, CGS_THREADS, 0) != cudaSuccess || per_sm < 1)
+    return 0;
+  int b = n_sm * (per_sm < 2 ? per_sm : 2);
+  return b > 304 ? 304 : b;
+}
+
 // Coarse direct solve: x = G b, G column-major D x D in FP64; vectors of type T.
 template <typename T>
 __global__ void k_coarse(int D, const double* __restrict__ Gcm, const T* __restrict__ b, T* __restrict__ x) {
