@@ -223,6 +223,17 @@ __device__ void block_partials(long long lo, long long hi, int nv, const double*
     __syncthreads();
   }
 }
+// out[i] = sum_bb part[bb * nv + i], i < nv: one warp per vector, lanes strided over the
+// blocks, then a fixed shuffle tree (deterministic)
+__device__ void sum_partials(const double* __restrict__ part, unsigned G, int nv, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = wid; i < nv; i += CGS_THREADS / 32) {
+    double s = 0.0;
+    for (unsigned bb = lane; bb < G; bb += 32) s += part[(size_t)bb * nv + i];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) out[i] = s;
+  }
+}
 }  // namespace
 
 // part: 3 regions of gridDim.x * CGS_MAXV doubles (first pass, second pass, norm), so that
@@ -246,11 +257,7 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2(long long n, int nv, const
     block_partials(lo, hi, nv, V, ld, w, pp + (size_t)blockIdx.x * nv, red);
     if (!grid_barrier(count, gen, G, err, &sh_ok)) return;
     double* hh = pass == 0 ? h : h2;
-    for (int i = threadIdx.x; i < nv; i += CGS_THREADS) {
-      double s = 0.0;
-      for (unsigned bb = 0; bb < G; ++bb) s += pp[(size_t)bb * nv + i];
-      hh[i] = s;
-    }
+    sum_partials(pp, G, nv, hh);
     __syncthreads();
     for (long long r = lo + threadIdx.x; r < hi; r += CGS_THREADS) {
       double s = 0.0;
@@ -264,10 +271,10 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2(long long n, int nv, const
   double* pn = part + 2 * region;
   block_partials(lo, hi, 1, w, 0, w, pn + blockIdx.x, red);
   if (!grid_barrier(count, gen, G, err, &sh_ok)) return;
+  sum_partials(pn, G, 1, &nrm);
+  __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (unsigned bb = 0; bb < G; ++bb) t += pn[bb];
-    nrm = sqrt(t);
+    nrm = sqrt(nrm);
     if (blockIdx.x == 0) hcol[nv] = nrm;
   }
   __syncthreads();
