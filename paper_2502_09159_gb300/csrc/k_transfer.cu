@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "pdl.h"
 
 namespace stmg {
 
@@ -100,6 +101,8 @@ __device__ __forceinline__ T pres_map(const TransferParams<T>& P, int o, int mf,
 // x_f += P y_c; one block handles P.cpb coarse cells, every phase runs over (cell, entry)
 template <typename T>
 __global__ void k_prolongate(const TransferParams<T> P, const T* __restrict__ yc, T* __restrict__ xf) {
+  pdl_trigger();
+  pdl_wait();
   const int dim = P.dim, npc = P.npc, ns = P.ns, ktc = P.ktc, ktf = P.ktf, cpb = P.cpb;
   const int ncd = dim == 2 ? P.nc * P.nc : P.nc * P.nc * P.nc;
   const int c0 = blockIdx.x * cpb;
@@ -213,6 +216,8 @@ __global__ void k_prolongate(const TransferParams<T> P, const T* __restrict__ yc
 // b_c = P^T r_f (b_c must be zero on entry for the velocity part; pressure is stored)
 template <typename T>
 __global__ void k_restrict(const TransferParams<T> P, const T* __restrict__ rf, T* __restrict__ bc) {
+  pdl_trigger();
+  pdl_wait();
   const int dim = P.dim, npc = P.npc, ns = P.ns, ktc = P.ktc, ktf = P.ktf, cpb = P.cpb;
   const int ncd = dim == 2 ? P.nc * P.nc : P.nc * P.nc * P.nc;
   const int c0 = blockIdx.x * cpb;
@@ -318,6 +323,8 @@ __global__ void k_restrict(const TransferParams<T> P, const T* __restrict__ rf, 
 // constants); same arithmetic as the generic kernels.
 template <typename T, int DIMc, int NPFc, int NPCc, int HTc>
 __global__ void __launch_bounds__(512) k_prolongate_s(const TransferParams<T> P, const T* __restrict__ yc, T* __restrict__ xf) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int dim = DIMc, npc = NPCc, ns = HTc ? 2 * (NPFc - 1) + 1 : NPFc;
   const int ktc = P.ktc, ktf = P.ktf, cpb = P.cpb;
   const int ncd = dim == 2 ? P.nc * P.nc : P.nc * P.nc * P.nc;
@@ -432,6 +439,8 @@ __global__ void __launch_bounds__(512) k_prolongate_s(const TransferParams<T> P,
 
 template <typename T, int DIMc, int NPFc, int NPCc, int HTc>
 __global__ void __launch_bounds__(512) k_restrict_s(const TransferParams<T> P, const T* __restrict__ rf, T* __restrict__ bc) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int dim = DIMc, npc = NPCc, ns = HTc ? 2 * (NPFc - 1) + 1 : NPFc;
   const int ktc = P.ktc, ktf = P.ktf, cpb = P.cpb;
   const int ncd = dim == 2 ? P.nc * P.nc : P.nc * P.nc * P.nc;
@@ -562,8 +571,7 @@ static cudaError_t launch_one(K kern, const TransferParams<T>& p, size_t smem, c
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<(ncd + p.cpb - 1) / p.cpb, transfer_threads(p), smem, st>>>(p, in, out);
-  return cudaGetLastError();
+  return pdl_launch(kern, dim3((ncd + p.cpb - 1) / p.cpb), dim3(transfer_threads(p)), smem, st, p, in, out);
 }
 
 // the (dim, fine nodes, coarse nodes, h/p) shapes of the default hierarchies

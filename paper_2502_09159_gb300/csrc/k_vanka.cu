@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "pdl.h"
 
 namespace stmg {
 
@@ -53,6 +54,8 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_vanka_sweep(const int* __restrict__ dofs, const T* __restrict__ inv,
                                                       const T* __restrict__ res, T* __restrict__ x,
                                                       long long n_patches, int B, int Bc, int ppb, int streaming) {
+  pdl_trigger();
+  pdl_wait();
   using V = typename Vec<T>::type;
   constexpr int VW = Vec<T>::W;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -110,8 +113,8 @@ cudaError_t launch_vanka_sweep(const int* dofs, const T* inv, const T* res, T* x
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_vanka_sweep<T><<<(unsigned)blocks, threads, smem, st>>>(dofs, inv, res, x, n_patches, B, Bc, ppb, streaming);
-  return cudaGetLastError();
+  return pdl_launch(k_vanka_sweep<T>, dim3((unsigned)blocks), dim3(threads), smem, st, dofs, inv, res, x, n_patches,
+                    B, Bc, ppb, streaming);
 }
 
 // Copy the inverse of each patch's class (FP64, row-major B x B) into the per-patch
