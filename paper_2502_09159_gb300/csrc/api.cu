@@ -307,9 +307,9 @@ static void free_level(LevelDev& lv) {
 template <typename T>
 static int op_apply(stmg_handle* h, int l, const T* x, const T* b, T* y, int mode, cudaStream_t s) {
   LevelDev& lv = h->L[l];
-  CK(launch_zero<T>(lv.H.size, y, s));
+  CK(cudaMemsetAsync(y, 0, sizeof(T) * lv.H.size, s));
   CK(launch_apply<T>(lv.H.dim, lv.H.np, lv.pd<T>().ap, x, b, y, mode, s));
-  h->launches += 2;
+  h->launches += 1;
   return STMG_OK;
 }
 
@@ -333,9 +333,9 @@ static int op_sweep(stmg_handle* h, int l, const T* res, T* x, cudaStream_t s) {
 template <typename T>
 static int op_restrict(stmg_handle* h, int l, const T* rf, T* bc, cudaStream_t s) {
   LevelDev& lc = h->L[l + 1];
-  CK(launch_zero<T>(lc.H.size, bc, s));
+  CK(cudaMemsetAsync(bc, 0, sizeof(T) * lc.H.size, s));
   CK(launch_restrict<T>(h->L[l].pd<T>().tp, rf, bc, s));
-  h->launches += 2;
+  h->launches += 1;
   return STMG_OK;
 }
 
@@ -351,7 +351,7 @@ static int op_coarse(stmg_handle* h, const T* b, T* x, cudaStream_t s) {
   LevelDev& lv = h->L.back();
   if (lv.Gacc) {
     CK(launch_coarse_tiled<T>((int)lv.H.size, lv.G, b, x, lv.Gacc, s));
-    h->launches += 3;
+    h->launches += 2;
   } else {
     CK(launch_coarse<T>((int)lv.H.size, lv.G, b, x, s));
     h->launches += 1;
@@ -460,9 +460,9 @@ template <typename T>
 static int vcycle_level(stmg_handle* h, int l, cudaStream_t s) {
   LevelDev& lv = h->L[l];
   PrecDev<T>& P = lv.pd<T>();
+  const size_t bytes = sizeof(T) * lv.H.size;
   if (l == (int)h->L.size() - 1) return op_coarse<T>(h, P.b, P.x, s);
-  CK(launch_zero<T>(lv.H.size, P.x, s));
-  h->launches += 1;
+  CK(cudaMemsetAsync(P.x, 0, bytes, s));
   for (int it = 0; it < h->cfg.nu1; ++it) {          // presmoothing (Eq. Alg:VGMGPre)
     if (it == 0) {
       CKS(op_sweep<T>(h, l, P.b, P.x, s));           // x = 0: the residual is b

@@ -139,8 +139,6 @@ cudaError_t launch_mass_coupling(const MassParams& p, const double* vprev, doubl
 cudaError_t launch_forcing(const ForcingParams& p, const double* fq, double* F, cudaStream_t st);
 
 // vector kernels
-template <typename T>
-cudaError_t launch_zero(long long n, T* out, cudaStream_t st);   // out = 0 (programmatic launch)
 template <typename Ti, typename To>
 cudaError_t launch_convert(long long n, const Ti* in, To* out, cudaStream_t st);
 cudaError_t launch_scale(long long n, double a, const double* x, double* y, cudaStream_t st);

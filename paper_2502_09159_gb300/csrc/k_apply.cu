@@ -21,7 +21,6 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
-#include "pdl.h"
 
 namespace stmg {
 
@@ -46,8 +45,6 @@ template <typename T, int DIM, int NP>
 __global__ void __launch_bounds__(256) k_apply(const ApplyParams<T> P, const T* __restrict__ x,
                                                const T* __restrict__ b, T* __restrict__ y,
                                                int mode) {
-  pdl_trigger();
-  pdl_wait();
   using S = Shape<DIM, NP>;
   constexpr int NQ = S::NQ, NL = S::NL;
   const int kt = P.kt, npm = P.npm, n = P.n, G = P.G;
@@ -73,6 +70,7 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams<T> P, const T* 
   // ---- gather ------------------------------------------------------------------------
   {
     const int tot = nc * VS;
+#pragma unroll 4
     for (int w = threadIdx.x; w < tot; w += blockDim.x) {
       int t = w;
       const int ix = t % NP; t /= NP;
@@ -274,6 +272,7 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams<T> P, const T* 
   {
     const int tot = nc * VS;
     const bool res = mode == RESIDUAL || mode == LIFT;
+#pragma unroll 4
     for (int w = threadIdx.x; w < tot; w += blockDim.x) {
       int t = w;
       const int ix = t % NP; t /= NP;
@@ -339,7 +338,8 @@ static cudaError_t launch_apply_t(const ApplyParams<T>& p, const T* x, const T* 
   int threads = ((lines + 31) / 32) * 32;
   threads = threads < 64 ? 64 : (threads > 256 ? 256 : threads);
   const int blocks = (ncells + p.cpb - 1) / p.cpb;
-  return pdl_launch(k_apply<T, DIM, NP>, dim3(blocks), dim3(threads), smem, st, p, x, b, y, mode);
+  k_apply<T, DIM, NP><<<blocks, threads, smem, st>>>(p, x, b, y, mode);
+  return cudaGetLastError();
 }
 
 template <typename T>

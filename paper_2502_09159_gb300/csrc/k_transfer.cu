@@ -17,7 +17,6 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
-#include "pdl.h"
 
 namespace stmg {
 
@@ -101,8 +100,6 @@ __device__ __forceinline__ T pres_map(const TransferParams<T>& P, int o, int mf,
 // x_f += P y_c; one block handles P.cpb coarse cells, every phase runs over (cell, entry)
 template <typename T>
 __global__ void k_prolongate(const TransferParams<T> P, const T* __restrict__ yc, T* __restrict__ xf) {
-  pdl_trigger();
-  pdl_wait();
   const int dim = P.dim, npc = P.npc, ns = P.ns, ktc = P.ktc, ktf = P.ktf, cpb = P.cpb;
   const int ncd = dim == 2 ? P.nc * P.nc : P.nc * P.nc * P.nc;
   const int c0 = blockIdx.x * cpb;
@@ -119,6 +116,7 @@ __global__ void k_prolongate(const TransferParams<T> P, const T* __restrict__ yc
   T* X2 = X1 + cpb * sx;
   T* PC = X2 + cpb * sx;                     // [cell][ktc][npmc]
   T* PT = PC + cpb * sp0;                    // [cell][ktf][npmc]
+#pragma unroll 4
   for (int w = threadIdx.x; w < ncl * s0; w += blockDim.x) {
     const int cl = w / s0, r = w % s0;
     const int node = r % nqc, t = r / nqc, comp = t % dim, a = t / dim;
@@ -187,6 +185,7 @@ __global__ void k_prolongate(const TransferParams<T> P, const T* __restrict__ yc
     __syncthreads();
     XF = X1;
   }
+#pragma unroll 4
   for (int w = threadIdx.x; w < ncl * kd * nsd; w += blockDim.x) {
     const int e = w % nsd, t = w / nsd;
     const int cl = t / kd, tt = t % kd, comp = tt % dim, af = tt / dim;
@@ -216,8 +215,6 @@ __global__ void k_prolongate(const TransferParams<T> P, const T* __restrict__ yc
 // b_c = P^T r_f (b_c must be zero on entry for the velocity part; pressure is stored)
 template <typename T>
 __global__ void k_restrict(const TransferParams<T> P, const T* __restrict__ rf, T* __restrict__ bc) {
-  pdl_trigger();
-  pdl_wait();
   const int dim = P.dim, npc = P.npc, ns = P.ns, ktc = P.ktc, ktf = P.ktf, cpb = P.cpb;
   const int ncd = dim == 2 ? P.nc * P.nc : P.nc * P.nc * P.nc;
   const int c0 = blockIdx.x * cpb;
@@ -232,6 +229,7 @@ __global__ void k_restrict(const TransferParams<T> P, const T* __restrict__ rf, 
   T* F1 = F0 + cpb * sf;                     // [cell][ktf][dim][nsd]
   T* C1 = F1 + cpb * sf;                     // [cell][ktf][dim][nqc]
   T* PF = C1 + cpb * sc;                     // [cell][ktf][npmc]
+#pragma unroll 4
   for (int w = threadIdx.x; w < ncl * sf; w += blockDim.x) {
     const int cl = w / sf, r = w % sf;
     const int e = r % nsd, t = r / nsd, comp = t % dim, af = t / dim;
@@ -323,8 +321,6 @@ __global__ void k_restrict(const TransferParams<T> P, const T* __restrict__ rf, 
 // constants); same arithmetic as the generic kernels.
 template <typename T, int DIMc, int NPFc, int NPCc, int HTc>
 __global__ void __launch_bounds__(512) k_prolongate_s(const TransferParams<T> P, const T* __restrict__ yc, T* __restrict__ xf) {
-  pdl_trigger();
-  pdl_wait();
   constexpr int dim = DIMc, npc = NPCc, ns = HTc ? 2 * (NPFc - 1) + 1 : NPFc;
   const int ktc = P.ktc, ktf = P.ktf, cpb = P.cpb;
   const int ncd = dim == 2 ? P.nc * P.nc : P.nc * P.nc * P.nc;
@@ -342,6 +338,7 @@ __global__ void __launch_bounds__(512) k_prolongate_s(const TransferParams<T> P,
   T* X2 = X1 + cpb * sx;
   T* PC = X2 + cpb * sx;                     // [cell][ktc][npmc]
   T* PT = PC + cpb * sp0;                    // [cell][ktf][npmc]
+#pragma unroll 4
   for (int w = threadIdx.x; w < ncl * s0; w += blockDim.x) {
     const int cl = w / s0, r = w % s0;
     const int node = r % nqc, t = r / nqc, comp = t % dim, a = t / dim;
@@ -410,6 +407,7 @@ __global__ void __launch_bounds__(512) k_prolongate_s(const TransferParams<T> P,
     __syncthreads();
     XF = X1;
   }
+#pragma unroll 4
   for (int w = threadIdx.x; w < ncl * kd * nsd; w += blockDim.x) {
     const int e = w % nsd, t = w / nsd;
     const int cl = t / kd, tt = t % kd, comp = tt % dim, af = tt / dim;
@@ -439,8 +437,6 @@ __global__ void __launch_bounds__(512) k_prolongate_s(const TransferParams<T> P,
 
 template <typename T, int DIMc, int NPFc, int NPCc, int HTc>
 __global__ void __launch_bounds__(512) k_restrict_s(const TransferParams<T> P, const T* __restrict__ rf, T* __restrict__ bc) {
-  pdl_trigger();
-  pdl_wait();
   constexpr int dim = DIMc, npc = NPCc, ns = HTc ? 2 * (NPFc - 1) + 1 : NPFc;
   const int ktc = P.ktc, ktf = P.ktf, cpb = P.cpb;
   const int ncd = dim == 2 ? P.nc * P.nc : P.nc * P.nc * P.nc;
@@ -456,6 +452,7 @@ __global__ void __launch_bounds__(512) k_restrict_s(const TransferParams<T> P, c
   T* F1 = F0 + cpb * sf;                     // [cell][ktf][dim][nsd]
   T* C1 = F1 + cpb * sf;                     // [cell][ktf][dim][nqc]
   T* PF = C1 + cpb * sc;                     // [cell][ktf][npmc]
+#pragma unroll 4
   for (int w = threadIdx.x; w < ncl * sf; w += blockDim.x) {
     const int cl = w / sf, r = w % sf;
     const int e = r % nsd, t = r / nsd, comp = t % dim, af = t / dim;
@@ -571,7 +568,8 @@ static cudaError_t launch_one(K kern, const TransferParams<T>& p, size_t smem, c
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  return pdl_launch(kern, dim3((ncd + p.cpb - 1) / p.cpb), dim3(transfer_threads(p)), smem, st, p, in, out);
+  kern<<<(ncd + p.cpb - 1) / p.cpb, transfer_threads(p), smem, st>>>(p, in, out);
+  return cudaGetLastError();
 }
 
 // the (dim, fine nodes, coarse nodes, h/p) shapes of the default hierarchies

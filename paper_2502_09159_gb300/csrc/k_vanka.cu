@@ -19,7 +19,6 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
-#include "pdl.h"
 
 namespace stmg {
 
@@ -54,13 +53,12 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_vanka_sweep(const int* __restrict__ dofs, const T* __restrict__ inv,
                                                       const T* __restrict__ res, T* __restrict__ x,
                                                       long long n_patches, int B, int Bc, int ppb, int streaming) {
-  pdl_trigger();
-  pdl_wait();
   using V = typename Vec<T>::type;
   constexpr int VW = Vec<T>::W;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* rs = reinterpret_cast<T*>(smraw);                // [ppb][Bc]
   const long long p0 = (long long)blockIdx.x * ppb;
+#pragma unroll 4
   for (int t = threadIdx.x; t < ppb * Bc; t += blockDim.x) {
     const int pl = t / Bc, i = t % Bc;
     const long long p = p0 + pl;
@@ -113,8 +111,8 @@ cudaError_t launch_vanka_sweep(const int* dofs, const T* inv, const T* res, T* x
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  return pdl_launch(k_vanka_sweep<T>, dim3((unsigned)blocks), dim3(threads), smem, st, dofs, inv, res, x, n_patches,
-                    B, Bc, ppb, streaming);
+  k_vanka_sweep<T><<<(unsigned)blocks, threads, smem, st>>>(dofs, inv, res, x, n_patches, B, Bc, ppb, streaming);
+  return cudaGetLastError();
 }
 
 // Copy the inverse of each patch's class (FP64, row-major B x B) into the per-patch

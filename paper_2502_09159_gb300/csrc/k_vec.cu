@@ -7,7 +7,6 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
-#include "pdl.h"
 
 namespace stmg {
 
@@ -16,19 +15,8 @@ constexpr int RED_THREADS = 256;
 constexpr int MD_VEC = 8;   // basis vectors handled per multidot pass
 }
 
-// out[0 .. n) = 0, as a kernel so that it joins the programmatic launch chain
-template <typename T>
-__global__ void k_zero(long long n, T* __restrict__ out) {
-  pdl_trigger();
-  pdl_wait();
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = T(0);
-}
-
 template <typename Ti, typename To>
 __global__ void k_convert(long long n, const Ti* __restrict__ in, To* __restrict__ out) {
-  pdl_trigger();
-  pdl_wait();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = (To)in[i];
 }
@@ -41,15 +29,9 @@ static unsigned grid_for(long long n) {
 
 template <typename Ti, typename To>
 cudaError_t launch_convert(long long n, const Ti* in, To* out, cudaStream_t st) {
-  return pdl_launch(k_convert<Ti, To>, dim3(grid_for(n)), dim3(256), 0, st, n, in, out);
+  k_convert<Ti, To><<<grid_for(n), 256, 0, st>>>(n, in, out);
+  return cudaGetLastError();
 }
-template <typename T>
-cudaError_t launch_zero(long long n, T* out, cudaStream_t st) {
-  return pdl_launch(k_zero<T>, dim3(grid_for(n)), dim3(256), 0, st, n, out);
-}
-template cudaError_t launch_zero<double>(long long, double*, cudaStream_t);
-template cudaError_t launch_zero<float>(long long, float*, cudaStream_t);
-
 template cudaError_t launch_convert<double, float>(long long, const double*, float*, cudaStream_t);
 template cudaError_t launch_convert<float, double>(long long, const float*, double*, cudaStream_t);
 
@@ -220,6 +202,7 @@ __device__ void block_partials(long long lo, long long hi, int nv, const double*
     double acc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i] = 0.0;
+#pragma unroll 4
     for (long long r = lo + threadIdx.x; r < hi; r += CGS_THREADS) {
       const double wr = w[r];
 #pragma unroll
@@ -247,6 +230,7 @@ __device__ void sum_partials(const double* __restrict__ part, unsigned G, int nv
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int i = wid; i < nv; i += CGS_THREADS / 32) {
     double s = 0.0;
+#pragma unroll 8
     for (unsigned bb = lane; bb < G; bb += 32) s += part[(size_t)bb * nv + i];
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if (lane == 0) out[i] = s;
@@ -277,8 +261,10 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2(long long n, int nv, const
     double* hh = pass == 0 ? h : h2;
     sum_partials(pp, G, nv, hh);
     __syncthreads();
+#pragma unroll 4
     for (long long r = lo + threadIdx.x; r < hi; r += CGS_THREADS) {
       double s = 0.0;
+#pragma unroll 8
       for (int i = 0; i < nv; ++i) s += hh[i] * V[(size_t)i * ld + r];
       w[r] -= s;
     }
@@ -322,8 +308,6 @@ int cgs2_blocks(int n_sm) {
 // Coarse direct solve: x = G b, G column-major D x D in FP64; vectors of type T.
 template <typename T>
 __global__ void k_coarse(int D, const double* __restrict__ Gcm, const T* __restrict__ b, T* __restrict__ x) {
-  pdl_trigger();
-  pdl_wait();
   extern __shared__ double bs[];
   for (int i = threadIdx.x; i < D; i += blockDim.x) bs[i] = (double)b[i];
   __syncthreads();
@@ -340,8 +324,6 @@ __global__ void k_coarse(int D, const double* __restrict__ Gcm, const T* __restr
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse_tiled(int D, const double* __restrict__ Gcm,
                                                       const T* __restrict__ b, double* __restrict__ acc) {
-  pdl_trigger();
-  pdl_wait();
   constexpr int CT = 64;
   __shared__ double bs[CT];
   const int c0 = blockIdx.y * CT;
@@ -365,20 +347,18 @@ __global__ void __launch_bounds__(256) k_coarse_tiled(int D, const double* __res
 
 template <typename T>
 __global__ void k_coarse_finish(int D, const double* __restrict__ acc, T* __restrict__ x) {
-  pdl_trigger();
-  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < D) x[i] = (T)acc[i];
 }
 
 template <typename T>
 cudaError_t launch_coarse_tiled(int D, const double* Gcm, const T* b, T* x, double* acc, cudaStream_t st) {
-  cudaError_t e = launch_zero(D, acc, st);
+  cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * D, st);
   if (e != cudaSuccess) return e;
   const int nr = (D + 255) / 256, nc = (D + 63) / 64;
-  e = pdl_launch(k_coarse_tiled<T>, dim3(nr, nc), dim3(256), 0, st, D, Gcm, b, acc);
-  if (e != cudaSuccess) return e;
-  return pdl_launch(k_coarse_finish<T>, dim3(nr), dim3(256), 0, st, D, (const double*)acc, x);
+  k_coarse_tiled<T><<<dim3(nr, nc), 256, 0, st>>>(D, Gcm, b, acc);
+  k_coarse_finish<T><<<nr, 256, 0, st>>>(D, acc, x);
+  return cudaGetLastError();
 }
 template cudaError_t launch_coarse_tiled<double>(int, const double*, const double*, double*, double*, cudaStream_t);
 template cudaError_t launch_coarse_tiled<float>(int, const double*, const float*, float*, double*, cudaStream_t);
@@ -391,7 +371,8 @@ cudaError_t launch_coarse(int D, const double* Gcm, const T* b, T* x, cudaStream
     cudaError_t e = cudaFuncSetAttribute(k_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  return pdl_launch(k_coarse<T>, dim3(blocks), dim3(256), smem, st, D, Gcm, b, x);
+  k_coarse<T><<<blocks, 256, smem, st>>>(D, Gcm, b, x);
+  return cudaGetLastError();
 }
 template cudaError_t launch_coarse<double>(int, const double*, const double*, double*, cudaStream_t);
 template cudaError_t launch_coarse<float>(int, const double*, const float*, float*, cudaStream_t);
