@@ -70,7 +70,6 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams<T> P, const T* 
   // ---- gather ------------------------------------------------------------------------
   {
     const int tot = nc * VS;
-#pragma unroll 4
     for (int w = threadIdx.x; w < tot; w += blockDim.x) {
       int t = w;
       const int ix = t % NP; t /= NP;
@@ -272,7 +271,6 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams<T> P, const T* 
   {
     const int tot = nc * VS;
     const bool res = mode == RESIDUAL || mode == LIFT;
-#pragma unroll 4
     for (int w = threadIdx.x; w < tot; w += blockDim.x) {
       int t = w;
       const int ix = t % NP; t /= NP;

@@ -116,7 +116,6 @@ __global__ void k_prolongate(const TransferParams<T> P, const T* __restrict__ yc
   T* X2 = X1 + cpb * sx;
   T* PC = X2 + cpb * sx;                     // [cell][ktc][npmc]
   T* PT = PC + cpb * sp0;                    // [cell][ktf][npmc]
-#pragma unroll 4
   for (int w = threadIdx.x; w < ncl * s0; w += blockDim.x) {
     const int cl = w / s0, r = w % s0;
     const int node = r % nqc, t = r / nqc, comp = t % dim, a = t / dim;
@@ -185,7 +184,6 @@ __global__ void k_prolongate(const TransferParams<T> P, const T* __restrict__ yc
     __syncthreads();
     XF = X1;
   }
-#pragma unroll 4
   for (int w = threadIdx.x; w < ncl * kd * nsd; w += blockDim.x) {
     const int e = w % nsd, t = w / nsd;
     const int cl = t / kd, tt = t % kd, comp = tt % dim, af = tt / dim;
@@ -229,7 +227,6 @@ __global__ void k_restrict(const TransferParams<T> P, const T* __restrict__ rf, 
   T* F1 = F0 + cpb * sf;                     // [cell][ktf][dim][nsd]
   T* C1 = F1 + cpb * sf;                     // [cell][ktf][dim][nqc]
   T* PF = C1 + cpb * sc;                     // [cell][ktf][npmc]
-#pragma unroll 4
   for (int w = threadIdx.x; w < ncl * sf; w += blockDim.x) {
     const int cl = w / sf, r = w % sf;
     const int e = r % nsd, t = r / nsd, comp = t % dim, af = t / dim;
@@ -338,7 +335,6 @@ __global__ void __launch_bounds__(512) k_prolongate_s(const TransferParams<T> P,
   T* X2 = X1 + cpb * sx;
   T* PC = X2 + cpb * sx;                     // [cell][ktc][npmc]
   T* PT = PC + cpb * sp0;                    // [cell][ktf][npmc]
-#pragma unroll 4
   for (int w = threadIdx.x; w < ncl * s0; w += blockDim.x) {
     const int cl = w / s0, r = w % s0;
     const int node = r % nqc, t = r / nqc, comp = t % dim, a = t / dim;
@@ -407,7 +403,6 @@ __global__ void __launch_bounds__(512) k_prolongate_s(const TransferParams<T> P,
     __syncthreads();
     XF = X1;
   }
-#pragma unroll 4
   for (int w = threadIdx.x; w < ncl * kd * nsd; w += blockDim.x) {
     const int e = w % nsd, t = w / nsd;
     const int cl = t / kd, tt = t % kd, comp = tt % dim, af = tt / dim;
@@ -452,7 +447,6 @@ __global__ void __launch_bounds__(512) k_restrict_s(const TransferParams<T> P, c
   T* F1 = F0 + cpb * sf;                     // [cell][ktf][dim][nsd]
   T* C1 = F1 + cpb * sf;                     // [cell][ktf][dim][nqc]
   T* PF = C1 + cpb * sc;                     // [cell][ktf][npmc]
-#pragma unroll 4
   for (int w = threadIdx.x; w < ncl * sf; w += blockDim.x) {
     const int cl = w / sf, r = w % sf;
     const int e = r % nsd, t = r / nsd, comp = t % dim, af = t / dim;

@@ -58,7 +58,6 @@ __global__ void __launch_bounds__(1024) k_vanka_sweep(const int* __restrict__ do
   extern __shared__ __align__(16) unsigned char smraw[];
   T* rs = reinterpret_cast<T*>(smraw);                // [ppb][Bc]
   const long long p0 = (long long)blockIdx.x * ppb;
-#pragma unroll 4
   for (int t = threadIdx.x; t < ppb * Bc; t += blockDim.x) {
     const int pl = t / Bc, i = t % Bc;
     const long long p = p0 + pl;

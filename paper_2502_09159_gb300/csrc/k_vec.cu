@@ -202,7 +202,6 @@ __device__ void block_partials(long long lo, long long hi, int nv, const double*
     double acc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i] = 0.0;
-#pragma unroll 4
     for (long long r = lo + threadIdx.x; r < hi; r += CGS_THREADS) {
       const double wr = w[r];
 #pragma unroll
@@ -230,7 +229,6 @@ __device__ void sum_partials(const double* __restrict__ part, unsigned G, int nv
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int i = wid; i < nv; i += CGS_THREADS / 32) {
     double s = 0.0;
-#pragma unroll 8
     for (unsigned bb = lane; bb < G; bb += 32) s += part[(size_t)bb * nv + i];
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if (lane == 0) out[i] = s;
@@ -261,10 +259,8 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2(long long n, int nv, const
     double* hh = pass == 0 ? h : h2;
     sum_partials(pp, G, nv, hh);
     __syncthreads();
-#pragma unroll 4
     for (long long r = lo + threadIdx.x; r < hi; r += CGS_THREADS) {
       double s = 0.0;
-#pragma unroll 8
       for (int i = 0; i < nv; ++i) s += hh[i] * V[(size_t)i * ld + r];
       w[r] -= s;
     }
