@@ -361,6 +361,14 @@ int  stmg_autotune(stmg_handle* h);
    stmg_solve_slab checks the same flag itself. */
 int  stmg_device_status(stmg_handle* h);
 
+/* Testing hook for failure handling without a GPU fault: arms the grid barrier of the next
+   stmg_solve_slab's first Arnoldi step (the cooperative CGS2 launch) so that it cannot
+   complete.  The barrier's bounded waits expire (after about a second), the kernel
+   returns, and the solve reports STMG_ERR_TIMEOUT; the handle stays usable and the next
+   solve runs normally.  STMG_ERR_UNIMPLEMENTED if the handle does not use the cooperative
+   step. */
+int  stmg_inject_wait_fault(stmg_handle* h);
+
 /* Total number of this library's kernel launches since the handle was created. */
 long long stmg_kernel_launches(const stmg_handle* h);
 

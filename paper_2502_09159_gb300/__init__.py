@@ -422,6 +422,10 @@ class SpaceTimeMG:
         """Synchronise; raise StmgError if a bounded device-side wait expired."""
         check("stmg_device_status", self._lib.stmg_device_status(self._h))
 
+    def inject_wait_fault(self):
+        """Testing hook: the next solve's grid barrier cannot complete and times out."""
+        check("stmg_inject_wait_fault", self._lib.stmg_inject_wait_fault(self._h))
+
     @property
     def kernel_launches(self) -> int:
         return int(self._lib.stmg_kernel_launches(self._h))

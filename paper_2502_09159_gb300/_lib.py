@@ -69,6 +69,7 @@ _SIGS = {
     "stmg_set_profiling": (_I, [_VP, _I]),
     "stmg_get_profile": (_I, [_VP, C.POINTER(_D), C.POINTER(_LL), _I]),
     "stmg_kernel_launches": (_LL, [_VP]),
+    "stmg_inject_wait_fault": (_I, [_VP]),
     "stmg_device_status": (_I, [_VP]),
     "stmg_autotune": (_I, [_VP]),
     "stmg_sweep_bytes": (_I, [_VP, _I, _I, C.POINTER(_D)]),

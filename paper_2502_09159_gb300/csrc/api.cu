@@ -64,6 +64,7 @@ struct stmg_handle {
   unsigned* cgs_bar = nullptr;    // grid barrier of the cooperative CGS2 step (count, generation)
   double* cgs_part = nullptr;     // its partial sums
   int cgs_blocks = 0;             // co-resident blocks of that launch (0: use the split kernels)
+  int inject_wait_fault = 0;      // testing hook: arm the next grid barrier so that it cannot complete
   int n_sm = 1;
   ForcingParams fp{};
   MassParams mp{};
@@ -610,6 +611,11 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
   double hv[2];
   info->iterations = 0; info->rel_residual = 0.0; info->status = STMG_OK; info->seconds = 0.0;
   if (h->cgs_bar) CK(cudaMemsetAsync(h->cgs_bar, 0, 2 * sizeof(unsigned), s));
+  if (h->inject_wait_fault && h->cgs_bar) {
+    // an arrival count far above the block count: no block is ever the last to arrive
+    CK(cudaMemsetAsync(h->cgs_bar, 0x7f, sizeof(unsigned), s));
+    h->inject_wait_fault = 0;
+  }
   CKS(dev_norm(h, b, D, h->bnorm));
   // the boundary rows of S are the identity: x_D = b_D exactly.  The V-cycle's corrections
   // vanish on boundary dofs, so FGMRES keeps x_D where it starts; start it there.
@@ -1154,6 +1160,13 @@ int stmg_get_profile(stmg_handle* h, double* ms, long long* n, int reset) {
     std::memset(h->prof_ms, 0, sizeof(h->prof_ms));
     std::memset(h->prof_n, 0, sizeof(h->prof_n));
   }
+  return STMG_OK;
+}
+
+int stmg_inject_wait_fault(stmg_handle* h) {
+  if (!h) return STMG_ERR_ARG;
+  if (!h->cgs_bar) return STMG_ERR_UNIMPLEMENTED;
+  h->inject_wait_fault = 1;
   return STMG_OK;
 }
 

@@ -301,6 +301,34 @@ def test_error_statuses():
         g.apply(torch.zeros(3, dtype=torch.float64, device="cuda"))
 
 
+def test_bounded_wait_timeout_is_reported_and_recoverable():
+    """Failure handling without a GPU fault: the Arnoldi step's grid barrier is armed so
+    that it cannot complete; its bounded waits expire, the solve reports STMG_ERR_TIMEOUT,
+    and the next solve on the same handle converges."""
+    g = stmg.SpaceTimeMG(dim=2, n_cells=8, r=1, k=1)
+    b = g.slab_rhs(g.forcing(manufactured_2d().forcing, 0))
+    _, ref = g.solve_slab(b)
+    g.inject_wait_fault()
+    _, info = g.solve_slab(b)
+    assert info["status"] == stmg._lib.ERR_TIMEOUT
+    _, again = g.solve_slab(b)
+    assert again["status"] == 0 and again["iterations"] == ref["iterations"]
+    g.device_status()
+    g.close()
+
+
+def test_out_of_memory_is_reported():
+    """3D 64^3 Q3/P2 DG(2) with FP64 patch inverses needs about 770 GB: stmg_create must
+    fail with STMG_ERR_OOM (and leave the device usable)."""
+    with pytest.raises(stmg.StmgError) as e:
+        stmg.SpaceTimeMG(dim=3, n_cells=64, r=2, k=2, precisions=("fp64",), precond_precision="fp64",
+                         autotune=False, use_graphs=False)
+    assert e.value.status == stmg._lib.ERR_OOM
+    g = stmg.SpaceTimeMG(dim=2, n_cells=4, r=1, k=1)
+    assert g.apply(torch.ones(g.size(0), dtype=torch.float64, device="cuda")).abs().sum().item() > 0
+    g.close()
+
+
 def test_profiling_counters():
     g = stmg.SpaceTimeMG(dim=2, n_cells=8, r=2, k=1, precond_precision="fp32")
     g.set_profiling(2)
