@@ -309,8 +309,9 @@ def test_bounded_wait_timeout_is_reported_and_recoverable():
     b = g.slab_rhs(g.forcing(manufactured_2d().forcing, 0))
     _, ref = g.solve_slab(b)
     g.inject_wait_fault()
-    _, info = g.solve_slab(b)
-    assert info["status"] == stmg._lib.ERR_TIMEOUT
+    with pytest.raises(stmg.StmgError) as e:
+        g.solve_slab(b)
+    assert e.value.status == stmg._lib.ERR_TIMEOUT
     _, again = g.solve_slab(b)
     assert again["status"] == 0 and again["iterations"] == ref["iterations"]
     g.device_status()
