@@ -310,6 +310,13 @@ int  stmg_cells_channels(const stmg_handle* h, int lvl, int* C);
 int  stmg_cells_gather(stmg_handle* h, int lvl, const double* x, const double* base, const float* inv_scale,
                        float* cells);
 
+/* The same gather into columns channel_offset .. channel_offset + C - 1 of a wider tensor
+   with rows of row_stride floats (cells[c * row_stride + channel_offset + ch]), e.g. to
+   stack the cell tensors of several slabs along the channels.  row_stride >=
+   channel_offset + C, else STMG_ERR_ARG. */
+int  stmg_cells_gather_strided(stmg_handle* h, int lvl, const double* x, const double* base,
+                               const float* inv_scale, float* cells, long long row_stride, int channel_offset);
+
 /* x += the average over the copies of each entry of scale[ch] * cells[c][ch] (the
    inverse of the gather on consistent tensors), on every non-boundary entry; boundary
    velocity entries of x are left unchanged.  Sums run in FP64 in increasing cell order.

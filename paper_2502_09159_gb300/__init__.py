@@ -317,6 +317,25 @@ class SpaceTimeMG:
             _ptr(inv_scale) if inv_scale is not None else None, _ptr(cells)))
         return cells
 
+    def cells_gather_strided(self, x, out, row_stride: int, offset: int, base=None, inv_scale=None, lvl: int = 0):
+        """Gather into columns offset .. offset + C - 1 of out (rows of row_stride floats)."""
+        torch = _torch()
+        if x.dtype != torch.float64:
+            raise ValueError("x: float64")
+        self._vec(x, lvl, "x")
+        if base is not None:
+            self._vec(base, lvl, "base")
+        Cn = self.n_channels(lvl)
+        ncell = self.levels[lvl]["n"] ** self.dim
+        self._f32(out, ncell * row_stride, "out")
+        if inv_scale is not None:
+            self._f32(inv_scale, Cn, "inv_scale")
+        self._stream()
+        check("stmg_cells_gather_strided", self._lib.stmg_cells_gather_strided(
+            self._h, lvl, _ptr(x), _ptr(base) if base is not None else None,
+            _ptr(inv_scale) if inv_scale is not None else None, _ptr(out), row_stride, offset))
+        return out
+
     def cells_scatter_add(self, cells, x, scale=None, lvl: int = 0):
         """x += average over copies of scale * cells (boundary entries untouched)."""
         self._vec(x, lvl, "x")

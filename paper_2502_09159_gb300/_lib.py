@@ -77,6 +77,7 @@ _SIGS = {
     "stmg_cells_channels": (_I, [_VP, _I, C.POINTER(_I)]),
     "stmg_cells_gather": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "stmg_cells_scatter_add": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "stmg_cells_gather_strided": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _LL, _I]),
     "stmg_cells_gather_adjoint": (_I, [_VP, _I, _VP, _VP, _VP]),
     "stmg_dot": (_I, [_VP, _LL, _VP, _VP, _VP]),
     "stmg_extrapolate": (_I, [_VP, _I, _VP, _VP]),

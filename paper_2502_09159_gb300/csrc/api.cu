@@ -1202,7 +1202,18 @@ int stmg_cells_channels(const stmg_handle* h, int lvl, int* C) {
 int stmg_cells_gather(stmg_handle* h, int lvl, const double* x, const double* base, const float* inv_scale,
                       float* cells) {
   if (!h || !x || !cells || lvl < 0 || lvl >= (int)h->L.size()) return STMG_ERR_ARG;
-  CK(launch_cells_gather(cells_params(h->L[lvl].H), x, base, inv_scale, cells, h->st));
+  const CellsParams p = cells_params(h->L[lvl].H);
+  CK(launch_cells_gather(p, x, base, inv_scale, cells, p.C, 0, h->st));
+  h->launches += 1;
+  return STMG_OK;
+}
+
+int stmg_cells_gather_strided(stmg_handle* h, int lvl, const double* x, const double* base, const float* inv_scale,
+                              float* cells, long long row_stride, int channel_offset) {
+  if (!h || !x || !cells || lvl < 0 || lvl >= (int)h->L.size()) return STMG_ERR_ARG;
+  const CellsParams p = cells_params(h->L[lvl].H);
+  if (channel_offset < 0 || row_stride < channel_offset + p.C) return STMG_ERR_ARG;
+  CK(launch_cells_gather(p, x, base, inv_scale, cells, row_stride, channel_offset, h->st));
   h->launches += 1;
   return STMG_OK;
 }

@@ -163,8 +163,9 @@ int cgs2_max_vectors();
 int cgs2_scratch(int nblocks);   // doubles of partial-sum scratch for nblocks
 
 // cell tensors (k_cells.cu)
+// cells[c * ld + offset + ch]; ld = C, offset = 0 for a plain [n_cells][C] tensor
 cudaError_t launch_cells_gather(const CellsParams& p, const double* x, const double* base, const float* inv_scale,
-                                float* cells, cudaStream_t st);
+                                float* cells, long long ld, int offset, cudaStream_t st);
 cudaError_t launch_cells_scatter_add(const CellsParams& p, const float* cells, const float* scale, double* x,
                                      cudaStream_t st);
 cudaError_t launch_cells_gather_adjoint(const CellsParams& p, const double* x, const float* scale, float* cells,

@@ -17,7 +17,8 @@ static unsigned grid_of(long long n, int threads) {
 }
 
 __global__ void k_cells_gather(CellsParams p, const double* __restrict__ x, const double* __restrict__ base,
-                               const float* __restrict__ inv_scale, float* __restrict__ cells) {
+                               const float* __restrict__ inv_scale, float* __restrict__ cells, long long ld,
+                               int offset) {
   const long long total = p.n_cells * p.C;
   const int nvch = p.kt * p.dim * p.Pn;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -41,13 +42,13 @@ __global__ void k_cells_gather(CellsParams p, const double* __restrict__ x, cons
     }
     double v = x[g] - (base ? base[g] : 0.0);
     if (inv_scale) v *= (double)inv_scale[ch];
-    cells[e] = (float)v;
+    cells[c * ld + offset + ch] = (float)v;
   }
 }
 
 cudaError_t launch_cells_gather(const CellsParams& p, const double* x, const double* base, const float* inv_scale,
-                                float* cells, cudaStream_t st) {
-  k_cells_gather<<<grid_of(p.n_cells * p.C, 256), 256, 0, st>>>(p, x, base, inv_scale, cells);
+                                float* cells, long long ld, int offset, cudaStream_t st) {
+  k_cells_gather<<<grid_of(p.n_cells * p.C, 256), 256, 0, st>>>(p, x, base, inv_scale, cells, ld, offset);
   return cudaGetLastError();
 }
 

@@ -204,22 +204,25 @@ class WarmStart:
     MODES = ("zero", "extrapolate", "net")
 
     def __init__(self, mg, hidden: int = 64, layers: int = 4, max_batch: int = 8, capacity: int = 128,
-                 seed: int = 0, skip: bool = True, residual_pairs: bool = True):
+                 seed: int = 0, skip: bool = True, residual_pairs: bool = True, history: int = 1):
         torch = _torch()
         if mg.dim != 2:
             raise NotImplementedError("the learned guess uses 2D convolutions (dim = 2 only)")
         self.mg = mg
         self.n = mg.levels[0]["n"]
         self.C = mg.n_channels(0)
-        self.net = ConvNet(self.n, self.n, self.C, self.C, hidden, layers, max_batch, seed, skip)
+        if history not in (1, 2):
+            raise ValueError("history: 1 (the previous slab) or 2 (the two previous slabs)")
+        self.history = history
+        self.Cin = history * self.C
+        self.net = ConvNet(self.n, self.n, self.Cin, self.C, hidden, layers, max_batch, seed, skip)
         self.capacity = capacity
-        shape = (capacity, self.n, self.n, self.C)
-        self.inputs = torch.empty(shape, dtype=torch.float32, device=mg.device)
-        self.targets = torch.empty(shape, dtype=torch.float32, device=mg.device)
+        self.inputs = torch.empty((capacity, self.n, self.n, self.Cin), dtype=torch.float32, device=mg.device)
+        self.targets = torch.empty((capacity, self.n, self.n, self.C), dtype=torch.float32, device=mg.device)
         self.count = 0
         self.inv_in = self.s_out = None
         self._ext = mg.empty(0)
-        self._cells = torch.empty((self.n * self.n, self.C), dtype=torch.float32, device=mg.device)
+        self._cells = torch.empty((self.n * self.n, self.Cin), dtype=torch.float32, device=mg.device)
         self._out = torch.empty((1, self.n, self.n, self.C), dtype=torch.float32, device=mg.device)
         self._amp = torch.empty(1, dtype=torch.float32, device=mg.device)
         self._inv_amp = torch.empty(1, dtype=torch.float32, device=mg.device)
@@ -230,16 +233,28 @@ class WarmStart:
         self.dens = torch.empty(capacity, dtype=torch.float64, device=mg.device)
         self._tmp = mg.empty(0)
 
-    def add_pair(self, x_prev, x_next):
-        """Store one training pair: input gather(x_prev), target gather(x_next - E x_prev),
-        both divided by the input's amplitude rms(gather(x_prev))."""
+    def _gather_input(self, x_prev, x_prev2, out):
+        """Input cell tensor: gather(x_prev), or [gather(x_prev2), gather(x_prev)] along the
+        channels with history 2."""
+        if self.history == 1:
+            self.mg.cells_gather(x_prev, out=out)
+        else:
+            if x_prev2 is None:
+                raise ValueError("history 2 needs the slab before the previous one (x_prev2)")
+            self.mg.cells_gather_strided(x_prev2, out, self.Cin, 0)
+            self.mg.cells_gather_strided(x_prev, out, self.Cin, self.C)
+
+    def add_pair(self, x_prev, x_next, x_prev2=None):
+        """Store one training pair: input gather(x_prev) (with history 2 stacked after
+        gather(x_prev2)), target gather(x_next - E x_prev), both divided by the input's
+        amplitude."""
         if self.inv_in is not None:
             raise RuntimeError("add_pair after fit")
         if self.count >= self.capacity:
             raise RuntimeError("training set is full")
         i = self.count
-        xi, yi = self.inputs[i].view(-1, self.C), self.targets[i].view(-1, self.C)
-        self.mg.cells_gather(x_prev, out=xi)
+        xi, yi = self.inputs[i].view(-1, self.Cin), self.targets[i].view(-1, self.C)
+        self._gather_input(x_prev, x_prev2, xi)
         lib = load()
         inv = self._inv_amp
         check("stmg_tensor_rms", lib.stmg_tensor_rms(xi.numel(), _ptr(xi), _ptr(self.amps[i:i + 1]), _ptr(inv),
@@ -266,7 +281,7 @@ class WarmStart:
         n = self.count
         X, Y = self.inputs[:n], self.targets[:n]
         if self.inv_in is None:
-            _, self.inv_in = channel_rms(X, self.C)
+            _, self.inv_in = channel_rms(X, self.Cin)
             self.s_out, inv_out = channel_rms(Y, self.C)
             scale_channels(X, self.inv_in)
             scale_channels(Y, inv_out)
@@ -347,8 +362,9 @@ class WarmStart:
             self.mg.dot(r, r, out=vals[b:b + 1])
         return float((vals.cpu().numpy() / self.dens[:n].cpu().numpy()).mean())
 
-    def guess(self, x_prev, mode: str = "net", out=None):
-        """Initial guess for the next slab from the previous slab's solution."""
+    def guess(self, x_prev, mode: str = "net", out=None, x_prev2=None):
+        """Initial guess for the next slab from the previous slab's solution (and, with
+        history 2, the one before it)."""
         torch = _torch()
         if mode not in self.MODES:
             raise ValueError(f"mode must be one of {self.MODES}")
@@ -360,7 +376,7 @@ class WarmStart:
             return x
         if self.inv_in is None:
             raise RuntimeError("guess(mode='net') before fit")
-        self.mg.cells_gather(x_prev, out=self._cells)
+        self._gather_input(x_prev, x_prev2, self._cells)
         lib = load()
         check("stmg_tensor_rms", lib.stmg_tensor_rms(self._cells.numel(), _ptr(self._cells), _ptr(self._amp),
                                                      _ptr(self._inv_amp), _stream_ptr()))
