@@ -112,8 +112,8 @@ class Clocks:
 
     def start(self):
         try:
-            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            import tempfile
+            self.path = os.path.join(tempfile.gettempdir(), f"stmg_clocks_{os.getpid()}.csv")
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],

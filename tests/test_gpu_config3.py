@@ -1,7 +1,7 @@
 """Config 3 at full size on the GPU: 3D unit cube, 32^3 cells, Q3/P2disc, DG(1), 8 slabs,
 nu = 1e-2, Taylor-Green-like velocity with polynomial pressure (6,131,398 dofs per slab,
 21.4 GB of FP32 cell-patch inverses).  Sampled parity against the oracle's row-wise
-evaluation, full forcing parity, and a solve judged by its true residual and by its
+evaluation, full forcing parity, and a solve checked by its true residual and by its
 error against the closed-form solution."""
 import numpy as np
 import pytest
