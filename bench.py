@@ -38,10 +38,16 @@ WORKLOADS = {
     "lid": (dict(dim=3, n_cells=16, r=2, k=2, nu=1.0, T=8.0, n_slabs=256),
             "3D lid-driven cavity (Sec. 5.3, c = 4): 16^3 Q3/P2disc DG(2), 256 slabs on [0, 8], lid velocity "
             "sin(pi t / 4) in x on z = 1, no-slip walls, nu = 1, cell Vanka, n_sm = 1", "lid"),
+    "lid5": (dict(dim=3, n_cells=32, r=2, k=2, nu=1.0, T=8.0, n_slabs=512),
+             "3D lid-driven cavity (Sec. 5.3, c = 5): 32^3 Q3/P2disc DG(2), 512 slabs on [0, 8], lid velocity "
+             "sin(pi t / 4) in x on z = 1, no-slip walls, nu = 1, cell Vanka, n_sm = 1", "lid"),
+    "lid_r3": (dict(dim=3, n_cells=16, r=3, k=3, nu=1.0, T=8.0, n_slabs=256),
+               "3D lid-driven cavity (Sec. 5.3, c = 4, r = 3): 16^3 Q4/P3disc DG(3), 256 slabs on [0, 8], lid "
+               "velocity sin(pi t / 4) in x on z = 1, no-slip walls, nu = 1, cell Vanka, n_sm = 1", "lid"),
 }
 WORKLOADS_KIND = {name: kind for _, name, kind in WORKLOADS.values()}
-# the paper's throughput on the same workload (Table 3, c = 4, r = 2, n_sm = 1; 13,824 CPU ranks)
-PAPER_THETA = {"lid": 302520576 / 149.4}
+# the paper's throughput on the same workloads (Table 3, n_sm = 1; 13,824 CPU ranks)
+PAPER_THETA = {"lid": 302520576 / 149.4, "lid5": 4708913664 / 329.0, "lid_r3": 927534080 / 629.4}
 WORKLOAD, WORKLOAD_NAME, _ = WORKLOADS["c2"]
 METRIC = "space-time DoFs/s (apply, Vanka sweep, V-cycle); time-to-1e-8 mixed vs FP64"
 
@@ -63,7 +69,7 @@ def parse():
                    help="wrap the timed steps in cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
                    help="c2: the 2D headline configuration; c3: the 3D 32^3 configuration; "
-                        "lid: the lid-driven cavity at c = 4")
+                        "lid: the lid-driven cavity at c = 4 (lid5: c = 5; lid_r3: c = 4 with Q4/P3 DG(3))")
     return p.parse_args()
 
 
