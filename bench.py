@@ -65,6 +65,8 @@ def parse():
                    help="coarsest mesh of the hierarchy (Alg. 2's 1/h_0); 0: 8 in 2D, 1 in 3D")
     p.add_argument("--k-min", type=int, default=0, help="lowest temporal degree of the hierarchy; 0: k in 2D, 1 in 3D")
     p.add_argument("--levels", default="", help="explicit level list n:r:k,... fine -> coarse")
+    p.add_argument("--half-inverses", action="store_true",
+                   help="store the FP32 V-cycle's patch inverses in FP16 with row scales (timed march)")
     p.add_argument("--profile-range", action="store_true",
                    help="wrap the timed steps in cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
@@ -214,10 +216,10 @@ def run_ours(args):
 
     levels = [tuple(int(v) for v in t.split(":")) for t in args.levels.split(",")] if args.levels else None
 
-    def make(prec, coarse_n=args.coarse_n, k_min=args.k_min):
+    def make(prec, coarse_n=args.coarse_n, k_min=args.k_min, half=args.half_inverses):
         return stmg.SpaceTimeMG(**w, precond_precision=prec, coarse_n=min(coarse_n, w["n_cells"]),
                                 k_min=k_min, levels=levels, precisions=precisions if prec == "fp32" else (prec,),
-                                gmres_max_iter=200 if w["dim"] == 2 else 80)
+                                gmres_max_iter=200 if w["dim"] == 2 else 80, half_inverses=half and prec == "fp32")
 
     mg = make("fp32")
     # resident per-slab inputs: the assembled forcing, or for the lid-driven cavity (no
@@ -320,7 +322,8 @@ def run_ours(args):
             "dtype": "f64 FGMRES + f32 V-cycle", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "dofs_per_slab": D, "slabs_per_step": N,
                        "levels": [(l["n"], l["r"], l["k"]) for l in mg.levels],
-                       "precond": "fp32", "rel_tol": 1e-8, "parallelism": f"replicas x{world}",
+                       "precond": "fp32" + (" (FP16 inverses)" if args.half_inverses else ""), "rel_tol": 1e-8,
+                       "parallelism": f"replicas x{world}",
                        "hierarchy": f"Alg. 2/3 with h_0 = 1/{args.coarse_n}, lowest temporal degree "
                                     f"{args.k_min}" if not levels else "explicit",
                        "l2_policy": "inputs larger than L2 (finest FP32 patch inverses "
@@ -538,6 +541,26 @@ def micro(mg, make, F, N, D, step_fn):
         tt[prec] = {"ms_per_slab": ms / N, "mean_iterations": statistics.mean(its), "theta_dofs_per_s": N * D / (ms / 1e3)}
         if g is not mg:
             g.close()
+    # the same march with half-precision patch inverses in the FP32 V-cycle
+    g = make("fp32", half=True)
+    its = []
+    step_fn(g, its)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its = []
+    e0.record()
+    step_fn(g, its)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    x = torch.randn(D, dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    t = timeit(lambda: g.vanka_sweep(x, y, 0))
+    tt["fp32_half_inverses"] = {"ms_per_slab": ms / N, "mean_iterations": statistics.mean(its),
+                                "theta_dofs_per_s": N * D / (ms / 1e3),
+                                "finest_sweep_GBs": g.sweep_bytes(0, "fp32") / (t / 1e3) / 1e9,
+                                "finest_inverse_bytes": g.levels[0]["inverse_bytes"][1]}
+    g.close()
     out["time_to_1e-8"] = tt
     return out
 

@@ -130,6 +130,11 @@ typedef struct {
                               temporal multigrid is p-coarsening per subinterval (no
                               h-coarsening in time).  tau = T / (n_slabs n_sub);
                               n_sub (k + 1) <= 8                                        */
+  int    half_inverses;    /* 1: the FP32 V-cycle stores its patch inverses in FP16, each
+                              row scaled to [-1, 1] with an FP32 row scale (half the
+                              bytes of the dominant stream; the sweep accumulates in
+                              FP32).  Default 0 (FP32 inverses).  Not an option of the
+                              paper: an extension of its mixed-precision form.          */
 } stmg_config;
 
 typedef struct {

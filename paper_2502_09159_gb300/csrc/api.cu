@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -26,6 +27,10 @@ struct PrecDev {
   ApplyParams<T> ap{};
   TransferParams<T> tp{};   // transfer between this level and the next coarser one
   bool has_inv = false;
+  // FP32 V-cycle with half-precision inverses: FP16 rows scaled to [-1, 1], FP32 row scales
+  __half* invh = nullptr;
+  float* rsc = nullptr;
+  bool half = false;
 };
 
 struct LevelDev {
@@ -282,10 +287,21 @@ static int setup_precision(stmg_handle* h, LevelDev& lv, const double* d_cls, co
     double* d_w = nullptr;
     CKS(dalloc(&d_w, H.size));
     CK(cudaMemcpy(d_w, w.data(), sizeof(double) * H.size, cudaMemcpyHostToDevice));
-    int s = dalloc(&P.inv, (size_t)H.n_patches * H.B * H.Bc);
-    if (s == STMG_OK && launch_replicate_inverses<T>(d_cls, d_cls_of, lv.dofs, d_w, P.inv, H.n_patches, H.B,
-                                                     H.Bc, h->st) != cudaSuccess)
-      s = STMG_ERR_CUDA;
+    int s = STMG_OK;
+    if (std::is_same<T, float>::value && h->cfg.half_inverses) {
+      const int Bh = (H.B + 7) / 8 * 8;
+      s = dalloc(&P.invh, (size_t)H.n_patches * H.B * Bh);
+      if (s == STMG_OK) s = dalloc(&P.rsc, (size_t)H.n_patches * H.B);
+      if (s == STMG_OK && launch_replicate_inverses_half(d_cls, d_cls_of, lv.dofs, d_w, P.invh, P.rsc, H.n_patches,
+                                                         H.B, Bh, h->st) != cudaSuccess)
+        s = STMG_ERR_CUDA;
+      P.half = true;
+    } else {
+      s = dalloc(&P.inv, (size_t)H.n_patches * H.B * H.Bc);
+      if (s == STMG_OK && launch_replicate_inverses<T>(d_cls, d_cls_of, lv.dofs, d_w, P.inv, H.n_patches, H.B,
+                                                       H.Bc, h->st) != cudaSuccess)
+        s = STMG_ERR_CUDA;
+    }
     cudaStreamSynchronize(h->st);
     cudaFree(d_w);
     if (s != STMG_OK) return s;
@@ -297,7 +313,7 @@ static int setup_precision(stmg_handle* h, LevelDev& lv, const double* d_cls, co
 static void free_level(LevelDev& lv) {
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(lv.dofs); f(lv.G); f(lv.Gacc);
-  f(lv.d.inv); f(lv.d.b); f(lv.d.x); f(lv.d.r);
+  f(lv.d.inv); f(lv.d.b); f(lv.d.x); f(lv.d.r); f(lv.f.invh); f(lv.f.rsc);
   f(lv.f.inv); f(lv.f.b); f(lv.f.x); f(lv.f.r);
   lv = LevelDev();
 }
@@ -321,7 +337,10 @@ static int op_sweep(stmg_handle* h, int l, const T* res, T* x, cudaStream_t s) {
   if (!P.has_inv) return STMG_ERR_ARG;
   Prof pr(h, l == 0 ? STMG_PROF_FINE_SWEEP : STMG_PROF_SMOOTHER, s, prec_of<T>());
   const int w = prec_of<T>();
-  if (lv.sweep_var[w] == 2 && tma_sweep_supported<T>(lv.H.B))
+  if (P.half)
+    CK(launch_vanka_sweep_half(lv.dofs, P.invh, P.rsc, (const float*)res, (float*)x, lv.H.n_patches, lv.H.B,
+                               (lv.H.B + 7) / 8 * 8, lv.ppb[w], lv.streaming, s));
+  else if (lv.sweep_var[w] == 2 && tma_sweep_supported<T>(lv.H.B))
     CK(launch_vanka_sweep_tma<T>(lv.dofs, P.inv, res, x, lv.H.n_patches, lv.H.B, lv.H.Bc, h->n_sm,
                                  lv.streaming, h->d_err, s));
   else
@@ -406,7 +425,7 @@ static int autotune_level(stmg_handle* h, int l) {
       CKS(time_it(h, [&]() { return op_sweep<T>(h, l, P.r, P.x, h->st); }, &ms));
       if (ms < best) { best = ms; best_var = 1; best_ppb = ppb; }
     }
-    if (only != 1 && tma_sweep_supported<T>(lv.H.B)) {
+    if (only != 1 && !P.half && tma_sweep_supported<T>(lv.H.B)) {
       lv.sweep_var[w] = 2;
       CKS(time_it(h, [&]() { return op_sweep<T>(h, l, P.r, P.x, h->st); }, &ms));
       if (ms < best) { best = ms; best_var = 2; }
@@ -793,6 +812,7 @@ int stmg_default_config(stmg_config* c) {
   c->coarse_n = 1;
   c->k_min = 1;
   c->n_sub = 1;
+  c->half_inverses = 0;
   return STMG_OK;
 }
 
@@ -984,7 +1004,9 @@ int stmg_level_info(const stmg_handle* h, int lvl, stmg_level_info_t* info) {
   info->n_patches = H.n_patches;
   info->n_patch_classes = (int)H.class_rep.size();
   if (L.d.has_inv) info->inverse_bytes[0] = (long long)H.n_patches * H.B * H.Bc * 8;
-  if (L.f.has_inv) info->inverse_bytes[1] = (long long)H.n_patches * H.B * H.Bc * 4;
+  if (L.f.has_inv)
+    info->inverse_bytes[1] = L.f.half ? (long long)H.n_patches * H.B * ((H.B + 7) / 8 * 8) * 2 + H.n_patches * H.B * 4
+                                      : (long long)H.n_patches * H.B * H.Bc * 4;
   for (int w = 0; w < 2; ++w) {
     info->sweep_variant[w] = L.sweep_var[w];
     info->patches_per_block[w] = L.ppb[w];
@@ -1259,8 +1281,11 @@ int stmg_sweep_bytes(const stmg_handle* h, int lvl, int prec, double* bytes) {
   const LevelHost& H = h->L[lvl].H;
   const double s = prec == STMG_FP64 ? 8.0 : 4.0;
   // inverses (valence weights folded in) + patch index table + gathered residual +
-  // read-modify-write of x
-  *bytes = (double)H.n_patches * H.B * H.Bc * s + (double)H.n_patches * H.B * 4.0 + 3.0 * H.size * s;
+  // read-modify-write of x; half-precision inverses: 2 bytes per entry plus a row scale
+  const double invb = (prec == STMG_FP32 && h->L[lvl].f.half)
+                          ? (double)H.n_patches * H.B * ((H.B + 7) / 8 * 8) * 2.0 + (double)H.n_patches * H.B * 4.0
+                          : (double)H.n_patches * H.B * H.Bc * s;
+  *bytes = invb + (double)H.n_patches * H.B * 4.0 + 3.0 * H.size * s;
   return STMG_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations of libstmg: level data, kernel parameter blocks and launchers.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <array>
@@ -113,6 +114,12 @@ template <typename T>
 cudaError_t launch_vanka_sweep(const int* dofs, const T* inv, const T* res, T* x, long long n_patches, int B,
                                int Bc, int ppb, int streaming, cudaStream_t st);
 constexpr int TMA_NCW = 4;   // consumer warps of the TMA-pipelined sweep (+1 producer warp)
+// half-precision inverses with FP32 row scales for the FP32 V-cycle (k_vanka.cu)
+cudaError_t launch_replicate_inverses_half(const double* cls, const int* cls_of_patch, const int* dofs, const double* w,
+                                           __half* inv, float* rscale, long long n_patches, int B, int Bh,
+                                           cudaStream_t st);
+cudaError_t launch_vanka_sweep_half(const int* dofs, const __half* inv, const float* rscale, const float* res, float* x,
+                                    long long n_patches, int B, int Bh, int ppb, int streaming, cudaStream_t st);
 template <typename T>
 cudaError_t launch_vanka_sweep_tma(const int* dofs, const T* inv, const T* res, T* x, long long n_patches, int B,
                                    int Bc, int n_sm, int streaming, int* err, cudaStream_t st);

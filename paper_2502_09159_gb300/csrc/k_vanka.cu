@@ -18,6 +18,8 @@
 //     rounding).
 #include <cuda_runtime.h>
 
+#include <cuda_fp16.h>
+
 #include "internal.h"
 
 namespace stmg {
@@ -147,6 +149,120 @@ cudaError_t launch_replicate_inverses(const double* cls, const int* cls_of_patch
   long long blocks = (tot + 255) / 256;
   if (blocks > 152LL * 64) blocks = 152LL * 64;
   k_replicate<T><<<(unsigned)blocks, 256, 0, st>>>(cls, cls_of_patch, dofs, w, inv, n_patches, B, Bc);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Half-precision inverses for the FP32 V-cycle.  Row j of patch p is stored as FP16 values
+// of w_j A_jc / s_pj with the row scale s_pj = max_c |w_j A_jc| kept in FP32, so every
+// stored value lies in [-1, 1] (no overflow, relative rounding 2^-11); the layout is the
+// interleaved one with 8-column chunks: [patch][chunk][row][8 halves] (16-byte vectors).
+// The sweep streams half the bytes of the FP32 inverses and accumulates in FP32.
+// ------------------------------------------------------------------------------------
+__global__ void k_replicate_half(const double* __restrict__ cls, const int* __restrict__ cls_of_patch,
+                                 const int* __restrict__ dofs, const double* __restrict__ w, __half* __restrict__ inv,
+                                 float* __restrict__ rscale, long long n_patches, int B, int Bh) {
+  const long long tot = n_patches * B;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long p = e / B;
+    const int row = (int)(e - p * B);
+    const double* A = cls + (size_t)cls_of_patch[p] * B * B + (size_t)row * B;
+    const int g = dofs[p * B + row];
+    const double wr = g >= 0 ? w[g] : 0.0;
+    double m = 0.0;
+    for (int c = 0; c < B; ++c) m = fmax(m, fabs(wr * A[c]));
+    const double s = m > 0.0 ? m : 1.0;
+    rscale[e] = (float)s;
+    __half* out = inv + (size_t)p * B * Bh + (size_t)row * 8;
+    for (int c = 0; c < Bh; ++c) {
+      const double v = c < B ? wr * A[c] / s : 0.0;
+      out[(size_t)(c / 8) * B * 8 + (c % 8)] = __double2half(v);
+    }
+  }
+}
+
+cudaError_t launch_replicate_inverses_half(const double* cls, const int* cls_of_patch, const int* dofs, const double* w,
+                                           __half* inv, float* rscale, long long n_patches, int B, int Bh,
+                                           cudaStream_t st) {
+  const long long tot = n_patches * (long long)B;
+  long long blocks = (tot + 255) / 256;
+  if (blocks > 152LL * 64) blocks = 152LL * 64;
+  k_replicate_half<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(cls, cls_of_patch, dofs, w, inv, rscale,
+                                                                      n_patches, B, Bh);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ float dot8h(const uint4& a, const float* r) {
+  const __half2* h = reinterpret_cast<const __half2*>(&a);
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __half22float2(h[i]);
+    s = fmaf(f.x, r[2 * i], s);
+    s = fmaf(f.y, r[2 * i + 1], s);
+  }
+  return s;
+}
+
+__global__ void __launch_bounds__(1024) k_vanka_sweep_half(const int* __restrict__ dofs, const __half* __restrict__ inv,
+                                                           const float* __restrict__ rscale,
+                                                           const float* __restrict__ res, float* __restrict__ x,
+                                                           long long n_patches, int B, int Bh, int ppb, int streaming) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* rs = reinterpret_cast<float*>(smraw);        // [ppb][Bh]
+  const long long p0 = (long long)blockIdx.x * ppb;
+  for (int t = threadIdx.x; t < ppb * Bh; t += blockDim.x) {
+    const int pl = t / Bh, i = t % Bh;
+    const long long p = p0 + pl;
+    float v = 0.f;
+    if (p < n_patches && i < B) {
+      const int g = dofs[p * B + i];
+      if (g >= 0) v = res[g];
+    }
+    rs[t] = v;
+  }
+  __syncthreads();
+  const int nch = Bh / 8;
+  const bool st = streaming != 0;
+  for (int t = threadIdx.x; t < ppb * B; t += blockDim.x) {
+    const int pl = t / B, j = t % B;
+    const long long p = p0 + pl;
+    if (p >= n_patches) break;
+    const uint4* A = reinterpret_cast<const uint4*>(inv + (size_t)p * B * Bh) + j;
+    const float* r = rs + pl * Bh;
+    float acc0 = 0.f, acc1 = 0.f;
+    int c = 0;
+    for (; c + 8 <= nch; c += 8) {
+      uint4 a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = st ? __ldcs(A + (size_t)(c + u) * B) : __ldg(A + (size_t)(c + u) * B);
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        acc0 += dot8h(a[u], r + (c + u) * 8);
+        acc1 += dot8h(a[u + 1], r + (c + u + 1) * 8);
+      }
+    }
+    for (; c < nch; ++c) acc0 += dot8h(st ? __ldcs(A + (size_t)c * B) : __ldg(A + (size_t)c * B), r + c * 8);
+    const int g = dofs[p * B + j];
+    if (g >= 0) atomicAdd(x + g, (acc0 + acc1) * rscale[p * B + j]);   // rows carry omega / valence
+  }
+}
+
+cudaError_t launch_vanka_sweep_half(const int* dofs, const __half* inv, const float* rscale, const float* res, float* x,
+                                    long long n_patches, int B, int Bh, int ppb, int streaming, cudaStream_t st) {
+  if (ppb * B > 1024) ppb = 1024 / B;
+  if (ppb < 1) ppb = 1;
+  if (B < 1 || Bh % 8 != 0) return cudaErrorInvalidValue;
+  const int threads = ppb * B > 1024 ? 1024 : ((ppb * B + 31) / 32) * 32;
+  const long long blocks = (n_patches + ppb - 1) / ppb;
+  const size_t smem = sizeof(float) * (size_t)ppb * Bh;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_vanka_sweep_half, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_vanka_sweep_half<<<(unsigned)blocks, threads, smem, st>>>(dofs, inv, rscale, res, x, n_patches, B, Bh, ppb,
+                                                              streaming);
   return cudaGetLastError();
 }
 
