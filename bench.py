@@ -297,8 +297,10 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_kind": peak_kind,
                 "traffic": ncu_traffic("k_vanka.cu", "vanka_sweep_fp32_finest" +
-                                       ("" if args.workload == "c2" else "_" + args.workload)),
-                "kernel": "k_vanka_sweep<float>, finest level", "bytes_per_launch": sweep_bytes,
+                                       ("" if args.workload == "c2" else "_" + args.workload) +
+                                       ("_half" if args.half_inverses else "")),
+                "kernel": "k_vanka_sweep_half, finest level" if args.half_inverses else
+                          "k_vanka_sweep<float>, finest level", "bytes_per_launch": sweep_bytes,
                 "avg_launch_ms": round(sweep_ms, 5), "launches_timed": prof["fine_sweep"]["launches"]}
 
     # ---- end to end through the public API: pinned host F in, host solution out, every slab
