@@ -355,7 +355,8 @@ def cell_patches(slab: Slab):
 def vertex_star_patches(slab: Slab):
     """Vertex-star patches: for every mesh vertex (boundary vertices included), all velocity
     dofs in the closure of the cells around it and all their pressure modes; whole slab in
-    time (remark after Eq. vanka).  Parity unpinned: Table 2(d) does not decode."""
+    time (remark after Eq. vanka).  The sets are pinned to this reading by closed-form
+    counts; the reading is parity unpinned: Table 2(d) does not decode."""
     s = slab.space
     d = slab.dim
     pats = []

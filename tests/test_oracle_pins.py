@@ -347,6 +347,44 @@ def test_vanka_patch_sizes_and_invariants():
     assert max(len(p) for p in vs) == B_int == 366
 
 
+def test_vertex_star_sets_closed_form():
+    """Vertex-star sets against counts that follow from the definition (closure of the
+    cells around a vertex, all their pressure modes, every temporal dof).  Per direction a
+    node strictly inside a cell sees 2 mesh vertices of the cells containing it, an
+    interior mesh vertex 3, a boundary vertex 2; a node lies in the stars of the product
+    of these.  A cell's pressure modes lie in its 2^d vertex stars.  A star with c_i cells
+    per direction holds prod((r+1) c_i + 1) nodes per component."""
+    for dim, n, r, k in ((2, 3, 2, 1), (3, 2, 1, 0), (2, 1, 1, 2)):
+        s = Slab(dim, n, r, k, 1.0, 0.5)
+        sp_ = s.space
+        G = (r + 1) * n + 1
+        pats = vertex_star_patches(s)
+        assert len(pats) == (n + 1) ** dim
+        cnt = np.zeros(s.size, dtype=int)
+        for p in pats:
+            assert len(np.unique(p)) == len(p)
+            cnt[p] += 1
+
+        def m(g):
+            if g % (r + 1):
+                return 2
+            j = g // (r + 1)
+            return 3 if 0 < j < n else 2
+
+        want_v = np.array([math.prod(m(g) for g in idx) for idx in
+                           (tuple(reversed(t)) for t in np.ndindex(*([G] * dim)))])
+        for a in range(s.kt):
+            for comp in range(dim):
+                base = a * s.nv + comp * sp_.n_nodes
+                assert np.array_equal(cnt[base:base + sp_.n_nodes], want_v)
+        assert np.all(cnt[s.kt * s.nv:] == 2 ** dim)
+        n_pm = math.comb(r + dim, dim)
+        for i, v in enumerate(np.ndindex(*([n + 1] * dim))):
+            c = [2 if 0 < j < n else 1 for j in v]
+            want = s.kt * (dim * math.prod((r + 1) * ci + 1 for ci in c) + math.prod(c) * n_pm)
+            assert len(pats[i]) == want
+
+
 def test_vanka_recovers_error_on_exclusive_dofs():
     """If the error e lives on dofs that only patch T contains (its interior velocity nodes
     and its pressure modes), then R_T S e = S_TT e_T, so one step with omega = 1 from x = 0
