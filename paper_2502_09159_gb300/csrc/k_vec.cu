@@ -160,9 +160,11 @@ cudaError_t launch_multiaxpy(long long n, int nvec, const double* V, long long l
 // in block order (deterministic).  The barriers are bounded: a wait that exceeds its
 // iteration limit raises *err and the kernel returns (the host reports STMG_ERR_TIMEOUT).
 // The launch is cooperative, so all blocks are resident and every barrier completes.
+// At the sizes of one slab the step is bound by FP64 issue and memory latency, not by
+// bandwidth: see the notes on the partial dot products below.
 // ------------------------------------------------------------------------------------
 namespace {
-constexpr int CGS_THREADS = 256;
+constexpr int CGS_THREADS = 512;
 constexpr int CGS_MAXV = 256;          // basis vectors per step (gmres_max_iter + 1)
 constexpr long long BARRIER_SPINS = 1LL << 22;
 
@@ -193,27 +195,86 @@ __device__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned n
   return *sh_ok != 0;
 }
 
+// FP64 instructions are the scarce resource of this step on GB300 (FP64 issues at about
+// 1/64 of the FP32 rate), so the partial dot products spend none on absent vectors and
+// reduce across lanes by a butterfly reduce-scatter (9 FP64 adds per lane for 8 sums,
+// not 40 for eight shuffle trees).
+constexpr int ROWS = 4;                // rows per thread per step, their loads issued together
+
+// acc[i] += sum over this thread's rows in [lo, hi) of V_i(r) w(r), i < CNT.  w is read
+// through L2 (__ldcg): it is rewritten inside the launch.  V is read-only here.
+template <int CNT>
+__device__ __forceinline__ void rows_dots(long long lo, long long hi, const double* __restrict__ V, long long ld,
+                                          const double* w, double* acc) {
+  for (long long r0 = lo + threadIdx.x; r0 < hi; r0 += ROWS * CGS_THREADS) {
+    if (r0 + (long long)(ROWS - 1) * CGS_THREADS < hi) {
+      double wr[ROWS], vv[CNT][ROWS];
+#pragma unroll
+      for (int u = 0; u < ROWS; ++u) {
+        wr[u] = __ldcg(w + r0 + (long long)u * CGS_THREADS);
+#pragma unroll
+        for (int i = 0; i < CNT; ++i) vv[i][u] = V[(size_t)i * ld + r0 + (long long)u * CGS_THREADS];
+      }
+#pragma unroll
+      for (int u = 0; u < ROWS; ++u)
+#pragma unroll
+        for (int i = 0; i < CNT; ++i) acc[i] += vv[i][u] * wr[u];
+    } else {
+      for (long long r = r0; r < hi; r += CGS_THREADS) {
+        const double wr = __ldcg(w + r);
+#pragma unroll
+        for (int i = 0; i < CNT; ++i) acc[i] += V[(size_t)i * ld + r] * wr;
+      }
+    }
+  }
+}
+
+// Butterfly reduce-scatter of eight per-lane values over a warp: returns, in every lane,
+// the warp sum of value *vidx (lanes with lane % 4 == 0 hold distinct indices 0..7).
+__device__ __forceinline__ double warp_reduce8(const double* acc, int lane, int* vidx) {
+  const int u1 = (lane >> 4) & 1, u2 = (lane >> 3) & 1, u3 = (lane >> 2) & 1;
+  double b[4], c[2];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double keep = u1 ? acc[4 + k] : acc[k], send = u1 ? acc[k] : acc[4 + k];
+    b[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double keep = u2 ? b[2 + k] : b[k], send = u2 ? b[k] : b[2 + k];
+    c[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const double keep = u3 ? c[1] : c[0], send = u3 ? c[0] : c[1];
+  double d = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  d += __shfl_xor_sync(0xffffffffu, d, 2);
+  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  *vidx = 4 * u1 + 2 * u2 + u3;
+  return d;
+}
+
 // partial[blk * nv + i] = sum over rows [lo, hi) of V_i w, eight vectors per sweep over w
 __device__ void block_partials(long long lo, long long hi, int nv, const double* __restrict__ V, long long ld,
-                               const double* __restrict__ w, double* __restrict__ out, double (*red)[8]) {
+                               const double* w, double* __restrict__ out, double (*red)[8]) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int v0 = 0; v0 < nv; v0 += 8) {
     const int cnt = nv - v0 < 8 ? nv - v0 : 8;
+    const double* Vg = V + (size_t)v0 * ld;
     double acc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i] = 0.0;
-    for (long long r = lo + threadIdx.x; r < hi; r += CGS_THREADS) {
-      const double wr = w[r];
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (i < cnt) acc[i] += V[(size_t)(v0 + i) * ld + r] * wr;
+    switch (cnt) {
+      case 1: rows_dots<1>(lo, hi, Vg, ld, w, acc); break;
+      case 2: rows_dots<2>(lo, hi, Vg, ld, w, acc); break;
+      case 3: rows_dots<3>(lo, hi, Vg, ld, w, acc); break;
+      case 4: rows_dots<4>(lo, hi, Vg, ld, w, acc); break;
+      case 5: rows_dots<5>(lo, hi, Vg, ld, w, acc); break;
+      case 6: rows_dots<6>(lo, hi, Vg, ld, w, acc); break;
+      case 7: rows_dots<7>(lo, hi, Vg, ld, w, acc); break;
+      default: rows_dots<8>(lo, hi, Vg, ld, w, acc); break;
     }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      double a = acc[i];
-      for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-      if (lane == 0) red[wid][i] = a;
-    }
+    int vi;
+    const double d = warp_reduce8(acc, lane, &vi);
+    if ((lane & 3) == 0) red[wid][vi] = d;
     __syncthreads();
     if (threadIdx.x < cnt) {
       double t = 0.0;
@@ -223,13 +284,45 @@ __device__ void block_partials(long long lo, long long hi, int nv, const double*
     __syncthreads();
   }
 }
+
+// *out = sum over rows [lo, hi) of w(r)^2 (w read through L2, as above)
+__device__ void block_norm_partial(long long lo, long long hi, const double* w, double* __restrict__ out,
+                                   double (*red)[8]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double acc = 0.0;
+  for (long long r = lo + threadIdx.x; r < hi; r += CGS_THREADS) {
+    const double t = __ldcg(w + r);
+    acc += t * t;
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if (lane == 0) red[wid][0] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < CGS_THREADS / 32; ++q) t += red[q][0];
+    *out = t;
+  }
+  __syncthreads();
+}
+
 // out[i] = sum_bb part[bb * nv + i], i < nv: one warp per vector, lanes strided over the
-// blocks, then a fixed shuffle tree (deterministic)
-__device__ void sum_partials(const double* __restrict__ part, unsigned G, int nv, double* out) {
+// blocks with all of a lane's loads issued together (read through L2: other blocks wrote
+// them in this launch), then a fixed shuffle tree (deterministic)
+constexpr int PLANE = 10;              // partial sums per lane per step
+__device__ void sum_partials(const double* part, unsigned G, int nv, double* out) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int i = wid; i < nv; i += CGS_THREADS / 32) {
     double s = 0.0;
-    for (unsigned bb = lane; bb < G; bb += 32) s += part[(size_t)bb * nv + i];
+    for (unsigned b0 = lane; b0 < G; b0 += 32u * PLANE) {
+      double t[PLANE];
+#pragma unroll
+      for (int u = 0; u < PLANE; ++u) {
+        const unsigned bb = b0 + 32u * u;
+        t[u] = bb < G ? __ldcg(part + (size_t)bb * nv + i) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < PLANE; ++u) s += t[u];
+    }
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if (lane == 0) out[i] = s;
   }
@@ -239,7 +332,7 @@ __device__ void sum_partials(const double* __restrict__ part, unsigned G, int nv
 // part: 3 regions of gridDim.x * CGS_MAXV doubles (first pass, second pass, norm), so that
 // no region is overwritten while another block may still read it.
 __global__ void __launch_bounds__(CGS_THREADS) k_cgs2(long long n, int nv, const double* __restrict__ V, long long ld,
-                                                    double* __restrict__ w, double* __restrict__ part,
+                                                    double* w, double* __restrict__ part,
                                                     double* __restrict__ hcol, double* __restrict__ vnext,
                                                     unsigned* bar, int* err) {
   __shared__ double h[CGS_MAXV], h2[CGS_MAXV], red[CGS_THREADS / 32][8];
@@ -269,7 +362,7 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2(long long n, int nv, const
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i < nv; i += CGS_THREADS) hcol[i] = h[i] + h2[i];
   double* pn = part + 2 * region;
-  block_partials(lo, hi, 1, w, 0, w, pn + blockIdx.x, red);
+  block_norm_partial(lo, hi, w, pn + blockIdx.x, red);
   if (!grid_barrier(count, gen, G, err, &sh_ok)) return;
   sum_partials(pn, G, 1, &nrm);
   __syncthreads();
@@ -293,12 +386,13 @@ cudaError_t launch_cgs2(long long n, int nv, const double* V, long long ld, doub
   return cudaLaunchCooperativeKernel((const void*)k_cgs2, dim3(nblocks), dim3(CGS_THREADS), args, 0, st);
 }
 
+// One 512-thread block per SM: fewer partial sums for every block to reduce than with two
+// 256-thread blocks per SM, measured 15-20 % faster per step at 3e5 rows.
 int cgs2_blocks(int n_sm) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs2, CGS_THREADS, 0) != cudaSuccess || per_sm < 1)
     return 0;
-  int b = n_sm * (per_sm < 2 ? per_sm : 2);
-  return b > 304 ? 304 : b;
+  return n_sm > 304 ? 304 : n_sm;
 }
 
 // Coarse direct solve: x = G b, G column-major D x D in FP64; vectors of type T.
@@ -314,13 +408,14 @@ __global__ void k_coarse(int D, const double* __restrict__ Gcm, const T* __restr
   }
 }
 
-// Large coarse levels (D > 1024): tiles of 256 rows x 64 columns of G, four independent
-// FP64 accumulators per row, partial products accumulated in FP64 (acc, zeroed first),
-// then rounded to the vector type.  Enough tiles to cover every SM.
+// Large coarse levels (D > 1024): tiles of 256 rows x 32 columns of G (enough tiles to
+// cover every SM several times), all 32 loads of a thread issued before the products,
+// eight independent FP64 accumulators per row, partial products accumulated in FP64
+// (acc, zeroed first), then rounded to the vector type.
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse_tiled(int D, const double* __restrict__ Gcm,
                                                       const T* __restrict__ b, double* __restrict__ acc) {
-  constexpr int CT = 64;
+  constexpr int CT = 32;
   __shared__ double bs[CT];
   const int c0 = blockIdx.y * CT;
   const int cn = min(CT, D - c0);
@@ -329,16 +424,19 @@ __global__ void __launch_bounds__(256) k_coarse_tiled(int D, const double* __res
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= D) return;
   const double* g = Gcm + (size_t)c0 * D + row;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int c = 0;
-  for (; c + 4 <= cn; c += 4) {
-    s0 += g[(size_t)c * D] * bs[c];
-    s1 += g[(size_t)(c + 1) * D] * bs[c + 1];
-    s2 += g[(size_t)(c + 2) * D] * bs[c + 2];
-    s3 += g[(size_t)(c + 3) * D] * bs[c + 3];
+  double s[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s[i] = 0.0;
+  if (cn == CT) {
+    double v[CT];
+#pragma unroll
+    for (int c = 0; c < CT; ++c) v[c] = g[(size_t)c * D];
+#pragma unroll
+    for (int c = 0; c < CT; ++c) s[c & 7] += v[c] * bs[c];
+  } else {
+    for (int c = 0; c < cn; ++c) s[0] += g[(size_t)c * D] * bs[c];
   }
-  for (; c < cn; ++c) s0 += g[(size_t)c * D] * bs[c];
-  atomicAdd(acc + row, (s0 + s1) + (s2 + s3));
+  atomicAdd(acc + row, ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])));
 }
 
 template <typename T>
@@ -351,7 +449,7 @@ template <typename T>
 cudaError_t launch_coarse_tiled(int D, const double* Gcm, const T* b, T* x, double* acc, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * D, st);
   if (e != cudaSuccess) return e;
-  const int nr = (D + 255) / 256, nc = (D + 63) / 64;
+  const int nr = (D + 255) / 256, nc = (D + 31) / 32;
   k_coarse_tiled<T><<<dim3(nr, nc), 256, 0, st>>>(D, Gcm, b, acc);
   k_coarse_finish<T><<<nr, 256, 0, st>>>(D, acc, x);
   return cudaGetLastError();
