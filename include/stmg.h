@@ -135,6 +135,12 @@ typedef struct {
                               bytes of the dominant stream; the sweep accumulates in
                               FP32).  Default 0 (FP32 inverses).  Not an option of the
                               paper: an extension of its mixed-precision form.          */
+  int    transfer_variant; /* grid-transfer kernels: 0 = chosen by the tuner (default),
+                              1 = per coarse cell (shared-memory sum factorisation,
+                              atomics on shared fine nodes), 2 = gather form, one
+                              thread per output value (2D levels only; 3D levels and
+                              other shapes keep 1).  Both compute P and P^T exactly
+                              (App. A); they differ in rounding order only.             */
 } stmg_config;
 
 typedef struct {
@@ -150,7 +156,8 @@ typedef struct {
   int       sweep_variant[2];            /* per precision: 1 block sweep, 2 TMA sweep      */
   int       patches_per_block[2];        /* block sweep launch shape, per precision          */
   int       apply_cells_per_block[2];    /* apply / residual launch shape, per precision     */
-  int       transfer_cells_per_block[2]; /* transfers to the next coarser level              */
+  int       transfer_cells_per_block[2]; /* transfers to the next coarser level; 0: the
+                                            gather form (one thread per value)           */
 } stmg_level_info_t;
 
 typedef struct {

@@ -50,7 +50,7 @@ class SpaceTimeMG:
                  nu2: int = 1, precond_precision="fp64", precisions=("fp64", "fp32"),
                  gmres_max_iter: int = 200, rel_tol: float = 1e-8, use_graphs: bool = True,
                  sweep_variant: int = 0, autotune: bool = True, coarse_n: int = 1, k_min: int = 1,
-                 n_sub: int = 1, half_inverses: bool = False):
+                 n_sub: int = 1, half_inverses: bool = False, transfer_variant: int = 0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("SpaceTimeMG needs a CUDA device (no CPU fallback)")
@@ -77,6 +77,7 @@ class SpaceTimeMG:
         cfg.k_min = int(k_min)
         cfg.n_sub = int(n_sub)
         cfg.half_inverses = int(half_inverses)
+        cfg.transfer_variant = int(transfer_variant)
         self.cfg = cfg
         self.dim, self.r, self.k, self.n_sub = dim, r, k, int(n_sub)
         self.kt = self.n_sub * (k + 1)

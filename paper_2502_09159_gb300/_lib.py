@@ -23,7 +23,8 @@ class Config(C.Structure):
                 ("precond_precision", C.c_int), ("precisions", C.c_int),
                 ("gmres_max_iter", C.c_int), ("rel_tol", C.c_double), ("use_graphs", C.c_int),
                 ("sweep_variant", C.c_int), ("autotune", C.c_int), ("coarse_n", C.c_int),
-                ("k_min", C.c_int), ("n_sub", C.c_int), ("half_inverses", C.c_int)]
+                ("k_min", C.c_int), ("n_sub", C.c_int), ("half_inverses", C.c_int),
+                ("transfer_variant", C.c_int)]
 
 
 class LevelInfo(C.Structure):

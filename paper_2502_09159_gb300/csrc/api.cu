@@ -204,6 +204,7 @@ static void fill_transfer_params(const LevelHost& F, const LevelHost& C, Transfe
   p->nnc = C.n_nodes; p->nnf = F.n_nodes; p->nvc = C.n_vel; p->nvf = F.n_vel;
   p->npc_tot = C.n_pres; p->npf_tot = F.n_pres;
   p->rc = C.r;
+  p->variant = 1;
   for (int s = 0; s < p->ns; ++s) {
     double xi;
     if (p->h_type) {
@@ -353,8 +354,10 @@ static int op_sweep(stmg_handle* h, int l, const T* res, T* x, cudaStream_t s) {
 template <typename T>
 static int op_restrict(stmg_handle* h, int l, const T* rf, T* bc, cudaStream_t s) {
   LevelDev& lc = h->L[l + 1];
-  CK(cudaMemsetAsync(bc, 0, sizeof(T) * lc.H.size, s));
-  CK(launch_restrict<T>(h->L[l].pd<T>().tp, rf, bc, s));
+  const TransferParams<T>& tp = h->L[l].pd<T>().tp;
+  if (!(tp.variant == 2 && transfer_gather_supported(tp)))     // the gather form writes all of b_c
+    CK(cudaMemsetAsync(bc, 0, sizeof(T) * lc.H.size, s));
+  CK(launch_restrict<T>(tp, rf, bc, s));
   h->launches += 1;
   return STMG_OK;
 }
@@ -479,17 +482,28 @@ static int autotune_level(stmg_handle* h, int l) {
     PrecDev<T>& C = h->L[l + 1].pd<T>();
     const int ncd = lv.H.dim == 2 ? h->L[l + 1].H.n * h->L[l + 1].H.n : h->L[l + 1].H.n * h->L[l + 1].H.n * h->L[l + 1].H.n;
     best = 1e30f;
-    int best_cpb = P.tp.cpb;
-    for (int cpb = 1; cpb <= 32 && cpb <= ncd; cpb *= 2) {
-      P.tp.cpb = cpb;
-      if (transfer_smem<T>(P.tp, 0) > 100 * 1024 || transfer_smem<T>(P.tp, 1) > 100 * 1024) break;
-      CKS(time_it(h, [&]() {
-        CKS(op_restrict<T>(h, l, P.r, C.b, h->st));
-        return op_prolongate_add<T>(h, l, C.x, P.x, h->st);
-      }, &ms));
-      if (ms < best) { best = ms; best_cpb = cpb; }
+    int best_cpb = P.tp.cpb, best_var = P.tp.variant;
+    const int fixed = h->cfg.transfer_variant;        // 0: free choice, 1 / 2: fixed variant
+    auto pair = [&]() {
+      CKS(op_restrict<T>(h, l, P.r, C.b, h->st));
+      return op_prolongate_add<T>(h, l, C.x, P.x, h->st);
+    };
+    if (fixed != 2 || !transfer_gather_supported(P.tp)) {
+      P.tp.variant = 1;
+      for (int cpb = 1; cpb <= 32 && cpb <= ncd; cpb *= 2) {
+        P.tp.cpb = cpb;
+        if (transfer_smem<T>(P.tp, 0) > 100 * 1024 || transfer_smem<T>(P.tp, 1) > 100 * 1024) break;
+        CKS(time_it(h, pair, &ms));
+        if (ms < best) { best = ms; best_cpb = cpb; best_var = 1; }
+      }
+    }
+    if (fixed != 1 && transfer_gather_supported(P.tp)) {
+      P.tp.variant = 2;
+      CKS(time_it(h, pair, &ms));
+      if (ms < best) { best = ms; best_var = 2; }
     }
     P.tp.cpb = best_cpb;
+    P.tp.variant = best_var;
   }
   h->launches = saved;
   return STMG_OK;
@@ -845,6 +859,7 @@ int stmg_default_config(stmg_config* c) {
   c->k_min = 1;
   c->n_sub = 1;
   c->half_inverses = 0;
+  c->transfer_variant = 0;
   return STMG_OK;
 }
 
@@ -859,6 +874,7 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
   if (c.gmres_max_iter < 1 || !(c.rel_tol > 0) || c.nu1 < 0 || c.nu2 < 0) return STMG_ERR_ARG;
   if ((c.precisions & 3) == 0) return STMG_ERR_ARG;
   if (c.sweep_variant < 0 || c.sweep_variant > 2) return STMG_ERR_ARG;
+  if (c.transfer_variant < 0 || c.transfer_variant > 2) return STMG_ERR_ARG;
   if (c.precond_precision != STMG_FP64 && c.precond_precision != STMG_FP32) return STMG_ERR_ARG;
   if (!(c.precisions & (1 << c.precond_precision))) return STMG_ERR_ARG;
   h->tau = c.T / ((double)c.n_slabs * c.n_sub);
@@ -951,6 +967,10 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
   for (size_t i = 0; i + 1 < h->L.size(); ++i) {
     fill_transfer_params<double>(h->L[i].H, h->L[i + 1].H, &h->L[i].d.tp);
     fill_transfer_params<float>(h->L[i].H, h->L[i + 1].H, &h->L[i].f.tp);
+    if (c.transfer_variant == 2) {
+      if (transfer_gather_supported(h->L[i].d.tp)) h->L[i].d.tp.variant = 2;
+      if (transfer_gather_supported(h->L[i].f.tp)) h->L[i].f.tp.variant = 2;
+    }
   }
   if (c.autotune) CKS(autotune_impl(h));
   // finest-level helpers: slab coupling and forcing
@@ -1045,8 +1065,8 @@ int stmg_level_info(const stmg_handle* h, int lvl, stmg_level_info_t* info) {
   }
   info->apply_cells_per_block[0] = L.d.ap.cpb;
   info->apply_cells_per_block[1] = L.f.ap.cpb;
-  info->transfer_cells_per_block[0] = L.d.tp.cpb;
-  info->transfer_cells_per_block[1] = L.f.tp.cpb;
+  info->transfer_cells_per_block[0] = L.d.tp.variant == 2 ? 0 : L.d.tp.cpb;
+  info->transfer_cells_per_block[1] = L.f.tp.variant == 2 ? 0 : L.f.tp.cpb;
   return STMG_OK;
 }
 

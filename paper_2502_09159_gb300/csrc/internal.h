@@ -75,6 +75,7 @@ struct TransferParams {
   T E[2][MAXNP * MAXNP];          // h-type pressure: E[o][i' * (rc+1) + i]
   signed char modes_c[MAXPM][3], modes_f[MAXPM][3];
   int rc;                         // coarse pressure degree
+  int variant;                    // 1: per coarse cell (shared memory), 2: gather form (2D)
 };
 
 struct ForcingParams {
@@ -136,6 +137,8 @@ template <typename T>
 cudaError_t launch_restrict(const TransferParams<T>& p, const T* rf, T* bc, cudaStream_t st);
 template <typename T>
 size_t transfer_smem(const TransferParams<T>& p, int restrict_);
+template <typename T>
+bool transfer_gather_supported(const TransferParams<T>& p);   // the gather form has this shape
 
 template <typename T>
 cudaError_t launch_coarse(int D, const double* Gcm, const T* b, T* x, cudaStream_t st);
