@@ -39,13 +39,13 @@ WORKLOADS = {
     "c3": (dict(dim=3, n_cells=32, r=2, k=1, nu=1e-2, T=1.0, n_slabs=8),
            "3D 32^3 Q3/P2disc DG(1), 8 slabs, Taylor-Green-like field, nu = 1e-2, cell Vanka", "taylor_green"),
     "lid": (dict(dim=3, n_cells=16, r=2, k=2, nu=1.0, T=8.0, n_slabs=256),
-            "3D lid-driven cavity (Sec. 5.3, c = 4): 16^3 Q3/P2disc DG(2), 256 slabs on [0, 8], lid velocity "
+            "3D lid-driven cavity (Sec. 5.2, c = 4): 16^3 Q3/P2disc DG(2), 256 slabs on [0, 8], lid velocity "
             "sin(pi t / 4) in x on z = 1, no-slip walls, nu = 1, cell Vanka, n_sm = 1", "lid"),
     "lid5": (dict(dim=3, n_cells=32, r=2, k=2, nu=1.0, T=8.0, n_slabs=512),
-             "3D lid-driven cavity (Sec. 5.3, c = 5): 32^3 Q3/P2disc DG(2), 512 slabs on [0, 8], lid velocity "
+             "3D lid-driven cavity (Sec. 5.2, c = 5): 32^3 Q3/P2disc DG(2), 512 slabs on [0, 8], lid velocity "
              "sin(pi t / 4) in x on z = 1, no-slip walls, nu = 1, cell Vanka, n_sm = 1", "lid"),
     "lid_r3": (dict(dim=3, n_cells=16, r=3, k=3, nu=1.0, T=8.0, n_slabs=256),
-               "3D lid-driven cavity (Sec. 5.3, c = 4, r = 3): 16^3 Q4/P3disc DG(3), 256 slabs on [0, 8], lid "
+               "3D lid-driven cavity (Sec. 5.2, c = 4, r = 3): 16^3 Q4/P3disc DG(3), 256 slabs on [0, 8], lid "
                "velocity sin(pi t / 4) in x on z = 1, no-slip walls, nu = 1, cell Vanka, n_sm = 1", "lid"),
 }
 WORKLOADS_KIND = {name: kind for _, name, kind in WORKLOADS.values()}

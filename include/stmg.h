@@ -225,17 +225,22 @@ int  stmg_smooth(stmg_handle* h, int lvl, int prec, const void* b, void* x, int 
    they run: a process whose device memory is given out only by its own pool allocator,
    or a time-critical loop that cannot absorb the implicit synchronisation of
    cudaMalloc/cudaFree.  Same arguments and result as stmg_smooth, but the residual lives
-   in a fixed device array inside the library (STMG_NOALLOC_MAX_ENTRIES values, 8 MB,
-   present on every GPU that loads the library until the process exits), so the call
-   allocates nothing.  The paper has no counterpart; it is an interface convenience.
+   in a fixed device array inside the library (STMG_NOALLOC_MAX_ENTRIES values, 8 MB), so
+   the call allocates nothing.  The paper has no counterpart; it is an interface
+   convenience.
+   - The array's 8 MB are taken on a device when the first handle is created there
+     (stmg_create looks up the array's device address once per device, which loads the
+     library's module holding it; STMG_ERR_OOM if that fails) and are held until the
+     process exits.  Create the handle before any stream capture.  A device reset
+     (cudaDeviceReset) invalidates the address, as it invalidates every handle.
    - Levels with more than STMG_NOALLOC_MAX_ENTRIES dofs are rejected with
      STMG_ERR_TOO_LARGE before any work is queued.
-   - The first call on each device looks up the array's device address
-     (cudaGetSymbolAddress) with that device current; make that first call before any
-     stream capture.
-   - All calls share the one array and it keeps whatever the last call left in it (the
-     residual is cleared at the start of every step): calls that can overlap on the GPU,
-     from different streams or handles, race with each other; order them on one stream. */
+   - All calls share the one array and it keeps whatever the last call left in it (each
+     step overwrites the whole residual before reading it): calls that can overlap on the
+     GPU, from different streams or handles, race with each other; order them on one
+     stream.
+   - Like stmg_smooth and the other asynchronous calls, it does not report an expired
+     bounded wait inside a kernel (the TMA sweep's); stmg_device_status does. */
 #define STMG_NOALLOC_MAX_ENTRIES (1 << 20)
 int  stmg_smooth_noalloc(stmg_handle* h, int lvl, int prec, const void* b, void* x, int steps);
 

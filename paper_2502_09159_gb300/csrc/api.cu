@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -86,7 +87,12 @@ struct stmg_handle {
   bool graph_pending[2] = {false, false};
   std::vector<cudaEvent_t> free_events;
   bool capturing = false;
+  void* noalloc = nullptr;        // device address of stmg_smooth_noalloc's fixed array (this device)
 };
+
+// Device address of the fixed array of stmg_smooth_noalloc on the current device (defined
+// at the end of this file); looked up once per device, at handle creation.
+static int noalloc_scratch_address(void** out);
 
 // ------------------------------------------------------------------------------------
 // helpers
@@ -914,6 +920,9 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
     CK(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
     CKS(dalloc(&h->d_err, 1));
     CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    // stmg_smooth_noalloc's array: its module (and the array's device memory) is loaded
+    // here, at set-up, so that the no-alloc call itself never triggers a load
+    CKS(noalloc_scratch_address(&h->noalloc));
     h->cgs_blocks = cgs2_blocks(h->n_sm);
     if (h->cgs_blocks > 0) {
       CKS(dalloc(&h->cgs_bar, 2));
@@ -1352,47 +1361,54 @@ int stmg_sweep_bytes(const stmg_handle* h, int lvl, int prec, double* bytes) {
 // pool allocator, or a time-critical loop that cannot absorb the implicit synchronisation
 // of cudaMalloc/cudaFree).  stmg_smooth_noalloc does the same smoothing step with the
 // residual held in the library's own fixed device array below, so the call itself
-// allocates nothing.  The array is part of the library image: every GPU on which the
-// library is loaded holds its STMG_NOALLOC_MAX_ENTRIES * 8 bytes until the process exits.
+// allocates nothing.
+//
+// The array lives in this file's module.  With lazy module loading (the CUDA default) the
+// module, and with it the array's STMG_NOALLOC_MAX_ENTRIES * 8 bytes of device memory, is
+// loaded by the first use of the symbol on a device; that first use is the address lookup
+// in stmg_create, so the memory is taken when the first handle is created on a device and
+// held until the process exits.  A failure there (no device memory left) is reported by
+// stmg_create as STMG_ERR_OOM.
 // ------------------------------------------------------------------------------------
 static __device__ __align__(256) double stmg_noalloc_scratch[STMG_NOALLOC_MAX_ENTRIES];
 
 namespace {
 constexpr int kMaxDevices = 64;
-void* g_noalloc_ptr[kMaxDevices] = {};   // device address of the array, per device
-
-// Device address of the scratch array on the current device, looked up once per device.
-// `stmg_noalloc_scratch` named in host code is only a host-side stand-in; the device
-// address has to come from cudaGetSymbolAddress with that device current.
-int noalloc_scratch(void** out) {
-  int dev = -1;
-  CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return STMG_ERR_ARG;
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    CK(cudaGetSymbolAddress(&p, stmg_noalloc_scratch));
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
-  return STMG_OK;
-}
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};   // device address of the array, per device (under the mutex)
 
 template <typename T>
 int smooth_noalloc_t(stmg_handle* h, int lvl, const T* b, T* x, int steps, T* res) {
   for (int s = 0; s < steps; ++s) {
-    CKS(op_apply<T>(h, lvl, x, b, res, RESIDUAL, h->st));   // clears res, then r = b - S x
+    CKS(op_apply<T>(h, lvl, x, b, res, RESIDUAL, h->st));   // overwrites res: r = b - S x
     CKS(op_sweep<T>(h, lvl, res, x, h->st));
   }
   return STMG_OK;
 }
 }  // namespace
 
+// `stmg_noalloc_scratch` named in host code is only a host-side stand-in; its device
+// address has to come from cudaGetSymbolAddress with the device current.  Looked up once
+// per device (the first stmg_create on it), cached under a mutex.
+static int noalloc_scratch_address(void** out) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return STMG_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, stmg_noalloc_scratch));   // cudaErrorMemoryAllocation -> STMG_ERR_OOM
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return STMG_OK;
+}
+
 extern "C" int stmg_smooth_noalloc(stmg_handle* h, int lvl, int prec, const void* b, void* x, int steps) {
   if (!prec_ok(h, lvl, prec) || !b || !x || steps < 0 || lvl == (int)h->L.size() - 1) return STMG_ERR_ARG;
   if (h->L[lvl].H.size > (long long)STMG_NOALLOC_MAX_ENTRIES) return STMG_ERR_TOO_LARGE;
-  void* scratch = nullptr;
-  CKS(noalloc_scratch(&scratch));
+  if (!h->noalloc) return STMG_ERR_CUDA;
   if (prec == STMG_FP64)
-    return smooth_noalloc_t<double>(h, lvl, (const double*)b, (double*)x, steps, (double*)scratch);
-  return smooth_noalloc_t<float>(h, lvl, (const float*)b, (float*)x, steps, (float*)scratch);
+    return smooth_noalloc_t<double>(h, lvl, (const double*)b, (double*)x, steps, (double*)h->noalloc);
+  return smooth_noalloc_t<float>(h, lvl, (const float*)b, (float*)x, steps, (float*)h->noalloc);
 }

@@ -1,6 +1,6 @@
 """Non-homogeneous Dirichlet data on the GPU (stmg_dirichlet_lift, boundary values in the
 slab coupling) against the oracle, exact reproduction, and a small lid-driven cavity run
-(Sec. 5.3) marched on both sides.  Needs a GPU."""
+(Sec. 5.2) marched on both sides.  Needs a GPU."""
 import numpy as np
 import pytest
 

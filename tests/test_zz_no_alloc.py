@@ -42,6 +42,7 @@ def test_smooth_noalloc_matches_smooth_twice(dtype):
             torch.cuda.synchronize()
             err = ((x - ref).abs().max() / ref.abs().max()).item()
             assert err < TOL[dtype], err
+    g.device_status()                                        # no bounded device-side wait expired
     g.close()
 
 
@@ -62,4 +63,5 @@ def test_smooth_noalloc_rejects_levels_beyond_its_scratch():
     g.smooth(b1, ref, 1, steps=1)
     torch.cuda.synchronize()
     assert ((x1 - ref).abs().max() / ref.abs().max()).item() < 1e-5
+    g.device_status()
     g.close()

@@ -269,7 +269,7 @@ def polynomial_boundary(dim: int = 2, nu: float = 1.0, T: float = 1.0) -> Proble
 
 
 def lid_driven_3d(nu: float = 1.0, T: float = 8.0) -> Problem:
-    """Lid-driven cavity of Sec. 5.3: no forcing, no-slip walls, and on the lid z = 1 the
+    """Lid-driven cavity of Sec. 5.2: no forcing, no-slip walls, and on the lid z = 1 the
     velocity sin(pi t / 4) in the x direction (the paper gives the profile as a scalar; the
     x component is this reading), imposed on every node of the closed lid face."""
     def zero(x, t):
