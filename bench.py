@@ -5,18 +5,22 @@ x [0,1], 64x64 cells, Q3/P2disc (r=2) in space, DG(2) in time, 16 slabs, nu = 1,
 forcing = seeded random Fourier modes (8 modes per potential, c ~ N(0,1), a,b ~ U{1..4},
 theta ~ U[0,2pi), numpy PCG64 seeds 1 and 2), hp hierarchy 64^2 Q3 -> 64^2 Q2 -> 32^2 ->
 16^2 -> 8^2 (direct solve) with DG(2) on every level (Alg. 2/3 with h_0 = 1/8; the Table
-2(b) hierarchy is reported beside it), cell Vanka with omega = 0.7, FGMRES to
-||b - S x|| <= 1e-8 ||b||.
+2(b) hierarchy and the r:2->1, k:2->0 hierarchy are reported beside it), cell Vanka with
+omega = 0.7, FGMRES to ||b - S x|| <= 1e-8 ||b||.
 One step = one time march over all 16 slabs (slab right-hand side with the coupling to
 the previous slab, FGMRES + one V-cycle per iteration).  value = 16 * D / step time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --only-kernel sweep|residual|apply|vcycle|restrict|prolong|cgs2 [--level L] [--prec fp32]
+        (one kernel of the headline handle in a loop inside cudaProfilerStart/Stop, for ncu)
 
 The headline runs the V-cycle in FP32 (FGMRES, true residual and coarse solve in FP64);
-the FP64-preconditioner solve, the apply / sweep / V-cycle rates and the roofline of the
-dominant kernel (the finest-level Vanka sweep) are reported beside it, and the one-time
-setup of the handle with theta including it.  --impl reference times the FP64 CPU oracle
-on the host cores on a bounded sample of the same workload.
+the timed march carries no instrumentation.  A second, instrumented march times the
+dominant kernel (the finest-level Vanka sweep) for the roofline.  Reported beside it: the
+end-to-end march through the host-buffer C call, the FP64-preconditioner solve, the
+apply / sweep / V-cycle rates, the error of slab 1 against the FP64 oracle, a subset of
+the (dim, r, k) throughput grid, and the one-time setup.  --impl reference times the FP64
+CPU oracle on the host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -72,6 +76,12 @@ def parse():
                    help="store the FP32 V-cycle's patch inverses in FP16 with row scales (timed march)")
     p.add_argument("--profile-range", action="store_true",
                    help="wrap the timed steps in cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    p.add_argument("--only-kernel", default="", choices=["", "sweep", "residual", "apply", "vcycle", "restrict",
+                                                          "prolong", "cgs2"],
+                   help="time one kernel of the headline handle in a loop (for ncu captures)")
+    p.add_argument("--level", type=int, default=0, help="level of --only-kernel")
+    p.add_argument("--prec", default="fp32", choices=["fp32", "fp64"], help="precision of --only-kernel")
+    p.add_argument("--reps", type=int, default=3, help="launches of --only-kernel inside the profiler range")
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
                    help="c2: the 2D headline configuration; c3: the 3D 32^3 configuration; "
                         "lid: the lid-driven cavity at c = 4 (lid5: c = 5; lid_r3: c = 4 with Q4/P3 DG(3))")
@@ -201,6 +211,13 @@ def ncu_traffic(kernel_file, kernel_name, key):
 
 
 # ----------------------------------------------------------------------------- our arm
+def sweep_alg_bytes(level, prec):
+    """Algorithmic bytes of one Vanka sweep: every patch's B x B inverse once plus about
+    three vectors (residual read, iterate read and written), n_patches B^2 s + 3 D s."""
+    s = 8 if prec == "fp64" else 4
+    return level["n_patches"] * level["patch_size"] ** 2 * s + 3 * level["size"] * s
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -237,9 +254,9 @@ def run_ours(args):
 
     levels = [tuple(int(v) for v in t.split(":")) for t in args.levels.split(",")] if args.levels else None
 
-    def make(prec, coarse_n=args.coarse_n, k_min=args.k_min, half=args.half_inverses):
+    def make(prec, coarse_n=args.coarse_n, k_min=args.k_min, half=args.half_inverses, lv=levels):
         return stmg.SpaceTimeMG(**w, precond_precision=prec, coarse_n=min(coarse_n, w["n_cells"]),
-                                k_min=k_min, levels=levels, precisions=precisions if prec == "fp32" else (prec,),
+                                k_min=k_min, levels=lv, precisions=precisions if prec == "fp32" else (prec,),
                                 gmres_max_iter=200 if w["dim"] == 2 else 80, half_inverses=half and prec == "fp32")
 
     torch.cuda.synchronize()
@@ -247,6 +264,9 @@ def run_ours(args):
     mg = make("fp32")                       # hierarchy, patch and coarse inverses, launch-shape tuning
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t_setup) * 1e3
+    if args.only_kernel:
+        print(json.dumps(only_kernel(mg, args)), flush=True)
+        return
     # resident per-slab inputs: the assembled forcing, or for the lid-driven cavity (no
     # forcing) the slab's boundary values
     if forcing_kind == "lid":
@@ -259,7 +279,6 @@ def run_ours(args):
     x_bufs = [mg.zeros() for _ in range(N)]
     b_buf = mg.empty()
     b_tmp = mg.empty()
-    launches0 = mg.kernel_launches
 
     def build_b(g, inp, x_prev):
         if F0 is None:
@@ -288,8 +307,6 @@ def run_ours(args):
     its = []
     for _ in range(args.warmup):
         step(mg, its)
-    mg.set_profiling(1)                     # events around the finest-level sweeps only
-    mg.profile(reset=True)
     clocks = Clocks(local)
     its = []
     barrier()
@@ -308,11 +325,10 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     launches = mg.kernel_launches - launches_before
     clk = clocks.stop()
-    prof = mg.profile(reset=True)
-    mg.set_profiling(0)
     ms = max_over_ranks(ms, world, device="cuda")
     ms_step = ms / args.steps
     value = aggregate_value(world, N, D, ms_step)
+    x1_fp32 = x_bufs[0].cpu().numpy()        # slab 1 of the timed march (parity against the oracle)
     # the one-time setup next to the march: the paper's theta divides by the total wall
     # time, which may or may not include its (CPU) smoother setup
     setup_ms = max_over_ranks(setup_ms, world, device="cuda")
@@ -321,11 +337,18 @@ def run_ours(args):
              "includes": "handle creation: level geometry, patch inverses (FP64 on the host, "
                          "stored per patch on the device), coarse inverse, launch-shape tuning"}
 
-    # ---- roofline of the dominant kernel: finest-level FP32 Vanka sweep
+    # ---- roofline of the dominant kernel (finest-level FP32 Vanka sweep): one more march,
+    # untimed, with CUDA events around every finest-level sweep on the stream it runs on
+    mg.set_profiling(1)
+    mg.profile(reset=True)
+    step(mg, [])
+    prof = mg.profile(reset=True)
+    mg.set_profiling(0)
+    lv0 = mg.levels[0]
     sweep_ms = prof["fine_sweep"]["ms"] / max(prof["fine_sweep"]["launches"], 1)
-    sweep_bytes = mg.sweep_bytes(0, "fp32")
+    alg_bytes = sweep_alg_bytes(lv0, "fp32") if not args.half_inverses else mg.sweep_bytes(0, "fp32")
     peaks, peak_kind = measured_peaks()
-    achieved = sweep_bytes / (sweep_ms / 1e3) / 1e9
+    achieved = alg_bytes / (sweep_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_kind": peak_kind,
                 "traffic": ncu_traffic("k_vanka.cu", "k_vanka_sweep_half" if args.half_inverses else "k_vanka_sweep",
@@ -333,24 +356,41 @@ def run_ours(args):
                                        ("" if args.workload == "c2" else "_" + args.workload) +
                                        ("_half" if args.half_inverses else "")),
                 "kernel": "k_vanka_sweep_half, finest level" if args.half_inverses else
-                          "k_vanka_sweep<float>, finest level", "bytes_per_launch": sweep_bytes,
-                "avg_launch_ms": round(sweep_ms, 5), "launches_timed": prof["fine_sweep"]["launches"]}
+                          "k_vanka_sweep<float>, finest level",
+                "bytes_per_launch": alg_bytes,
+                "bytes_rule": "n_patches * B^2 * 4 + 3 * D * 4 (stored inverses, residual, iterate)"
+                              if not args.half_inverses else "stmg_sweep_bytes (FP16 inverses + row scales)",
+                "stored_bytes_per_launch": mg.sweep_bytes(0, "fp32"),
+                "avg_launch_ms": round(sweep_ms, 5), "launches_timed": prof["fine_sweep"]["launches"],
+                "timed_in": "a separate instrumented march right after the timed region (events around each "
+                            "finest-level sweep inside the V-cycle graph)",
+                "redundancy": f"{lv0['n_patch_classes']} distinct patch matrices among {lv0['n_patches']} stored "
+                              "per-patch inverses (uniform mesh); the stream is the paper's matrix-based smoother's"}
 
-    # ---- end to end through the public API: pinned host F in, host solution out, every slab
+    # ---- end to end through the C ABI: stmg_march_host, host inputs in, host solutions out
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(mg, F, x_bufs, b_buf, N, D, world, args, barrier, build_b)
+        e2e = run_e2e(mg, F, N, D, world, args, barrier, forcing_kind == "lid")
 
     # ---- per-kernel rates and FP64 vs mixed time-to-1e-8 (not part of the timed step)
     extra = {}
+    x1_fp64 = None
     if not args.no_micro and rank == 0:
-        extra = micro(mg, make, F, N, D, step)
+        extra, x1_fp64 = micro(mg, make, N, D, step, x_bufs)
         extra["time_split"] = time_split(mg, step)
-        extra["paper_hierarchy"] = paper_rule(make, step, N, D)
+        extra["paper_hierarchy"] = other_hierarchy(make, step, N, D, coarse_n=1, k_min=1,
+                                                   what="the Table 2(b) rule: coarsest mesh 1x1, DG(1) on the two "
+                                                        "coarsest levels")
         if args.workload == "c2":
+            k0 = [(64, 2, 2), (64, 1, 1), (64, 1, 0), (32, 1, 0), (16, 1, 0), (8, 1, 0), (4, 1, 0), (2, 1, 0),
+                  (1, 1, 0)]
+            extra["k0_hierarchy"] = other_hierarchy(make, step, N, D, lv=k0,
+                                                    what="r:2->1 with k:2->1, then k:1->0, then geometric to 1x1 "
+                                                         "with DG(0)")
             mg.close()
             torch.cuda.empty_cache()
             extra["warm_start"] = warm_start_bench()
+            extra["throughput_grid"] = throughput_grid()
     line = {"metric": METRIC, "value": value, "unit": "space-time DoFs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": (value / PAPER_THETA[args.workload]) if args.workload in PAPER_THETA else None,
@@ -368,11 +408,98 @@ def run_ours(args):
     line.update(extra)
     if rank == 0:
         if not args.no_baseline:
-            line["cpu_baseline"] = cpu_baseline(coarse_n=args.coarse_n, k_min=args.k_min)
+            base, x1_oracle = cpu_baseline(coarse_n=args.coarse_n, k_min=args.k_min)
+            line["cpu_baseline"] = base
+            line["parity"] = parity_against_oracle(x1_oracle, x1_fp32, x1_fp64)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def parity_against_oracle(x_oracle, x_fp32, x_fp64):
+    """Slab 1 of the march: the GPU solutions (FP32 and FP64 V-cycle, FGMRES to 1e-8)
+    against the FP64 oracle's solution of the same slab (FGMRES + V-cycle to 1e-12), after
+    removing the pressure mean of every temporal dof (the pressure is determined up to these
+    constants)."""
+    if x_oracle is None:
+        return {"slab": 1, "note": "the oracle sample is not the benched workload's size; see tests/"}
+    import numpy as np
+    w = WORKLOAD
+    d, n, r, k = w["dim"], w["n_cells"], w["r"], w["k"]
+    nv = d * ((r + 1) * n + 1) ** d
+    npm = math.comb(r + d, d)
+    kt = k + 1
+
+    def center(x):
+        x = x.copy()
+        o = kt * nv
+        npr = npm * n ** d
+        for a in range(kt):
+            p = x[o + a * npr:o + (a + 1) * npr]
+            p[::npm] -= p[::npm].mean()
+        return x
+
+    ref = center(x_oracle)
+    vel = slice(0, kt * nv)
+    pre = slice(kt * nv, None)
+    out = {"slab": 1, "reference": "FP64 oracle, FGMRES + V-cycle to 1e-12 (same hierarchy)",
+           "tolerance_gpu": 1e-8}
+    for tag, x in (("fp32_vcycle", x_fp32), ("fp64_vcycle", x_fp64)):
+        if x is None:
+            continue
+        xc = center(x)
+        out[tag] = {"rel_err_max": float(np.abs(xc - ref).max() / np.abs(ref).max()),
+                    "rel_err_velocity_l2": float(np.linalg.norm(xc[vel] - ref[vel]) / np.linalg.norm(ref[vel])),
+                    "rel_err_pressure_l2": float(np.linalg.norm(xc[pre] - ref[pre]) / np.linalg.norm(ref[pre]))}
+    return out
+
+
+def only_kernel(mg, args):
+    """One kernel of the headline handle, `reps` launches inside cudaProfilerStart/Stop after
+    three warm-up launches (for `ncu --profile-from-start off`); CUDA-event time per launch."""
+    import torch
+    prec = args.prec
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    lvl = args.level
+    D = mg.size(lvl)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand(D, generator=gen, device="cuda", dtype=dt)
+    b = torch.rand(D, generator=gen, device="cuda", dtype=dt)
+    y = torch.zeros_like(x)
+    v64 = torch.rand(mg.size(0), generator=gen, device="cuda", dtype=torch.float64)
+    z64 = torch.empty_like(v64)
+    if args.only_kernel in ("restrict", "prolong"):
+        xc = torch.rand(mg.size(lvl + 1), generator=gen, device="cuda", dtype=dt)
+    fns = {"apply": lambda: mg.apply(x, lvl, out=y),
+           "residual": lambda: mg.residual(b, x, lvl, out=y),
+           "sweep": lambda: mg.vanka_sweep(b, y, lvl),
+           "restrict": lambda: mg.restrict(x, lvl, out=xc),
+           "prolong": lambda: mg.prolongate_add(xc, y, lvl),
+           "vcycle": lambda: mg.vcycle(v64, prec, out=z64)}
+    if args.only_kernel == "cgs2":
+        # one FGMRES solve of slab 1's right-hand side: the Arnoldi steps are the k_cgs2 launches
+        fb = torch.rand(mg.size(0), generator=gen, device="cuda", dtype=torch.float64)
+        fns["cgs2"] = lambda: mg.solve_slab(fb, out=torch.zeros_like(fb))
+    fn = fns[args.only_kernel]
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()
+    e0.record()
+    for _ in range(args.reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    ms = e0.elapsed_time(e1) / args.reps
+    out = {"kernel": args.only_kernel, "prec": prec, "level": lvl, "dofs": D, "ms": ms, "dofs_per_s": D / (ms / 1e3),
+           "levels": [(l["n"], l["r"], l["k"]) for l in mg.levels]}
+    if args.only_kernel == "sweep":
+        out["alg_bytes"] = sweep_alg_bytes(mg.levels[lvl], prec)
+        out["GBs"] = out["alg_bytes"] / (ms / 1e3) / 1e9
+    return out
 
 
 def warm_start_bench():
@@ -457,32 +584,27 @@ def warm_start_bench():
     return out
 
 
-def run_e2e(mg, F, x_bufs, b_buf, N, D, world, args, barrier, build_b):
+def run_e2e(mg, F, N, D, world, args, barrier, boundary_data):
+    """The march end to end through the C ABI's host-buffer call (stmg_march_host): every
+    step copies all slabs' inputs (forcing, or boundary values for the cavity) from pinned
+    host memory and every solution back, inside the timed region (the library overlaps the
+    copies with the solves on a copy stream)."""
     import torch
-    Fh = [f.cpu().pin_memory() for f in F]
-    Xh = [torch.empty(D, dtype=torch.float64).pin_memory() for _ in range(N)]
-    Fd = mg.empty()
-
-    def e2e_step():
-        x_prev = None
-        for s in range(N):
-            Fd.copy_(Fh[s], non_blocking=True)
-            build_b(mg, Fd, x_prev)
-            x_bufs[s].zero_()
-            mg.solve_slab(b_buf, out=x_bufs[s])
-            Xh[s].copy_(x_bufs[s], non_blocking=True)
-            x_prev = x_bufs[s]
-    e2e_step()
+    Fh = torch.stack([f.cpu() for f in F]).pin_memory()
+    Xh = torch.empty_like(Fh).pin_memory()
+    Fn, Xn = Fh.numpy(), Xh.numpy()
+    mg.march_host(Fn, Xn, boundary_data=boundary_data)          # warm-up
     barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
+    t0 = time.perf_counter()
     for _ in range(args.steps):
-        e2e_step()
-    e1.record()
+        infos = mg.march_host(Fn, Xn, boundary_data=boundary_data)
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    return {"value": world * N * D / (e2e_ms / 1e3), "unit": "space-time DoFs/s",
-            "h2d_bytes_per_step": N * D * 8, "d2h_bytes_per_step": N * D * 8}
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    e2e_ms = max_over_ranks(e2e_ms, world, device="cuda")
+    return {"value": world * N * D / (e2e_ms / 1e3), "unit": "space-time DoFs/s", "ms_per_step": e2e_ms,
+            "h2d_bytes_per_step": N * D * 8, "d2h_bytes_per_step": N * D * 8,
+            "api": "stmg_march_host (C ABI, host FP64 buffers in pinned memory)",
+            "mean_gmres_iterations": statistics.mean(i["iterations"] for i in infos)}
 
 
 def time_split(mg, step_fn):
@@ -503,11 +625,18 @@ def time_split(mg, step_fn):
     return out
 
 
-def paper_rule(make, step_fn, N, D):
-    """The hierarchy pinned by Table 2(b) (coarsest mesh 1x1, DG(1) on the two coarsest
-    levels), same workload, FP32 V-cycle."""
+def other_hierarchy(make, step_fn, N, D, coarse_n=None, k_min=None, lv=None, what=""):
+    """The same workload and FP32 V-cycle on another level list: its march, timed once after
+    one warm-up march."""
     import torch
-    g = make("fp32", coarse_n=1, k_min=1)
+    kw = {}
+    if coarse_n is not None:
+        kw["coarse_n"] = coarse_n
+    if k_min is not None:
+        kw["k_min"] = k_min
+    if lv is not None:
+        kw["lv"] = lv
+    g = make("fp32", **kw)
     its = []
     step_fn(g, its)
     torch.cuda.synchronize()
@@ -519,12 +648,15 @@ def paper_rule(make, step_fn, N, D):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     out = {"value": N * D / (ms / 1e3), "ms_per_step": ms, "mean_iterations": statistics.mean(its),
-           "levels": [(l["n"], l["r"], l["k"]) for l in g.levels]}
+           "levels": [(l["n"], l["r"], l["k"]) for l in g.levels], "hierarchy": what}
     g.close()
     return out
 
 
-def micro(mg, make, F, N, D, step_fn):
+def micro(mg, make, N, D, step_fn, x_bufs):
+    """Per-kernel rates on the finest level (CUDA events, 20 back-to-back calls after 3
+    warm-ups), and time-to-1e-8 of the FP64 vs the FP32 V-cycle (and FP16 inverses) over
+    the same march.  Returns the report and slab 1's solution with the FP64 V-cycle."""
     import torch
     out = {}
 
@@ -550,17 +682,18 @@ def micro(mg, make, F, N, D, step_fn):
         rates[f"apply_{tag}"] = D / (t / 1e3)
         t = timeit(lambda: mg.vanka_sweep(x, y, 0))
         rates[f"vanka_sweep_{tag}"] = D / (t / 1e3)
-        sb = mg.sweep_bytes(0, tag)
-        rates[f"vanka_sweep_{tag}_GBs"] = sb / (t / 1e3) / 1e9
+        rates[f"vanka_sweep_{tag}_GBs"] = sweep_alg_bytes(mg.levels[0], tag) / (t / 1e3) / 1e9
         t = timeit(lambda: (mg.residual(x, y, 0, out=y), mg.vanka_sweep(y, x, 0)))
         rates[f"smoothing_step_{tag}"] = D / (t / 1e3)
         b = x64.clone()
         z = torch.empty_like(b)
         t = timeit(lambda: mg.vcycle(b, tag, out=z))
         rates[f"vcycle_{tag}"] = D / (t / 1e3)
+        rates[f"vcycle_{tag}_us"] = t * 1e3
     out["rates_dofs_per_s"] = {k: float(f"{v:.4g}") for k, v in rates.items()}
     # time-to-1e-8: FP64 preconditioner vs FP32 preconditioner, same march
     tt = {}
+    x1_fp64 = None
     for prec in ("fp64", "fp32"):
         g = mg if prec == "fp32" else make("fp64")     # FP64 V-cycle (FP64 inverses)
         its = []
@@ -575,6 +708,7 @@ def micro(mg, make, F, N, D, step_fn):
         ms = e0.elapsed_time(e1)
         tt[prec] = {"ms_per_slab": ms / N, "mean_iterations": statistics.mean(its), "theta_dofs_per_s": N * D / (ms / 1e3)}
         if g is not mg:
+            x1_fp64 = x_bufs[0].cpu().numpy()
             g.close()
     # the same march with half-precision patch inverses in the FP32 V-cycle
     g = make("fp32", half=True)
@@ -597,14 +731,80 @@ def micro(mg, make, F, N, D, step_fn):
                                 "finest_inverse_bytes": g.levels[0]["inverse_bytes"][1]}
     g.close()
     out["time_to_1e-8"] = tt
-    return out
+    return out, x1_fp64
+
+
+def throughput_grid(reps=10):
+    """A subset of the (dim, r, k) throughput grid: 2D 256^2 and 3D 16^3, r = 1, 2, 4,
+    k = 0, 2, FP32 and FP64, random inputs U[0,1) (cost is data independent), launch shapes
+    autotuned, V-cycle as a CUDA graph.  Per point: the finest level's apply, Vanka sweep and
+    V-cycle in dofs/s (CUDA events, `reps` back-to-back calls after 3 warm-ups) and the
+    sweep's and apply's fraction of the measured HBM bandwidth (sweep: n_patches B^2 s +
+    3 D s bytes; apply: 2 D s, x in and y out)."""
+    import torch
+
+    import paper_2502_09159_gb300 as stmg
+    peaks, peak_kind = measured_peaks()
+    peak = peaks["hbm_gbs"]
+    rows = []
+
+    def timeit(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_all = time.perf_counter()
+    for dim in (2, 3):
+        n = 256 if dim == 2 else 16
+        for r in (1, 2, 4):
+            for k in (0, 2):
+                t0 = time.perf_counter()
+                g = stmg.SpaceTimeMG(dim=dim, n_cells=n, r=r, k=k, precisions=("fp64", "fp32"),
+                                     precond_precision="fp32", use_graphs=True)
+                setup_s = time.perf_counter() - t0
+                D = g.size(0)
+                lv = g.levels[0]
+                for prec in ("fp32", "fp64"):
+                    dt = torch.float32 if prec == "fp32" else torch.float64
+                    sz = 4 if prec == "fp32" else 8
+                    gen = torch.Generator(device="cuda").manual_seed(3)
+                    x = torch.rand(D, generator=gen, device="cuda", dtype=dt)
+                    y = torch.zeros_like(x)
+                    b64 = torch.rand(D, generator=gen, device="cuda", dtype=torch.float64)
+                    z64 = torch.empty_like(b64)
+                    ta = timeit(lambda: g.apply(x, 0, out=y))
+                    ts = timeit(lambda: g.vanka_sweep(x, y, 0))
+                    tv = timeit(lambda: g.vcycle(b64, prec, out=z64))
+                    sb = sweep_alg_bytes(lv, prec)
+                    rows.append({"dim": dim, "n": n, "r": r, "k": k, "prec": prec, "D": D, "B": lv["patch_size"],
+                                 "apply_Gdofs": round(D / ta / 1e6, 3), "apply_us": round(ta * 1e3, 1),
+                                 "apply_hbm_frac": round(2 * D * sz / (ta / 1e3) / 1e9 / peak, 4),
+                                 "sweep_Gdofs": round(D / ts / 1e6, 3), "sweep_us": round(ts * 1e3, 1),
+                                 "sweep_GBs": round(sb / (ts / 1e3) / 1e9, 1),
+                                 "sweep_hbm_frac": round(sb / (ts / 1e3) / 1e9 / peak, 4),
+                                 "vcycle_Gdofs": round(D / tv / 1e6, 3), "vcycle_us": round(tv * 1e3, 1),
+                                 "vectors_fit_l2": 3 * D * sz < 129e6, "setup_s": round(setup_s, 1)})
+                g.close()
+                del g
+                torch.cuda.empty_cache()
+    return {"peak_GBs": peak, "peak_kind": peak_kind, "seconds": round(time.perf_counter() - t_all, 1),
+            "note": "back-to-back calls; where vectors_fit_l2 the apply's vectors are L2-resident",
+            "rows": rows}
 
 
 # ----------------------------------------------------------------------------- oracle
 _ORACLE_SNIPPET = r"""
-import json, sys, time
+import json, os, sys, time
 sys.path.insert(0, {root!r})
-from oracle.stokes import MGConfig, march, Multigrid, default_hierarchy, fgmres
+import numpy as np
+from oracle.stokes import MGConfig, Multigrid, default_hierarchy, fgmres
 from workloads import fourier_forcing_2d, lid_driven_3d, taylor_green_3d
 w = {w!r}
 kind = {kind!r}
@@ -619,11 +819,20 @@ slab = mg.slabs[0]
 b = slab.rhs_forcing(pb.forcing, 0.0)
 if pb.boundary is not None:
     b = slab.lift(slab.boundary_vector(pb.boundary, 0.0), b)
+bar, nproc, me = {barrier!r}, {nproc!r}, {me!r}
+if bar:                                   # start the timed solves of all processes together
+    open(os.path.join(bar, "ready.%d" % me), "w").close()
+    t_wait = time.time()
+    while sum(f.startswith("ready.") for f in os.listdir(bar)) < nproc and time.time() - t_wait < 900:
+        time.sleep(0.05)
 times = []
 for rep in range({reps}):
     t0 = time.time()
     x, info = fgmres(lambda z: slab.S @ z, mg.vcycle, b, tol=1e-8)
     times.append(time.time() - t0)
+if {save!r}:                              # reference solution for the parity report (untimed)
+    x12, info12 = fgmres(lambda z: slab.S @ z, mg.vcycle, b, tol=1e-12)
+    np.save({save!r}, x12)
 print(json.dumps({{"setup_s": t_setup, "solve_s": times, "iterations": info.iterations, "D": slab.size}}))
 """
 
@@ -637,28 +846,122 @@ def oracle_workload():
     return w
 
 
-def oracle_sample(reps, coarse_n=8, k_min=2):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def host_cpu():
+    """CPU model and the cores this process may use."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    return model or "unknown", cores
+
+
+def _mem_available_gb():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 1e6
+    except Exception:
+        pass
+    return 16.0
+
+
+def _oracle_code(reps, coarse_n, k_min, save=None, barrier=None, nproc=1, me=0):
     w = oracle_workload()
     kind = WORKLOADS_KIND.get(WORKLOAD_NAME, "fourier")
-    code = _ORACLE_SNIPPET.format(root=ROOT, w=w, kind=kind, reps=reps, coarse_n=min(coarse_n, w["n_cells"]),
-                                  k_min=k_min)
-    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    return _ORACLE_SNIPPET.format(root=ROOT, w=w, kind=kind, reps=reps, coarse_n=min(coarse_n, w["n_cells"]),
+                                  k_min=k_min, save=save, barrier=barrier, nproc=nproc, me=me)
+
+
+_ENV1 = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+
+def oracle_sample(reps, coarse_n=8, k_min=2, save=None):
+    """One oracle process on one core: setup, then `reps` timed slab-1 solves to 1e-8."""
+    p = subprocess.run([sys.executable, "-c", _oracle_code(reps, coarse_n, k_min, save)], capture_output=True,
+                       text=True, env=_ENV1, timeout=1800)
     if p.returncode != 0:
         raise RuntimeError(p.stderr[-2000:])
     return json.loads(p.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline(reps=1, coarse_n=8, k_min=2):
+def oracle_sample_parallel(nproc, reps, coarse_n=8, k_min=2):
+    """`nproc` single-threaded oracle processes, one per core, each solving slab 1 `reps`
+    times; their timed solves start together (file barrier after the untimed setup)."""
+    import shutil
+    import tempfile
+    bar = tempfile.mkdtemp(prefix="stmg_oracle_")
     try:
-        r = oracle_sample(reps, coarse_n, k_min)
-        t = min(r["solve_s"])
-        return {"value": r["D"] / t, "unit": "space-time DoFs/s", "cores": 1, "kind": "oracle",
-                "sample": f"slab 1 of {WORKLOAD['n_slabs']} ({oracle_workload()['n_cells']}^{WORKLOAD['dim']} "
-                          f"cells) solved by the FP64 oracle (FGMRES + V-cycle to 1e-8, "
-                          f"{r['iterations']} iterations, {t:.1f} s; setup {r['setup_s']:.1f} s not timed)"}
+        procs = [subprocess.Popen([sys.executable, "-c", _oracle_code(reps, coarse_n, k_min, None, bar, nproc, i)],
+                                  stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=_ENV1)
+                 for i in range(nproc)]
+        res = []
+        for p in procs:
+            out, err = p.communicate(timeout=1800)
+            if p.returncode != 0:
+                raise RuntimeError(err[-2000:])
+            res.append(json.loads(out.strip().splitlines()[-1]))
+        return res
+    finally:
+        shutil.rmtree(bar, ignore_errors=True)
+
+
+def oracle_procs():
+    """Processes for the all-cores oracle: one per usable core, at most one per 2.5 GB of
+    available host memory (the config-2 oracle holds about 2 GB)."""
+    _, cores = host_cpu()
+    n = max(1, min(cores, int(_mem_available_gb() / 2.5)))
+    cap = os.environ.get("STMG_ORACLE_PROCS")            # an upper limit, e.g. for a quick CPU test
+    return min(n, max(1, int(cap))) if cap else n
+
+
+def cpu_baseline(coarse_n=8, k_min=2):
+    """The FP64 oracle on the host cores: one process per core solving slab 1 concurrently
+    (value), and one process alone (single_core).  Also returns the oracle's slab-1 solution
+    to 1e-12 when the sample is the benched workload itself (2D), else None."""
+    import tempfile
+
+    import numpy as np
+    model, _ = host_cpu()
+    ow = oracle_workload()
+    same = ow["n_cells"] == WORKLOAD["n_cells"]
+    save = os.path.join(tempfile.gettempdir(), f"stmg_oracle_x1_{os.getpid()}.npy") if same else None
+    x_ref = None
+    out = {"value": None, "unit": "space-time DoFs/s", "cores": None, "kind": "oracle", "cpu": model}
+    try:
+        r1 = oracle_sample(1, coarse_n, k_min, save)
+        t1 = min(r1["solve_s"])
+        out["single_core"] = {"value": r1["D"] / t1, "cores": 1, "solve_s": round(t1, 2),
+                              "setup_s": round(r1["setup_s"], 1), "iterations": r1["iterations"]}
+        if save:
+            x_ref = np.load(save)
+            os.remove(save)
     except Exception as e:  # the baseline is reported, not required
-        return {"value": None, "unit": "space-time DoFs/s", "cores": 1, "kind": "oracle", "error": str(e)[:300]}
+        out["single_core"] = {"error": str(e)[:300]}
+    try:
+        P = oracle_procs()
+        rs = oracle_sample_parallel(P, 1, coarse_n, k_min)
+        tmax = max(min(r["solve_s"]) for r in rs)
+        out["value"] = P * rs[0]["D"] / tmax
+        out["cores"] = P
+        out["solve_s_slowest"] = round(tmax, 2)
+    except Exception as e:
+        out["error"] = str(e)[:300]
+        if "value" in out.get("single_core", {}):
+            out["value"], out["cores"] = out["single_core"]["value"], 1
+    out["sample"] = (f"slab 1 of {WORKLOAD['n_slabs']} ({ow['n_cells']}^{WORKLOAD['dim']} cells) solved by the FP64 "
+                     f"oracle (FGMRES + V-cycle to 1e-8, setup not timed): value = {out['cores']} single-threaded "
+                     f"processes solving it concurrently, one per core ({model}); single_core = one process alone")
+    return out, x_ref
 
 
 def run_reference(args):
@@ -671,20 +974,24 @@ def run_reference(args):
         args.coarse_n = 8 if WORKLOAD["dim"] == 2 else 1
     if args.k_min == 0:
         args.k_min = WORKLOAD["k"] if WORKLOAD["dim"] == 2 else 1
-    r = oracle_sample(args.warmup + args.steps, args.coarse_n, args.k_min)
-    times = r["solve_s"][args.warmup:]
-    t = sum(times) / len(times)
-    value = r["D"] / t
+    model, _ = host_cpu()
+    P = oracle_procs()
+    rs = oracle_sample_parallel(P, args.warmup + args.steps, args.coarse_n, args.k_min)
+    # per step: the slowest process's solve time of that step (all processes solve concurrently)
+    per_step = [max(r["solve_s"][i] for r in rs) for i in range(args.warmup, args.warmup + args.steps)]
+    t = sum(per_step) / len(per_step)
+    D = rs[0]["D"]
+    value = P * D / t
     ow = oracle_workload()
     sample = (f"per step: slab 1 of {WORKLOAD['n_slabs']} of the same workload on {ow['n_cells']}^{ow['dim']} cells "
-              f"solved by the FP64 oracle (FGMRES + V-cycle to 1e-8, {r['iterations']} iterations); "
-              f"setup {r['setup_s']:.1f} s not timed")
+              f"solved by the FP64 oracle (FGMRES + V-cycle to 1e-8, {rs[0]['iterations']} iterations) in each of "
+              f"{P} single-threaded processes at once, one per core ({model}); setup not timed")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "space-time DoFs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "dofs_per_slab": r["D"]},
-            "cpu_baseline": {"value": value, "unit": "space-time DoFs/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "config": {"workload": WORKLOAD_NAME, "dofs_per_slab": D, "oracle_processes": P},
+            "cpu_baseline": {"value": value, "unit": "space-time DoFs/s", "cores": P, "kind": "oracle",
+                             "cpu": model, "sample": sample},
             "e2e": {"value": value, "unit": "space-time DoFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

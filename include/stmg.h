@@ -21,13 +21,13 @@
  *   another unless a call says so.  "prec" selects their element type:
  *   STMG_FP64 -> double, STMG_FP32 -> float.  The handle owns its hierarchy, patch
  *   inverses and work vectors; stmg_destroy frees them.  The only host-pointer calls
- *   are stmg_solve_slab_host (host vectors in, host vectors out) and the info/config
- *   structs.
+ *   are stmg_solve_slab_host and stmg_march_host (host vectors in, host vectors out) and
+ *   the info/config structs.
  *
  * Streams.  Calls enqueue work on the handle's stream (stmg_set_stream; default: the
  *   legacy default stream) and return without waiting, except stmg_create,
- *   stmg_solve_slab, stmg_solve_slab_host and stmg_get_profile, which synchronise
- *   the stream.  A handle must not be used from two host threads at once.
+ *   stmg_solve_slab, stmg_solve_slab_host, stmg_march_host and stmg_get_profile, which
+ *   synchronise the stream.  A handle must not be used from two host threads at once.
  *
  * Slab vector layout (Eq. DefX / DefSubvec, per slab):
  *     [ V^1 ... V^{k+1} , P^1 ... P^{k+1} ]                      length D
@@ -158,6 +158,9 @@ typedef struct {
   int       apply_cells_per_block[2];    /* apply / residual launch shape, per precision     */
   int       transfer_cells_per_block[2]; /* transfers to the next coarser level; 0: the
                                             gather form (one thread per value)           */
+  int       streaming;     /* 1: the sweep reads the stored inverses with evict-first loads
+                              (inverses larger than about a third of L2), so that the
+                              coarser levels' inverses stay L2-resident                   */
 } stmg_level_info_t;
 
 typedef struct {
@@ -293,6 +296,24 @@ int  stmg_solve_slab(stmg_handle* h, const double* b, double* x, stmg_solve_info
    device buffers.  Synchronous. */
 int  stmg_solve_slab_host(stmg_handle* h, const double* b_host, double* x_host,
                           stmg_solve_info* info);
+
+/* Time marching with HOST buffers (Eq. AlgSysTMS, slab by slab, V_0 = 0): for slab
+   s = 0 .. n_slabs-1 the right-hand side is
+     kind STMG_MARCH_FORCING:  b_s = F_s + (C_tau (x) M_h) V_{s-1}      (stmg_slab_rhs)
+     kind STMG_MARCH_BOUNDARY: b_s = lift of the boundary values g_s (stmg_dirichlet_lift)
+                               applied to (C_tau (x) M_h) V_{s-1}, no forcing
+   with in_host + s D holding F_s (forcing part, Eq. DefFn) or g_s (slab vector whose
+   boundary entries are the Dirichlet values); S x_s = b_s is solved from a zero initial
+   guess (stmg_solve_slab) and x_s is written to x_host + s D.  The host-to-device copy of
+   slab s+1's input and the device-to-host copy of slab s-1's solution run on an internal
+   copy stream while slab s is solved (pinned host memory makes them asynchronous).
+   in_host, x_host: host FP64 arrays of n_slabs * D values.  infos: n_slabs entries or
+   NULL.  Synchronous.  Stops at the first slab whose solve does not return STMG_OK and
+   returns that status; the slabs before it are complete in x_host. */
+#define STMG_MARCH_FORCING  0
+#define STMG_MARCH_BOUNDARY 1
+int  stmg_march_host(stmg_handle* h, int n_slabs, int kind, const double* in_host, double* x_host,
+                     stmg_solve_info* infos);
 
 /* ---- forcing (Eq. DefFn) ----------------------------------------------------------- */
 

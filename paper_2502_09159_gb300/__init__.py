@@ -99,7 +99,8 @@ class SpaceTimeMG:
                                 "sweep_variant": tuple(li.sweep_variant),
                                 "patches_per_block": tuple(li.patches_per_block),
                                 "apply_cells_per_block": tuple(li.apply_cells_per_block),
-                                "transfer_cells_per_block": tuple(li.transfer_cells_per_block)})
+                                "transfer_cells_per_block": tuple(li.transfer_cells_per_block),
+                                "streaming": li.streaming})
 
     # ---------------------------------------------------------------- plumbing
     def close(self):
@@ -286,6 +287,26 @@ class SpaceTimeMG:
             raise StmgError("stmg_solve_slab_host", st)
         return {"iterations": info.iterations, "rel_residual": info.rel_residual, "status": info.status,
                 "seconds": info.seconds}
+
+    def march_host(self, inputs: np.ndarray, out: np.ndarray, boundary_data: bool = False):
+        """Whole time march through stmg_march_host with host arrays: inputs[s] is slab s's
+        forcing F_s (or, with boundary_data, its Dirichlet values g_s); out[s] receives x_s.
+        Both (n_slabs, D) float64, C-contiguous (pinned memory lets the copies overlap the
+        solves).  Returns the per-slab info dicts."""
+        for a, name in ((inputs, "inputs"), (out, "out")):
+            if a.dtype != np.float64 or not a.flags.c_contiguous or a.ndim != 2 or a.shape[1] != self.size(0):
+                raise ValueError(f"march_host: {name} must be a C-contiguous float64 (n_slabs, D) array")
+        if inputs.shape != out.shape:
+            raise ValueError("march_host: inputs and out differ in shape")
+        n = inputs.shape[0]
+        infos = (_lib.SolveInfo * n)()
+        self._stream()
+        st = self._lib.stmg_march_host(self._h, n, _lib.MARCH_BOUNDARY if boundary_data else _lib.MARCH_FORCING,
+                                       inputs.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p), infos)
+        if st != _lib.OK:
+            raise StmgError("stmg_march_host", st)
+        return [{"iterations": i.iterations, "rel_residual": i.rel_residual, "status": i.status,
+                 "seconds": i.seconds} for i in infos]
 
     # ---------------------------------------------------------------- cell tensors
     def n_channels(self, lvl: int = 0) -> int:

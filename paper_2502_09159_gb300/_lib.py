@@ -10,6 +10,7 @@ OK, ERR_ARG, ERR_OOM, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_NONFINITE, ERR_CUDA,
 NOALLOC_MAX_ENTRIES = 1 << 20
 FP64, FP32 = 0, 1
 CELL, VSP = 0, 1
+MARCH_FORCING, MARCH_BOUNDARY = 0, 1
 PROF_SMOOTHER, PROF_MG_OTHER, PROF_OPERATOR, PROF_OTHER, PROF_FINE_SWEEP, PROF_N = range(6)
 
 
@@ -33,7 +34,8 @@ class LevelInfo(C.Structure):
                 ("smoother", C.c_int), ("patch_size", C.c_int), ("n_patches", C.c_longlong),
                 ("n_patch_classes", C.c_int), ("inverse_bytes", C.c_longlong * 2),
                 ("sweep_variant", C.c_int * 2), ("patches_per_block", C.c_int * 2),
-                ("apply_cells_per_block", C.c_int * 2), ("transfer_cells_per_block", C.c_int * 2)]
+                ("apply_cells_per_block", C.c_int * 2), ("transfer_cells_per_block", C.c_int * 2),
+                ("streaming", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -63,6 +65,7 @@ _SIGS = {
     "stmg_dirichlet_lift": (_I, [_VP, _VP, _VP, _VP]),
     "stmg_solve_slab": (_I, [_VP, _VP, _VP, C.POINTER(SolveInfo)]),
     "stmg_solve_slab_host": (_I, [_VP, _VP, _VP, C.POINTER(SolveInfo)]),
+    "stmg_march_host": (_I, [_VP, _I, _I, _VP, _VP, C.POINTER(SolveInfo)]),
     "stmg_forcing_npoints": (_I, [_VP, C.POINTER(_I)]),
     "stmg_forcing_points": (_I, [_VP, _VP]),
     "stmg_slab_times": (_I, [_VP, _I, C.POINTER(_D)]),

@@ -88,6 +88,10 @@ struct stmg_handle {
   std::vector<cudaEvent_t> free_events;
   bool capturing = false;
   void* noalloc = nullptr;        // device address of stmg_smooth_noalloc's fixed array (this device)
+  // stmg_march_host: double-buffered device inputs / solutions, a copy stream and its events
+  double *mh_in[2] = {nullptr, nullptr}, *mh_x[2] = {nullptr, nullptr}, *mh_b = nullptr, *mh_t = nullptr;
+  cudaStream_t cst = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
 };
 
 // Device address of the fixed array of stmg_smooth_noalloc on the current device (defined
@@ -1034,6 +1038,14 @@ void stmg_destroy(stmg_handle* h) {
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(h->V); f(h->Z); f(h->w); f(h->hcol); f(h->tmp); f(h->partial); f(h->bnorm);
   f(h->xhost_b); f(h->xhost_x); f(h->d_err); f(h->dot_part); f(h->cgs_bar); f(h->cgs_part);
+  if (h->cst) cudaStreamSynchronize(h->cst);
+  for (int i = 0; i < 2; ++i) {
+    f(h->mh_in[i]); f(h->mh_x[i]);
+    if (h->ev_in[i]) cudaEventDestroy(h->ev_in[i]);
+    if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
+  }
+  f(h->mh_b); f(h->mh_t);
+  if (h->cst) cudaStreamDestroy(h->cst);
   for (auto e : h->all_events) cudaEventDestroy(e);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -1076,6 +1088,7 @@ int stmg_level_info(const stmg_handle* h, int lvl, stmg_level_info_t* info) {
   info->apply_cells_per_block[1] = L.f.ap.cpb;
   info->transfer_cells_per_block[0] = L.d.tp.variant == 2 ? 0 : L.d.tp.cpb;
   info->transfer_cells_per_block[1] = L.f.tp.variant == 2 ? 0 : L.f.tp.cpb;
+  info->streaming = L.streaming;
   return STMG_OK;
 }
 
@@ -1175,6 +1188,77 @@ int stmg_solve_slab_host(stmg_handle* h, const double* bh, double* xh, stmg_solv
   CK(cudaMemcpyAsync(xh, h->xhost_x, sizeof(double) * D, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   return s;
+}
+
+// Time marching with host buffers.  Slab s's input is copied in on the copy stream while
+// slab s-1 is solved (two device input buffers), and slab s's solution is copied out on
+// the copy stream while slab s+1 is solved (two device solution buffers); the solves
+// themselves run on the handle's stream and synchronise it, so the copies overlap them.
+static int march_host_impl(stmg_handle* h, int n_slabs, int kind, const double* in_h, double* x_h,
+                           stmg_solve_info* infos) {
+  const LevelHost& H = h->L[0].H;
+  const long long D = H.size;
+  const size_t bytes = sizeof(double) * D;
+  if (!h->cst) {
+    CK(cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      CK(cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming));
+    }
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (!h->mh_in[i]) CKS(dalloc(&h->mh_in[i], D));
+    if (!h->mh_x[i]) CKS(dalloc(&h->mh_x[i], D));
+  }
+  if (!h->mh_b) CKS(dalloc(&h->mh_b, D));
+  if (!h->mh_t) CKS(dalloc(&h->mh_t, D));
+  cudaStream_t s = h->st;
+  // the copy stream starts after everything already queued on the handle's stream
+  CK(cudaEventRecord(h->ev_out[0], s));
+  CK(cudaStreamWaitEvent(h->cst, h->ev_out[0], 0));
+  CK(cudaMemcpyAsync(h->mh_in[0], in_h, bytes, cudaMemcpyHostToDevice, h->cst));
+  CK(cudaEventRecord(h->ev_in[0], h->cst));
+  CK(cudaEventRecord(h->ev_out[1], h->cst));
+  int status = STMG_OK;
+  for (int sl = 0; sl < n_slabs; ++sl) {
+    const int cur = sl & 1, nxt = cur ^ 1;
+    if (sl + 1 < n_slabs) {
+      // mh_in[nxt] was last read by slab sl-1's right-hand side, which the (synchronous)
+      // solve of slab sl-1 has completed
+      CK(cudaMemcpyAsync(h->mh_in[nxt], in_h + (size_t)(sl + 1) * D, bytes, cudaMemcpyHostToDevice, h->cst));
+      CK(cudaEventRecord(h->ev_in[nxt], h->cst));
+    }
+    CK(cudaStreamWaitEvent(s, h->ev_in[cur], 0));
+    const double* x_prev = sl > 0 ? h->mh_x[nxt] : nullptr;
+    if (kind == STMG_MARCH_FORCING) {
+      CKS(stmg_slab_rhs(h, h->mh_in[cur], x_prev, h->mh_b));
+    } else {
+      CK(cudaMemsetAsync(h->mh_t, 0, bytes, s));
+      if (x_prev) {
+        CK(launch_mass_coupling(h->mp, x_prev + (size_t)(H.kt - 1) * H.n_vel, h->mh_t, s));
+        h->launches += 1;
+      }
+      CKS(op_apply<double>(h, 0, h->mh_in[cur], h->mh_t, h->mh_b, LIFT, s));
+    }
+    // mh_x[cur] held slab sl-2's solution: its copy to the host must have finished
+    CK(cudaStreamWaitEvent(s, h->ev_out[cur], 0));
+    CK(cudaMemsetAsync(h->mh_x[cur], 0, bytes, s));
+    stmg_solve_info info{};
+    const int st = solve_impl(h, h->mh_b, h->mh_x[cur], &info);
+    if (infos) infos[sl] = info;
+    if (st != STMG_OK) { status = st; break; }
+    CK(cudaMemcpyAsync(x_h + (size_t)sl * D, h->mh_x[cur], bytes, cudaMemcpyDeviceToHost, h->cst));
+    CK(cudaEventRecord(h->ev_out[cur], h->cst));
+  }
+  CK(cudaStreamSynchronize(h->cst));
+  return status;
+}
+
+int stmg_march_host(stmg_handle* h, int n_slabs, int kind, const double* in_host, double* x_host,
+                    stmg_solve_info* infos) {
+  if (!h || n_slabs < 1 || !in_host || !x_host) return STMG_ERR_ARG;
+  if (kind != STMG_MARCH_FORCING && kind != STMG_MARCH_BOUNDARY) return STMG_ERR_ARG;
+  return march_host_impl(h, n_slabs, kind, in_host, x_host, infos);
 }
 
 int stmg_forcing_npoints(const stmg_handle* h, int* nq) {

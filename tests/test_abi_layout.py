@@ -18,7 +18,7 @@ STRUCTS = {
                     "half_inverses", "transfer_variant"],
     "stmg_level_info_t": ["n", "r", "k", "size", "n_vel", "n_pres", "smoother", "patch_size", "n_patches",
                           "n_patch_classes", "inverse_bytes", "sweep_variant", "patches_per_block",
-                          "apply_cells_per_block", "transfer_cells_per_block"],
+                          "apply_cells_per_block", "transfer_cells_per_block", "streaming"],
     "stmg_solve_info": ["iterations", "rel_residual", "status", "seconds"],
 }
 

@@ -9,8 +9,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_json_line():
+    env = dict(os.environ, STMG_ORACLE_PROCS="2")        # two concurrent oracle processes keep the test short
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0"], cwd=ROOT, check=True, capture_output=True, text=True, timeout=600)
+                          "--warmup", "0"], cwd=ROOT, check=True, capture_output=True, text=True, timeout=600,
+                         env=env)
     lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
@@ -21,7 +23,8 @@ def test_reference_arm_json_line():
     assert d["value"] > 0 and d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 1
     assert d["unit"] == "space-time DoFs/s" and "workload" in d["config"]
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 2 and cb["value"] == d["value"] and cb["sample"]
+    assert d["config"]["oracle_processes"] == 2 and cb["cpu"]
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0

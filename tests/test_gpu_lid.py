@@ -84,3 +84,19 @@ def test_lid_driven_cavity_small_matches_oracle():
         got = slab.remove_pressure_mean(x.cpu().numpy())
         assert rel(got, slab.remove_pressure_mean(sols_o[s])) < 1e-9
     g.close()
+
+
+def test_march_host_boundary_data_matches_oracle():
+    """The same cavity through stmg_march_host (host boundary data in, host solutions out,
+    copies overlapped with the solves) against the oracle's direct march."""
+    pb = lid_driven_3d()
+    n, r, k, N, run = 2, 1, 1, 16, 4
+    sols_o, _, slab, _ = march(pb, n, r, k, N, solver="direct", slabs_to_run=run)
+    g = stmg.SpaceTimeMG(dim=3, n_cells=n, r=r, k=k, nu=1.0, T=8.0, n_slabs=N, rel_tol=1e-12)
+    G = np.stack([g.boundary_vector(pb.boundary, s).cpu().numpy() for s in range(run)])
+    X = np.full_like(G, np.nan)
+    infos = g.march_host(G, X, boundary_data=True)
+    assert [i["status"] for i in infos] == [0] * run
+    for s in range(run):
+        assert rel(slab.remove_pressure_mean(X[s]), slab.remove_pressure_mean(sols_o[s])) < 1e-9
+    g.close()
