@@ -141,6 +141,12 @@ typedef struct {
                               thread per output value (2D levels only; 3D levels and
                               other shapes keep 1).  Both compute P and P^T exactly
                               (App. A); they differ in rounding order only.             */
+  int    apply_variant;    /* operator kernels: 0 = chosen by the tuner (default),
+                              1 = one thread block per group of cells (shared-memory sum
+                              factorisation, atomics on shared nodes), 2 = node-centred
+                              form on tiles of cells, every output written once (2D
+                              levels only; 3D levels keep 1).  Same operator; they differ
+                              in rounding order only.                                    */
 } stmg_config;
 
 typedef struct {
@@ -161,6 +167,10 @@ typedef struct {
   int       streaming;     /* 1: the sweep reads the stored inverses with evict-first loads
                               (inverses larger than about a third of L2), so that the
                               coarser levels' inverses stay L2-resident                   */
+  int       apply_variant[2]; /* per precision: 1 = one thread block per group of cells
+                                 (apply_cells_per_block), 2 = node-centred 2D form on tiles
+                                 of apply_tile cells (no atomics)                          */
+  int       apply_tile[2][2]; /* per precision: cells per block in x and y (variant 2)    */
 } stmg_level_info_t;
 
 typedef struct {

@@ -50,7 +50,8 @@ class SpaceTimeMG:
                  nu2: int = 1, precond_precision="fp64", precisions=("fp64", "fp32"),
                  gmres_max_iter: int = 200, rel_tol: float = 1e-8, use_graphs: bool = True,
                  sweep_variant: int = 0, autotune: bool = True, coarse_n: int = 1, k_min: int = 1,
-                 n_sub: int = 1, half_inverses: bool = False, transfer_variant: int = 0):
+                 n_sub: int = 1, half_inverses: bool = False, transfer_variant: int = 0,
+                 apply_variant: int = 0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("SpaceTimeMG needs a CUDA device (no CPU fallback)")
@@ -78,6 +79,7 @@ class SpaceTimeMG:
         cfg.n_sub = int(n_sub)
         cfg.half_inverses = int(half_inverses)
         cfg.transfer_variant = int(transfer_variant)
+        cfg.apply_variant = int(apply_variant)
         self.cfg = cfg
         self.dim, self.r, self.k, self.n_sub = dim, r, k, int(n_sub)
         self.kt = self.n_sub * (k + 1)
@@ -100,7 +102,9 @@ class SpaceTimeMG:
                                 "patches_per_block": tuple(li.patches_per_block),
                                 "apply_cells_per_block": tuple(li.apply_cells_per_block),
                                 "transfer_cells_per_block": tuple(li.transfer_cells_per_block),
-                                "streaming": li.streaming})
+                                "streaming": li.streaming,
+                                "apply_variant": tuple(li.apply_variant),
+                                "apply_tile": tuple(tuple(t) for t in li.apply_tile)})
 
     # ---------------------------------------------------------------- plumbing
     def close(self):

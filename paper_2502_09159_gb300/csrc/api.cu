@@ -180,7 +180,7 @@ template <> constexpr int prec_of<float>() { return STMG_FP32; }
 static int ipow(int b, int e) { int r = 1; while (e-- > 0) r *= b; return r; }
 
 template <typename T>
-static void fill_apply_params(const LevelHost& H, ApplyParams<T>* p) {
+static void fill_apply_params(const LevelHost& H, ApplyParams<T>* p, int variant) {
   std::memset(p, 0, sizeof(*p));
   p->n = H.n; p->G = H.G; p->kt = H.kt; p->npm = H.npm;
   p->n_nodes = H.n_nodes; p->n_vel = H.n_vel; p->n_pres = H.n_pres;
@@ -201,6 +201,10 @@ static void fill_apply_params(const LevelHost& H, ApplyParams<T>* p) {
   while (cpb > 1 && apply_smem_bytes<T>(H.dim, np, H.kt, H.npm, cpb) > 64 * 1024) --cpb;
   cpb = std::min(cpb, H.n_cells);
   p->cpb = cpb;
+  p->variant = 1;
+  p->tcx = p->tcy = std::min(4, H.n);
+  while (p->tcx > 1 && apply2d_smem_bytes<T>(np, H.kt, H.npm, p->tcx, p->tcy) > 96 * 1024) p->tcx = p->tcy = p->tcx / 2;
+  if (H.dim == 2 && variant != 1) p->variant = 2;   // node-centred form (2D levels)
 }
 
 template <typename T>
@@ -286,7 +290,7 @@ static int setup_precision(stmg_handle* h, LevelDev& lv, const double* d_cls, co
                            bool with_inverses = true) {
   PrecDev<T>& P = lv.pd<T>();
   const LevelHost& H = lv.H;
-  fill_apply_params<T>(H, &P.ap);
+  fill_apply_params<T>(H, &P.ap, h->cfg.apply_variant);
   CKS(dalloc(&P.b, H.size));
   CKS(dalloc(&P.x, H.size));
   CKS(dalloc(&P.r, H.size));
@@ -335,8 +339,13 @@ static void free_level(LevelDev& lv) {
 template <typename T>
 static int op_apply(stmg_handle* h, int l, const T* x, const T* b, T* y, int mode, cudaStream_t s) {
   LevelDev& lv = h->L[l];
-  CK(cudaMemsetAsync(y, 0, sizeof(T) * lv.H.size, s));
-  CK(launch_apply<T>(lv.H.dim, lv.H.np, lv.pd<T>().ap, x, b, y, mode, s));
+  const ApplyParams<T>& ap = lv.pd<T>().ap;
+  if (ap.variant == 2) {                 // writes every entry of y
+    CK(launch_apply2d<T>(lv.H.np, ap, x, b, y, mode, s));
+  } else {
+    CK(cudaMemsetAsync(y, 0, sizeof(T) * lv.H.size, s));
+    CK(launch_apply<T>(lv.H.dim, lv.H.np, ap, x, b, y, mode, s));
+  }
   h->launches += 1;
   return STMG_OK;
 }
@@ -479,14 +488,31 @@ static int autotune_level(stmg_handle* h, int l) {
   }
   {
     best = 1e30f;
-    int best_cpb = P.ap.cpb;
-    for (int cpb = 1; cpb <= 32 && cpb <= lv.H.n_cells; cpb *= 2) {
+    int best_cpb = P.ap.cpb, best_var = 1, best_tx = P.ap.tcx, best_ty = P.ap.tcy;
+    const int fixed = lv.H.dim == 2 ? h->cfg.apply_variant : 1;   // 0: free choice, 1 / 2: fixed variant
+    P.ap.variant = 1;
+    for (int cpb = 1; cpb <= 32 && cpb <= lv.H.n_cells && fixed != 2; cpb *= 2) {
       if (apply_smem_bytes<T>(lv.H.dim, lv.H.np, lv.H.kt, lv.H.npm, cpb) > 100 * 1024) break;
       P.ap.cpb = cpb;
       CKS(time_it(h, [&]() { return op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, h->st); }, &ms));
       if (ms < best) { best = ms; best_cpb = cpb; }
     }
+    if (lv.H.dim == 2 && fixed != 1) {   // node-centred form: tiles of tx x ty cells
+      static const int tiles[][2] = {{2, 2}, {4, 2}, {4, 4}, {8, 4}, {8, 8}, {16, 8}};
+      P.ap.variant = 2;
+      for (const auto& t : tiles) {
+        if (t[0] > 2 * lv.H.n || t[1] > 2 * lv.H.n) continue;
+        if (apply2d_smem_bytes<T>(lv.H.np, lv.H.kt, lv.H.npm, t[0], t[1]) > 100 * 1024) continue;
+        P.ap.tcx = std::min(t[0], lv.H.n);
+        P.ap.tcy = std::min(t[1], lv.H.n);
+        CKS(time_it(h, [&]() { return op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, h->st); }, &ms));
+        if (ms < best) { best = ms; best_var = 2; best_tx = P.ap.tcx; best_ty = P.ap.tcy; }
+      }
+    }
     P.ap.cpb = best_cpb;
+    P.ap.variant = best_var;
+    P.ap.tcx = best_tx;
+    P.ap.tcy = best_ty;
   }
   if (!last && h->L[l + 1].pd<T>().b) {
     PrecDev<T>& C = h->L[l + 1].pd<T>();
@@ -870,6 +896,7 @@ int stmg_default_config(stmg_config* c) {
   c->n_sub = 1;
   c->half_inverses = 0;
   c->transfer_variant = 0;
+  c->apply_variant = 0;
   return STMG_OK;
 }
 
@@ -885,6 +912,7 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
   if ((c.precisions & 3) == 0) return STMG_ERR_ARG;
   if (c.sweep_variant < 0 || c.sweep_variant > 2) return STMG_ERR_ARG;
   if (c.transfer_variant < 0 || c.transfer_variant > 2) return STMG_ERR_ARG;
+  if (c.apply_variant < 0 || c.apply_variant > 2) return STMG_ERR_ARG;
   if (c.precond_precision != STMG_FP64 && c.precond_precision != STMG_FP32) return STMG_ERR_ARG;
   if (!(c.precisions & (1 << c.precond_precision))) return STMG_ERR_ARG;
   h->tau = c.T / ((double)c.n_slabs * c.n_sub);
@@ -1089,6 +1117,10 @@ int stmg_level_info(const stmg_handle* h, int lvl, stmg_level_info_t* info) {
   info->transfer_cells_per_block[0] = L.d.tp.variant == 2 ? 0 : L.d.tp.cpb;
   info->transfer_cells_per_block[1] = L.f.tp.variant == 2 ? 0 : L.f.tp.cpb;
   info->streaming = L.streaming;
+  info->apply_variant[0] = L.d.ap.variant;
+  info->apply_variant[1] = L.f.ap.variant;
+  info->apply_tile[0][0] = L.d.ap.tcx; info->apply_tile[0][1] = L.d.ap.tcy;
+  info->apply_tile[1][0] = L.f.ap.tcx; info->apply_tile[1][1] = L.f.ap.tcy;
   return STMG_OK;
 }
 

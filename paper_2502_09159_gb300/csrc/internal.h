@@ -55,6 +55,8 @@ double legendre_unit(int i, double xi);                       // sqrt(2i+1) P_i(
 template <typename T>
 struct ApplyParams {
   int n, G, kt, npm, cpb;
+  int variant;                    // 1: per-cell kernel (k_apply), 2: node-centred 2D kernel (k_apply2d)
+  int tcx, tcy;                   // variant 2: cells per block in x and y
   long long n_nodes, n_vel, n_pres;
   T M1[MAXNP * MAXNP], K1[MAXNP * MAXNP], G1[MAXNP * MAXNP], N1[MAXNP * MAXNP];
   T Kt[MAXKT * MAXKT];
@@ -110,6 +112,11 @@ cudaError_t launch_apply(int dim, int np, const ApplyParams<T>& p, const T* x, c
                          int mode, cudaStream_t st);
 template <typename T>
 size_t apply_smem_bytes(int dim, int np, int kt, int npm, int cpb);
+// node-centred form on 2D levels (k_apply2d.cu): writes every entry of y, no zero-fill needed
+template <typename T>
+cudaError_t launch_apply2d(int np, const ApplyParams<T>& p, const T* x, const T* b, T* y, int mode, cudaStream_t st);
+template <typename T>
+size_t apply2d_smem_bytes(int np, int kt, int npm, int tcx, int tcy);
 
 template <typename T>
 cudaError_t launch_vanka_sweep(const int* dofs, const T* inv, const T* res, T* x, long long n_patches, int B,

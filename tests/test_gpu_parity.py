@@ -87,6 +87,34 @@ def test_apply_and_residual(case):
         assert rel(g.apply_transpose(dev(x, torch.float32), l).double(), s.S.T @ x) < 2e-6
 
 
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("case", [c for c in CASES if c[0] == 2], ids=[i for c, i in zip(CASES, IDS) if c[0] == 2])
+def test_apply_variants_2d(case, variant):
+    """Both operator kernels forced on every 2D level: the per-cell form (atomics on shared
+    nodes) and the node-centred form (tiles of 4x4 cells, ragged tiles on 3x3 / 5x5 meshes,
+    every output written once): apply, residual, S^T and the lift against the oracle."""
+    og, _ = setup_case(case)
+    dim, n, r, k, levels = case
+    levels = levels or stmg.host_default_hierarchy(n, r, k)
+    g = stmg.SpaceTimeMG(dim=dim, n_cells=n, r=r, k=k, nu=NU, T=TAU * 5, n_slabs=5, levels=levels,
+                         use_graphs=False, autotune=False, apply_variant=variant)
+    for l, s in enumerate(og.slabs):
+        assert g.levels[l]["apply_variant"] == (variant, variant)
+        x = random_vector(s.size, 63 + l)
+        b = random_vector(s.size, 67 + l)
+        ref = s.S @ x
+        y = torch.full((s.size,), float("nan"), dtype=torch.float64, device="cuda")   # every entry is written
+        assert rel(g.apply(dev(x), l, out=y), ref) < 1e-12
+        assert rel(g.residual(dev(b), dev(x), l), b - ref) < 1e-12
+        assert rel(g.apply_transpose(dev(x), l), s.S.T @ x) < 1e-12
+        assert rel(g.apply(dev(x, torch.float32), l).double(), ref) < 2e-6
+        assert rel(g.residual(dev(b, torch.float32), dev(x, torch.float32), l).double(), b - ref) < 2e-6
+    s0 = og.slabs[0]
+    gv, bv = random_vector(s0.size, 71), random_vector(s0.size, 73)
+    assert rel(g.dirichlet_lift(dev(gv), dev(bv)), s0.lift(gv, bv)) < 1e-12
+    g.close()
+
+
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_vanka_sweep_and_smoothing_step(case):
     og, g = setup_case(case)
