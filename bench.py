@@ -82,6 +82,8 @@ def parse():
     p.add_argument("--level", type=int, default=0, help="level of --only-kernel")
     p.add_argument("--prec", default="fp32", choices=["fp32", "fp64"], help="precision of --only-kernel")
     p.add_argument("--reps", type=int, default=3, help="launches of --only-kernel inside the profiler range")
+    p.add_argument("--apply-variant", type=int, default=0, help="force the operator kernel (1 per-cell, 2 node-centred)")
+    p.add_argument("--sweep-variant", type=int, default=0, help="force the sweep kernel (1 block, 2 TMA, 3 pipelined)")
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
                    help="c2: the 2D headline configuration; c3: the 3D 32^3 configuration; "
                         "lid: the lid-driven cavity at c = 4 (lid5: c = 5; lid_r3: c = 4 with Q4/P3 DG(3))")
@@ -258,7 +260,8 @@ def run_ours(args):
         return stmg.SpaceTimeMG(**w, precond_precision=prec, coarse_n=min(coarse_n, w["n_cells"]),
                                 k_min=k_min, levels=lv, precisions=precisions if prec == "fp32" else (prec,),
                                 gmres_max_iter=max_iter or (200 if w["dim"] == 2 else 80),
-                                half_inverses=half and prec == "fp32")
+                                half_inverses=half and prec == "fp32", apply_variant=args.apply_variant,
+                                sweep_variant=args.sweep_variant)
 
     torch.cuda.synchronize()
     t_setup = time.perf_counter()
@@ -508,7 +511,9 @@ def only_kernel(mg, args):
     torch.cuda.profiler.stop()
     ms = e0.elapsed_time(e1) / args.reps
     out = {"kernel": args.only_kernel, "prec": prec, "level": lvl, "dofs": D, "ms": ms, "dofs_per_s": D / (ms / 1e3),
-           "levels": [(l["n"], l["r"], l["k"]) for l in mg.levels]}
+           "levels": [(l["n"], l["r"], l["k"]) for l in mg.levels],
+           "launch_shapes": [{k: l[k] for k in ("apply_variant", "apply_tile", "apply_cells_per_block", "sweep_variant",
+                                                "patches_per_block", "transfer_cells_per_block")} for l in mg.levels]}
     if args.only_kernel == "sweep":
         out["alg_bytes"] = sweep_alg_bytes(mg.levels[lvl], prec)
         out["GBs"] = out["alg_bytes"] / (ms / 1e3) / 1e9

@@ -114,7 +114,10 @@ typedef struct {
   int    sweep_variant;    /* Vanka sweep kernel: 0 = chosen by the tuner (default),
                               1 = one thread block per group of patches,
                               2 = persistent TMA-pipelined (one CTA per SM,
-                              cp.async.bulk + mbarrier; patches with B <= 512)          */
+                              cp.async.bulk + mbarrier; patches with B <= 512),
+                              3 = pipelined block sweep (the first loads of every row
+                              issued before the residual gather, double-buffered rounds;
+                              patches with B <= 512, FP32/FP64 inverses)                */
   int    autotune;         /* 1 (default): stmg_create times the candidate launch shapes
                               of every level (see stmg_autotune) and keeps the fastest  */
   int    coarse_n;         /* coarsest mesh of the default hierarchy (Alg. 2's h_0 =
@@ -159,7 +162,7 @@ typedef struct {
   long long n_patches;
   int       n_patch_classes;/* distinct patch matrices inverted at setup                 */
   long long inverse_bytes[2]; /* stored patch-inverse bytes for FP64 / FP32 (0: none)    */
-  int       sweep_variant[2];            /* per precision: 1 block sweep, 2 TMA sweep      */
+  int       sweep_variant[2];            /* per precision: 1 block, 2 TMA, 3 pipelined block */
   int       patches_per_block[2];        /* block sweep launch shape, per precision          */
   int       apply_cells_per_block[2];    /* apply / residual launch shape, per precision     */
   int       transfer_cells_per_block[2]; /* transfers to the next coarser level; 0: the

@@ -42,8 +42,9 @@ struct LevelDev {
   double* G = nullptr;      // coarsest level: bordered inverse, column-major
   double* Gacc = nullptr;   // coarsest level with D > 1024: FP64 accumulator of the tiled GEMV
   int streaming = 0;        // read the inverses with evict-first loads
-  int sweep_var[2] = {1, 1};  // per precision: 1 = block per patch group, 2 = TMA-pipelined
-  int ppb[2] = {1, 1};        // per precision: patches per block of the block sweep
+  int sweep_var[2] = {1, 1};  // per precision: 1 = block per patch group, 2 = TMA-pipelined, 3 = pipelined block
+  int ppb[2] = {1, 1};        // per precision: patches per block of the block sweeps
+  int unroll[2] = {8, 8};     // per precision: chunks per round of the pipelined block sweep
   template <typename T> PrecDev<T>& pd();
 };
 template <> PrecDev<double>& LevelDev::pd<double>() { return d; }
@@ -363,6 +364,9 @@ static int op_sweep(stmg_handle* h, int l, const T* res, T* x, cudaStream_t s) {
   else if (lv.sweep_var[w] == 2 && tma_sweep_supported<T>(lv.H.B))
     CK(launch_vanka_sweep_tma<T>(lv.dofs, P.inv, res, x, lv.H.n_patches, lv.H.B, lv.H.Bc, h->n_sm,
                                  lv.streaming, h->d_err, s));
+  else if (lv.sweep_var[w] == 3 && pipe_sweep_supported<T>(lv.H.B, lv.ppb[w]))
+    CK(launch_vanka_sweep_pipe<T>(lv.dofs, P.inv, res, x, lv.H.n_patches, lv.H.B, lv.H.Bc, lv.ppb[w], lv.unroll[w],
+                                  lv.streaming, s));
   else
     CK(launch_vanka_sweep<T>(lv.dofs, P.inv, res, x, lv.H.n_patches, lv.H.B, lv.H.Bc, lv.ppb[w],
                              lv.streaming, s));
@@ -370,13 +374,18 @@ static int op_sweep(stmg_handle* h, int l, const T* res, T* x, cudaStream_t s) {
   return STMG_OK;
 }
 
+// b_c = P^T r_f; with zc != NULL also zc = 0 (the coarse iterate), by the gather form in the
+// same launch, else by a zero-fill
 template <typename T>
-static int op_restrict(stmg_handle* h, int l, const T* rf, T* bc, cudaStream_t s) {
+static int op_restrict(stmg_handle* h, int l, const T* rf, T* bc, cudaStream_t s, T* zc = nullptr) {
   LevelDev& lc = h->L[l + 1];
   const TransferParams<T>& tp = h->L[l].pd<T>().tp;
-  if (!(tp.variant == 2 && transfer_gather_supported(tp)))     // the gather form writes all of b_c
+  const bool gather = tp.variant == 2 && transfer_gather_supported(tp);
+  if (!gather) {                                  // the gather form writes all of b_c (and zc)
     CK(cudaMemsetAsync(bc, 0, sizeof(T) * lc.H.size, s));
-  CK(launch_restrict<T>(tp, rf, bc, s));
+    if (zc) CK(cudaMemsetAsync(zc, 0, sizeof(T) * lc.H.size, s));
+  }
+  CK(launch_restrict<T>(tp, rf, bc, gather ? zc : nullptr, s));
   h->launches += 1;
   return STMG_OK;
 }
@@ -412,26 +421,55 @@ static int op_coarse(stmg_handle* h, const T* b, T* x, cudaStream_t s) {
 //   apply      1 ... 32 cells per block (shared memory <= 100 KB)
 //   transfers  1 ... 32 coarse cells per block for restriction + prolongation
 // ------------------------------------------------------------------------------------
+// Device time of one candidate: five back-to-back launches captured in a CUDA graph on the
+// internal stream (so the host's launch overhead, larger than a small level's kernel, does
+// not enter), the graph replayed three times after a warm-up, the fastest replay counting.
+// The launches that precede the capture run eagerly, outside capture (kernel attributes).
 template <typename F>
 static int time_it(stmg_handle* h, F&& fn, float* ms) {
   cudaEvent_t a = new_event(h), b = new_event(h);
   if (!a || !b) return STMG_ERR_CUDA;
-  for (int i = 0; i < 3; ++i) CKS(fn());
-  float best = 1e30f;
-  for (int trial = 0; trial < 3; ++trial) {
-    CK(cudaEventRecord(a, h->st));
-    for (int i = 0; i < 5; ++i) CKS(fn());
-    CK(cudaEventRecord(b, h->st));
-    CK(cudaEventSynchronize(b));
-    float t = 0.f;
-    CK(cudaEventElapsedTime(&t, a, b));
-    if (t < best) best = t;
-    if (t > 5.f) break;                  // long launches: one trial is stable
-  }
-  *ms = best;
+  cudaStream_t saved = h->st;
+  const int saved_prof = h->prof;
+  h->prof = 0;
+  h->st = h->gst;
+  int st = STMG_OK;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  auto run = [&]() -> int {
+    for (int i = 0; i < 2; ++i) CKS(fn());
+    CK(cudaStreamSynchronize(h->gst));
+    CK(cudaStreamBeginCapture(h->gst, cudaStreamCaptureModeRelaxed));
+    int s = STMG_OK;
+    for (int i = 0; i < 5 && s == STMG_OK; ++i) s = fn();
+    cudaError_t e = cudaStreamEndCapture(h->gst, &g);
+    CKS(s);
+    CK(e);
+    CK(cudaGraphInstantiate(&ge, g, 0));
+    CK(cudaGraphLaunch(ge, h->gst));
+    float best = 1e30f;
+    for (int trial = 0; trial < 3; ++trial) {
+      CK(cudaEventRecord(a, h->gst));
+      CK(cudaGraphLaunch(ge, h->gst));
+      CK(cudaEventRecord(b, h->gst));
+      CK(cudaEventSynchronize(b));
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, a, b));
+      if (t < best) best = t;
+      if (t > 5.f) break;                  // long launches: one trial is stable
+    }
+    *ms = best;
+    return STMG_OK;
+  };
+  st = run();
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  if (st != STMG_OK) cudaGetLastError();
+  h->st = saved;
+  h->prof = saved_prof;
   h->free_events.push_back(a);
   h->free_events.push_back(b);
-  return STMG_OK;
+  return st;
 }
 
 // level 0's residual, repeated until about 20 ms of device time has passed
@@ -469,22 +507,33 @@ static int autotune_level(stmg_handle* h, int l) {
   const bool last = l + 1 == (int)h->L.size();
   float best = 1e30f, ms = 0.f;
   if (!last && P.has_inv) {
-    int best_var = 1, best_ppb = lv.ppb[w];
-    const int only = h->cfg.sweep_variant;             // 0: free choice, 1 / 2: fixed variant
-    for (int ppb = 1; ppb <= 8 && only != 2; ppb *= 2) {
+    int best_var = 1, best_ppb = lv.ppb[w], best_unroll = lv.unroll[w];
+    const int only = h->cfg.sweep_variant;             // 0: free choice, 1 / 2 / 3: fixed variant
+    for (int ppb = 1; ppb <= 8 && (only == 0 || only == 1); ppb *= 2) {
       if (ppb > 1 && ppb * lv.H.B > 1024) break;
       lv.sweep_var[w] = 1;
       lv.ppb[w] = ppb;
       CKS(time_it(h, [&]() { return op_sweep<T>(h, l, P.r, P.x, h->st); }, &ms));
       if (ms < best) { best = ms; best_var = 1; best_ppb = ppb; }
     }
-    if (only != 1 && !P.half && tma_sweep_supported<T>(lv.H.B)) {
+    if ((only == 0 || only == 2) && !P.half && tma_sweep_supported<T>(lv.H.B)) {
       lv.sweep_var[w] = 2;
       CKS(time_it(h, [&]() { return op_sweep<T>(h, l, P.r, P.x, h->st); }, &ms));
       if (ms < best) { best = ms; best_var = 2; }
     }
+    for (int ppb = 1; ppb <= 8 && (only == 0 || only == 3) && !P.half; ppb *= 2) {
+      if (!pipe_sweep_supported<T>(lv.H.B, ppb)) break;
+      for (int u = 4; u <= 8; u += 4) {
+        lv.sweep_var[w] = 3;
+        lv.ppb[w] = ppb;
+        lv.unroll[w] = u;
+        CKS(time_it(h, [&]() { return op_sweep<T>(h, l, P.r, P.x, h->st); }, &ms));
+        if (ms < best) { best = ms; best_var = 3; best_ppb = ppb; best_unroll = u; }
+      }
+    }
     lv.sweep_var[w] = best_var;
     lv.ppb[w] = best_ppb;
+    lv.unroll[w] = best_unroll;
   }
   {
     best = 1e30f;
@@ -557,14 +606,14 @@ static int autotune_impl(stmg_handle* h) {
   return STMG_OK;
 }
 
-// V-cycle on level l: input L[l].b, output L[l].x (zero initial guess), Alg. 1.
+// V-cycle on level l: input L[l].b, output L[l].x from the zero initial guess, Alg. 1.
+// L[l].x must be zero on entry: on the finest level the caller zeroes it (with the
+// conversion of the right-hand side), on the coarser ones the restriction does.
 template <typename T>
 static int vcycle_level(stmg_handle* h, int l, cudaStream_t s) {
   LevelDev& lv = h->L[l];
   PrecDev<T>& P = lv.pd<T>();
-  const size_t bytes = sizeof(T) * lv.H.size;
   if (l == (int)h->L.size() - 1) return op_coarse<T>(h, P.b, P.x, s);
-  CK(cudaMemsetAsync(P.x, 0, bytes, s));
   for (int it = 0; it < h->cfg.nu1; ++it) {          // presmoothing (Eq. Alg:VGMGPre)
     if (it == 0) {
       CKS(op_sweep<T>(h, l, P.b, P.x, s));           // x = 0: the residual is b
@@ -579,7 +628,7 @@ static int vcycle_level(stmg_handle* h, int l, cudaStream_t s) {
     res = P.r;
   }
   PrecDev<T>& C = h->L[l + 1].pd<T>();
-  CKS(op_restrict<T>(h, l, res, C.b, s));            // step 2/3 of Alg. 4 / 5
+  CKS(op_restrict<T>(h, l, res, C.b, s, C.x));       // step 2/3 of Alg. 4 / 5; C.x = 0
   CKS(vcycle_level<T>(h, l + 1, s));
   CKS(op_prolongate_add<T>(h, l, C.x, P.x, s));      // Alg. 6 / 7
   for (int it = 0; it < h->cfg.nu2; ++it) {          // postsmoothing (Eq. Alg:VGMGPost)
@@ -636,12 +685,13 @@ static int precondition(stmg_handle* h, int prec, const double* v, double* z) {
   Prof pr(h, PROF_VCYCLE, h->st);
   if (prec == STMG_FP64) {
     if (!l0.d.b) return STMG_ERR_ARG;
-    CK(cudaMemcpyAsync(l0.d.b, v, sizeof(double) * D, cudaMemcpyDeviceToDevice, h->st));
+    CK((launch_convert_zero<double, double>(D, v, l0.d.b, l0.d.x, h->st)));   // b = v, x = 0
     CKS(run_vcycle<double>(h));
     CK(cudaMemcpyAsync(z, l0.d.x, sizeof(double) * D, cudaMemcpyDeviceToDevice, h->st));
+    h->launches += 1;
   } else {
     if (!l0.f.b) return STMG_ERR_ARG;
-    CK((launch_convert<double, float>(D, v, l0.f.b, h->st)));
+    CK((launch_convert_zero<double, float>(D, v, l0.f.b, l0.f.x, h->st)));    // b = (float) v, x = 0
     CKS(run_vcycle<float>(h));
     CK((launch_convert<float, double>(D, l0.f.x, z, h->st)));
     h->launches += 2;
@@ -910,7 +960,7 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
   if (c.n_sub * (c.k + 1) > MAXKT) return STMG_ERR_UNIMPLEMENTED;
   if (c.gmres_max_iter < 1 || !(c.rel_tol > 0) || c.nu1 < 0 || c.nu2 < 0) return STMG_ERR_ARG;
   if ((c.precisions & 3) == 0) return STMG_ERR_ARG;
-  if (c.sweep_variant < 0 || c.sweep_variant > 2) return STMG_ERR_ARG;
+  if (c.sweep_variant < 0 || c.sweep_variant > 3) return STMG_ERR_ARG;
   if (c.transfer_variant < 0 || c.transfer_variant > 2) return STMG_ERR_ARG;
   if (c.apply_variant < 0 || c.apply_variant > 2) return STMG_ERR_ARG;
   if (c.precond_precision != STMG_FP64 && c.precond_precision != STMG_FP32) return STMG_ERR_ARG;
@@ -984,13 +1034,20 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
       for (int w = 0; w < 2; ++w) {
         L.ppb[w] = std::max(1, std::min(8, 1024 / H.B));
         L.sweep_var[w] = c.sweep_variant == 2 ? 2 : 1;
+        if (c.sweep_variant == 3) {
+          L.ppb[w] = std::max(1, std::min(4, 512 / H.B));
+          L.sweep_var[w] = 3;
+        }
       }
     } else {
       std::vector<double> Gcm;
       if (!build_coarse_inverse(&H, &Gcm)) return STMG_ERR_SINGULAR;
       CKS(dalloc(&L.G, Gcm.size()));
       CK(cudaMemcpy(L.G, Gcm.data(), sizeof(double) * Gcm.size(), cudaMemcpyHostToDevice));
-      if (H.size > 1024) CKS(dalloc(&L.Gacc, H.size));
+      if (H.size > 1024) {
+        CKS(dalloc(&L.Gacc, H.size));
+        CK(cudaMemset(L.Gacc, 0, sizeof(double) * H.size));   // the tiled product keeps it zero between solves
+      }
     }
     int st = STMG_OK;
     if (c.precisions & 1) st = setup_precision<double>(h, L, d_cls, d_cls_of);

@@ -121,6 +121,13 @@ size_t apply2d_smem_bytes(int np, int kt, int npm, int tcx, int tcy);
 template <typename T>
 cudaError_t launch_vanka_sweep(const int* dofs, const T* inv, const T* res, T* x, long long n_patches, int B,
                                int Bc, int ppb, int streaming, cudaStream_t st);
+// pipelined block sweep (first loads before the gather, double-buffered rounds of `unroll`
+// = 4 or 8 chunks); needs ppb * B <= 512
+template <typename T>
+cudaError_t launch_vanka_sweep_pipe(const int* dofs, const T* inv, const T* res, T* x, long long n_patches, int B,
+                                    int Bc, int ppb, int unroll, int streaming, cudaStream_t st);
+template <typename T>
+bool pipe_sweep_supported(int B, int ppb);
 constexpr int TMA_NCW = 4;   // consumer warps of the TMA-pipelined sweep (+1 producer warp)
 // half-precision inverses with FP32 row scales for the FP32 V-cycle (k_vanka.cu)
 cudaError_t launch_replicate_inverses_half(const double* cls, const int* cls_of_patch, const int* dofs, const double* w,
@@ -140,8 +147,10 @@ cudaError_t launch_replicate_inverses(const double* cls, const int* cls_of_patch
 
 template <typename T>
 cudaError_t launch_prolongate(const TransferParams<T>& p, const T* yc, T* xf, cudaStream_t st);
+// zc (may be NULL): the gather form also writes zeros to it (the coarse iterate of the
+// V-cycle); the per-cell form leaves it alone
 template <typename T>
-cudaError_t launch_restrict(const TransferParams<T>& p, const T* rf, T* bc, cudaStream_t st);
+cudaError_t launch_restrict(const TransferParams<T>& p, const T* rf, T* bc, T* zc, cudaStream_t st);
 template <typename T>
 size_t transfer_smem(const TransferParams<T>& p, int restrict_);
 template <typename T>
@@ -158,6 +167,9 @@ cudaError_t launch_forcing(const ForcingParams& p, const double* fq, double* F, 
 // vector kernels
 template <typename Ti, typename To>
 cudaError_t launch_convert(long long n, const Ti* in, To* out, cudaStream_t st);
+// out = (To) in, zero = 0
+template <typename Ti, typename To>
+cudaError_t launch_convert_zero(long long n, const Ti* in, To* out, To* zero, cudaStream_t st);
 cudaError_t launch_scale(long long n, double a, const double* x, double* y, cudaStream_t st);
 cudaError_t launch_multidot(long long n, int nvec, const double* V, long long ld, const double* w,
                             double* partial, int nblocks, cudaStream_t st);

@@ -649,7 +649,7 @@ __device__ __forceinline__ void support_1d(const TransferParams<T>& P, int J, in
 // fastest; the fine temporal sums meet in shared memory for the temporal restriction
 template <typename T, int NPF, int NPC, int HT>
 __global__ void __launch_bounds__(256) k_restrict_g(const TransferParams<T> P, const T* __restrict__ rf,
-                                                    T* __restrict__ bc) {
+                                                    T* __restrict__ bc, T* __restrict__ zc) {
   constexpr int NS = HT ? 2 * (NPF - 1) + 1 : NPF;
   constexpr int BX = 2 * (NS - 1) + 1;
   __shared__ T tsh[256];
@@ -693,6 +693,7 @@ __global__ void __launch_bounds__(256) k_restrict_g(const TransferParams<T> P, c
       if (!dirc)
         for (int f = 0; f < ktf; ++f) o += P.Pt[f * MAXKT + a] * tsh[nl * per + comp * ktf + f];
       bc[a * P.nvc + comp * P.nnc + G] = o;
+      if (zc) zc[a * P.nvc + comp * P.nnc + G] = T(0);
     }
     return;
   }
@@ -720,6 +721,7 @@ __global__ void __launch_bounds__(256) k_restrict_g(const TransferParams<T> P, c
     v += pt * u;
   }
   bc[(long long)ktc * P.nvc + ac * P.npc_tot + cc * P.npmc + mc] = v;
+  if (zc) zc[(long long)ktc * P.nvc + ac * P.npc_tot + cc * P.npmc + mc] = T(0);
 }
 
 template <typename T>
@@ -794,7 +796,7 @@ cudaError_t launch_prolongate(const TransferParams<T>& p, const T* yc, T* xf, cu
 // b_c = P^T r_f.  The per-cell form needs the velocity part of b_c zero on entry; the
 // gather form writes all of b_c.
 template <typename T>
-cudaError_t launch_restrict(const TransferParams<T>& p, const T* rf, T* bc, cudaStream_t st) {
+cudaError_t launch_restrict(const TransferParams<T>& p, const T* rf, T* bc, T* zc, cudaStream_t st) {
   if (p.variant == 2 && transfer_gather_supported(p)) {
     const int npb = 256 / (2 * p.ktf);
     const long long nvb = ((long long)p.Gc * p.Gc + npb - 1) / npb;
@@ -802,7 +804,7 @@ cudaError_t launch_restrict(const TransferParams<T>& p, const T* rf, T* bc, cuda
     const unsigned blocks = (unsigned)(nvb + (npt + 255) / 256);
 #define STMG_RG(F, C, H) \
     if (p.npf == F && p.npc == C && p.h_type == H) { \
-      k_restrict_g<T, F, C, H><<<blocks, 256, 0, st>>>(p, rf, bc); \
+      k_restrict_g<T, F, C, H><<<blocks, 256, 0, st>>>(p, rf, bc, zc); \
       return cudaGetLastError(); \
     }
     STMG_GATHER_SHAPES(STMG_RG)
@@ -822,7 +824,8 @@ template size_t transfer_smem<double>(const TransferParams<double>&, int);
 template size_t transfer_smem<float>(const TransferParams<float>&, int);
 template cudaError_t launch_prolongate<double>(const TransferParams<double>&, const double*, double*, cudaStream_t);
 template cudaError_t launch_prolongate<float>(const TransferParams<float>&, const float*, float*, cudaStream_t);
-template cudaError_t launch_restrict<double>(const TransferParams<double>&, const double*, double*, cudaStream_t);
-template cudaError_t launch_restrict<float>(const TransferParams<float>&, const float*, float*, cudaStream_t);
+template cudaError_t launch_restrict<double>(const TransferParams<double>&, const double*, double*, double*,
+                                            cudaStream_t);
+template cudaError_t launch_restrict<float>(const TransferParams<float>&, const float*, float*, float*, cudaStream_t);
 
 }  // namespace stmg

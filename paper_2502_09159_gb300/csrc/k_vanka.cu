@@ -266,6 +266,120 @@ cudaError_t launch_vanka_sweep_half(const int* dofs, const __half* inv, const fl
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------
+// Pipelined block sweep.  Same work split as k_vanka_sweep (one thread per patch row, ppb
+// patches per block), but the inverse stream never waits on anything else:
+//   * the first U column chunks of the thread's row are loaded before the residual gather
+//     (the gather's two dependent loads, index then value, overlap the inverse stream);
+//   * round c+1's U loads are issued before round c is consumed (double buffer), so a
+//     thread keeps up to 2U 16-byte loads in flight through its whole row;
+//   * the last round is predicated instead of a serial tail loop (a row of 29 chunks is
+//     4 rounds of 8, not 3 rounds and 5 single loads).
+// The residual is zero-padded in shared memory to whole rounds.
+// ------------------------------------------------------------------------------------
+template <typename T, int U>
+__global__ void __launch_bounds__(512) k_vanka_sweep_pipe(const int* __restrict__ dofs, const T* __restrict__ inv,
+                                                          const T* __restrict__ res, T* __restrict__ x,
+                                                          long long n_patches, int B, int Bc, int ppb, int streaming) {
+  using V = typename Vec<T>::type;
+  constexpr int VW = Vec<T>::W;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nch = Bc / VW;
+  const int nrd = (nch + U - 1) / U;                  // rounds per row
+  const int Bp = nrd * U * VW;                        // padded residual length per patch
+  T* rs = reinterpret_cast<T*>(smraw);                // [ppb][Bp]
+  const long long p0 = (long long)blockIdx.x * ppb;
+  const bool st = streaming != 0;
+  const int t = threadIdx.x;
+  const int pl = t / B, j = t - pl * B;
+  const long long p = p0 + pl;
+  const bool active = pl < ppb && p < n_patches;
+  const V* A = active ? reinterpret_cast<const V*>(inv + (size_t)p * B * Bc) + j : nullptr;
+  V cur[U], nxt[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    cur[u] = V{};
+    if (active && u < nch) cur[u] = load_vec(A + (size_t)u * B, st);
+  }
+  int g = -1;
+  if (active) g = dofs[p * B + j];
+  for (int e = t; e < ppb * Bp; e += blockDim.x) {
+    const int q = e / Bp, i = e - q * Bp;
+    const long long pq = p0 + q;
+    T v = 0;
+    if (pq < n_patches && i < B) {
+      const int gi = dofs[pq * B + i];
+      if (gi >= 0) v = res[gi];
+    }
+    rs[e] = v;
+  }
+  __syncthreads();
+  if (!active) return;
+  const T* r = rs + pl * Bp;
+  T acc0 = 0, acc1 = 0;
+  for (int rd = 0; rd < nrd; ++rd) {
+    const int c0 = rd * U;
+    if (rd + 1 < nrd) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = c0 + U + u;
+        nxt[u] = V{};
+        if (c < nch) nxt[u] = load_vec(A + (size_t)c * B, st);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u += 2) {
+      acc0 += dotv(cur[u], r + (c0 + u) * VW);
+      acc1 += dotv(cur[u + 1], r + (c0 + u + 1) * VW);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) cur[u] = nxt[u];
+  }
+  if (g >= 0) atomicAdd(x + g, acc0 + acc1);          // rows carry omega / valence
+}
+
+template <typename T>
+bool pipe_sweep_supported(int B, int ppb) {
+  return B >= 1 && ppb >= 1 && ppb * B <= 512;
+}
+
+template <typename T>
+cudaError_t launch_vanka_sweep_pipe(const int* dofs, const T* inv, const T* res, T* x, long long n_patches, int B,
+                                    int Bc, int ppb, int unroll, int streaming, cudaStream_t st) {
+  constexpr int VW = Vec<T>::W;
+  if (!pipe_sweep_supported<T>(B, ppb)) return cudaErrorInvalidValue;
+  const int nch = Bc / VW;
+  const int threads = ((ppb * B + 31) / 32) * 32;
+  const long long blocks = (n_patches + ppb - 1) / ppb;
+  const int U = unroll == 4 ? 4 : 8;
+  const size_t smem = sizeof(T) * (size_t)ppb * ((nch + U - 1) / U) * U * VW;
+  if (U == 4) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_vanka_sweep_pipe<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    k_vanka_sweep_pipe<T, 4><<<(unsigned)blocks, threads, smem, st>>>(dofs, inv, res, x, n_patches, B, Bc, ppb,
+                                                                     streaming);
+  } else {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_vanka_sweep_pipe<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    k_vanka_sweep_pipe<T, 8><<<(unsigned)blocks, threads, smem, st>>>(dofs, inv, res, x, n_patches, B, Bc, ppb,
+                                                                     streaming);
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_vanka_sweep_pipe<double>(const int*, const double*, const double*, double*, long long,
+                                                     int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_vanka_sweep_pipe<float>(const int*, const float*, const float*, float*, long long, int,
+                                                    int, int, int, int, cudaStream_t);
+template bool pipe_sweep_supported<double>(int, int);
+template bool pipe_sweep_supported<float>(int, int);
+
 template cudaError_t launch_vanka_sweep<double>(const int*, const double*, const double*, double*, long long, int,
                                                 int, int, int, cudaStream_t);
 template cudaError_t launch_vanka_sweep<float>(const int*, const float*, const float*, float*, long long, int, int,

@@ -35,6 +35,24 @@ cudaError_t launch_convert(long long n, const Ti* in, To* out, cudaStream_t st) 
 template cudaError_t launch_convert<double, float>(long long, const double*, float*, cudaStream_t);
 template cudaError_t launch_convert<float, double>(long long, const float*, double*, cudaStream_t);
 
+// out = (To) in and zero = 0 in one pass (the V-cycle's right-hand side and its zero
+// initial iterate on the finest level)
+template <typename Ti, typename To>
+__global__ void k_convert_zero(long long n, const Ti* __restrict__ in, To* __restrict__ out, To* __restrict__ zero) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    out[i] = (To)in[i];
+    zero[i] = To(0);
+  }
+}
+
+template <typename Ti, typename To>
+cudaError_t launch_convert_zero(long long n, const Ti* in, To* out, To* zero, cudaStream_t st) {
+  k_convert_zero<Ti, To><<<grid_for(n), 256, 0, st>>>(n, in, out, zero);
+  return cudaGetLastError();
+}
+template cudaError_t launch_convert_zero<double, float>(long long, const double*, float*, float*, cudaStream_t);
+template cudaError_t launch_convert_zero<double, double>(long long, const double*, double*, double*, cudaStream_t);
+
 __global__ void k_scale(long long n, double a, const double* __restrict__ x, double* __restrict__ y) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = a * x[i];
@@ -439,16 +457,19 @@ __global__ void __launch_bounds__(256) k_coarse_tiled(int D, const double* __res
   atomicAdd(acc + row, ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])));
 }
 
+// x = acc, and acc = 0 again for the next solve (acc is zeroed once when it is allocated)
 template <typename T>
-__global__ void k_coarse_finish(int D, const double* __restrict__ acc, T* __restrict__ x) {
+__global__ void k_coarse_finish(int D, double* __restrict__ acc, T* __restrict__ x) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < D) x[i] = (T)acc[i];
+  if (i < D) {
+    x[i] = (T)acc[i];
+    acc[i] = 0.0;
+  }
 }
 
+// acc: D doubles, zero on entry (and on return)
 template <typename T>
 cudaError_t launch_coarse_tiled(int D, const double* Gcm, const T* b, T* x, double* acc, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * D, st);
-  if (e != cudaSuccess) return e;
   const int nr = (D + 255) / 256, nc = (D + 31) / 32;
   k_coarse_tiled<T><<<dim3(nr, nc), 256, 0, st>>>(D, Gcm, b, acc);
   k_coarse_finish<T><<<nr, 256, 0, st>>>(D, acc, x);

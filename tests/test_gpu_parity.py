@@ -115,6 +115,28 @@ def test_apply_variants_2d(case, variant):
     g.close()
 
 
+@pytest.mark.parametrize("variant", [1, 3])
+@pytest.mark.parametrize("case", CASES[:7], ids=IDS[:7])
+def test_sweep_variants_against_oracle(case, variant):
+    """The block sweep and the pipelined block sweep forced on every level (B <= 512 for the
+    pipelined one; these cases have B <= 404) against the oracle's correction."""
+    og, _ = setup_case(case)
+    dim, n, r, k, levels = case
+    levels = levels or stmg.host_default_hierarchy(n, r, k)
+    g = stmg.SpaceTimeMG(dim=dim, n_cells=n, r=r, k=k, nu=NU, T=TAU * 5, n_slabs=5, levels=levels,
+                         use_graphs=False, autotune=False, sweep_variant=variant)
+    for l, (s, W) in enumerate(zip(og.slabs[:-1], og.smoothers)):
+        assert g.levels[l]["sweep_variant"] == (variant, variant)
+        res = free_vec(s, 77 + l)
+        ref = W.omega * W.correction(res)
+        x = torch.zeros(s.size, dtype=torch.float64, device="cuda")
+        assert rel(g.vanka_sweep(dev(res), x, l), ref) < 1e-12
+        x32 = torch.zeros(s.size, dtype=torch.float32, device="cuda")
+        assert rel(g.vanka_sweep(dev(res, torch.float32), x32, l).double(), ref) < 1e-5
+    g.device_status()
+    g.close()
+
+
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_vanka_sweep_and_smoothing_step(case):
     og, g = setup_case(case)
@@ -164,8 +186,9 @@ def test_sweep_variants_agree_full_size(dtype):
     sweep and the tuner's choice equal the one-block-per-patch-group sweep."""
     gs = [stmg.SpaceTimeMG(dim=2, n_cells=64, r=2, k=2, n_slabs=16, sweep_variant=v, use_graphs=False,
                            precisions=("fp64",) if dtype == torch.float64 else ("fp32",),
-                           precond_precision="fp64" if dtype == torch.float64 else "fp32") for v in (2, 1, 0)]
-    assert all(v == 2 for v in gs[0].levels[0]["sweep_variant"][1 if dtype == torch.float32 else 0:][:1])
+                           precond_precision="fp64" if dtype == torch.float64 else "fp32") for v in (2, 1, 0, 3)]
+    w = 1 if dtype == torch.float32 else 0
+    assert gs[0].levels[0]["sweep_variant"][w] == 2 and gs[3].levels[0]["sweep_variant"][w] == 3
     for l in range(len(gs[0].levels) - 1):
         res = torch.from_numpy(random_vector(gs[0].size(l), 50 + l)).to("cuda", dtype)
         out = []
@@ -175,7 +198,7 @@ def test_sweep_variants_agree_full_size(dtype):
                 g.vanka_sweep(res, x, l)
             out.append(x)
         tol = 1e-13 if dtype == torch.float64 else 2e-6
-        for o in (out[0], out[2]):                      # TMA and tuned against the block sweep
+        for o in (out[0], out[2], out[3]):              # TMA, tuned and pipelined against the block sweep
             assert ((o - out[1]).abs().max() / out[1].abs().max()).item() < tol
     for g in gs:
         g.device_status()
