@@ -147,9 +147,12 @@ typedef struct {
   int    apply_variant;    /* operator kernels: 0 = chosen by the tuner (default),
                               1 = one thread block per group of cells (shared-memory sum
                               factorisation, atomics on shared nodes), 2 = node-centred
-                              form on tiles of cells, every output written once (2D
-                              levels only; 3D levels keep 1).  Same operator; they differ
-                              in rounding order only.                                    */
+                              form on tiles of cells, every output written once, 3 =
+                              register-resident form, one thread per (cell, temporal dof)
+                              (FP32 up to Q5, FP64 up to Q3, k + 1 <= 4).  2 and 3 are for
+                              2D levels; 3D levels and shapes that 3 does not cover keep
+                              1 (resp. 1 or 2).  Same operator; they differ in rounding
+                              order only.                                                */
 } stmg_config;
 
 typedef struct {
@@ -172,7 +175,8 @@ typedef struct {
                               coarser levels' inverses stay L2-resident                   */
   int       apply_variant[2]; /* per precision: 1 = one thread block per group of cells
                                  (apply_cells_per_block), 2 = node-centred 2D form on tiles
-                                 of apply_tile cells (no atomics)                          */
+                                 of apply_tile cells (no atomics), 3 = register-resident
+                                 2D form (one thread per cell and temporal dof)            */
   int       apply_tile[2][2]; /* per precision: cells per block in x and y (variant 2)    */
 } stmg_level_info_t;
 

@@ -26,6 +26,7 @@ struct PrecDev {
   T* x = nullptr;     // V-cycle iterate of this level
   T* r = nullptr;     // residual work vector
   ApplyParams<T> ap{};
+  ApplyRegParams<T> rp{};   // tables of the register-resident 2D operator (apply variant 3)
   TransferParams<T> tp{};   // transfer between this level and the next coarser one
   bool has_inv = false;
   // FP32 V-cycle with half-precision inverses: FP16 rows scaled to [-1, 1], FP32 row scales
@@ -209,6 +210,30 @@ static void fill_apply_params(const LevelHost& H, ApplyParams<T>* p, int variant
 }
 
 template <typename T>
+static void fill_apply_reg_params(const LevelHost& H, ApplyRegParams<T>* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->n = H.n; p->G = H.G; p->kt = H.kt; p->npm = H.npm;
+  p->n_nodes = H.n_nodes; p->n_vel = H.n_vel; p->n_pres = H.n_pres;
+  const int np = H.np;
+  for (int i = 0; i < np * np; ++i) { p->M1[i] = (T)H.t1.M1[i]; p->K1[i] = (T)H.t1.K1[i]; }
+  if (H.dim == 2 && H.npm <= MAXPM2)
+    for (int d = 0; d < 2; ++d)
+      for (int m = 0; m < H.npm; ++m)
+        for (int iy = 0; iy < np; ++iy)
+          for (int ix = 0; ix < np; ++ix) {
+            const double fx = (d == 0 ? H.t1.G1 : H.t1.N1)[H.modes[m][0] * np + ix];
+            const double fy = (d == 1 ? H.t1.G1 : H.t1.N1)[H.modes[m][1] * np + iy];
+            p->CB[d][m][iy * np + ix] = (T)(fx * fy);
+          }
+  for (int a = 0; a < H.kt; ++a) {
+    for (int b = 0; b < H.kt; ++b) p->Kt[a * MAXKT + b] = (T)H.tt.K[a * H.kt + b];
+    p->beta[a] = (T)(H.tt.M[a] * H.nu * std::pow(H.h, H.dim - 2));
+    p->bscale[a] = (T)(-H.tt.M[a] * std::pow(H.h, H.dim - 1));
+  }
+  p->hd = (T)std::pow(H.h, H.dim);
+}
+
+template <typename T>
 static void fill_transfer_params(const LevelHost& F, const LevelHost& C, TransferParams<T>* p) {
   std::memset(p, 0, sizeof(*p));
   p->dim = F.dim;
@@ -292,6 +317,10 @@ static int setup_precision(stmg_handle* h, LevelDev& lv, const double* d_cls, co
   PrecDev<T>& P = lv.pd<T>();
   const LevelHost& H = lv.H;
   fill_apply_params<T>(H, &P.ap, h->cfg.apply_variant);
+  fill_apply_reg_params<T>(H, &P.rp);
+  if (H.dim == 2 && apply2d_reg_supported<T>(H.np, H.kt, H.npm) &&
+      (h->cfg.apply_variant == 0 || h->cfg.apply_variant == 3))
+    P.ap.variant = 3;                    // register-resident form where the cell tile fits
   CKS(dalloc(&P.b, H.size));
   CKS(dalloc(&P.x, H.size));
   CKS(dalloc(&P.r, H.size));
@@ -343,6 +372,9 @@ static int op_apply(stmg_handle* h, int l, const T* x, const T* b, T* y, int mod
   const ApplyParams<T>& ap = lv.pd<T>().ap;
   if (ap.variant == 2) {                 // writes every entry of y
     CK(launch_apply2d<T>(lv.H.np, ap, x, b, y, mode, s));
+  } else if (ap.variant == 3) {          // scatter-adds the velocity rows, stores the pressure rows
+    CK(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)lv.H.kt * lv.H.n_vel, s));
+    CK(launch_apply2d_reg<T>(lv.H.np, lv.pd<T>().rp, x, b, y, mode, s));
   } else {
     CK(cudaMemsetAsync(y, 0, sizeof(T) * lv.H.size, s));
     CK(launch_apply<T>(lv.H.dim, lv.H.np, ap, x, b, y, mode, s));
@@ -540,13 +572,13 @@ static int autotune_level(stmg_handle* h, int l) {
     int best_cpb = P.ap.cpb, best_var = 1, best_tx = P.ap.tcx, best_ty = P.ap.tcy;
     const int fixed = lv.H.dim == 2 ? h->cfg.apply_variant : 1;   // 0: free choice, 1 / 2: fixed variant
     P.ap.variant = 1;
-    for (int cpb = 1; cpb <= 32 && cpb <= lv.H.n_cells && fixed != 2; cpb *= 2) {
+    for (int cpb = 1; cpb <= 32 && cpb <= lv.H.n_cells && (fixed == 0 || fixed == 1); cpb *= 2) {
       if (apply_smem_bytes<T>(lv.H.dim, lv.H.np, lv.H.kt, lv.H.npm, cpb) > 100 * 1024) break;
       P.ap.cpb = cpb;
       CKS(time_it(h, [&]() { return op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, h->st); }, &ms));
       if (ms < best) { best = ms; best_cpb = cpb; }
     }
-    if (lv.H.dim == 2 && fixed != 1) {   // node-centred form: tiles of tx x ty cells
+    if (lv.H.dim == 2 && (fixed == 0 || fixed == 2)) {   // node-centred form: tiles of tx x ty cells
       static const int tiles[][2] = {{2, 2}, {4, 2}, {4, 4}, {8, 4}, {8, 8}, {16, 8}};
       P.ap.variant = 2;
       for (const auto& t : tiles) {
@@ -557,6 +589,11 @@ static int autotune_level(stmg_handle* h, int l) {
         CKS(time_it(h, [&]() { return op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, h->st); }, &ms));
         if (ms < best) { best = ms; best_var = 2; best_tx = P.ap.tcx; best_ty = P.ap.tcy; }
       }
+    }
+    if (lv.H.dim == 2 && (fixed == 0 || fixed == 3) && apply2d_reg_supported<T>(lv.H.np, lv.H.kt, lv.H.npm)) {
+      P.ap.variant = 3;                  // register-resident form (no launch-shape parameter)
+      CKS(time_it(h, [&]() { return op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, h->st); }, &ms));
+      if (ms < best) { best = ms; best_var = 3; }
     }
     P.ap.cpb = best_cpb;
     P.ap.variant = best_var;
@@ -962,7 +999,7 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
   if ((c.precisions & 3) == 0) return STMG_ERR_ARG;
   if (c.sweep_variant < 0 || c.sweep_variant > 3) return STMG_ERR_ARG;
   if (c.transfer_variant < 0 || c.transfer_variant > 2) return STMG_ERR_ARG;
-  if (c.apply_variant < 0 || c.apply_variant > 2) return STMG_ERR_ARG;
+  if (c.apply_variant < 0 || c.apply_variant > 3) return STMG_ERR_ARG;
   if (c.precond_precision != STMG_FP64 && c.precond_precision != STMG_FP32) return STMG_ERR_ARG;
   if (!(c.precisions & (1 << c.precond_precision))) return STMG_ERR_ARG;
   h->tau = c.T / ((double)c.n_slabs * c.n_sub);

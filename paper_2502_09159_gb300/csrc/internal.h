@@ -66,6 +66,18 @@ struct ApplyParams {
   signed char modes[MAXPM][3];
 };
 
+// register-resident 2D operator (k_apply2d_reg.cu): tables in the parameter bank
+constexpr int MAXPM2 = 15;  // pressure modes per cell in 2D, C(4+2, 2)
+template <typename T>
+struct ApplyRegParams {
+  int n, G, kt, npm;
+  long long n_nodes, n_vel, n_pres;
+  T M1[MAXNP * MAXNP], K1[MAXNP * MAXNP];
+  T CB[2][MAXPM2][MAXNP * MAXNP];   // [component][mode][node ix + np iy] = F_x(mode, ix) F_y(mode, iy)
+  T Kt[MAXKT * MAXKT];
+  T hd, beta[MAXKT], bscale[MAXKT];
+};
+
 template <typename T>
 struct TransferParams {
   int dim, h_type;                // h_type: 1 = n -> 2n in space, 0 = same mesh
@@ -112,6 +124,13 @@ cudaError_t launch_apply(int dim, int np, const ApplyParams<T>& p, const T* x, c
                          int mode, cudaStream_t st);
 template <typename T>
 size_t apply_smem_bytes(int dim, int np, int kt, int npm, int cpb);
+// register-resident form on 2D levels (k_apply2d_reg.cu), kt <= 4: the velocity part of y
+// must be zero on entry (scatter-adds), the pressure part is overwritten
+template <typename T>
+cudaError_t launch_apply2d_reg(int np, const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode,
+                               cudaStream_t st);
+template <typename T>
+bool apply2d_reg_supported(int np, int kt, int npm);
 // node-centred form on 2D levels (k_apply2d.cu): writes every entry of y, no zero-fill needed
 template <typename T>
 cudaError_t launch_apply2d(int np, const ApplyParams<T>& p, const T* x, const T* b, T* y, int mode, cudaStream_t st);

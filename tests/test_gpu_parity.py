@@ -87,19 +87,28 @@ def test_apply_and_residual(case):
         assert rel(g.apply_transpose(dev(x, torch.float32), l).double(), s.S.T @ x) < 2e-6
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+def reg_supported(r, k, prec):
+    """The register-resident 2D operator covers FP32 up to Q5 (r <= 3), FP64 up to Q3 (r <= 1)
+    and k + 1 <= 4; other shapes fall back to the node-centred form when it is forced."""
+    return k + 1 <= 4 and r <= (3 if prec == "fp32" else 1)
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("case", [c for c in CASES if c[0] == 2], ids=[i for c, i in zip(CASES, IDS) if c[0] == 2])
 def test_apply_variants_2d(case, variant):
-    """Both operator kernels forced on every 2D level: the per-cell form (atomics on shared
-    nodes) and the node-centred form (tiles of 4x4 cells, ragged tiles on 3x3 / 5x5 meshes,
-    every output written once): apply, residual, S^T and the lift against the oracle."""
+    """Every operator kernel forced on every 2D level: the per-cell form (atomics on shared
+    nodes), the node-centred form (tiles of 4x4 cells, ragged tiles on 3x3 / 5x5 meshes,
+    every output written once) and the register-resident form (one thread per cell and
+    temporal dof): apply, residual, S^T and the lift against the oracle."""
     og, _ = setup_case(case)
     dim, n, r, k, levels = case
     levels = levels or stmg.host_default_hierarchy(n, r, k)
     g = stmg.SpaceTimeMG(dim=dim, n_cells=n, r=r, k=k, nu=NU, T=TAU * 5, n_slabs=5, levels=levels,
                          use_graphs=False, autotune=False, apply_variant=variant)
     for l, s in enumerate(og.slabs):
-        assert g.levels[l]["apply_variant"] == (variant, variant)
+        lr, lk = levels[l][1], levels[l][2]
+        want = tuple(variant if variant != 3 or reg_supported(lr, lk, p) else 2 for p in ("fp64", "fp32"))
+        assert g.levels[l]["apply_variant"] == want
         x = random_vector(s.size, 63 + l)
         b = random_vector(s.size, 67 + l)
         ref = s.S @ x
