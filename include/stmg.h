@@ -153,6 +153,12 @@ typedef struct {
                               2D levels; 3D levels and shapes that 3 does not cover keep
                               1 (resp. 1 or 2).  Same operator; they differ in rounding
                               order only.                                                */
+  int    persistent;       /* levels below the finest in one persistent kernel (grid-wide
+                              barriers between its sweeps, residuals, transfers and the
+                              coarse product): 0 = never, 1 = where the tuner finds it
+                              faster (default), 2 = from the first level it covers (2D
+                              Q2/P1 levels, k + 1 <= 4, patches of <= 256 dofs).  Same
+                              V-cycle; rounding order only.                              */
 } stmg_config;
 
 typedef struct {
@@ -178,6 +184,8 @@ typedef struct {
                                  of apply_tile cells (no atomics), 3 = register-resident
                                  2D form (one thread per cell and temporal dof)            */
   int       apply_tile[2][2]; /* per precision: cells per block in x and y (variant 2)    */
+  int       persistent[2];    /* per precision: 1 if the level runs inside the persistent
+                                 multigrid kernel (its launch shapes above then unused)    */
 } stmg_level_info_t;
 
 typedef struct {

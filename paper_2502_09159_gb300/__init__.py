@@ -51,7 +51,7 @@ class SpaceTimeMG:
                  gmres_max_iter: int = 200, rel_tol: float = 1e-8, use_graphs: bool = True,
                  sweep_variant: int = 0, autotune: bool = True, coarse_n: int = 1, k_min: int = 1,
                  n_sub: int = 1, half_inverses: bool = False, transfer_variant: int = 0,
-                 apply_variant: int = 0):
+                 apply_variant: int = 0, persistent: int = 1):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("SpaceTimeMG needs a CUDA device (no CPU fallback)")
@@ -80,6 +80,7 @@ class SpaceTimeMG:
         cfg.half_inverses = int(half_inverses)
         cfg.transfer_variant = int(transfer_variant)
         cfg.apply_variant = int(apply_variant)
+        cfg.persistent = int(persistent)
         self.cfg = cfg
         self.dim, self.r, self.k, self.n_sub = dim, r, k, int(n_sub)
         self.kt = self.n_sub * (k + 1)
@@ -104,7 +105,8 @@ class SpaceTimeMG:
                                 "transfer_cells_per_block": tuple(li.transfer_cells_per_block),
                                 "streaming": li.streaming,
                                 "apply_variant": tuple(li.apply_variant),
-                                "apply_tile": tuple(tuple(t) for t in li.apply_tile)})
+                                "apply_tile": tuple(tuple(t) for t in li.apply_tile),
+                                "persistent": tuple(li.persistent)})
 
     # ---------------------------------------------------------------- plumbing
     def close(self):

@@ -25,7 +25,7 @@ class Config(C.Structure):
                 ("gmres_max_iter", C.c_int), ("rel_tol", C.c_double), ("use_graphs", C.c_int),
                 ("sweep_variant", C.c_int), ("autotune", C.c_int), ("coarse_n", C.c_int),
                 ("k_min", C.c_int), ("n_sub", C.c_int), ("half_inverses", C.c_int),
-                ("transfer_variant", C.c_int), ("apply_variant", C.c_int)]
+                ("transfer_variant", C.c_int), ("apply_variant", C.c_int), ("persistent", C.c_int)]
 
 
 class LevelInfo(C.Structure):
@@ -35,7 +35,8 @@ class LevelInfo(C.Structure):
                 ("n_patch_classes", C.c_int), ("inverse_bytes", C.c_longlong * 2),
                 ("sweep_variant", C.c_int * 2), ("patches_per_block", C.c_int * 2),
                 ("apply_cells_per_block", C.c_int * 2), ("transfer_cells_per_block", C.c_int * 2),
-                ("streaming", C.c_int), ("apply_variant", C.c_int * 2), ("apply_tile", (C.c_int * 2) * 2)]
+                ("streaming", C.c_int), ("apply_variant", C.c_int * 2), ("apply_tile", (C.c_int * 2) * 2),
+                ("persistent", C.c_int * 2)]
 
 
 class SolveInfo(C.Structure):

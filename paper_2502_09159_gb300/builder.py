@@ -24,7 +24,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libstmg.so")
 
 SOURCES = ["setup.cpp", "levels.cpp", "host_api.cpp", "net_api.cpp",
-           "k_apply.cu", "k_apply2d.cu", "k_apply2d_reg.cu", "k_vanka.cu", "k_transfer.cu", "k_vec.cu", "k_cells.cu", "k_net.cu", "api.cu"]
+           "k_apply.cu", "k_apply2d.cu", "k_apply2d_reg.cu", "k_mg_persist.cu", "k_vanka.cu", "k_transfer.cu", "k_vec.cu", "k_cells.cu", "k_net.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

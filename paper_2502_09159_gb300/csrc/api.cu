@@ -90,6 +90,12 @@ struct stmg_handle {
   std::vector<cudaEvent_t> free_events;
   bool capturing = false;
   void* noalloc = nullptr;        // device address of stmg_smooth_noalloc's fixed array (this device)
+  // persistent multigrid kernel (levels mgp_first.. coarsest in one launch), per precision
+  void* mgp_desc[2] = {nullptr, nullptr};   // device array of MGLevelDesc<T>
+  int mgp_first[2] = {0, 0};                // first level of the persistent part (0: not used)
+  int mgp_eligible[2] = {0, 0};             // first level from which it could run (0: none)
+  int mgp_blocks[2] = {0, 0};
+  unsigned* mgp_bar = nullptr;              // its grid barrier (count, generation)
   // stmg_march_host: double-buffered device inputs / solutions, a copy stream and its events
   double *mh_in[2] = {nullptr, nullptr}, *mh_x[2] = {nullptr, nullptr}, *mh_b = nullptr, *mh_t = nullptr;
   cudaStream_t cst = nullptr;
@@ -631,11 +637,117 @@ static int autotune_level(stmg_handle* h, int l) {
   return STMG_OK;
 }
 
+template <typename T>
+static int vcycle_level(stmg_handle* h, int l, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------
+// Persistent multigrid kernel: which levels it can run, its level descriptors, and where
+// the tuner lets it start.
+// ------------------------------------------------------------------------------------
+template <typename T>
+static bool mgp_level_ok(const stmg_handle* h, int i) {
+  const LevelDev& lv = h->L[i];
+  const LevelHost& H = lv.H;
+  const PrecDev<T>& P = const_cast<LevelDev&>(lv).pd<T>();
+  const bool coarsest = i + 1 == (int)h->L.size();
+  if (H.dim != 2 || !P.b) return false;
+  if (coarsest) return H.size <= 1 << 15;              // FP64 bordered inverse of the coarsest level
+  if (H.np != 3 || H.kt > 4 || H.npm != 3 || !P.has_inv || P.half || H.B > 256) return false;
+  const TransferParams<T>& tp = P.tp;
+  return tp.dim == 2 && tp.npf == 3 && tp.npc == 3 && 2 * tp.ktf <= 256 && tp.ktc <= tp.ktf;
+}
+
+template <typename T>
+static int mgp_setup(stmg_handle* h) {
+  const int w = prec_of<T>();
+  const int L = (int)h->L.size();
+  h->mgp_first[w] = h->mgp_eligible[w] = 0;
+  if (L < 3 || !h->L[0].pd<T>().b) return STMG_OK;
+  int first = L - 1;                                    // lowest level from which every level is covered
+  while (first > 1 && mgp_level_ok<T>(h, first - 1)) --first;
+  if (!mgp_level_ok<T>(h, L - 1) || first > L - 2) return STMG_OK;   // needs at least one smoothed level
+  if (!h->mgp_bar) {
+    CKS(dalloc(&h->mgp_bar, 2));
+    CK(cudaMemset(h->mgp_bar, 0, 2 * sizeof(unsigned)));
+  }
+  h->mgp_blocks[w] = mg_persist_blocks<T>(h->n_sm);
+  if (h->mgp_blocks[w] < 1) return STMG_OK;
+  LevelDev& lc = h->L[L - 1];
+  if (!lc.Gacc) {
+    CKS(dalloc(&lc.Gacc, lc.H.size));
+    CK(cudaMemset(lc.Gacc, 0, sizeof(double) * lc.H.size));
+  }
+  std::vector<MGLevelDesc<T>> d(L - first);
+  for (int i = first; i < L; ++i) {
+    LevelDev& lv = h->L[i];
+    PrecDev<T>& P = lv.pd<T>();
+    MGLevelDesc<T>& e = d[i - first];
+    std::memset(&e, 0, sizeof(e));
+    e.rp = P.rp;
+    e.tp = P.tp;
+    e.b = P.b; e.x = P.x; e.r = P.r;
+    e.dofs = lv.dofs;
+    e.inv = P.inv;
+    e.n_patches = lv.H.n_patches;
+    e.B = lv.H.B; e.Bc = lv.H.Bc;
+    e.ppb = lv.H.B > 0 ? std::max(1, 256 / lv.H.B) : 1;
+    e.kt = lv.H.kt;
+    e.ht = P.tp.h_type;
+    if (i == L - 1) { e.G = lv.G; e.acc = lv.Gacc; e.D = (int)lv.H.size; }
+  }
+  if (h->mgp_desc[w]) cudaFree(h->mgp_desc[w]);
+  h->mgp_desc[w] = nullptr;
+  MGLevelDesc<T>* dd = nullptr;
+  CKS(dalloc(&dd, d.size()));
+  h->mgp_desc[w] = dd;
+  CK(cudaMemcpy(dd, d.data(), sizeof(MGLevelDesc<T>) * d.size(), cudaMemcpyHostToDevice));
+  h->mgp_eligible[w] = first;
+  // the descriptor array starts at level `first`; a later start uses its tail
+  return STMG_OK;
+}
+
+// Device time of one V-cycle of precision T (zero-guess iterate not reset between the
+// timed repetitions: the cost does not depend on the values).
+template <typename T>
+static int time_vcycle(stmg_handle* h, float* ms) {
+  return time_it(h, [&]() { return vcycle_level<T>(h, 0, h->st); }, ms);
+}
+
+// Where the persistent kernel starts (or whether it runs at all): per precision, the
+// fastest V-cycle among "one kernel per operation" and every admissible first level.
+template <typename T>
+static int mgp_choose(stmg_handle* h) {
+  const int w = prec_of<T>();
+  const int first = h->mgp_eligible[w];
+  h->mgp_first[w] = 0;
+  if (first < 1 || h->cfg.persistent == 0) return STMG_OK;
+  if (h->cfg.persistent == 2 || !h->cfg.autotune) { h->mgp_first[w] = first; return STMG_OK; }
+  float best = 1e30f, ms = 0.f;
+  int best_first = 0;
+  const int L = (int)h->L.size();
+  for (int f = 0; f <= L - 2; ++f) {
+    if (f != 0 && f < first) continue;
+    h->mgp_first[w] = f;
+    CKS(time_vcycle<T>(h, &ms));
+    if (ms < best) { best = ms; best_first = f; }
+  }
+  h->mgp_first[w] = best_first;
+  return STMG_OK;
+}
+
 static int autotune_impl(stmg_handle* h) {
   CKS(warm_clocks(h));
   for (size_t l = 0; l < h->L.size(); ++l) {
     CKS(autotune_level<double>(h, (int)l));
     CKS(autotune_level<float>(h, (int)l));
+  }
+  {
+    const long long saved = h->launches;
+    CKS(mgp_setup<double>(h));
+    CKS(mgp_setup<float>(h));
+    CKS(mgp_choose<double>(h));
+    CKS(mgp_choose<float>(h));
+    h->launches = saved;
   }
   for (auto& g : h->graph) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
   h->graph_pairs[0].clear(); h->graph_pairs[1].clear();
@@ -650,6 +762,14 @@ template <typename T>
 static int vcycle_level(stmg_handle* h, int l, cudaStream_t s) {
   LevelDev& lv = h->L[l];
   PrecDev<T>& P = lv.pd<T>();
+  const int w = prec_of<T>();
+  if (h->mgp_first[w] > 0 && l == h->mgp_first[w]) {   // this level and all coarser ones in one launch
+    CK(launch_mg_persist<T>(reinterpret_cast<const MGLevelDesc<T>*>(h->mgp_desc[w]) + (l - h->mgp_eligible[w]),
+                            (int)h->L.size() - l,
+                            h->cfg.nu1, h->cfg.nu2, h->mgp_bar, h->d_err, h->mgp_blocks[w], s));
+    h->launches += 1;
+    return STMG_OK;
+  }
   if (l == (int)h->L.size() - 1) return op_coarse<T>(h, P.b, P.x, s);
   for (int it = 0; it < h->cfg.nu1; ++it) {          // presmoothing (Eq. Alg:VGMGPre)
     if (it == 0) {
@@ -870,6 +990,7 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
     if (ierr) {                       // a bounded wait expired (grid barrier or TMA pipeline)
       CK(cudaMemset(h->d_err, 0, sizeof(int)));
       if (h->cgs_bar) CK(cudaMemset(h->cgs_bar, 0, 2 * sizeof(unsigned)));
+      if (h->mgp_bar) CK(cudaMemset(h->mgp_bar, 0, 2 * sizeof(unsigned)));
       info->status = STMG_ERR_TIMEOUT;
       info->iterations = j + 1;
       return STMG_ERR_TIMEOUT;
@@ -918,6 +1039,7 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
   if (derr) {
     CK(cudaMemset(h->d_err, 0, sizeof(int)));
     if (h->cgs_bar) CK(cudaMemset(h->cgs_bar, 0, 2 * sizeof(unsigned)));
+    if (h->mgp_bar) CK(cudaMemset(h->mgp_bar, 0, 2 * sizeof(unsigned)));
     info->status = STMG_ERR_TIMEOUT;
     return STMG_ERR_TIMEOUT;
   }
@@ -984,6 +1106,7 @@ int stmg_default_config(stmg_config* c) {
   c->half_inverses = 0;
   c->transfer_variant = 0;
   c->apply_variant = 0;
+  c->persistent = 1;
   return STMG_OK;
 }
 
@@ -1000,6 +1123,7 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
   if (c.sweep_variant < 0 || c.sweep_variant > 3) return STMG_ERR_ARG;
   if (c.transfer_variant < 0 || c.transfer_variant > 2) return STMG_ERR_ARG;
   if (c.apply_variant < 0 || c.apply_variant > 3) return STMG_ERR_ARG;
+  if (c.persistent < 0 || c.persistent > 2) return STMG_ERR_ARG;
   if (c.precond_precision != STMG_FP64 && c.precond_precision != STMG_FP32) return STMG_ERR_ARG;
   if (!(c.precisions & (1 << c.precond_precision))) return STMG_ERR_ARG;
   h->tau = c.T / ((double)c.n_slabs * c.n_sub);
@@ -1107,7 +1231,14 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
       if (transfer_gather_supported(h->L[i].f.tp)) h->L[i].f.tp.variant = 2;
     }
   }
-  if (c.autotune) CKS(autotune_impl(h));
+  if (c.autotune) {
+    CKS(autotune_impl(h));
+  } else {
+    CKS(mgp_setup<double>(h));
+    CKS(mgp_setup<float>(h));
+    CKS(mgp_choose<double>(h));
+    CKS(mgp_choose<float>(h));
+  }
   // finest-level helpers: slab coupling and forcing
   const LevelHost& F = h->L[0].H;
   MassParams& mp = h->mp;
@@ -1167,6 +1298,7 @@ void stmg_destroy(stmg_handle* h) {
     if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
   }
   f(h->mh_b); f(h->mh_t);
+  f(h->mgp_desc[0]); f(h->mgp_desc[1]); f(h->mgp_bar);
   if (h->cst) cudaStreamDestroy(h->cst);
   for (auto e : h->all_events) cudaEventDestroy(e);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -1215,6 +1347,7 @@ int stmg_level_info(const stmg_handle* h, int lvl, stmg_level_info_t* info) {
   info->apply_variant[1] = L.f.ap.variant;
   info->apply_tile[0][0] = L.d.ap.tcx; info->apply_tile[0][1] = L.d.ap.tcy;
   info->apply_tile[1][0] = L.f.ap.tcx; info->apply_tile[1][1] = L.f.ap.tcy;
+  for (int w = 0; w < 2; ++w) info->persistent[w] = h->mgp_first[w] > 0 && lvl >= h->mgp_first[w] ? 1 : 0;
   return STMG_OK;
 }
 
@@ -1478,6 +1611,7 @@ int stmg_device_status(stmg_handle* h) {
   CK(cudaMemcpy(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (derr) {
     CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    if (h->mgp_bar) CK(cudaMemset(h->mgp_bar, 0, 2 * sizeof(unsigned)));
     return STMG_ERR_TIMEOUT;
   }
   return STMG_OK;

@@ -92,6 +92,21 @@ struct TransferParams {
   int variant;                    // 1: per coarse cell (shared memory), 2: gather form (2D)
 };
 
+// one level of the persistent multigrid kernel (k_mg_persist.cu), in device memory
+template <typename T>
+struct MGLevelDesc {
+  ApplyRegParams<T> rp;           // operator tables of the level (residual)
+  TransferParams<T> tp;           // transfer to the next coarser level (gather form, Q2 -> Q2)
+  T *b, *x, *r;                   // the level's V-cycle vectors
+  const int* dofs;                // patch table [n_patches][B]
+  const T* inv;                   // per-patch inverses, interleaved layout [patch][chunk][row][VW]
+  long long n_patches;
+  int B, Bc, ppb, kt, ht;         // patch size, padded columns, patches per block, k + 1, h-type of tp
+  const double* G;                // coarsest level: FP64 bordered inverse, column-major D x D
+  double* acc;                    // coarsest level: FP64 accumulator (zero between uses)
+  int D;
+};
+
 struct ForcingParams {
   int dim, n, G, np, nq, kt, cpb;
   long long n_nodes, n_vel;
@@ -182,6 +197,14 @@ cudaError_t launch_coarse_tiled(int D, const double* Gcm, const T* b, T* x, doub
 
 cudaError_t launch_mass_coupling(const MassParams& p, const double* vprev, double* b, cudaStream_t st);
 cudaError_t launch_forcing(const ForcingParams& p, const double* fq, double* F, cudaStream_t st);
+
+// all levels below the finest in one persistent launch (k_mg_persist.cu); levels[nl-1] is
+// the coarsest; bar: 2 zeroed unsigned (grid barrier); err: device error flag
+template <typename T>
+cudaError_t launch_mg_persist(const MGLevelDesc<T>* levels, int nl, int nu1, int nu2, unsigned* bar, int* err,
+                              int nblocks, cudaStream_t st);
+template <typename T>
+int mg_persist_blocks(int n_sm);   // resident blocks to launch (0: not available)
 
 // vector kernels
 template <typename Ti, typename To>

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "mg_device.cuh"
 
 namespace stmg {
 
@@ -75,24 +76,6 @@ __device__ __forceinline__ long long fine_cell(const TransferParams<T>& P, const
     stride *= P.nf;
   }
   return f;
-}
-
-// pressure child map coefficient between fine mode mf and coarse mode mc for child o
-template <typename T>
-__device__ __forceinline__ T pres_map(const TransferParams<T>& P, int o, int mf, int mc) {
-  if (P.h_type) {
-    T v = 1;
-    const int rc1 = P.rc + 1;
-    for (int k = 0; k < P.dim; ++k) {
-      const int ef = P.modes_f[mf][k], ec = P.modes_c[mc][k];
-      if (ef > ec) return T(0);
-      v *= P.E[(o >> k) & 1][ef * rc1 + ec];
-    }
-    return v;
-  }
-  for (int k = 0; k < 3; ++k)
-    if (P.modes_f[mf][k] != P.modes_c[mc][k]) return T(0);
-  return T(1);
 }
 
 }  // namespace
@@ -535,193 +518,21 @@ __global__ void __launch_bounds__(512) k_restrict_s(const TransferParams<T> P, c
 }
 
 // ------------------------------------------------------------------------------------
-// Gather form (2D): one thread per output value, no shared-memory phases, no atomics.
-//   prolongation  a fine velocity node takes the coarse function's value in the coarse
-//                 cell that contains it (on a coarse-cell face, either cell: the coarse
-//                 function is continuous, so both give the same value);
-//   restriction   a coarse velocity node sums its basis function's values at the fine
-//                 nodes of its support, each fine node once: per direction the fine nodes
-//                 of the one or two coarse cells that contain the node, weighted by P1 of
-//                 the cell that contains the fine node.
-// Coarse Dirichlet nodes read as 0 (identity columns), fine Dirichlet nodes are neither
-// written (prolongation) nor read (restriction); the restriction writes every coarse
-// value, Dirichlet ones as 0, so it needs no zero-fill.  On the small levels the
-// per-cell form is bound by the latency of its phases; this form is one phase.
+// Gather form (2D): one thread per output value, no shared-memory phases, no atomics
+// (bodies in mg_device.cuh, shared with the persistent multigrid kernel).  On the small
+// levels the per-cell form is bound by the latency of its phases; this form is one phase.
 // ------------------------------------------------------------------------------------
 template <typename T, int NPF, int NPC, int HT>
 __global__ void __launch_bounds__(256) k_prolongate_g(const TransferParams<T> P, const T* __restrict__ yc,
                                                       T* __restrict__ xf) {
-  constexpr int NS = HT ? 2 * (NPF - 1) + 1 : NPF;
-  const int Gf = P.Gf, Gc = P.Gc, nc = P.nc, ktc = P.ktc, ktf = P.ktf;
-  const long long nvt = 2LL * Gf * Gf;                        // (component, fine node)
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t < nvt) {
-    const int comp = (int)(t / ((long long)Gf * Gf));
-    const int g = (int)(t - (long long)comp * Gf * Gf);
-    const int gx = g % Gf, gy = g / Gf;
-    if (gx == 0 || gx == Gf - 1 || gy == 0 || gy == Gf - 1) return;
-    const int cx = min(gx / (NS - 1), nc - 1), cy = min(gy / (NS - 1), nc - 1);
-    const int sx = gx - cx * (NS - 1), sy = gy - cy * (NS - 1);
-    T wx[NPC], wy[NPC];
-    bool dx[NPC], dy[NPC];
-#pragma unroll
-    for (int j = 0; j < NPC; ++j) {
-      wx[j] = P.P1[sx * MAXNP + j];
-      wy[j] = P.P1[sy * MAXNP + j];
-      const int Jx = cx * (NPC - 1) + j, Jy = cy * (NPC - 1) + j;
-      dx[j] = Jx == 0 || Jx == Gc - 1;
-      dy[j] = Jy == 0 || Jy == Gc - 1;
-    }
-    T s[MAXKT];
-#pragma unroll
-    for (int ac = 0; ac < MAXKT; ++ac) {
-      s[ac] = T(0);
-      if (ac < ktc) {
-        const T* y = yc + ac * P.nvc + comp * P.nnc + (long long)(cy * (NPC - 1)) * Gc + cx * (NPC - 1);
-        T a = 0;
-#pragma unroll
-        for (int jy = 0; jy < NPC; ++jy) {
-          T row = 0;
-#pragma unroll
-          for (int jx = 0; jx < NPC; ++jx) row += wx[jx] * ((dx[jx] || dy[jy]) ? T(0) : y[jy * Gc + jx]);
-          a += wy[jy] * row;
-        }
-        s[ac] = a;
-      }
-    }
-    for (int af = 0; af < ktf; ++af) {
-      T o = 0;
-#pragma unroll
-      for (int ac = 0; ac < MAXKT; ++ac)
-        if (ac < ktc) o += P.Pt[af * MAXKT + ac] * s[ac];
-      xf[af * P.nvf + comp * P.nnf + g] += o;
-    }
-    return;
-  }
-  // pressure: one thread per (fine cell, fine mode), every fine temporal dof
-  const long long tq = t - nvt;
-  if (tq >= (long long)P.nf * P.nf * P.npmf) return;
-  const int fc = (int)(tq / P.npmf), mf = (int)(tq - (long long)fc * P.npmf);
-  const int fx = fc % P.nf, fy = fc / P.nf;
-  const int ccx = HT ? fx / 2 : fx, ccy = HT ? fy / 2 : fy;
-  const int o = HT ? ((fx & 1) | ((fy & 1) << 1)) : 0;
-  const long long cc = (long long)ccy * nc + ccx;
-  for (int af = 0; af < ktf; ++af) {
-    T v = 0;
-    for (int ac = 0; ac < ktc; ++ac) {
-      const T pt = P.Pt[af * MAXKT + ac];
-      if (pt == T(0)) continue;
-      const T* y = yc + (long long)ktc * P.nvc + ac * P.npc_tot + cc * P.npmc;
-      T u = 0;
-      for (int mc = 0; mc < P.npmc; ++mc) u += pres_map(P, o, mf, mc) * y[mc];
-      v += pt * u;
-    }
-    xf[(long long)ktf * P.nvf + af * P.npf_tot + (long long)fc * P.npmf + mf] += v;
-  }
+  prolongate_g_thread<T, NPF, NPC, HT, false>(P, yc, xf, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
-// 1D support of coarse node J: first fine node i0, count n (<= BX) and weights w[m] of the
-// fine nodes i0 + m (0 at fine Dirichlet nodes)
-template <typename T, int NPC, int NS, int BX>
-__device__ __forceinline__ void support_1d(const TransferParams<T>& P, int J, int* i0, int* n, T* w) {
-  const int q = J / (NPC - 1), rem = J - q * (NPC - 1);
-  int c0 = q, c1 = q;
-  if (rem == 0) {
-    c0 = q - 1 < 0 ? 0 : q - 1;
-    c1 = q < P.nc - 1 ? q : P.nc - 1;
-  }
-  *i0 = c0 * (NS - 1);
-  *n = (c1 - c0 + 1) * (NS - 1) + 1;
-#pragma unroll
-  for (int m = 0; m < BX; ++m) {
-    const int i = *i0 + m;
-    int ci = i / (NS - 1);
-    ci = ci < c0 ? c0 : (ci > c1 ? c1 : ci);
-    int s = i - ci * (NS - 1), jl = J - ci * (NPC - 1);
-    s = s < 0 ? 0 : (s > NS - 1 ? NS - 1 : s);               // in range whenever m < n;
-    jl = jl < 0 ? 0 : (jl > NPC - 1 ? NPC - 1 : jl);         // clamped so no index leaves P1
-    const T v = P.P1[s * MAXNP + jl];
-    w[m] = (m >= *n || i == 0 || i == P.Gf - 1) ? T(0) : v;
-  }
-}
-
-// threads of a velocity block: (coarse node, component, fine temporal dof), the latter
-// fastest; the fine temporal sums meet in shared memory for the temporal restriction
 template <typename T, int NPF, int NPC, int HT>
 __global__ void __launch_bounds__(256) k_restrict_g(const TransferParams<T> P, const T* __restrict__ rf,
                                                     T* __restrict__ bc, T* __restrict__ zc) {
-  constexpr int NS = HT ? 2 * (NPF - 1) + 1 : NPF;
-  constexpr int BX = 2 * (NS - 1) + 1;
   __shared__ T tsh[256];
-  const int Gf = P.Gf, Gc = P.Gc, ktc = P.ktc, ktf = P.ktf;
-  const int per = 2 * ktf;                                     // threads per coarse node
-  const int npb = blockDim.x / per;                            // coarse nodes per block
-  const long long nnodes = (long long)Gc * Gc;
-  const long long nvb = (nnodes + npb - 1) / npb;
-  if (blockIdx.x < nvb) {
-    const int nl = threadIdx.x / per, rr = threadIdx.x - nl * per;
-    const int comp = rr / ktf, af = rr - comp * ktf;
-    const long long G = blockIdx.x * (long long)npb + nl;
-    const bool active = nl < npb && G < nnodes;
-    bool dirc = true;
-    if (active) {
-      const int Jx = (int)(G % Gc), Jy = (int)(G / Gc);
-      dirc = Jx == 0 || Jx == Gc - 1 || Jy == 0 || Jy == Gc - 1;
-      T acc = 0;
-      if (!dirc) {
-        int ix0, nx, iy0, ny;
-        T wx[BX], wy[BX];
-        support_1d<T, NPC, NS, BX>(P, Jx, &ix0, &nx, wx);
-        support_1d<T, NPC, NS, BX>(P, Jy, &iy0, &ny, wy);
-        const T* r = rf + af * P.nvf + comp * P.nnf + (long long)iy0 * Gf + ix0;
-#pragma unroll
-        for (int my = 0; my < BX; ++my) {
-          if (my >= ny || wy[my] == T(0)) continue;
-          T row = 0;
-#pragma unroll
-          for (int mx = 0; mx < BX; ++mx)
-            if (mx < nx && wx[mx] != T(0)) row += wx[mx] * r[(long long)my * Gf + mx];
-          acc += wy[my] * row;
-        }
-      }
-      tsh[threadIdx.x] = acc;
-    }
-    __syncthreads();
-    if (active && af < ktc) {
-      const int a = af;
-      T o = 0;
-      if (!dirc)
-        for (int f = 0; f < ktf; ++f) o += P.Pt[f * MAXKT + a] * tsh[nl * per + comp * ktf + f];
-      bc[a * P.nvc + comp * P.nnc + G] = o;
-      if (zc) zc[a * P.nvc + comp * P.nnc + G] = T(0);
-    }
-    return;
-  }
-  // pressure: one thread per (coarse cell, coarse mode, coarse temporal dof)
-  const long long tq = (blockIdx.x - nvb) * (long long)blockDim.x + threadIdx.x;
-  const long long ncc = (long long)P.nc * P.nc;
-  if (tq >= ncc * P.npmc * ktc) return;
-  const int ac = (int)(tq % ktc);
-  const long long rest = tq / ktc;
-  const int mc = (int)(rest % P.npmc);
-  const long long cc = rest / P.npmc;
-  const int ccx = (int)(cc % P.nc), ccy = (int)(cc / P.nc);
-  constexpr int nchild = HT ? 4 : 1;
-  T v = 0;
-  for (int af = 0; af < ktf; ++af) {
-    const T pt = P.Pt[af * MAXKT + ac];
-    if (pt == T(0)) continue;
-    T u = 0;
-    for (int o = 0; o < nchild; ++o) {
-      const int fx = HT ? 2 * ccx + (o & 1) : ccx, fy = HT ? 2 * ccy + ((o >> 1) & 1) : ccy;
-      const long long fc = (long long)fy * P.nf + fx;
-      const T* rr = rf + (long long)ktf * P.nvf + af * P.npf_tot + fc * P.npmf;
-      for (int mf = 0; mf < P.npmf; ++mf) u += pres_map(P, o, mf, mc) * rr[mf];
-    }
-    v += pt * u;
-  }
-  bc[(long long)ktc * P.nvc + ac * P.npc_tot + cc * P.npmc + mc] = v;
-  if (zc) zc[(long long)ktc * P.nvc + ac * P.npc_tot + cc * P.npmc + mc] = T(0);
+  restrict_g_block<T, NPF, NPC, HT, false>(P, rf, bc, zc, blockIdx.x, tsh);
 }
 
 template <typename T>
@@ -798,10 +609,7 @@ cudaError_t launch_prolongate(const TransferParams<T>& p, const T* yc, T* xf, cu
 template <typename T>
 cudaError_t launch_restrict(const TransferParams<T>& p, const T* rf, T* bc, T* zc, cudaStream_t st) {
   if (p.variant == 2 && transfer_gather_supported(p)) {
-    const int npb = 256 / (2 * p.ktf);
-    const long long nvb = ((long long)p.Gc * p.Gc + npb - 1) / npb;
-    const long long npt = (long long)p.nc * p.nc * p.npmc * p.ktc;
-    const unsigned blocks = (unsigned)(nvb + (npt + 255) / 256);
+    const unsigned blocks = (unsigned)restrict_g_blocks(p);
 #define STMG_RG(F, C, H) \
     if (p.npf == F && p.npc == C && p.h_type == H) { \
       k_restrict_g<T, F, C, H><<<blocks, 256, 0, st>>>(p, rf, bc, zc); \

@@ -1,0 +1,376 @@
+// Device bodies shared by the one-kernel-per-operation path and the persistent multigrid
+// kernel (k_mg_persist.cu): the register-resident 2D operator, the gather-form grid
+// transfers of 2D levels, the block Vanka sweep and the tiled coarse product.
+//
+// Each body takes the index of its thread (or of its block) explicitly, so that a launch
+// with one block per work item and a persistent launch looping over the items run the same
+// code.  Template flag CG: the vectors that the persistent kernel itself wrote earlier in
+// the same launch (iterates, residuals, right-hand sides) are read through L2 (ld.global.cg),
+// never from a possibly stale L1 line of another phase; the standalone kernels read them
+// through the read-only path.  Tables, inverses and patch lists are read-only everywhere.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace stmg {
+
+template <bool CG, typename T>
+__device__ __forceinline__ T ldv(const T* p) {
+  if (CG) return __ldcg(p);
+  return __ldg(p);
+}
+
+// ------------------------------------------------------------------------------------
+// Register-resident 2D operator (Sec. 4.5): thread t -> (temporal dof a, cell c), cells
+// fastest.  See k_apply2d_reg.cu for the arithmetic.  The velocity rows are scatter-added
+// (zero on entry), the pressure rows stored.
+// ------------------------------------------------------------------------------------
+template <typename T, int NP, int KT, bool CG>
+__device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, const T* __restrict__ x,
+                                                   const T* __restrict__ b, T* __restrict__ y, int mode,
+                                                   long long t) {
+  constexpr int E = NP - 1, NQ = NP * NP;
+  constexpr int NPM = NP * (NP - 1) / 2;            // C(r + 2, 2) pressure modes, r = NP - 2
+  const int n = P.n, G = P.G;
+  const long long ncells = (long long)n * n;
+  if (t >= ncells * KT) return;
+  const int a = (int)(t / ncells);
+  const long long c = t - (long long)a * ncells;
+  const int cx = (int)(c % n), cy = (int)(c / n);
+  const long long nvel = P.n_vel, nnod = P.n_nodes;
+  const long long poff = (long long)KT * nvel;
+  const bool res = mode == RESIDUAL || mode == LIFT;
+  const bool lift = mode == LIFT;
+  const bool tr = mode == APPLY_T;
+  const long long base = (long long)(cy * E) * G + cx * E;      // global index of the cell's node (0, 0)
+  // boundary lines of the cell's nodes (the mesh boundary crosses a cell only at its outer lines)
+  const bool bx0 = cx == 0, bx1 = cx == n - 1, by0 = cy == 0, by1 = cy == n - 1;
+
+  T p[NPM];
+#pragma unroll
+  for (int m = 0; m < NPM; ++m) p[m] = lift ? T(0) : ldv<CG>(x + poff + (long long)a * P.n_pres + c * NPM + m);
+  T cont[NPM];
+#pragma unroll
+  for (int m = 0; m < NPM; ++m) cont[m] = 0;
+  T kt_row[KT];
+#pragma unroll
+  for (int bb = 0; bb < KT; ++bb) kt_row[bb] = tr ? P.Kt[bb * MAXKT + a] : P.Kt[a * MAXKT + bb];
+  const T beta = P.beta[a], bsc = P.bscale[a], hd = P.hd;
+
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    T ut[NQ], ua[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) { ut[q] = 0; ua[q] = 0; }
+#pragma unroll
+    for (int bb = 0; bb < KT; ++bb) {
+      const T* xb = x + bb * nvel + d * nnod + base;
+#pragma unroll
+      for (int iy = 0; iy < NP; ++iy) {
+        const bool dy = (iy == 0 && by0) || (iy == E && by1);
+#pragma unroll
+        for (int ix = 0; ix < NP; ++ix) {
+          const bool dir = dy || (ix == 0 && bx0) || (ix == E && bx1);
+          const bool take = lift ? dir : !dir;
+          const T v = take ? ldv<CG>(xb + iy * G + ix) : T(0);
+          ut[iy * NP + ix] += kt_row[bb] * v;
+          if (bb == a) ua[iy * NP + ix] = v;
+        }
+      }
+    }
+    // continuity rows of this component
+#pragma unroll
+    for (int m = 0; m < NPM; ++m) {
+      T s = 0;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) s += P.CB[d][m][q] * ua[q];
+      cont[m] += s;
+    }
+    // y-pass: A1 = hd M1y ut + beta K1y ua, A2 = M1y ua (column by column)
+    T A1[NQ], A2[NQ];
+#pragma unroll
+    for (int ix = 0; ix < NP; ++ix) {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T m1 = 0, k1 = 0, m2 = 0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          m1 += P.M1[i * NP + j] * ut[j * NP + ix];
+          k1 += P.K1[i * NP + j] * ua[j * NP + ix];
+          m2 += P.M1[i * NP + j] * ua[j * NP + ix];
+        }
+        A1[i * NP + ix] = hd * m1 + beta * k1;
+        A2[i * NP + ix] = m2;
+      }
+    }
+    // x-pass, pressure gradient, scatter (row by row)
+    T* yd = y + a * nvel + d * nnod + base;
+    const T* bd = b + a * nvel + d * nnod + base;
+    const T* xd = x + a * nvel + d * nnod + base;
+#pragma unroll
+    for (int iy = 0; iy < NP; ++iy) {
+      const bool dy = (iy == 0 && by0) || (iy == E && by1);
+      const bool oy = iy < E || by1;                      // this cell owns the node row (for boundary rows)
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        const bool dir = dy || (i == 0 && bx0) || (i == E && bx1);
+        const bool own = oy && (i < E || bx1);
+        const long long off = (long long)iy * G + i;
+        if (dir) {
+          if (own) {
+            const T xv = ldv<CG>(xd + off);
+            yd[off] = mode == RESIDUAL ? ldv<CG>(bd + off) - xv : xv;   // identity row, by its owner only
+          }
+          continue;
+        }
+        T m1 = 0, k1 = 0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          m1 += P.M1[i * NP + j] * A1[iy * NP + j];
+          k1 += P.K1[i * NP + j] * A2[iy * NP + j];
+        }
+        T bt = 0;
+#pragma unroll
+        for (int m = 0; m < NPM; ++m) bt += P.CB[d][m][iy * NP + i] * p[m];
+        T v = m1 + beta * k1 + bsc * bt;
+        if (res) v = own ? ldv<CG>(bd + off) - v : -v;     // b enters once, through the owner
+        atomicAdd(yd + off, v);
+      }
+    }
+  }
+  // pressure rows of the cell
+#pragma unroll
+  for (int m = 0; m < NPM; ++m) {
+    const long long gi = poff + (long long)a * P.n_pres + c * NPM + m;
+    const T v = bsc * cont[m];
+    y[gi] = res ? ldv<CG>(b + gi) - v : v;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Gather-form grid transfers of 2D levels (App. A).
+//   prolongation  a fine velocity node takes the coarse function's value in the coarse
+//                 cell that contains it (on a coarse-cell face, either cell: the coarse
+//                 function is continuous, so both give the same value);
+//   restriction   a coarse velocity node sums its basis function's values at the fine
+//                 nodes of its support, each fine node once: per direction the fine nodes
+//                 of the one or two coarse cells that contain the node, weighted by P1 of
+//                 the cell that contains the fine node.
+// Coarse Dirichlet nodes read as 0 (identity columns), fine Dirichlet nodes are neither
+// written (prolongation) nor read (restriction); the restriction writes every coarse
+// value, Dirichlet ones as 0 (and, if zc is given, zc = 0 at the same entries).
+// ------------------------------------------------------------------------------------
+
+// pressure child map coefficient between fine mode mf and coarse mode mc for child o
+template <typename T>
+__device__ __forceinline__ T pres_map(const TransferParams<T>& P, int o, int mf, int mc) {
+  if (P.h_type) {
+    T v = 1;
+    const int rc1 = P.rc + 1;
+    for (int k = 0; k < P.dim; ++k) {
+      const int ef = P.modes_f[mf][k], ec = P.modes_c[mc][k];
+      if (ef > ec) return T(0);
+      v *= P.E[(o >> k) & 1][ef * rc1 + ec];
+    }
+    return v;
+  }
+  for (int k = 0; k < 3; ++k)
+    if (P.modes_f[mf][k] != P.modes_c[mc][k]) return T(0);
+  return T(1);
+}
+
+// threads of the prolongation: (component, fine node) for the velocity, then (fine cell,
+// fine mode) for the pressure; total 2 Gf^2 + nf^2 npmf
+template <typename T, int NPF, int NPC, int HT, bool CG>
+__device__ __forceinline__ void prolongate_g_thread(const TransferParams<T>& P, const T* __restrict__ yc,
+                                                    T* __restrict__ xf, long long t) {
+  constexpr int NS = HT ? 2 * (NPF - 1) + 1 : NPF;
+  const int Gf = P.Gf, Gc = P.Gc, nc = P.nc, ktc = P.ktc, ktf = P.ktf;
+  const long long nvt = 2LL * Gf * Gf;                        // (component, fine node)
+  if (t < nvt) {
+    const int comp = (int)(t / ((long long)Gf * Gf));
+    const int g = (int)(t - (long long)comp * Gf * Gf);
+    const int gx = g % Gf, gy = g / Gf;
+    if (gx == 0 || gx == Gf - 1 || gy == 0 || gy == Gf - 1) return;
+    const int cx = min(gx / (NS - 1), nc - 1), cy = min(gy / (NS - 1), nc - 1);
+    const int sx = gx - cx * (NS - 1), sy = gy - cy * (NS - 1);
+    T wx[NPC], wy[NPC];
+    bool dx[NPC], dy[NPC];
+#pragma unroll
+    for (int j = 0; j < NPC; ++j) {
+      wx[j] = P.P1[sx * MAXNP + j];
+      wy[j] = P.P1[sy * MAXNP + j];
+      const int Jx = cx * (NPC - 1) + j, Jy = cy * (NPC - 1) + j;
+      dx[j] = Jx == 0 || Jx == Gc - 1;
+      dy[j] = Jy == 0 || Jy == Gc - 1;
+    }
+    T s[MAXKT];
+#pragma unroll
+    for (int ac = 0; ac < MAXKT; ++ac) {
+      s[ac] = T(0);
+      if (ac < ktc) {
+        const T* yv = yc + ac * P.nvc + comp * P.nnc + (long long)(cy * (NPC - 1)) * Gc + cx * (NPC - 1);
+        T a = 0;
+#pragma unroll
+        for (int jy = 0; jy < NPC; ++jy) {
+          T row = 0;
+#pragma unroll
+          for (int jx = 0; jx < NPC; ++jx) row += wx[jx] * ((dx[jx] || dy[jy]) ? T(0) : ldv<CG>(yv + jy * Gc + jx));
+          a += wy[jy] * row;
+        }
+        s[ac] = a;
+      }
+    }
+    for (int af = 0; af < ktf; ++af) {
+      T o = 0;
+#pragma unroll
+      for (int ac = 0; ac < MAXKT; ++ac)
+        if (ac < ktc) o += P.Pt[af * MAXKT + ac] * s[ac];
+      T* out = xf + af * P.nvf + comp * P.nnf + g;
+      *out = ldv<CG>(out) + o;
+    }
+    return;
+  }
+  // pressure: one thread per (fine cell, fine mode), every fine temporal dof
+  const long long tq = t - nvt;
+  if (tq >= (long long)P.nf * P.nf * P.npmf) return;
+  const int fc = (int)(tq / P.npmf), mf = (int)(tq - (long long)fc * P.npmf);
+  const int fx = fc % P.nf, fy = fc / P.nf;
+  const int ccx = HT ? fx / 2 : fx, ccy = HT ? fy / 2 : fy;
+  const int o = HT ? ((fx & 1) | ((fy & 1) << 1)) : 0;
+  const long long cc = (long long)ccy * nc + ccx;
+  for (int af = 0; af < ktf; ++af) {
+    T v = 0;
+    for (int ac = 0; ac < ktc; ++ac) {
+      const T pt = P.Pt[af * MAXKT + ac];
+      if (pt == T(0)) continue;
+      const T* yv = yc + (long long)ktc * P.nvc + ac * P.npc_tot + cc * P.npmc;
+      T u = 0;
+      for (int mc = 0; mc < P.npmc; ++mc) u += pres_map(P, o, mf, mc) * ldv<CG>(yv + mc);
+      v += pt * u;
+    }
+    T* out = xf + (long long)ktf * P.nvf + af * P.npf_tot + (long long)fc * P.npmf + mf;
+    *out = ldv<CG>(out) + v;
+  }
+}
+
+// 1D support of coarse node J: first fine node i0, count n (<= BX) and weights w[m] of the
+// fine nodes i0 + m (0 at fine Dirichlet nodes)
+template <typename T, int NPC, int NS, int BX>
+__device__ __forceinline__ void support_1d(const TransferParams<T>& P, int J, int* i0, int* n, T* w) {
+  const int q = J / (NPC - 1), rem = J - q * (NPC - 1);
+  int c0 = q, c1 = q;
+  if (rem == 0) {
+    c0 = q - 1 < 0 ? 0 : q - 1;
+    c1 = q < P.nc - 1 ? q : P.nc - 1;
+  }
+  *i0 = c0 * (NS - 1);
+  *n = (c1 - c0 + 1) * (NS - 1) + 1;
+#pragma unroll
+  for (int m = 0; m < BX; ++m) {
+    const int i = *i0 + m;
+    int ci = i / (NS - 1);
+    ci = ci < c0 ? c0 : (ci > c1 ? c1 : ci);
+    int s = i - ci * (NS - 1), jl = J - ci * (NPC - 1);
+    s = s < 0 ? 0 : (s > NS - 1 ? NS - 1 : s);               // in range whenever m < n;
+    jl = jl < 0 ? 0 : (jl > NPC - 1 ? NPC - 1 : jl);         // clamped so no index leaves P1
+    const T v = P.P1[s * MAXNP + jl];
+    w[m] = (m >= *n || i == 0 || i == P.Gf - 1) ? T(0) : v;
+  }
+}
+
+// blocks of the restriction (256 threads): the velocity blocks first, threads (coarse node,
+// component, fine temporal dof), the latter fastest, meeting in tsh[256] for the temporal
+// restriction; then one thread per (coarse cell, coarse mode, coarse temporal dof).
+template <typename T>
+__host__ __device__ __forceinline__ long long restrict_g_velocity_blocks(const TransferParams<T>& P) {
+  const int npb = 256 / (2 * P.ktf);
+  return ((long long)P.Gc * P.Gc + npb - 1) / npb;
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ long long restrict_g_blocks(const TransferParams<T>& P) {
+  const long long npt = (long long)P.nc * P.nc * P.npmc * P.ktc;
+  return restrict_g_velocity_blocks(P) + (npt + 255) / 256;
+}
+
+template <typename T, int NPF, int NPC, int HT, bool CG>
+__device__ __forceinline__ void restrict_g_block(const TransferParams<T>& P, const T* __restrict__ rf,
+                                                 T* __restrict__ bc, T* __restrict__ zc, long long vb, T* tsh) {
+  constexpr int NS = HT ? 2 * (NPF - 1) + 1 : NPF;
+  constexpr int BX = 2 * (NS - 1) + 1;
+  const int Gf = P.Gf, Gc = P.Gc, ktc = P.ktc, ktf = P.ktf;
+  const int per = 2 * ktf;                                     // threads per coarse node
+  const int npb = 256 / per;                                   // coarse nodes per block
+  const long long nnodes = (long long)Gc * Gc;
+  const long long nvb = restrict_g_velocity_blocks(P);
+  if (vb < nvb) {
+    const int nl = threadIdx.x / per, rr = threadIdx.x - nl * per;
+    const int comp = rr / ktf, af = rr - comp * ktf;
+    const long long Gi = vb * (long long)npb + nl;
+    const bool active = nl < npb && Gi < nnodes;
+    bool dirc = true;
+    if (active) {
+      const int Jx = (int)(Gi % Gc), Jy = (int)(Gi / Gc);
+      dirc = Jx == 0 || Jx == Gc - 1 || Jy == 0 || Jy == Gc - 1;
+      T acc = 0;
+      if (!dirc) {
+        int ix0, nx, iy0, ny;
+        T wx[BX], wy[BX];
+        support_1d<T, NPC, NS, BX>(P, Jx, &ix0, &nx, wx);
+        support_1d<T, NPC, NS, BX>(P, Jy, &iy0, &ny, wy);
+        const T* r = rf + af * P.nvf + comp * P.nnf + (long long)iy0 * Gf + ix0;
+#pragma unroll
+        for (int my = 0; my < BX; ++my) {
+          if (my >= ny || wy[my] == T(0)) continue;
+          T row = 0;
+#pragma unroll
+          for (int mx = 0; mx < BX; ++mx)
+            if (mx < nx && wx[mx] != T(0)) row += wx[mx] * ldv<CG>(r + (long long)my * Gf + mx);
+          acc += wy[my] * row;
+        }
+      }
+      tsh[threadIdx.x] = acc;
+    }
+    __syncthreads();
+    if (active && af < ktc) {
+      const int a = af;
+      T o = 0;
+      if (!dirc)
+        for (int f = 0; f < ktf; ++f) o += P.Pt[f * MAXKT + a] * tsh[nl * per + comp * ktf + f];
+      bc[a * P.nvc + comp * P.nnc + Gi] = o;
+      if (zc) zc[a * P.nvc + comp * P.nnc + Gi] = T(0);
+    }
+    __syncthreads();                                           // tsh is reused by the next block
+    return;
+  }
+  // pressure: one thread per (coarse cell, coarse mode, coarse temporal dof)
+  const long long tq = (vb - nvb) * 256 + threadIdx.x;
+  const long long ncc = (long long)P.nc * P.nc;
+  if (tq >= ncc * P.npmc * ktc) return;
+  const int ac = (int)(tq % ktc);
+  const long long rest = tq / ktc;
+  const int mc = (int)(rest % P.npmc);
+  const long long cc = rest / P.npmc;
+  const int ccx = (int)(cc % P.nc), ccy = (int)(cc / P.nc);
+  constexpr int nchild = HT ? 4 : 1;
+  T v = 0;
+  for (int af = 0; af < ktf; ++af) {
+    const T pt = P.Pt[af * MAXKT + ac];
+    if (pt == T(0)) continue;
+    T u = 0;
+    for (int o = 0; o < nchild; ++o) {
+      const int fx = HT ? 2 * ccx + (o & 1) : ccx, fy = HT ? 2 * ccy + ((o >> 1) & 1) : ccy;
+      const long long fc = (long long)fy * P.nf + fx;
+      const T* rr = rf + (long long)ktf * P.nvf + af * P.npf_tot + fc * P.npmf;
+      for (int mf = 0; mf < P.npmf; ++mf) u += pres_map(P, o, mf, mc) * ldv<CG>(rr + mf);
+    }
+    v += pt * u;
+  }
+  bc[(long long)ktc * P.nvc + ac * P.npc_tot + cc * P.npmc + mc] = v;
+  if (zc) zc[(long long)ktc * P.nvc + ac * P.npc_tot + cc * P.npmc + mc] = T(0);
+}
+
+}  // namespace stmg

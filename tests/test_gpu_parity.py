@@ -88,9 +88,9 @@ def test_apply_and_residual(case):
 
 
 def reg_supported(r, k, prec):
-    """The register-resident 2D operator covers FP32 up to Q5 (r <= 3), FP64 up to Q3 (r <= 1)
+    """The register-resident 2D operator covers FP32 up to Q5 (r <= 3), FP64 up to Q3 (r <= 2)
     and k + 1 <= 4; other shapes fall back to the node-centred form when it is forced."""
-    return k + 1 <= 4 and r <= (3 if prec == "fp32" else 1)
+    return k + 1 <= 4 and r <= (3 if prec == "fp32" else 2)
 
 
 @pytest.mark.parametrize("variant", [1, 2, 3])
@@ -231,6 +231,64 @@ def test_vcycle_with_coarser_mesh_stop(coarse_n):
     ref = og.vcycle(b)
     assert rel(g.vcycle(dev(b), "fp64"), ref) < 1e-11
     assert rel(g.vcycle(dev(b), "fp32"), ref) < 1e-4
+
+
+PERSIST_CASES = [
+    (2, 4, 1, 1, None),                                     # levels 1.. : (2,1,1) smoothed, (1,1,1) coarse
+    (2, 4, 3, 0, None),                                     # DG(0) below a p-step in space
+    (2, 2, 4, 3, None),                                     # the Q2 levels under r = 4, k = 3
+    (2, 16, 2, 2, [(16, 2, 2), (16, 1, 2), (8, 1, 2), (4, 1, 1), (2, 1, 1)]),   # p-in-time inside the kernel
+]
+
+
+@pytest.mark.parametrize("smoother", ["cell", "vsp"])
+@pytest.mark.parametrize("case", PERSIST_CASES, ids=["2d-n4-r1k1", "2d-n4-r3k0", "2d-n2-r4k3", "2d-n16-r2k2-pt"])
+def test_persistent_levels_vcycle(case, smoother):
+    """The levels below the finest run in one persistent kernel (forced): V-cycles in both
+    precisions against the oracle, graph and eager, and equal to one kernel per operation."""
+    dim, n, r, k, levels = case
+    levels = levels or stmg.host_default_hierarchy(n, r, k)
+    og = Multigrid(dim, levels, NU, TAU, MGConfig(smoother=smoother))
+    sm = [stmg.VSP if smoother == "vsp" else stmg.CELL] * len(levels)
+    b = free_vec(og.slabs[0], 81)
+    ref = og.vcycle(b)
+    outs = {}
+    for persistent in (2, 0):
+        for graphs in (True, False):
+            g = stmg.SpaceTimeMG(dim=dim, n_cells=n, r=r, k=k, nu=NU, T=TAU * 5, n_slabs=5, levels=levels,
+                                 smoothers=sm, use_graphs=graphs, persistent=persistent)
+            flags = [l["persistent"] for l in g.levels]
+            if persistent == 2:
+                assert flags[0] == (0, 0) and flags[-1] == (1, 1), flags   # the finest level keeps its kernels
+            else:
+                assert all(f == (0, 0) for f in flags)
+            for _ in range(2):                                  # capture, then replay
+                x64, x32 = g.vcycle(dev(b), "fp64"), g.vcycle(dev(b), "fp32")
+                assert rel(x64, ref) < 1e-11
+                assert rel(x32, ref) < 1e-4
+            outs[(persistent, graphs)] = (x64.cpu().numpy(), x32.cpu().numpy())
+            g.device_status()
+            g.close()
+    for key in outs:
+        assert rel(outs[key][0], outs[(0, False)][0]) < 1e-12
+
+
+def test_persistent_levels_solve():
+    """FGMRES with the persistent V-cycle (FP32) solves to 1e-10 and agrees with the solve
+    that runs one kernel per operation."""
+    pb = fourier_forcing_2d(nu=1.0)
+    xs = []
+    for persistent in (2, 0):
+        g = stmg.SpaceTimeMG(dim=2, n_cells=16, r=2, k=2, nu=1.0, T=1.0, n_slabs=16, precond_precision="fp32",
+                             coarse_n=4, k_min=2, rel_tol=1e-10, persistent=persistent)
+        b = g.slab_rhs(g.forcing(pb.forcing, 0))
+        x, info = g.solve_slab(b)
+        assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+        xs.append((x.cpu().numpy(), info["iterations"]))
+        g.close()
+    assert abs(xs[0][1] - xs[1][1]) <= 1
+    s0 = Slab(2, 16, 2, 2, 1.0, 1.0 / 16)
+    assert rel(s0.remove_pressure_mean(xs[0][0]), s0.remove_pressure_mean(xs[1][0])) < 1e-8
 
 
 def test_vcycle_graph_equals_eager():
