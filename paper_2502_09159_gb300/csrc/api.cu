@@ -94,7 +94,8 @@ struct stmg_handle {
   void* mgp_desc[2] = {nullptr, nullptr};   // device array of MGLevelDesc<T>
   int mgp_first[2] = {0, 0};                // first level of the persistent part (0: not used)
   int mgp_eligible[2] = {0, 0};             // first level from which it could run (0: none)
-  int mgp_blocks[2] = {0, 0};
+  int mgp_blocks[2] = {0, 0};                // grid of the persistent kernel
+  int mgp_bpsm[2] = {0, 0};                  // resident blocks per SM it may use
   unsigned* mgp_bar = nullptr;              // its grid barrier (count, generation)
   // stmg_march_host: double-buffered device inputs / solutions, a copy stream and its events
   double *mh_in[2] = {nullptr, nullptr}, *mh_x[2] = {nullptr, nullptr}, *mh_b = nullptr, *mh_t = nullptr;
@@ -378,8 +379,8 @@ static int op_apply(stmg_handle* h, int l, const T* x, const T* b, T* y, int mod
   const ApplyParams<T>& ap = lv.pd<T>().ap;
   if (ap.variant == 2) {                 // writes every entry of y
     CK(launch_apply2d<T>(lv.H.np, ap, x, b, y, mode, s));
-  } else if (ap.variant == 3) {          // scatter-adds the velocity rows, stores the pressure rows
-    CK(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)lv.H.kt * lv.H.n_vel, s));
+  } else if (ap.variant == 3) {          // scatter-adds every row
+    CK(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)lv.H.size, s));
     CK(launch_apply2d_reg<T>(lv.H.np, lv.pd<T>().rp, x, b, y, mode, s));
   } else {
     CK(cudaMemsetAsync(y, 0, sizeof(T) * lv.H.size, s));
@@ -670,7 +671,8 @@ static int mgp_setup(stmg_handle* h) {
     CKS(dalloc(&h->mgp_bar, 2));
     CK(cudaMemset(h->mgp_bar, 0, 2 * sizeof(unsigned)));
   }
-  h->mgp_blocks[w] = mg_persist_blocks<T>(h->n_sm);
+  h->mgp_bpsm[w] = mg_persist_blocks<T>(h->n_sm);
+  h->mgp_blocks[w] = h->n_sm * h->mgp_bpsm[w];
   if (h->mgp_blocks[w] < 1) return STMG_OK;
   LevelDev& lc = h->L[L - 1];
   if (!lc.Gacc) {
@@ -689,6 +691,7 @@ static int mgp_setup(stmg_handle* h) {
     e.dofs = lv.dofs;
     e.inv = P.inv;
     e.n_patches = lv.H.n_patches;
+    e.size = lv.H.size;
     e.B = lv.H.B; e.Bc = lv.H.Bc;
     e.ppb = lv.H.B > 0 ? std::max(1, 256 / lv.H.B) : 1;
     e.kt = lv.H.kt;
@@ -723,15 +726,20 @@ static int mgp_choose(stmg_handle* h) {
   if (first < 1 || h->cfg.persistent == 0) return STMG_OK;
   if (h->cfg.persistent == 2 || !h->cfg.autotune) { h->mgp_first[w] = first; return STMG_OK; }
   float best = 1e30f, ms = 0.f;
-  int best_first = 0;
+  int best_first = 0, best_blocks = h->mgp_blocks[w];
   const int L = (int)h->L.size();
   for (int f = 0; f <= L - 2; ++f) {
     if (f != 0 && f < first) continue;
-    h->mgp_first[w] = f;
-    CKS(time_vcycle<T>(h, &ms));
-    if (ms < best) { best = ms; best_first = f; }
+    for (int bps = 1; bps <= h->mgp_bpsm[w]; ++bps) {   // grid: 1 or 2 blocks per SM (barrier cost vs width)
+      if (f == 0 && bps > 1) break;
+      h->mgp_first[w] = f;
+      h->mgp_blocks[w] = h->n_sm * bps;
+      CKS(time_vcycle<T>(h, &ms));
+      if (ms < best) { best = ms; best_first = f; best_blocks = h->mgp_blocks[w]; }
+    }
   }
   h->mgp_first[w] = best_first;
+  h->mgp_blocks[w] = best_blocks;
   return STMG_OK;
 }
 

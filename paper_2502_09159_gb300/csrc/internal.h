@@ -100,7 +100,7 @@ struct MGLevelDesc {
   T *b, *x, *r;                   // the level's V-cycle vectors
   const int* dofs;                // patch table [n_patches][B]
   const T* inv;                   // per-patch inverses, interleaved layout [patch][chunk][row][VW]
-  long long n_patches;
+  long long n_patches, size;      // patches; D of the level
   int B, Bc, ppb, kt, ht;         // patch size, padded columns, patches per block, k + 1, h-type of tp
   const double* G;                // coarsest level: FP64 bordered inverse, column-major D x D
   double* acc;                    // coarsest level: FP64 accumulator (zero between uses)
@@ -139,8 +139,8 @@ cudaError_t launch_apply(int dim, int np, const ApplyParams<T>& p, const T* x, c
                          int mode, cudaStream_t st);
 template <typename T>
 size_t apply_smem_bytes(int dim, int np, int kt, int npm, int cpb);
-// register-resident form on 2D levels (k_apply2d_reg.cu), kt <= 4: the velocity part of y
-// must be zero on entry (scatter-adds), the pressure part is overwritten
+// register-resident form on 2D levels (k_apply2d_reg.cu), kt <= 4: y must be zero on entry
+// (every row is scatter-added)
 template <typename T>
 cudaError_t launch_apply2d_reg(int np, const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode,
                                cudaStream_t st);
@@ -204,7 +204,7 @@ template <typename T>
 cudaError_t launch_mg_persist(const MGLevelDesc<T>* levels, int nl, int nu1, int nu2, unsigned* bar, int* err,
                               int nblocks, cudaStream_t st);
 template <typename T>
-int mg_persist_blocks(int n_sm);   // resident blocks to launch (0: not available)
+int mg_persist_blocks(int n_sm);   // resident blocks per SM (at most 2; 0: not available)
 
 // vector kernels
 template <typename Ti, typename To>

@@ -1,20 +1,20 @@
 // Matrix-free slab operator on 2D levels, register-resident form (Sec. 4.5, Eq. InAlg /
 // DefDtauh).
 //
-// One thread per (cell, temporal dof a), threads of a warp on consecutive cells of one cell
-// row and the same a, so that the loads of a warp are unit-stride runs and every read of
-// the parameter bank (the 1D factors, K_tau, the mode tables) is uniform across the warp.
-// Per velocity component the thread holds the cell's NP x NP node values in registers and
-// applies, with compile-time loop bounds and indices throughout:
+// One thread per (cell, temporal dof a, velocity component d), threads of a warp on
+// consecutive cells of one (a, d), so that the loads of a warp are unit-stride runs and
+// every read of the parameter bank (the 1D factors, K_tau, the mode tables) is uniform
+// across the warp.  The thread holds the cell's NP x NP node values of its component in
+// registers and applies, with compile-time loop bounds and indices throughout:
 //   u~     = sum_b K_tau[a,b] u_b                                  (time combination)
 //   cont_m += sum_q CB_d[m][q] u_a[q]                              (continuity rows)
 //   A1     = h^d (M1 along y) u~ + beta_a (K1 along y) u_a,  A2 = (M1 along y) u_a
 //   y_q    = (M1 along x) A1 + beta_a (K1 along x) A2 + bscale_a sum_m CB_d[m][q] p_a[m]
 // with CB_d[m][q] = F(mode m, x, ix) F(mode m, y, iy), F = G1 = int L ell' in the direction
 // of component d and N1 = int L ell in the other one (the B_h^T / B_h factors of the
-// Legendre pressure modes).  The velocity rows are scatter-added (nodes on cell faces
-// belong to two or four cells; y zero-filled before the launch), the cell's pressure rows
-// are stored.  Boundary rows are the identity, written by the cell that owns the node;
+// Legendre pressure modes).  Every row is scatter-added (nodes on cell faces belong to two
+// or four cells, a cell's pressure rows get one share per component; y zero-filled before
+// the launch).  Boundary rows are the identity, added by the cell that owns the node;
 // boundary columns read as 0.  LIFT reads only the boundary values of x and no pressure;
 // APPLY_T transposes K_tau.  About 35 multiply-adds per dof, no shared memory, no barrier.
 #include <cuda_runtime.h>
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(64) k_apply2d_reg(const ApplyRegParams<T> P, c
 template <typename T, int NP, int KT>
 static cudaError_t launch_apply2d_reg_t(const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode,
                                         cudaStream_t st) {
-  const long long tot = (long long)p.n * p.n * KT;
+  const long long tot = (long long)p.n * p.n * KT * 2;      // (cell, temporal dof, component)
   const unsigned blocks = (unsigned)((tot + 63) / 64);      // small blocks: the finest levels have few cells
   k_apply2d_reg<T, NP, KT><<<blocks, 64, 0, st>>>(p, x, b, y, mode);
   return cudaGetLastError();

@@ -64,9 +64,41 @@ __device__ __forceinline__ float vdot(const float4& a, const float* r) {
 }
 __device__ __forceinline__ double vdot(const double2& a, const double* r) { return a.x * r[0] + a.y * r[1]; }
 
+// Work items of the thread-indexed phases: warps interleaved over the blocks, so that the
+// few warps of a small level run on as many SMs as they can instead of a block's worth of
+// them queueing on one SM (their instruction chains, not bandwidth, bound those levels).
+__device__ __forceinline__ long long item_first() {
+  return ((long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
+}
+__device__ __forceinline__ long long item_stride() { return (long long)gridDim.x * PT; }
+
 template <typename T>
 __device__ void zero_fill(T* p, long long n) {
-  for (long long i = blockIdx.x * (long long)PT + threadIdx.x; i < n; i += (long long)gridDim.x * PT) p[i] = T(0);
+  for (long long i = item_first(); i < n; i += item_stride()) p[i] = T(0);
+}
+
+// the level's operator tables into shared memory (the entries a Q2 level uses), so that the
+// operator's coefficients are shared-memory operands rather than global loads
+template <typename T>
+__device__ void stage_apply_tables(const ApplyRegParams<T>& g, ApplyRegParams<T>* s) {
+  const int t = threadIdx.x;
+  if (t < 9) { s->M1[t] = g.M1[t]; s->K1[t] = g.K1[t]; }
+  if (t < 54) { const int d = t / 27, m = (t / 9) % 3, q = t % 9; s->CB[d][m][q] = g.CB[d][m][q]; }
+  if (t < MAXKT * MAXKT) s->Kt[t] = g.Kt[t];
+  if (t < MAXKT) { s->beta[t] = g.beta[t]; s->bscale[t] = g.bscale[t]; }
+  if (t == 0) {
+    s->n = g.n; s->G = g.G; s->kt = g.kt; s->npm = g.npm;
+    s->n_nodes = g.n_nodes; s->n_vel = g.n_vel; s->n_pres = g.n_pres; s->hd = g.hd;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void stage_transfer_tables(const TransferParams<T>& g, TransferParams<T>* s) {
+  const int* src = reinterpret_cast<const int*>(&g);
+  int* dst = reinterpret_cast<int*>(s);
+  for (int i = threadIdx.x; i < (int)(sizeof(TransferParams<T>) / sizeof(int)); i += PT) dst[i] = src[i];
+  __syncthreads();
 }
 
 // x += W res over all patches (Eq. vanka; rows carry omega / valence): ppb patches per
@@ -113,35 +145,43 @@ __device__ __noinline__ void phase_sweep(const MGLevelDesc<T>& L, const T* res, 
 
 // r = b - S x on a Q2/P1 level (register-resident operator, velocity rows of r zero on entry)
 template <typename T>
-__device__ __noinline__ void phase_residual(const MGLevelDesc<T>& L) {
-  const long long tot = (long long)L.rp.n * L.rp.n * L.kt;
-  for (long long t = blockIdx.x * (long long)PT + threadIdx.x; t < tot; t += (long long)gridDim.x * PT) {
+__device__ __noinline__ void phase_residual(const MGLevelDesc<T>& L, ApplyRegParams<T>* sp) {
+  stage_apply_tables(L.rp, sp);
+  const ApplyRegParams<T>& P = *sp;
+  const long long tot = (long long)L.rp.n * L.rp.n * L.kt * 2;      // (cell, temporal dof, component)
+  for (long long t = item_first(); t < tot; t += item_stride()) {
     switch (L.kt) {
-      case 1: apply2d_reg_thread<T, 3, 1, true>(L.rp, L.x, L.b, L.r, RESIDUAL, t); break;
-      case 2: apply2d_reg_thread<T, 3, 2, true>(L.rp, L.x, L.b, L.r, RESIDUAL, t); break;
-      case 3: apply2d_reg_thread<T, 3, 3, true>(L.rp, L.x, L.b, L.r, RESIDUAL, t); break;
-      default: apply2d_reg_thread<T, 3, 4, true>(L.rp, L.x, L.b, L.r, RESIDUAL, t); break;
+      case 1: apply2d_reg_thread<T, 3, 1, true>(P, L.x, L.b, L.r, RESIDUAL, t); break;
+      case 2: apply2d_reg_thread<T, 3, 2, true>(P, L.x, L.b, L.r, RESIDUAL, t); break;
+      case 3: apply2d_reg_thread<T, 3, 3, true>(P, L.x, L.b, L.r, RESIDUAL, t); break;
+      default: apply2d_reg_thread<T, 3, 4, true>(P, L.x, L.b, L.r, RESIDUAL, t); break;
     }
   }
 }
 
 // b_c = P^T src (and x_c = 0)
 template <typename T>
-__device__ __noinline__ void phase_restrict(const MGLevelDesc<T>& L, const T* src, const MGLevelDesc<T>& C, T* tsh) {
-  const long long nvb = restrict_g_blocks(L.tp);
+__device__ __noinline__ void phase_restrict(const MGLevelDesc<T>& L, const T* src, const MGLevelDesc<T>& C, T* tsh,
+                                            TransferParams<T>* sp) {
+  stage_transfer_tables(L.tp, sp);
+  const TransferParams<T>& P = *sp;
+  const long long nvb = restrict_g_blocks(P);
   for (long long vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
-    if (L.ht) restrict_g_block<T, 3, 3, 1, true>(L.tp, src, C.b, C.x, vb, tsh);
-    else restrict_g_block<T, 3, 3, 0, true>(L.tp, src, C.b, C.x, vb, tsh);
+    if (L.ht) restrict_g_block<T, 3, 3, 1, true>(P, src, C.b, C.x, vb, tsh);
+    else restrict_g_block<T, 3, 3, 0, true>(P, src, C.b, C.x, vb, tsh);
   }
 }
 
 // x += P x_c
 template <typename T>
-__device__ __noinline__ void phase_prolongate(const MGLevelDesc<T>& L, const MGLevelDesc<T>& C) {
-  const long long tot = 2LL * L.tp.Gf * L.tp.Gf + (long long)L.tp.nf * L.tp.nf * L.tp.npmf;
-  for (long long t = blockIdx.x * (long long)PT + threadIdx.x; t < tot; t += (long long)gridDim.x * PT) {
-    if (L.ht) prolongate_g_thread<T, 3, 3, 1, true>(L.tp, C.x, L.x, t);
-    else prolongate_g_thread<T, 3, 3, 0, true>(L.tp, C.x, L.x, t);
+__device__ __noinline__ void phase_prolongate(const MGLevelDesc<T>& L, const MGLevelDesc<T>& C,
+                                              TransferParams<T>* sp) {
+  stage_transfer_tables(L.tp, sp);
+  const TransferParams<T>& P = *sp;
+  const long long tot = 2LL * P.Gf * P.Gf + (long long)P.nf * P.nf * P.npmf;
+  for (long long t = item_first(); t < tot; t += item_stride()) {
+    if (L.ht) prolongate_g_thread<T, 3, 3, 1, true>(P, C.x, L.x, t);
+    else prolongate_g_thread<T, 3, 3, 0, true>(P, C.x, L.x, t);
   }
 }
 
@@ -178,7 +218,7 @@ __device__ __noinline__ void phase_coarse(const MGLevelDesc<T>& C, double* bs) {
 // x_c = acc (rounded to T), acc = 0 again for the next V-cycle
 template <typename T>
 __device__ __noinline__ void phase_finish(const MGLevelDesc<T>& C) {
-  for (long long i = blockIdx.x * (long long)PT + threadIdx.x; i < C.D; i += (long long)gridDim.x * PT) {
+  for (long long i = item_first(); i < C.D; i += item_stride()) {
     C.x[i] = (T)__ldcg(C.acc + i);
     C.acc[i] = 0.0;
   }
@@ -187,9 +227,18 @@ __device__ __noinline__ void phase_finish(const MGLevelDesc<T>& C) {
 }  // namespace
 
 template <typename T>
-__global__ void __launch_bounds__(PT) k_mg_persist(const MGLevelDesc<T>* __restrict__ Ld, int nl, int nu1, int nu2,
+__global__ void __launch_bounds__(PT, 2) k_mg_persist(const MGLevelDesc<T>* __restrict__ Ld, int nl, int nu1, int nu2,
                                                    unsigned* bar, int* err) {
-  __shared__ __align__(16) T rs[1024];
+  // phases use one shared scratch at a time: the sweep's patch residuals, or a level's
+  // operator tables, or its transfer tables (the barrier between phases separates them)
+  constexpr size_t SCR = sizeof(T) * 1024 > sizeof(ApplyRegParams<T>)
+                             ? (sizeof(T) * 1024 > sizeof(TransferParams<T>) ? sizeof(T) * 1024 : sizeof(TransferParams<T>))
+                             : (sizeof(ApplyRegParams<T>) > sizeof(TransferParams<T>) ? sizeof(ApplyRegParams<T>)
+                                                                                        : sizeof(TransferParams<T>));
+  __shared__ __align__(16) unsigned char scratch[SCR];
+  T* rs = reinterpret_cast<T*>(scratch);
+  ApplyRegParams<T>* sap = reinterpret_cast<ApplyRegParams<T>*>(scratch);
+  TransferParams<T>* stp = reinterpret_cast<TransferParams<T>*>(scratch);
   __shared__ T tsh[PT];
   __shared__ double bs[32];
   __shared__ int sh_ok;
@@ -200,25 +249,25 @@ __global__ void __launch_bounds__(PT) k_mg_persist(const MGLevelDesc<T>* __restr
   // ---- down
   for (int l = 0; l + 1 < nl; ++l) {
     const MGLevelDesc<T>& L = Ld[l];
-    const long long nv = (long long)L.kt * L.rp.n_vel;
+    const long long nv = L.size;              // the residual is scatter-added: all of r zero first
     for (int it = 0; it < nu1; ++it) {
       if (it == 0) {
         phase_sweep(L, L.b, rs);                 // x = 0: the residual is b
       } else {
-        phase_residual(L);
+        phase_residual(L, sap);
         STMG_SYNC();
         phase_sweep(L, L.r, rs);
         STMG_SYNC();
       }
-      zero_fill(L.r, nv);                        // velocity rows of r: scatter-added next
+      zero_fill(L.r, nv);                        // r: scatter-added next
       STMG_SYNC();
     }
     if (nu1 > 0) {
-      phase_residual(L);
+      phase_residual(L, sap);
       STMG_SYNC();
-      phase_restrict(L, L.r, Ld[l + 1], tsh);    // next level: b = P^T r, x = 0
+      phase_restrict(L, L.r, Ld[l + 1], tsh, stp);    // next level: b = P^T r, x = 0
     } else {
-      phase_restrict(L, L.b, Ld[l + 1], tsh);    // no presmoothing: the residual is b
+      phase_restrict(L, L.b, Ld[l + 1], tsh, stp);    // no presmoothing: the residual is b
     }
     STMG_SYNC();
   }
@@ -230,12 +279,12 @@ __global__ void __launch_bounds__(PT) k_mg_persist(const MGLevelDesc<T>* __restr
   // ---- up
   for (int l = nl - 2; l >= 0; --l) {
     const MGLevelDesc<T>& L = Ld[l];
-    const long long nv = (long long)L.kt * L.rp.n_vel;
-    phase_prolongate(L, Ld[l + 1]);
+    const long long nv = L.size;
+    phase_prolongate(L, Ld[l + 1], stp);
     zero_fill(L.r, nv);
     STMG_SYNC();
     for (int it = 0; it < nu2; ++it) {
-      phase_residual(L);
+      phase_residual(L, sap);
       STMG_SYNC();
       phase_sweep(L, L.r, rs);
       if (it + 1 < nu2) {
@@ -248,6 +297,7 @@ __global__ void __launch_bounds__(PT) k_mg_persist(const MGLevelDesc<T>* __restr
 #undef STMG_SYNC
 }
 
+// resident blocks per SM of the persistent kernel (at most 2; 0: not available)
 template <typename T>
 int mg_persist_blocks(int n_sm) {
   int per_sm = 0;
@@ -255,7 +305,8 @@ int mg_persist_blocks(int n_sm) {
     cudaGetLastError();
     return 0;
   }
-  return n_sm * (per_sm < 2 ? per_sm : 2);
+  (void)n_sm;
+  return per_sm < 2 ? per_sm : 2;
 }
 
 template <typename T>

@@ -1,6 +1,6 @@
 // Device bodies shared by the one-kernel-per-operation path and the persistent multigrid
-// kernel (k_mg_persist.cu): the register-resident 2D operator, the gather-form grid
-// transfers of 2D levels, the block Vanka sweep and the tiled coarse product.
+// kernel (k_mg_persist.cu): the register-resident 2D operator and the gather-form grid
+// transfers of 2D levels.
 //
 // Each body takes the index of its thread (or of its block) explicitly, so that a launch
 // with one block per work item and a persistent launch looping over the items run the same
@@ -23,9 +23,12 @@ __device__ __forceinline__ T ldv(const T* p) {
 }
 
 // ------------------------------------------------------------------------------------
-// Register-resident 2D operator (Sec. 4.5): thread t -> (temporal dof a, cell c), cells
-// fastest.  See k_apply2d_reg.cu for the arithmetic.  The velocity rows are scatter-added
-// (zero on entry), the pressure rows stored.
+// Register-resident 2D operator (Sec. 4.5): thread t -> (temporal dof a, velocity
+// component d, cell c), cells fastest, so that a warp covers consecutive cells of one
+// (a, d) and its loads are unit-stride runs.  See k_apply2d_reg.cu for the arithmetic.
+// Every row of y is scatter-added (y zero on entry): the velocity rows of component d by
+// the cells holding the node, the pressure rows of a cell by its two component threads
+// (continuity is a sum over the components).
 // ------------------------------------------------------------------------------------
 template <typename T, int NP, int KT, bool CG>
 __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, const T* __restrict__ x,
@@ -35,9 +38,10 @@ __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, c
   constexpr int NPM = NP * (NP - 1) / 2;            // C(r + 2, 2) pressure modes, r = NP - 2
   const int n = P.n, G = P.G;
   const long long ncells = (long long)n * n;
-  if (t >= ncells * KT) return;
-  const int a = (int)(t / ncells);
-  const long long c = t - (long long)a * ncells;
+  if (t >= ncells * KT * 2) return;
+  const long long ad = t / ncells;
+  const long long c = t - ad * ncells;
+  const int a = (int)(ad >> 1), d = (int)(ad & 1);
   const int cx = (int)(c % n), cy = (int)(c / n);
   const long long nvel = P.n_vel, nnod = P.n_nodes;
   const long long poff = (long long)KT * nvel;
@@ -47,105 +51,128 @@ __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, c
   const long long base = (long long)(cy * E) * G + cx * E;      // global index of the cell's node (0, 0)
   // boundary lines of the cell's nodes (the mesh boundary crosses a cell only at its outer lines)
   const bool bx0 = cx == 0, bx1 = cx == n - 1, by0 = cy == 0, by1 = cy == n - 1;
+  const T* cb = &P.CB[d][0][0];                     // [mode][node] factors of component d
 
-  T p[NPM];
+  T ut[NQ], ua[NQ], p[NPM];
 #pragma unroll
-  for (int m = 0; m < NPM; ++m) p[m] = lift ? T(0) : ldv<CG>(x + poff + (long long)a * P.n_pres + c * NPM + m);
-  T cont[NPM];
-#pragma unroll
-  for (int m = 0; m < NPM; ++m) cont[m] = 0;
+  for (int q = 0; q < NQ; ++q) { ut[q] = 0; ua[q] = 0; }
   T kt_row[KT];
 #pragma unroll
   for (int bb = 0; bb < KT; ++bb) kt_row[bb] = tr ? P.Kt[bb * MAXKT + a] : P.Kt[a * MAXKT + bb];
-  const T beta = P.beta[a], bsc = P.bscale[a], hd = P.hd;
-
-#pragma unroll
-  for (int d = 0; d < 2; ++d) {
-    T ut[NQ], ua[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) { ut[q] = 0; ua[q] = 0; }
-#pragma unroll
-    for (int bb = 0; bb < KT; ++bb) {
-      const T* xb = x + bb * nvel + d * nnod + base;
-#pragma unroll
-      for (int iy = 0; iy < NP; ++iy) {
-        const bool dy = (iy == 0 && by0) || (iy == E && by1);
-#pragma unroll
-        for (int ix = 0; ix < NP; ++ix) {
-          const bool dir = dy || (ix == 0 && bx0) || (ix == E && bx1);
-          const bool take = lift ? dir : !dir;
-          const T v = take ? ldv<CG>(xb + iy * G + ix) : T(0);
-          ut[iy * NP + ix] += kt_row[bb] * v;
-          if (bb == a) ua[iy * NP + ix] = v;
-        }
-      }
-    }
-    // continuity rows of this component
-#pragma unroll
-    for (int m = 0; m < NPM; ++m) {
-      T s = 0;
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) s += P.CB[d][m][q] * ua[q];
-      cont[m] += s;
-    }
-    // y-pass: A1 = hd M1y ut + beta K1y ua, A2 = M1y ua (column by column)
-    T A1[NQ], A2[NQ];
-#pragma unroll
-    for (int ix = 0; ix < NP; ++ix) {
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        T m1 = 0, k1 = 0, m2 = 0;
-#pragma unroll
-        for (int j = 0; j < NP; ++j) {
-          m1 += P.M1[i * NP + j] * ut[j * NP + ix];
-          k1 += P.K1[i * NP + j] * ua[j * NP + ix];
-          m2 += P.M1[i * NP + j] * ua[j * NP + ix];
-        }
-        A1[i * NP + ix] = hd * m1 + beta * k1;
-        A2[i * NP + ix] = m2;
-      }
-    }
-    // x-pass, pressure gradient, scatter (row by row)
-    T* yd = y + a * nvel + d * nnod + base;
-    const T* bd = b + a * nvel + d * nnod + base;
-    const T* xd = x + a * nvel + d * nnod + base;
+  // the KT slices of the thread's component: in single precision all loads at once; in
+  // double precision slice by slice (the registers of all KT slices at once would spill)
+  auto slice = [&](int bb) {
+    const T* xb = x + bb * nvel + d * nnod + base;
+    const T kb = kt_row[bb];
 #pragma unroll
     for (int iy = 0; iy < NP; ++iy) {
       const bool dy = (iy == 0 && by0) || (iy == E && by1);
-      const bool oy = iy < E || by1;                      // this cell owns the node row (for boundary rows)
 #pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        const bool dir = dy || (i == 0 && bx0) || (i == E && bx1);
-        const bool own = oy && (i < E || bx1);
-        const long long off = (long long)iy * G + i;
-        if (dir) {
-          if (own) {
-            const T xv = ldv<CG>(xd + off);
-            yd[off] = mode == RESIDUAL ? ldv<CG>(bd + off) - xv : xv;   // identity row, by its owner only
-          }
-          continue;
-        }
-        T m1 = 0, k1 = 0;
-#pragma unroll
-        for (int j = 0; j < NP; ++j) {
-          m1 += P.M1[i * NP + j] * A1[iy * NP + j];
-          k1 += P.K1[i * NP + j] * A2[iy * NP + j];
-        }
-        T bt = 0;
-#pragma unroll
-        for (int m = 0; m < NPM; ++m) bt += P.CB[d][m][iy * NP + i] * p[m];
-        T v = m1 + beta * k1 + bsc * bt;
-        if (res) v = own ? ldv<CG>(bd + off) - v : -v;     // b enters once, through the owner
-        atomicAdd(yd + off, v);
+      for (int ix = 0; ix < NP; ++ix) {
+        const bool dir = dy || (ix == 0 && bx0) || (ix == E && bx1);
+        const bool take = lift ? dir : !dir;
+        const T v = take ? ldv<CG>(xb + iy * G + ix) : T(0);
+        ut[iy * NP + ix] += kb * v;
+        if (bb == a) ua[iy * NP + ix] = v;
       }
     }
+  };
+  if (sizeof(T) == 4) {
+#pragma unroll
+    for (int bb = 0; bb < KT; ++bb) slice(bb);
+  } else {
+#pragma unroll 1
+    for (int bb = 0; bb < KT; ++bb) slice(bb);
   }
-  // pressure rows of the cell
+#pragma unroll
+  for (int m = 0; m < NPM; ++m) p[m] = lift ? T(0) : ldv<CG>(x + poff + (long long)a * P.n_pres + c * NPM + m);
+  // the right-hand side rows this thread adds b to (residual / lift): loaded with x in
+  // single precision (latency bound); in double precision the registers are scarcer and the
+  // FP64 arithmetic hides the later loads
+  constexpr bool HOIST_B = sizeof(T) == 4;
+  T bv[HOIST_B ? NQ : 1], bp[HOIST_B ? NPM : 1];
+  const T* bd = b + a * nvel + d * nnod + base;
+  if (HOIST_B) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int iy = q / NP, i = q % NP;
+      const bool own = (iy < E || by1) && (i < E || bx1);
+      bv[q] = own && res ? ldv<CG>(bd + (long long)iy * G + i) : T(0);
+    }
+#pragma unroll
+    for (int m = 0; m < NPM; ++m) bp[m] = res && d == 0 ? ldv<CG>(b + poff + (long long)a * P.n_pres + c * NPM + m) : T(0);
+  }
+  auto bvel = [&](int iy, int i) -> T { return HOIST_B ? bv[(iy * NP + i) % (HOIST_B ? NQ : 1)] : ldv<CG>(bd + (long long)iy * G + i); };
+  auto bpre = [&](int m) -> T {
+    return HOIST_B ? bp[m % (HOIST_B ? NPM : 1)] : ldv<CG>(b + poff + (long long)a * P.n_pres + c * NPM + m);
+  };
+  const T beta = P.beta[a], bsc = P.bscale[a], hd = P.hd;
+  // continuity rows: this component's share
+  T cont[NPM];
+#pragma unroll
+  for (int m = 0; m < NPM; ++m) {
+    T s = 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) s += cb[m * (MAXNP * MAXNP) + q] * ua[q];
+    cont[m] = s;
+  }
+  // y-pass: A1 = hd M1y ut + beta K1y ua, A2 = M1y ua (column by column)
+  T A1[NQ], A2[NQ];
+#pragma unroll
+  for (int ix = 0; ix < NP; ++ix) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T m1 = 0, k1 = 0, m2 = 0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        m1 += P.M1[i * NP + j] * ut[j * NP + ix];
+        k1 += P.K1[i * NP + j] * ua[j * NP + ix];
+        m2 += P.M1[i * NP + j] * ua[j * NP + ix];
+      }
+      A1[i * NP + ix] = hd * m1 + beta * k1;
+      A2[i * NP + ix] = m2;
+    }
+  }
+  // x-pass, pressure gradient, scatter (row by row)
+  T* yd = y + a * nvel + d * nnod + base;
+  const T* xd = x + a * nvel + d * nnod + base;
+#pragma unroll
+  for (int iy = 0; iy < NP; ++iy) {
+    const bool dy = (iy == 0 && by0) || (iy == E && by1);
+    const bool oy = iy < E || by1;                      // this cell owns the node row (for boundary rows)
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      const bool dir = dy || (i == 0 && bx0) || (i == E && bx1);
+      const bool own = oy && (i < E || bx1);
+      const long long off = (long long)iy * G + i;
+      if (dir) {
+        if (own) {
+          const T xv = ldv<CG>(xd + off);
+          atomicAdd(yd + off, mode == RESIDUAL ? bvel(iy, i) - xv : xv);   // identity row, by its owner
+        }
+        continue;
+      }
+      T m1 = 0, k1 = 0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        m1 += P.M1[i * NP + j] * A1[iy * NP + j];
+        k1 += P.K1[i * NP + j] * A2[iy * NP + j];
+      }
+      T bt = 0;
+#pragma unroll
+      for (int m = 0; m < NPM; ++m) bt += cb[m * (MAXNP * MAXNP) + iy * NP + i] * p[m];
+      T v = m1 + beta * k1 + bsc * bt;
+      if (res) v = own ? bvel(iy, i) - v : -v;           // b enters once, through the owner
+      atomicAdd(yd + off, v);
+    }
+  }
+  // pressure rows of the cell: this component's share (b through component 0)
 #pragma unroll
   for (int m = 0; m < NPM; ++m) {
     const long long gi = poff + (long long)a * P.n_pres + c * NPM + m;
-    const T v = bsc * cont[m];
-    y[gi] = res ? ldv<CG>(b + gi) - v : v;
+    T v = bsc * cont[m];
+    if (res) v = d == 0 ? bpre(m) - v : -v;
+    atomicAdd(y + gi, v);
   }
 }
 
@@ -223,17 +250,24 @@ __device__ __forceinline__ void prolongate_g_thread(const TransferParams<T>& P, 
         s[ac] = a;
       }
     }
-    for (int af = 0; af < ktf; ++af) {
-      T o = 0;
+    T old[MAXKT];                                     // the fine values first, all at once
 #pragma unroll
-      for (int ac = 0; ac < MAXKT; ++ac)
-        if (ac < ktc) o += P.Pt[af * MAXKT + ac] * s[ac];
-      T* out = xf + af * P.nvf + comp * P.nnf + g;
-      *out = ldv<CG>(out) + o;
+    for (int af = 0; af < MAXKT; ++af) old[af] = af < ktf ? ldv<CG>(xf + af * P.nvf + comp * P.nnf + g) : T(0);
+#pragma unroll
+    for (int af = 0; af < MAXKT; ++af) {
+      if (af < ktf) {
+        T o = 0;
+#pragma unroll
+        for (int ac = 0; ac < MAXKT; ++ac)
+          if (ac < ktc) o += P.Pt[af * MAXKT + ac] * s[ac];
+        xf[af * P.nvf + comp * P.nnf + g] = old[af] + o;
+      }
     }
     return;
   }
-  // pressure: one thread per (fine cell, fine mode), every fine temporal dof
+  // pressure: one thread per (fine cell, fine mode), every fine temporal dof; the parent
+  // cell's coarse modes of every coarse temporal dof are loaded first, all at once
+  constexpr int NPMC = NPC * (NPC - 1) / 2;           // 2D pressure modes of the coarse degree
   const long long tq = t - nvt;
   if (tq >= (long long)P.nf * P.nf * P.npmf) return;
   const int fc = (int)(tq / P.npmf), mf = (int)(tq - (long long)fc * P.npmf);
@@ -241,18 +275,31 @@ __device__ __forceinline__ void prolongate_g_thread(const TransferParams<T>& P, 
   const int ccx = HT ? fx / 2 : fx, ccy = HT ? fy / 2 : fy;
   const int o = HT ? ((fx & 1) | ((fy & 1) << 1)) : 0;
   const long long cc = (long long)ccy * nc + ccx;
-  for (int af = 0; af < ktf; ++af) {
-    T v = 0;
-    for (int ac = 0; ac < ktc; ++ac) {
-      const T pt = P.Pt[af * MAXKT + ac];
-      if (pt == T(0)) continue;
-      const T* yv = yc + (long long)ktc * P.nvc + ac * P.npc_tot + cc * P.npmc;
-      T u = 0;
-      for (int mc = 0; mc < P.npmc; ++mc) u += pres_map(P, o, mf, mc) * ldv<CG>(yv + mc);
-      v += pt * u;
+  T u[MAXKT];
+#pragma unroll
+  for (int ac = 0; ac < MAXKT; ++ac) {
+    T yv[NPMC];
+    const T* src = yc + (long long)ktc * P.nvc + ac * P.npc_tot + cc * NPMC;
+#pragma unroll
+    for (int mc = 0; mc < NPMC; ++mc) yv[mc] = ac < ktc ? ldv<CG>(src + mc) : T(0);
+    T s = 0;
+#pragma unroll
+    for (int mc = 0; mc < NPMC; ++mc) s += pres_map(P, o, mf, mc) * yv[mc];
+    u[ac] = s;
+  }
+  T old[MAXKT];
+#pragma unroll
+  for (int af = 0; af < MAXKT; ++af)
+    old[af] = af < ktf ? ldv<CG>(xf + (long long)ktf * P.nvf + af * P.npf_tot + (long long)fc * P.npmf + mf) : T(0);
+#pragma unroll
+  for (int af = 0; af < MAXKT; ++af) {
+    if (af < ktf) {
+      T v = 0;
+#pragma unroll
+      for (int ac = 0; ac < MAXKT; ++ac)
+        if (ac < ktc) v += P.Pt[af * MAXKT + ac] * u[ac];
+      xf[(long long)ktf * P.nvf + af * P.npf_tot + (long long)fc * P.npmf + mf] = old[af] + v;
     }
-    T* out = xf + (long long)ktf * P.nvf + af * P.npf_tot + (long long)fc * P.npmf + mf;
-    *out = ldv<CG>(out) + v;
   }
 }
 
@@ -321,14 +368,16 @@ __device__ __forceinline__ void restrict_g_block(const TransferParams<T>& P, con
         T wx[BX], wy[BX];
         support_1d<T, NPC, NS, BX>(P, Jx, &ix0, &nx, wx);
         support_1d<T, NPC, NS, BX>(P, Jy, &iy0, &ny, wy);
-        const T* r = rf + af * P.nvf + comp * P.nnf + (long long)iy0 * Gf + ix0;
+        // every load unconditional (indices clamped into the grid, weights 0 outside the
+        // support), so that all of them are in flight at once
+        const T* r = rf + af * P.nvf + comp * P.nnf;
+        (void)nx; (void)ny;
 #pragma unroll
         for (int my = 0; my < BX; ++my) {
-          if (my >= ny || wy[my] == T(0)) continue;
+          const long long iy = min(iy0 + my, Gf - 1);
           T row = 0;
 #pragma unroll
-          for (int mx = 0; mx < BX; ++mx)
-            if (mx < nx && wx[mx] != T(0)) row += wx[mx] * ldv<CG>(r + (long long)my * Gf + mx);
+          for (int mx = 0; mx < BX; ++mx) row += wx[mx] * ldv<CG>(r + iy * Gf + min(ix0 + mx, Gf - 1));
           acc += wy[my] * row;
         }
       }
@@ -355,19 +404,38 @@ __device__ __forceinline__ void restrict_g_block(const TransferParams<T>& P, con
   const int mc = (int)(rest % P.npmc);
   const long long cc = rest / P.npmc;
   const int ccx = (int)(cc % P.nc), ccy = (int)(cc / P.nc);
+  // the children's fine modes of one fine temporal dof are loaded together, then combined
   constexpr int nchild = HT ? 4 : 1;
+  constexpr int NPMF = NPF * (NPF - 1) / 2;           // 2D pressure modes of the fine degree
+  long long fcs[nchild];
+#pragma unroll
+  for (int o = 0; o < nchild; ++o) {
+    const int fx = HT ? 2 * ccx + (o & 1) : ccx, fy = HT ? 2 * ccy + ((o >> 1) & 1) : ccy;
+    fcs[o] = (long long)fy * P.nf + fx;
+  }
+  // fine temporal dofs in groups of four, every load of a group in flight at once
   T v = 0;
-  for (int af = 0; af < ktf; ++af) {
-    const T pt = P.Pt[af * MAXKT + ac];
-    if (pt == T(0)) continue;
-    T u = 0;
-    for (int o = 0; o < nchild; ++o) {
-      const int fx = HT ? 2 * ccx + (o & 1) : ccx, fy = HT ? 2 * ccy + ((o >> 1) & 1) : ccy;
-      const long long fc = (long long)fy * P.nf + fx;
-      const T* rr = rf + (long long)ktf * P.nvf + af * P.npf_tot + fc * P.npmf;
-      for (int mf = 0; mf < P.npmf; ++mf) u += pres_map(P, o, mf, mc) * ldv<CG>(rr + mf);
+  for (int a0 = 0; a0 < ktf; a0 += 4) {
+    T rv[4][nchild][NPMF];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int o = 0; o < nchild; ++o) {
+        const T* rr = rf + (long long)ktf * P.nvf + (a0 + q) * P.npf_tot + fcs[o] * NPMF;
+#pragma unroll
+        for (int mf = 0; mf < NPMF; ++mf) rv[q][o][mf] = a0 + q < ktf ? ldv<CG>(rr + mf) : T(0);
+      }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (a0 + q < ktf) {
+        T u = 0;
+#pragma unroll
+        for (int o = 0; o < nchild; ++o)
+#pragma unroll
+          for (int mf = 0; mf < NPMF; ++mf) u += pres_map(P, o, mf, mc) * rv[q][o][mf];
+        v += P.Pt[(a0 + q) * MAXKT + ac] * u;
+      }
     }
-    v += pt * u;
   }
   bc[(long long)ktc * P.nvc + ac * P.npc_tot + cc * P.npmc + mc] = v;
   if (zc) zc[(long long)ktc * P.nvc + ac * P.npc_tot + cc * P.npmc + mc] = T(0);
