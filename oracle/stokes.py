@@ -268,10 +268,26 @@ def prolong_space(coarse: SpaceFE, fine: SpaceFE):
 
 
 def prolong_time(tc: TimeFE, tf: TimeFE):
-    """p-prolongation in time (Eq. DefPrRek): P[a, b] = phi_b^coarse(t_a^fine) on each
-    subinterval of the system (block diagonal over the subintervals)."""
-    assert tc.nsub == tf.nsub
-    return np.kron(np.eye(tf.nsub), lagrange_values(tc.nodes1, tf.nodes1).T)
+    """Prolongation in time: P[a, b] = phi_b^coarse(t_a^fine), the coarse DG function
+    evaluated at the fine temporal nodes (the canonical embedding of Eq. DeftPrRe for a
+    coarser temporal mesh, of Eq. DefPrRek for a lower degree, or both).
+
+    The system's time span is split into tf.nsub fine and tc.nsub coarse subintervals,
+    tf.nsub = m tc.nsub (m = 1: p in time only; m = 2: h in time, each coarse subinterval
+    the union of two fine ones).  Fine node a lies in fine subinterval j_f at the local
+    Radau coordinate s in (-1, 1]; it belongs to coarse subinterval j_c = j_f // m, at the
+    local coordinate xi = (2 (j_f - m j_c) + s + 1) / m - 1.  A fine node at the right end
+    of a coarse subinterval (s = 1, last fine subinterval of it) takes the value of that
+    coarse subinterval's polynomial: DG functions are evaluated from the left there."""
+    m = tf.nsub // tc.nsub
+    assert tf.nsub == m * tc.nsub and abs(tc.tau - m * tf.tau) <= 1e-14 * tc.tau
+    kf1, kc1 = tf.k + 1, tc.k + 1
+    P = np.zeros((tf.kt, tc.kt))
+    for jf in range(tf.nsub):
+        jc = jf // m
+        xi = (2.0 * (jf - m * jc) + tf.nodes1 + 1.0) / m - 1.0
+        P[jf * kf1:(jf + 1) * kf1, jc * kc1:(jc + 1) * kc1] = lagrange_values(tc.nodes1, xi).T
+    return P
 
 
 def slab_prolongation(coarse: Slab, fine: Slab):
@@ -434,9 +450,14 @@ class Multigrid:
     transfer is whatever (n, r, k) change they have (h or p in space, p in time)."""
 
     def __init__(self, dim, levels, nu, tau, cfg: MGConfig = MGConfig(), nsub=1):
+        """levels: (n, r, k) or (n, r, k, nsub_l) fine -> coarse; tau and nsub are the
+        finest level's subinterval length and count (a level of nsub_l subintervals covers
+        the same system time span with subintervals of length tau nsub / nsub_l: h-coarsening
+        in time when nsub_l < nsub)."""
         self.cfg = cfg
-        self.levels = list(levels)
-        self.slabs = [Slab(dim, n, r, k, nu, tau, nsub) for (n, r, k) in levels]
+        self.levels = [tuple(l) if len(l) == 4 else (l[0], l[1], l[2], nsub) for l in levels]
+        span = tau * nsub
+        self.slabs = [Slab(dim, n, r, k, nu, span / ns, ns) for (n, r, k, ns) in self.levels]
         self.P = [slab_prolongation(self.slabs[i + 1], self.slabs[i]) for i in range(len(levels) - 1)]
         self.smoothers = []
         for s in self.slabs[:-1]:

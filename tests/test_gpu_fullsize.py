@@ -66,7 +66,7 @@ def gpu():
 
 
 def test_hierarchy_is_the_benched_one(oracle, gpu):
-    assert [(l["n"], l["r"], l["k"]) for l in gpu.levels] == [tuple(l) for l in oracle.levels]
+    assert [(l["n"], l["r"], l["k"]) for l in gpu.levels] == [tuple(l[:3]) for l in oracle.levels]
     assert [l["size"] for l in gpu.levels] == [s.size for s in oracle.slabs]
     assert gpu.levels[0]["size"] == 297222 and gpu.levels[-1]["size"] == 2310
     fin = gpu.levels[0]

@@ -497,3 +497,71 @@ def test_macro_step_exact_reproduction_and_multigrid():
         a, b = slab2.remove_pressure_mean(xm), slab2.remove_pressure_mean(xd)
         assert np.abs(a - b).max() < 1e-7 * np.abs(b).max()
     assert max(i.iterations for i in infos) <= 30
+
+
+# ---------------------------------------------------------------------------
+# h-coarsening in time inside a macro step (App. A, Eq. DeftPrRe, DefTlspr)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("k,nsub_f,kc", [(0, 2, 0), (1, 2, 1), (2, 4, 2), (3, 2, 3), (2, 2, 1)])
+def test_time_h_prolongation_interpolates_coarse_polynomials(k, nsub_f, kc):
+    """A coarse DG(kc) function on nsub_f / 2 subintervals of length 2 tau (one random
+    polynomial per coarse subinterval), given by its values at the coarse Radau points, is
+    reproduced by the prolongation at the fine Radau points of the nsub_f subintervals of
+    length tau (degree k >= kc), each fine point taking the polynomial of the coarse
+    subinterval that contains it (its right end included).  Checked against direct
+    polynomial evaluation in physical time."""
+    from oracle.stokes import prolong_time
+    tau = 0.3
+    tf, tc = TimeFE(k, tau, nsub_f), TimeFE(kc, 2 * tau, nsub_f // 2)
+    rng = np.random.default_rng(7)
+    polys = [Polynomial(rng.standard_normal(kc + 1)) for _ in range(tc.nsub)]
+    # physical times of the Radau points: subinterval j of length h starts at j h
+    coarse_vals = np.concatenate([polys[j](2 * tau * (j + (tc.nodes1 + 1) / 2)) for j in range(tc.nsub)])
+    fine_vals = np.concatenate([polys[jf // 2](tau * (jf + (tf.nodes1 + 1) / 2)) for jf in range(nsub_f)])
+    P = prolong_time(tc, tf)
+    assert P.shape == (tf.kt, tc.kt)
+    assert np.abs(P @ coarse_vals - fine_vals).max() < 1e-12 * max(1.0, np.abs(fine_vals).max())
+
+
+@pytest.mark.parametrize("fine,coarse", [
+    ((2, 2, 1, 1, 2), (2, 2, 1, 1, 1)),     # h in time only
+    ((2, 2, 1, 2, 4), (2, 2, 1, 2, 2)),     # h in time, DG(2)
+    ((2, 4, 1, 1, 2), (2, 2, 1, 1, 1)),     # h in space and in time
+    ((2, 2, 2, 2, 2), (2, 2, 1, 1, 1)),     # h in time, p in space and time
+])
+def test_galerkin_identity_h_in_time(fine, coarse):
+    """The macro system on the coarser temporal mesh is the Galerkin projection of the finer
+    one: P^T S_f P = S_c on free dofs.  Coarse functions are continuous at the fine
+    subinterval borders inside a coarse subinterval, so the fine jump terms there vanish and
+    the integrals add up (exact integration in time and space)."""
+    dim, nf, rf, kf, msf = fine
+    _, nc, rc, kc, msc = coarse
+    span = 0.4
+    sf = Slab(dim, nf, rf, kf, 1.3, span / msf, msf)
+    sc = Slab(dim, nc, rc, kc, 1.3, span / msc, msc)
+    P = slab_prolongation(sc, sf)
+    G = (P.T @ sf.S @ P).toarray()
+    Sc = sc.S.toarray()
+    free = ~sc.dirichlet
+    assert np.abs(G[np.ix_(free, free)] - Sc[np.ix_(free, free)]).max() < 1e-12 * np.abs(Sc).max()
+    # the identity fails if the coarse operator keeps the fine subinterval length
+    wrong = Slab(dim, nc, rc, kc, 1.3, span / msf, msc).S.toarray()
+    assert np.abs(G[np.ix_(free, free)] - wrong[np.ix_(free, free)]).max() > 1e-6 * np.abs(Sc).max()
+
+
+def test_mg_with_h_in_time_levels_equals_direct_solve():
+    """A macro step of four subintervals, the hierarchy coarsening in time (4 -> 2 -> 1
+    subintervals) before the spatial levels: FGMRES with the V-cycle reaches the bordered
+    direct solve of the macro system."""
+    pb = manufactured_2d(nu=1.0, time="sin_pi")
+    levels = [(4, 1, 1, 4), (4, 1, 1, 2), (4, 1, 1, 1), (2, 1, 1, 1), (1, 1, 1, 1)]
+    tau = 0.25 / 4
+    mg = Multigrid(2, levels, 1.0, tau, MGConfig(), nsub=4)
+    s0 = mg.slabs[0]
+    assert [s.kt for s in mg.slabs] == [8, 4, 2, 2, 2]
+    b = s0.rhs_forcing(pb.forcing, 0.0)
+    xd = s0.direct_solve(b)
+    x, info = fgmres(lambda z: s0.S @ z, mg.vcycle, b, tol=1e-11)
+    assert info.converged and info.iterations <= 40
+    a, c = s0.remove_pressure_mean(x), s0.remove_pressure_mean(xd)
+    assert np.abs(a - c).max() < 1e-8 * np.abs(c).max()
