@@ -130,9 +130,9 @@ typedef struct {
   int    n_sub;            /* DG(k) subintervals per system (a macro time step, Remark
                               rem:GLSP; default 1 = time marching, Eq. AlgSysTMS); the
                               system of n_sub subintervals is solved at once and the
-                              temporal multigrid is p-coarsening per subinterval (no
-                              h-coarsening in time).  tau = T / (n_slabs n_sub);
-                              n_sub (k + 1) <= 8                                        */
+                              temporal multigrid is p-coarsening per subinterval, with
+                              h-coarsening in time by level_nsub / time_h.  tau = T /
+                              (n_slabs n_sub); n_sub (k + 1) <= 8                       */
   int    half_inverses;    /* 1: the FP32 V-cycle stores its patch inverses in FP16, each
                               row scaled to [-1, 1] with an FP32 row scale (half the
                               bytes of the dominant stream; the sweep accumulates in
@@ -159,10 +159,23 @@ typedef struct {
                               faster (default), 2 = from the first level it covers (2D
                               Q2/P1 levels, k + 1 <= 4, patches of <= 256 dofs).  Same
                               V-cycle; rounding order only.                              */
+  int    level_nsub[STMG_MAX_LEVELS];  /* explicit hierarchies: subintervals of each level's
+                              temporal mesh (0 = n_sub); the first must equal n_sub and each
+                              must divide the previous one.  A level of fewer subintervals
+                              covers the same system span T / n_slabs with longer ones: the
+                              temporal h-coarsening of App. A (Eq. DeftPrRe), transfers =
+                              the canonical embedding of the coarser DG(k) function and
+                              its transpose                                              */
+  int    time_h;           /* default hierarchy with n_sub > 1: 1 = first halve the
+                              subintervals on the finest space level (n_sub -> n_sub/2 ->
+                              ... -> 1, h in time), then the spatial and temporal-degree
+                              levels on one subinterval; 0 (default) = p in time per
+                              subinterval only (the paper's choice for macro steps)      */
 } stmg_config;
 
 typedef struct {
   int       n, r, k;       /* cells per direction, spatial and temporal degree          */
+  int       n_sub;         /* subintervals of the level's temporal mesh in one system     */
   long long size;          /* D of this level                                            */
   long long n_vel;         /* velocity dofs per temporal dof (d ((r+1)n+1)^d)           */
   long long n_pres;        /* pressure dofs per temporal dof (C(r+d,d) n^d)             */

@@ -51,7 +51,7 @@ class SpaceTimeMG:
                  gmres_max_iter: int = 200, rel_tol: float = 1e-8, use_graphs: bool = True,
                  sweep_variant: int = 0, autotune: bool = True, coarse_n: int = 1, k_min: int = 1,
                  n_sub: int = 1, half_inverses: bool = False, transfer_variant: int = 0,
-                 apply_variant: int = 0, persistent: int = 1):
+                 apply_variant: int = 0, persistent: int = 1, time_h: bool = False):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("SpaceTimeMG needs a CUDA device (no CPU fallback)")
@@ -62,8 +62,9 @@ class SpaceTimeMG:
         cfg.nu, cfg.T, cfg.n_slabs = nu, T, n_slabs
         if levels:
             cfg.n_levels = len(levels)
-            for i, (ln, lr, lk) in enumerate(levels):
-                cfg.level_n[i], cfg.level_r[i], cfg.level_k[i] = ln, lr, lk
+            for i, lvl in enumerate(levels):
+                cfg.level_n[i], cfg.level_r[i], cfg.level_k[i] = lvl[0], lvl[1], lvl[2]
+                cfg.level_nsub[i] = lvl[3] if len(lvl) > 3 else 0        # (n, r, k[, n_sub])
         if smoothers is not None:
             for i, s in enumerate(smoothers):
                 cfg.smoother[i] = s
@@ -81,6 +82,7 @@ class SpaceTimeMG:
         cfg.transfer_variant = int(transfer_variant)
         cfg.apply_variant = int(apply_variant)
         cfg.persistent = int(persistent)
+        cfg.time_h = int(time_h)
         self.cfg = cfg
         self.dim, self.r, self.k, self.n_sub = dim, r, k, int(n_sub)
         self.kt = self.n_sub * (k + 1)
@@ -95,7 +97,7 @@ class SpaceTimeMG:
         for l in range(n.value):
             li = _lib.LevelInfo()
             check("stmg_level_info", lib.stmg_level_info(h, l, C.byref(li)))
-            self.levels.append({"n": li.n, "r": li.r, "k": li.k, "size": li.size, "n_vel": li.n_vel,
+            self.levels.append({"n": li.n, "r": li.r, "k": li.k, "n_sub": li.n_sub, "size": li.size, "n_vel": li.n_vel,
                                 "n_pres": li.n_pres, "smoother": li.smoother, "patch_size": li.patch_size,
                                 "n_patches": li.n_patches, "n_patch_classes": li.n_patch_classes,
                                 "inverse_bytes": tuple(li.inverse_bytes),

@@ -25,11 +25,12 @@ class Config(C.Structure):
                 ("gmres_max_iter", C.c_int), ("rel_tol", C.c_double), ("use_graphs", C.c_int),
                 ("sweep_variant", C.c_int), ("autotune", C.c_int), ("coarse_n", C.c_int),
                 ("k_min", C.c_int), ("n_sub", C.c_int), ("half_inverses", C.c_int),
-                ("transfer_variant", C.c_int), ("apply_variant", C.c_int), ("persistent", C.c_int)]
+                ("transfer_variant", C.c_int), ("apply_variant", C.c_int), ("persistent", C.c_int),
+                ("level_nsub", C.c_int * MAX_LEVELS), ("time_h", C.c_int)]
 
 
 class LevelInfo(C.Structure):
-    _fields_ = [("n", C.c_int), ("r", C.c_int), ("k", C.c_int),
+    _fields_ = [("n", C.c_int), ("r", C.c_int), ("k", C.c_int), ("n_sub", C.c_int),
                 ("size", C.c_longlong), ("n_vel", C.c_longlong), ("n_pres", C.c_longlong),
                 ("smoother", C.c_int), ("patch_size", C.c_int), ("n_patches", C.c_longlong),
                 ("n_patch_classes", C.c_int), ("inverse_bytes", C.c_longlong * 2),

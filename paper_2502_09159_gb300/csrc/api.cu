@@ -268,16 +268,21 @@ static void fill_transfer_params(const LevelHost& F, const LevelHost& C, Transfe
       p->P1[s * MAXNP + j] = (T)v;
     }
   }
-  // per subinterval (block diagonal): phi_ac^coarse at the fine Radau points
+  // phi_ac^coarse at the fine Radau points.  The system's span has F.nsub = m C.nsub
+  // subintervals on the fine level (m = 1: p in time per subinterval; m = 2: h in time);
+  // fine subinterval jf lies in coarse subinterval jf / m, and its local Radau coordinate s
+  // maps to xi = (2 (jf - m jc) + s + 1) / m - 1 there (right ends belong to their own
+  // coarse subinterval: DG functions are evaluated from the left at interval ends).
+  const int mt = F.nsub / C.nsub;
   for (int af = 0; af < F.kt; ++af)
     for (int ac = 0; ac < C.kt; ++ac) {
       const int jf = af / F.tt.k1, bf = af % F.tt.k1, jc = ac / C.tt.k1, bc = ac % C.tt.k1;
       double v = 0.0;
-      if (jf == jc) {
-        const double s = F.tt.nodes1[bf];
-        v = lagrange_eval(C.tt.nodes1, C.tt.k1, bc, s);
+      if (jf / mt == jc) {
+        const double xi = (2.0 * (jf - mt * jc) + F.tt.nodes1[bf] + 1.0) / mt - 1.0;
+        v = lagrange_eval(C.tt.nodes1, C.tt.k1, bc, xi);
         for (int jj = 0; jj < C.tt.k1; ++jj)
-          if (std::fabs(s - C.tt.nodes1[jj]) < 1e-14) v = (jj == bc) ? 1.0 : 0.0;
+          if (std::fabs(xi - C.tt.nodes1[jj]) < 1e-14) v = (jj == bc) ? 1.0 : 0.0;
       }
       p->Pt[af * MAXKT + ac] = (T)v;
     }
@@ -1115,6 +1120,8 @@ int stmg_default_config(stmg_config* c) {
   c->transfer_variant = 0;
   c->apply_variant = 0;
   c->persistent = 1;
+  c->time_h = 0;
+  for (int i = 0; i < STMG_MAX_LEVELS; ++i) c->level_nsub[i] = 0;
   return STMG_OK;
 }
 
@@ -1135,31 +1142,46 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
   if (c.precond_precision != STMG_FP64 && c.precond_precision != STMG_FP32) return STMG_ERR_ARG;
   if (!(c.precisions & (1 << c.precond_precision))) return STMG_ERR_ARG;
   h->tau = c.T / ((double)c.n_slabs * c.n_sub);
-  std::vector<std::array<int, 3>> lv;
+  if (c.time_h < 0 || c.time_h > 1) return STMG_ERR_ARG;
+  // levels (n, r, k, nsub) fine -> coarse; a level of fewer subintervals covers the same
+  // system time span T / n_slabs with longer ones (h-coarsening in time, App. A)
+  std::vector<std::array<int, 4>> lv;
   if (c.n_levels == 0) {
     if (c.n_cells & (c.n_cells - 1)) return STMG_ERR_ARG;   // default rule needs n = 2^c
     if (c.coarse_n < 1 || c.coarse_n > c.n_cells || (c.coarse_n & (c.coarse_n - 1))) return STMG_ERR_ARG;
     if (c.k_min < 1) return STMG_ERR_ARG;
-    lv = default_hierarchy(c.n_cells, c.r, c.k, c.coarse_n, c.k_min);
+    const auto dh = default_hierarchy(c.n_cells, c.r, c.k, c.coarse_n, c.k_min);
+    int ns = c.n_sub;
+    if (c.time_h) {                      // halve the subintervals on the finest space level first
+      while (ns > 1 && ns % 2 == 0) {
+        lv.push_back({dh[0][0], dh[0][1], dh[0][2], ns});
+        ns /= 2;
+      }
+    }
+    for (const auto& l : dh) lv.push_back({l[0], l[1], l[2], ns});
   } else {
     if (c.n_levels > STMG_MAX_LEVELS) return STMG_ERR_ARG;
-    for (int i = 0; i < c.n_levels; ++i) lv.push_back({c.level_n[i], c.level_r[i], c.level_k[i]});
-    if (lv[0][0] != c.n_cells || lv[0][1] != c.r || lv[0][2] != c.k) return STMG_ERR_ARG;
+    for (int i = 0; i < c.n_levels; ++i)
+      lv.push_back({c.level_n[i], c.level_r[i], c.level_k[i], c.level_nsub[i] > 0 ? c.level_nsub[i] : c.n_sub});
+    if (lv[0][0] != c.n_cells || lv[0][1] != c.r || lv[0][2] != c.k || lv[0][3] != c.n_sub) return STMG_ERR_ARG;
   }
   if (lv.size() > STMG_MAX_LEVELS) return STMG_ERR_ARG;
   for (size_t i = 0; i < lv.size(); ++i) {
-    if (lv[i][1] < 1 || lv[i][1] > 4 || lv[i][2] < 0 || lv[i][2] > 3 || lv[i][0] < 1) return STMG_ERR_ARG;
+    if (lv[i][1] < 1 || lv[i][1] > 4 || lv[i][2] < 0 || lv[i][2] > 3 || lv[i][0] < 1 || lv[i][3] < 1) return STMG_ERR_ARG;
+    if (lv[i][3] * (lv[i][2] + 1) > MAXKT) return STMG_ERR_UNIMPLEMENTED;
     if (i + 1 < lv.size()) {
       const auto &f = lv[i], &cc = lv[i + 1];
       const bool hstep = f[0] == 2 * cc[0], same = f[0] == cc[0];
       if (!(hstep || same) || cc[1] > f[1] || cc[2] > f[2]) return STMG_ERR_ARG;
+      if (cc[3] > f[3] || f[3] % cc[3] != 0) return STMG_ERR_ARG;    // coarser temporal mesh nested in the finer
     }
   }
   h->L.resize(lv.size());
   try {
+    const double span = c.T / c.n_slabs;
     for (size_t i = 0; i < lv.size(); ++i) {
       LevelDev& L = h->L[i];
-      init_level_geometry(&L.H, c.dim, lv[i][0], lv[i][1], lv[i][2], h->tau, c.nu, c.n_sub);
+      init_level_geometry(&L.H, c.dim, lv[i][0], lv[i][1], lv[i][2], span / lv[i][3], c.nu, lv[i][3]);
     }
   } catch (const std::exception&) {
     return STMG_ERR_ARG;
@@ -1333,6 +1355,7 @@ int stmg_level_info(const stmg_handle* h, int lvl, stmg_level_info_t* info) {
   const LevelHost& H = L.H;
   std::memset(info, 0, sizeof(*info));
   info->n = H.n; info->r = H.r; info->k = H.k;
+  info->n_sub = H.nsub;
   info->size = H.size; info->n_vel = H.n_vel; info->n_pres = H.n_pres;
   info->smoother = H.smoother;
   info->patch_size = H.B;

@@ -117,3 +117,66 @@ def test_macro_exact_reproduction():
     e = errors(pb, slab, sols)
     assert e["v_L2L2"] < 1e-9 and e["v_L2H1"] < 1e-8 and e["p_L2L2"] < 1e-8
     g.close()
+
+
+# h-coarsening in time inside a macro step (App. A, Eq. DeftPrRe / DefTlspr): levels of
+# fewer, longer subintervals; (n, r, k, n_sub) fine -> coarse
+H_TIME_CASES = [
+    (2, 4, 1, 1, 4, [(4, 1, 1, 4), (4, 1, 1, 2), (4, 1, 1, 1), (2, 1, 1, 1), (1, 1, 1, 1)]),
+    (2, 4, 2, 1, 2, [(4, 2, 1, 2), (4, 1, 1, 1), (2, 1, 1, 1), (1, 1, 1, 1)]),       # h in time with p in space
+    (2, 2, 1, 3, 2, [(2, 1, 3, 2), (2, 1, 3, 1), (2, 1, 1, 1), (1, 1, 1, 1)]),       # DG(3), then p in time
+    (2, 4, 1, 0, 4, [(4, 1, 0, 4), (2, 1, 0, 2), (1, 1, 0, 1)]),                      # h in space and time together
+    (3, 2, 1, 1, 2, [(2, 1, 1, 2), (2, 1, 1, 1), (1, 1, 1, 1)]),
+]
+H_TIME_IDS = ["2d-q2-dg1-x4-421", "2d-q3-dg1-x2-p", "2d-q2-dg3-x2", "2d-dg0-x4-hst", "3d-q2-dg1-x2"]
+
+
+@pytest.mark.parametrize("hc", H_TIME_CASES, ids=H_TIME_IDS)
+def test_h_in_time_levels_match_oracle(hc):
+    """Operator, sweep and both transfers on every level pair, and the V-cycle, against the
+    oracle's hierarchy with the same temporal meshes (FP64 1e-12 / 1e-11, FP32 2e-6 / 1e-4)."""
+    dim, n, r, k, nsub, levels = hc
+    og = Multigrid(dim, levels, NU, TAU, MGConfig(), nsub=nsub)
+    g = stmg.SpaceTimeMG(dim=dim, n_cells=n, r=r, k=k, nu=NU, T=TAU * nsub * 5, n_slabs=5, n_sub=nsub,
+                         levels=levels, use_graphs=False)
+    assert [l["n_sub"] for l in g.levels] == [l[3] for l in levels]
+    for l, s in enumerate(og.slabs):
+        assert g.size(l) == s.size
+        x = random_vector(s.size, 53 + l)
+        assert rel(g.apply(dev(x), l), s.S @ x) < 1e-12
+    for l, (s, W) in enumerate(zip(og.slabs[:-1], og.smoothers)):
+        res = free_vec(s, 57 + l)
+        x = torch.zeros(s.size, dtype=torch.float64, device="cuda")
+        assert rel(g.vanka_sweep(dev(res), x, l), W.omega * W.correction(res)) < 1e-12
+        P = og.P[l]
+        r_f = random_vector(s.size, 61 + l)
+        assert rel(g.restrict(dev(r_f), l), P.T @ r_f) < 1e-12
+        assert rel(g.restrict(dev(r_f, torch.float32), l).double(), P.T @ r_f) < 2e-6
+        y_c = random_vector(og.slabs[l + 1].size, 67 + l)
+        x_f = free_vec(s, 71 + l)
+        assert rel(g.prolongate_add(dev(y_c), dev(x_f), l), x_f + P @ y_c) < 1e-12
+    b = free_vec(og.slabs[0], 73)
+    ref = og.vcycle(b)
+    assert rel(g.vcycle(dev(b), "fp64"), ref) < 1e-11
+    assert rel(g.vcycle(dev(b), "fp32"), ref) < 1e-4
+    g.device_status()
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_h_in_time_default_hierarchy_solves_macro_march(prec):
+    """time_h = 1: the default hierarchy first halves the subintervals (4 -> 2 -> 1) on the
+    finest mesh; two macro systems of four subintervals, Q2/P1, DG(1) on 8x8 cells, solved
+    to 1e-12, equal the oracle's direct macro march."""
+    pb = manufactured_2d(nu=1.0, time="sin_pi")
+    sols_o, _, slab, _ = march(pb, 8, 1, 1, 2, solver="direct", nsub=4)
+    g = stmg.SpaceTimeMG(dim=2, n_cells=8, r=1, k=1, nu=1.0, T=1.0, n_slabs=2, n_sub=4, time_h=True,
+                         precond_precision=prec, rel_tol=1e-12)
+    assert [(l["n"], l["n_sub"]) for l in g.levels[:3]] == [(8, 4), (8, 2), (8, 1)]
+    x = None
+    for s in range(2):
+        x, info = g.solve_slab(g.slab_rhs(g.forcing(pb.forcing, s), x))
+        assert info["status"] == 0 and info["rel_residual"] <= 1e-12
+        got = slab.remove_pressure_mean(x.cpu().numpy())
+        assert rel(got, slab.remove_pressure_mean(sols_o[s])) < 1e-9
+    g.close()
