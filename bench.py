@@ -84,6 +84,8 @@ def parse():
     p.add_argument("--reps", type=int, default=3, help="launches of --only-kernel inside the profiler range")
     p.add_argument("--apply-variant", type=int, default=0, help="force the operator kernel (1 per-cell, 2 node-centred)")
     p.add_argument("--sweep-variant", type=int, default=0, help="force the sweep kernel (1 block, 2 TMA, 3 pipelined)")
+    p.add_argument("--persistent", type=int, default=1,
+                   help="levels below the finest in one persistent kernel: 0 never, 1 tuner (default), 2 always")
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
                    help="c2: the 2D headline configuration; c3: the 3D 32^3 configuration; "
                         "lid: the lid-driven cavity at c = 4 (lid5: c = 5; lid_r3: c = 4 with Q4/P3 DG(3))")
@@ -261,7 +263,7 @@ def run_ours(args):
                                 k_min=k_min, levels=lv, precisions=precisions if prec == "fp32" else (prec,),
                                 gmres_max_iter=max_iter or (200 if w["dim"] == 2 else 80),
                                 half_inverses=half and prec == "fp32", apply_variant=args.apply_variant,
-                                sweep_variant=args.sweep_variant)
+                                sweep_variant=args.sweep_variant, persistent=args.persistent)
 
     torch.cuda.synchronize()
     t_setup = time.perf_counter()
@@ -357,14 +359,17 @@ def run_ours(args):
     alg_bytes = sweep_alg_bytes(lv0, "fp32") if not args.half_inverses else mg.sweep_bytes(0, "fp32")
     peaks, peak_kind = measured_peaks()
     achieved = alg_bytes / (sweep_ms / 1e3) / 1e9
+    # the sweep kernel the tuner chose for the finest level (FP32)
+    sv = lv0["sweep_variant"][1]
+    kname = ("k_vanka_sweep_half" if args.half_inverses else
+             {1: "k_vanka_sweep", 2: "k_vanka_sweep_tma", 3: "k_vanka_sweep_pipe"}.get(sv, "k_vanka_sweep"))
+    traffic_key = ("vanka_sweep_fp32_finest" + ("" if args.workload == "c2" else "_" + args.workload) +
+                   ("_half" if args.half_inverses else "") + ("_pipe" if sv == 3 and not args.half_inverses else ""))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_kind": peak_kind,
-                "traffic": ncu_traffic("k_vanka.cu", "k_vanka_sweep_half" if args.half_inverses else "k_vanka_sweep",
-                                       "vanka_sweep_fp32_finest" +
-                                       ("" if args.workload == "c2" else "_" + args.workload) +
-                                       ("_half" if args.half_inverses else "")),
-                "kernel": "k_vanka_sweep_half, finest level" if args.half_inverses else
-                          "k_vanka_sweep<float>, finest level",
+                "traffic": ncu_traffic("k_vanka.cu", kname, traffic_key),
+                "kernel": f"{kname}<float>, finest level, {lv0['patches_per_block'][1]} patches per block, "
+                          f"rounds of {lv0['sweep_unroll'][1]} column chunks",
                 "bytes_per_launch": alg_bytes,
                 "bytes_rule": "n_patches * B^2 * 4 + 3 * D * 4 (stored inverses, residual, iterate)"
                               if not args.half_inverses else "stmg_sweep_bytes (FP16 inverses + row scales)",
@@ -513,7 +518,8 @@ def only_kernel(mg, args):
     out = {"kernel": args.only_kernel, "prec": prec, "level": lvl, "dofs": D, "ms": ms, "dofs_per_s": D / (ms / 1e3),
            "levels": [(l["n"], l["r"], l["k"]) for l in mg.levels],
            "launch_shapes": [{k: l[k] for k in ("apply_variant", "apply_tile", "apply_cells_per_block", "sweep_variant",
-                                                "patches_per_block", "transfer_cells_per_block")} for l in mg.levels]}
+                                                "patches_per_block", "sweep_unroll", "transfer_cells_per_block",
+                                                "persistent")} for l in mg.levels]}
     if args.only_kernel == "sweep":
         out["alg_bytes"] = sweep_alg_bytes(mg.levels[lvl], prec)
         out["GBs"] = out["alg_bytes"] / (ms / 1e3) / 1e9

@@ -199,6 +199,8 @@ typedef struct {
   int       apply_tile[2][2]; /* per precision: cells per block in x and y (variant 2)    */
   int       persistent[2];    /* per precision: 1 if the level runs inside the persistent
                                  multigrid kernel (its launch shapes above then unused)    */
+  int       sweep_unroll[2];  /* per precision: column chunks per load round of the block
+                                 sweeps (4 or 8)                                           */
 } stmg_level_info_t;
 
 typedef struct {

@@ -108,7 +108,8 @@ class SpaceTimeMG:
                                 "streaming": li.streaming,
                                 "apply_variant": tuple(li.apply_variant),
                                 "apply_tile": tuple(tuple(t) for t in li.apply_tile),
-                                "persistent": tuple(li.persistent)})
+                                "persistent": tuple(li.persistent),
+                                "sweep_unroll": tuple(li.sweep_unroll)})
 
     # ---------------------------------------------------------------- plumbing
     def close(self):

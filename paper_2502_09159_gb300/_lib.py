@@ -37,7 +37,7 @@ class LevelInfo(C.Structure):
                 ("sweep_variant", C.c_int * 2), ("patches_per_block", C.c_int * 2),
                 ("apply_cells_per_block", C.c_int * 2), ("transfer_cells_per_block", C.c_int * 2),
                 ("streaming", C.c_int), ("apply_variant", C.c_int * 2), ("apply_tile", (C.c_int * 2) * 2),
-                ("persistent", C.c_int * 2)]
+                ("persistent", C.c_int * 2), ("sweep_unroll", C.c_int * 2)]
 
 
 class SolveInfo(C.Structure):

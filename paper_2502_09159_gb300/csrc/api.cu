@@ -45,7 +45,7 @@ struct LevelDev {
   int streaming = 0;        // read the inverses with evict-first loads
   int sweep_var[2] = {1, 1};  // per precision: 1 = block per patch group, 2 = TMA-pipelined, 3 = pipelined block
   int ppb[2] = {1, 1};        // per precision: patches per block of the block sweeps
-  int unroll[2] = {8, 8};     // per precision: chunks per round of the pipelined block sweep
+  int unroll[2] = {8, 8};     // per precision: chunks per load round of the block sweeps (4 or 8)
   template <typename T> PrecDev<T>& pd();
 };
 template <> PrecDev<double>& LevelDev::pd<double>() { return d; }
@@ -412,7 +412,7 @@ static int op_sweep(stmg_handle* h, int l, const T* res, T* x, cudaStream_t s) {
     CK(launch_vanka_sweep_pipe<T>(lv.dofs, P.inv, res, x, lv.H.n_patches, lv.H.B, lv.H.Bc, lv.ppb[w], lv.unroll[w],
                                   lv.streaming, s));
   else
-    CK(launch_vanka_sweep<T>(lv.dofs, P.inv, res, x, lv.H.n_patches, lv.H.B, lv.H.Bc, lv.ppb[w],
+    CK(launch_vanka_sweep<T>(lv.dofs, P.inv, res, x, lv.H.n_patches, lv.H.B, lv.H.Bc, lv.ppb[w], lv.unroll[w],
                              lv.streaming, s));
   h->launches += 1;
   return STMG_OK;
@@ -555,10 +555,13 @@ static int autotune_level(stmg_handle* h, int l) {
     const int only = h->cfg.sweep_variant;             // 0: free choice, 1 / 2 / 3: fixed variant
     for (int ppb = 1; ppb <= 8 && (only == 0 || only == 1); ppb *= 2) {
       if (ppb > 1 && ppb * lv.H.B > 1024) break;
-      lv.sweep_var[w] = 1;
-      lv.ppb[w] = ppb;
-      CKS(time_it(h, [&]() { return op_sweep<T>(h, l, P.r, P.x, h->st); }, &ms));
-      if (ms < best) { best = ms; best_var = 1; best_ppb = ppb; }
+      for (int u = 4; u <= 8; u += 4) {
+        lv.sweep_var[w] = 1;
+        lv.ppb[w] = ppb;
+        lv.unroll[w] = u;
+        CKS(time_it(h, [&]() { return op_sweep<T>(h, l, P.r, P.x, h->st); }, &ms));
+        if (ms < best) { best = ms; best_var = 1; best_ppb = ppb; best_unroll = u; }
+      }
     }
     if ((only == 0 || only == 2) && !P.half && tma_sweep_supported<T>(lv.H.B)) {
       lv.sweep_var[w] = 2;
@@ -1379,6 +1382,7 @@ int stmg_level_info(const stmg_handle* h, int lvl, stmg_level_info_t* info) {
   info->apply_tile[0][0] = L.d.ap.tcx; info->apply_tile[0][1] = L.d.ap.tcy;
   info->apply_tile[1][0] = L.f.ap.tcx; info->apply_tile[1][1] = L.f.ap.tcy;
   for (int w = 0; w < 2; ++w) info->persistent[w] = h->mgp_first[w] > 0 && lvl >= h->mgp_first[w] ? 1 : 0;
+  for (int w = 0; w < 2; ++w) info->sweep_unroll[w] = L.unroll[w];
   return STMG_OK;
 }
 

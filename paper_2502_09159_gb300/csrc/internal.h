@@ -152,9 +152,10 @@ cudaError_t launch_apply2d(int np, const ApplyParams<T>& p, const T* x, const T*
 template <typename T>
 size_t apply2d_smem_bytes(int np, int kt, int npm, int tcx, int tcy);
 
+// block sweep: rounds of `unroll` (4 or 8) column chunks per load burst
 template <typename T>
 cudaError_t launch_vanka_sweep(const int* dofs, const T* inv, const T* res, T* x, long long n_patches, int B,
-                               int Bc, int ppb, int streaming, cudaStream_t st);
+                               int Bc, int ppb, int unroll, int streaming, cudaStream_t st);
 // pipelined block sweep (first loads before the gather, double-buffered rounds of `unroll`
 // = 4 or 8 chunks); needs ppb * B <= 512
 template <typename T>

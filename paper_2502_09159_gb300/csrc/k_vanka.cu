@@ -51,17 +51,19 @@ __device__ __forceinline__ double dotvv(const double2& a, const double2& r) {
 
 }  // namespace
 
-template <typename T>
+template <typename T, int U>
 __global__ void __launch_bounds__(1024) k_vanka_sweep(const int* __restrict__ dofs, const T* __restrict__ inv,
                                                       const T* __restrict__ res, T* __restrict__ x,
                                                       long long n_patches, int B, int Bc, int ppb, int streaming) {
   using V = typename Vec<T>::type;
   constexpr int VW = Vec<T>::W;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* rs = reinterpret_cast<T*>(smraw);                // [ppb][Bc]
+  const int nch = Bc / VW;
+  const int Bp = (nch + U - 1) / U * U * VW;          // residual padded to whole rounds of U chunks
+  T* rs = reinterpret_cast<T*>(smraw);                // [ppb][Bp]
   const long long p0 = (long long)blockIdx.x * ppb;
-  for (int t = threadIdx.x; t < ppb * Bc; t += blockDim.x) {
-    const int pl = t / Bc, i = t % Bc;
+  for (int t = threadIdx.x; t < ppb * Bp; t += blockDim.x) {
+    const int pl = t / Bp, i = t % Bp;
     const long long p = p0 + pl;
     T v = 0;
     if (p < n_patches && i < B) {
@@ -71,28 +73,29 @@ __global__ void __launch_bounds__(1024) k_vanka_sweep(const int* __restrict__ do
     rs[t] = v;
   }
   __syncthreads();
-  const int nch = Bc / VW;
   const bool st = streaming != 0;
-  // one row per thread; blocks of fewer threads than ppb * B rows (B > 1024) loop
+  // one row per thread; blocks of fewer threads than ppb * B rows (B > 1024) loop.  Rounds
+  // of U chunks, the last one predicated, so that every round has U loads in flight.
   for (int t = threadIdx.x; t < ppb * B; t += blockDim.x) {
     const int pl = t / B, j = t % B;
     const long long p = p0 + pl;
     if (p >= n_patches) break;
     const V* A = reinterpret_cast<const V*>(inv + (size_t)p * B * Bc) + j;
-    const T* r = rs + pl * Bc;
+    const T* r = rs + pl * Bp;
     T acc0 = 0, acc1 = 0;
-    int c = 0;
-    for (; c + 8 <= nch; c += 8) {
-      V a[8];
+    for (int c = 0; c < nch; c += U) {
+      V a[U];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) a[u] = load_vec(A + (size_t)(c + u) * B, st);
+      for (int u = 0; u < U; ++u) {
+        a[u] = V{};
+        if (c + u < nch) a[u] = load_vec(A + (size_t)(c + u) * B, st);
+      }
 #pragma unroll
-      for (int u = 0; u < 8; u += 2) {
+      for (int u = 0; u < U; u += 2) {
         acc0 += dotv(a[u], r + (c + u) * VW);
         acc1 += dotv(a[u + 1], r + (c + u + 1) * VW);
       }
     }
-    for (; c < nch; ++c) acc0 += dotv(load_vec(A + (size_t)c * B, st), r + c * VW);
     const int g = dofs[p * B + j];
     if (g >= 0) atomicAdd(x + g, acc0 + acc1);   // rows carry omega / valence
   }
@@ -100,19 +103,22 @@ __global__ void __launch_bounds__(1024) k_vanka_sweep(const int* __restrict__ do
 
 template <typename T>
 cudaError_t launch_vanka_sweep(const int* dofs, const T* inv, const T* res, T* x, long long n_patches, int B,
-                               int Bc, int ppb, int streaming, cudaStream_t st) {
+                               int Bc, int ppb, int unroll, int streaming, cudaStream_t st) {
+  constexpr int VW = Vec<T>::W;
   if (ppb * B > 1024) ppb = 1024 / B;
   if (ppb < 1) ppb = 1;
   if (B < 1) return cudaErrorInvalidValue;
+  const int U = unroll == 4 ? 4 : 8;
+  const int nch = Bc / VW;
   const int threads = ppb * B > 1024 ? 1024 : ((ppb * B + 31) / 32) * 32;
   const long long blocks = (n_patches + ppb - 1) / ppb;
-  const size_t smem = sizeof(T) * (size_t)ppb * Bc;
+  const size_t smem = sizeof(T) * (size_t)ppb * ((nch + U - 1) / U * U * VW);
+  auto kern = U == 4 ? k_vanka_sweep<T, 4> : k_vanka_sweep<T, 8>;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_vanka_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_vanka_sweep<T><<<(unsigned)blocks, threads, smem, st>>>(dofs, inv, res, x, n_patches, B, Bc, ppb, streaming);
+  kern<<<(unsigned)blocks, threads, smem, st>>>(dofs, inv, res, x, n_patches, B, Bc, ppb, streaming);
   return cudaGetLastError();
 }
 
@@ -381,9 +387,9 @@ template bool pipe_sweep_supported<double>(int, int);
 template bool pipe_sweep_supported<float>(int, int);
 
 template cudaError_t launch_vanka_sweep<double>(const int*, const double*, const double*, double*, long long, int,
-                                                int, int, int, cudaStream_t);
+                                                int, int, int, int, cudaStream_t);
 template cudaError_t launch_vanka_sweep<float>(const int*, const float*, const float*, float*, long long, int, int,
-                                               int, int, cudaStream_t);
+                                               int, int, int, cudaStream_t);
 template cudaError_t launch_replicate_inverses<double>(const double*, const int*, const int*, const double*,
                                                        double*, long long, int, int, cudaStream_t);
 template cudaError_t launch_replicate_inverses<float>(const double*, const int*, const int*, const double*, float*,

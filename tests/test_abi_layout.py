@@ -20,7 +20,7 @@ STRUCTS = {
     "stmg_level_info_t": ["n", "r", "k", "n_sub", "size", "n_vel", "n_pres", "smoother", "patch_size", "n_patches",
                           "n_patch_classes", "inverse_bytes", "sweep_variant", "patches_per_block",
                           "apply_cells_per_block", "transfer_cells_per_block", "streaming", "apply_variant",
-                          "apply_tile", "persistent"],
+                          "apply_tile", "persistent", "sweep_unroll"],
     "stmg_solve_info": ["iterations", "rel_residual", "status", "seconds"],
 }
 
