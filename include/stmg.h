@@ -225,6 +225,11 @@ typedef struct {
    up, 200 iterations, rel_tol 1e-8, graphs on. */
 int  stmg_default_config(stmg_config* cfg);
 
+/* Tuning cache: if the environment variable STMG_TUNE_CACHE names a file, stmg_create with
+   autotune = 1 reads the launch shapes of an earlier tuning of the same configuration from
+   it (and skips the timing), or tunes and appends them to it.  For runs whose timings would
+   be distorted, e.g. under a profiler.  A file that cannot be read or written is ignored. */
+
 /* Build the hierarchy (Alg. 2/3 or the explicit list), the level operators, transfers,
    Vanka patch inverses (Eq. vanka0: the global submatrix R_T S R_T^T of every patch,
    inverted in FP64 by Gauss-Jordan elimination with partial pivoting once per distinct

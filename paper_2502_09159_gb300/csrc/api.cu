@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -1128,6 +1129,96 @@ int stmg_default_config(stmg_config* c) {
   return STMG_OK;
 }
 
+// ------------------------------------------------------------------------------------
+// Tuning cache.  With the environment variable STMG_TUNE_CACHE naming a file, stmg_create
+// writes the launch shapes the tuner chose there, and a later stmg_create of the same
+// configuration (same levels, precisions and options) reads them instead of timing the
+// candidates again: a process running under a profiler, whose timings are distorted, then
+// runs the shapes that were chosen without it.  One text line per configuration.
+// ------------------------------------------------------------------------------------
+static std::string tune_key(const stmg_handle* h) {
+  const stmg_config& c = h->cfg;
+  std::string k = "v1 d" + std::to_string(c.dim) + " p" + std::to_string(c.precisions) + " h" +
+                  std::to_string(c.half_inverses) + " sv" + std::to_string(c.sweep_variant) + " av" +
+                  std::to_string(c.apply_variant) + " tv" + std::to_string(c.transfer_variant) + " pe" +
+                  std::to_string(c.persistent) + " nu" + std::to_string(c.nu1) + std::to_string(c.nu2);
+  for (const auto& L : h->L)
+    k += " L" + std::to_string(L.H.n) + "." + std::to_string(L.H.r) + "." + std::to_string(L.H.k) + "." +
+         std::to_string(L.H.nsub) + "." + std::to_string(L.H.smoother);
+  return k;
+}
+
+static void tune_cache_save(const stmg_handle* h, const char* path) {
+  std::string line = tune_key(h) + " |";
+  for (const auto& L : h->L) {
+    for (int w = 0; w < 2; ++w) {
+      const int tv = w == 0 ? L.d.tp.variant : L.f.tp.variant, tc = w == 0 ? L.d.tp.cpb : L.f.tp.cpb;
+      const ApplyParams<double>& ad = L.d.ap;
+      const ApplyParams<float>& af = L.f.ap;
+      const int av = w == 0 ? ad.variant : af.variant, ac = w == 0 ? ad.cpb : af.cpb;
+      const int tx = w == 0 ? ad.tcx : af.tcx, ty = w == 0 ? ad.tcy : af.tcy;
+      line += " " + std::to_string(L.sweep_var[w]) + "," + std::to_string(L.ppb[w]) + "," + std::to_string(L.unroll[w]) +
+              "," + std::to_string(av) + "," + std::to_string(ac) + "," + std::to_string(tx) + "," + std::to_string(ty) +
+              "," + std::to_string(tv) + "," + std::to_string(tc);
+    }
+  }
+  for (int w = 0; w < 2; ++w) line += " m" + std::to_string(h->mgp_first[w]) + "," + std::to_string(h->mgp_blocks[w]);
+  // keep the other configurations' lines
+  std::vector<std::string> keep;
+  if (FILE* f = std::fopen(path, "r")) {
+    char buf[8192];
+    const std::string key = tune_key(h) + " |";
+    while (std::fgets(buf, sizeof(buf), f)) {
+      std::string l(buf);
+      if (l.compare(0, key.size(), key) != 0) keep.push_back(l);
+    }
+    std::fclose(f);
+  }
+  if (FILE* f = std::fopen(path, "w")) {
+    for (const auto& l : keep) std::fputs(l.c_str(), f);
+    std::fputs((line + "\n").c_str(), f);
+    std::fclose(f);
+  }
+}
+
+static bool tune_cache_load(stmg_handle* h, const char* path) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  const std::string key = tune_key(h) + " |";
+  char buf[8192];
+  std::string found;
+  while (std::fgets(buf, sizeof(buf), f)) {
+    std::string l(buf);
+    if (l.compare(0, key.size(), key) == 0) found = l.substr(key.size());
+  }
+  std::fclose(f);
+  if (found.empty()) return false;
+  const char* p = found.c_str();
+  for (auto& L : h->L) {
+    for (int w = 0; w < 2; ++w) {
+      int v[9];
+      int used = 0;
+      if (std::sscanf(p, " %d,%d,%d,%d,%d,%d,%d,%d,%d%n", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7], &v[8],
+                      &used) != 9)
+        return false;
+      p += used;
+      L.sweep_var[w] = v[0]; L.ppb[w] = v[1]; L.unroll[w] = v[2];
+      if (w == 0) { L.d.ap.variant = v[3]; L.d.ap.cpb = v[4]; L.d.ap.tcx = v[5]; L.d.ap.tcy = v[6]; L.d.tp.variant = v[7]; L.d.tp.cpb = v[8]; }
+      else { L.f.ap.variant = v[3]; L.f.ap.cpb = v[4]; L.f.ap.tcx = v[5]; L.f.ap.tcy = v[6]; L.f.tp.variant = v[7]; L.f.tp.cpb = v[8]; }
+    }
+  }
+  // the persistent kernel's descriptors are built as after tuning; its start and grid as cached
+  if (mgp_setup<double>(h) != STMG_OK || mgp_setup<float>(h) != STMG_OK) return false;
+  for (int w = 0; w < 2; ++w) {
+    int first = 0, blocks = 0, used = 0;
+    if (std::sscanf(p, " m%d,%d%n", &first, &blocks, &used) != 2) return false;
+    p += used;
+    h->mgp_first[w] = h->mgp_eligible[w] > 0 ? first : 0;
+    if (blocks > 0) h->mgp_blocks[w] = blocks;
+  }
+  return true;
+}
+
 static int create_impl(const stmg_config* cfg, stmg_handle* h) {
   h->cfg = *cfg;
   const stmg_config& c = h->cfg;
@@ -1264,8 +1355,12 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
       if (transfer_gather_supported(h->L[i].f.tp)) h->L[i].f.tp.variant = 2;
     }
   }
-  if (c.autotune) {
+  const char* cache = std::getenv("STMG_TUNE_CACHE");
+  if (c.autotune && cache && *cache && tune_cache_load(h, cache)) {
+    // launch shapes of an earlier tuning of the same configuration (profiling runs)
+  } else if (c.autotune) {
     CKS(autotune_impl(h));
+    if (cache && *cache) tune_cache_save(h, cache);
   } else {
     CKS(mgp_setup<double>(h));
     CKS(mgp_setup<float>(h));

@@ -474,3 +474,23 @@ def test_profiling_counters():
     p = g.profile(reset=True)
     assert p["fine_sweep"]["launches"] == 2 * info["iterations"]
     assert p["fine_sweep"]["ms"] > 0 and p["operator"]["launches"] >= info["iterations"]
+
+
+def test_tune_cache_round_trip(tmp_path, monkeypatch):
+    """STMG_TUNE_CACHE: the first handle tunes and writes its launch shapes, a second handle
+    of the same configuration reads them (no timing) and runs the same V-cycle."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("STMG_TUNE_CACHE", str(cache))
+    kw = dict(dim=2, n_cells=16, r=2, k=2, nu=1.0, T=1.0, n_slabs=16, coarse_n=4, k_min=2)
+    g1 = stmg.SpaceTimeMG(**kw)
+    assert cache.exists() and cache.read_text().count("\n") == 1
+    g2 = stmg.SpaceTimeMG(**kw)
+    assert g1.levels == g2.levels
+    b = torch.from_numpy(random_vector(g1.size(0), 5)).to("cuda")
+    for prec in ("fp64", "fp32"):
+        x1, x2 = g1.vcycle(b, prec), g2.vcycle(b, prec)
+        assert rel(x2, x1.cpu().numpy()) < (1e-13 if prec == "fp64" else 1e-6)
+    g3 = stmg.SpaceTimeMG(**{**kw, "k": 1, "k_min": 1})         # another configuration: a second line
+    assert cache.read_text().count("\n") == 2
+    for g in (g1, g2, g3):
+        g.close()
