@@ -82,8 +82,10 @@ def parse():
     p.add_argument("--level", type=int, default=0, help="level of --only-kernel")
     p.add_argument("--prec", default="fp32", choices=["fp32", "fp64"], help="precision of --only-kernel")
     p.add_argument("--reps", type=int, default=3, help="launches of --only-kernel inside the profiler range")
-    p.add_argument("--apply-variant", type=int, default=0, help="force the operator kernel (1 per-cell, 2 node-centred)")
+    p.add_argument("--apply-variant", type=int, default=0, help="force the operator kernel (1 per-cell, 2 node-centred, 3 register, 4 pair-split register)")
     p.add_argument("--sweep-variant", type=int, default=0, help="force the sweep kernel (1 block, 2 TMA, 3 pipelined)")
+    p.add_argument("--arnoldi-form", type=int, default=0,
+                   help="Arnoldi step: 0 rows of w in registers where they fit (default), 1 split passes")
     p.add_argument("--persistent", type=int, default=1,
                    help="levels below the finest in one persistent kernel: 0 never, 1 tuner (default), 2 always")
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
@@ -263,7 +265,8 @@ def run_ours(args):
                                 k_min=k_min, levels=lv, precisions=precisions if prec == "fp32" else (prec,),
                                 gmres_max_iter=max_iter or (200 if w["dim"] == 2 else 80),
                                 half_inverses=half and prec == "fp32", apply_variant=args.apply_variant,
-                                sweep_variant=args.sweep_variant, persistent=args.persistent)
+                                sweep_variant=args.sweep_variant, persistent=args.persistent,
+                                arnoldi_form=args.arnoldi_form)
 
     torch.cuda.synchronize()
     t_setup = time.perf_counter()

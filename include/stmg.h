@@ -149,10 +149,13 @@ typedef struct {
                               factorisation, atomics on shared nodes), 2 = node-centred
                               form on tiles of cells, every output written once, 3 =
                               register-resident form, one thread per (cell, temporal dof)
-                              (FP32 up to Q5, FP64 up to Q3, k + 1 <= 4).  2 and 3 are for
-                              2D levels; 3D levels and shapes that 3 does not cover keep
-                              1 (resp. 1 or 2).  Same operator; they differ in rounding
-                              order only.                                                */
+                              (FP32 up to Q5, FP64 up to Q3, k + 1 <= 4), 4 = its
+                              pair-split form, two threads per (cell, temporal dof), each
+                              with half of the cell's node columns (Q3, k + 1 <= 4).  2, 3
+                              and 4 are for 2D levels; 3D levels and shapes that 3 does
+                              not cover keep 1 (resp. 1 or 2); levels that 4 does not
+                              cover take 3.  Same operator; they differ in rounding order
+                              only.                                                      */
   int    persistent;       /* levels below the finest in one persistent kernel (grid-wide
                               barriers between its sweeps, residuals, transfers and the
                               coarse product): 0 = never, 1 = where the tuner finds it
@@ -171,6 +174,11 @@ typedef struct {
                               ... -> 1, h in time), then the spatial and temporal-degree
                               levels on one subinterval; 0 (default) = p in time per
                               subinterval only (the paper's choice for macro steps)      */
+  int    arnoldi_form;     /* the cooperative Arnoldi step (CGS2) of FGMRES: 0 (default) =
+                              the block's rows of w held in registers across its three
+                              passes where they fit (at most 16 basis vectors, at most
+                              2048 rows per SM), else 1 = the split-pass form that reads w
+                              and V from memory in every pass; both give the same sums   */
 } stmg_config;
 
 typedef struct {
@@ -195,7 +203,8 @@ typedef struct {
   int       apply_variant[2]; /* per precision: 1 = one thread block per group of cells
                                  (apply_cells_per_block), 2 = node-centred 2D form on tiles
                                  of apply_tile cells (no atomics), 3 = register-resident
-                                 2D form (one thread per cell and temporal dof)            */
+                                 2D form (one thread per cell and temporal dof), 4 = its
+                                 pair-split form (two threads per cell and temporal dof) */
   int       apply_tile[2][2]; /* per precision: cells per block in x and y (variant 2)    */
   int       persistent[2];    /* per precision: 1 if the level runs inside the persistent
                                  multigrid kernel (its launch shapes above then unused)    */

@@ -51,7 +51,8 @@ class SpaceTimeMG:
                  gmres_max_iter: int = 200, rel_tol: float = 1e-8, use_graphs: bool = True,
                  sweep_variant: int = 0, autotune: bool = True, coarse_n: int = 1, k_min: int = 1,
                  n_sub: int = 1, half_inverses: bool = False, transfer_variant: int = 0,
-                 apply_variant: int = 0, persistent: int = 1, time_h: bool = False):
+                 apply_variant: int = 0, persistent: int = 1, time_h: bool = False,
+                 arnoldi_form: int = 0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("SpaceTimeMG needs a CUDA device (no CPU fallback)")
@@ -83,6 +84,7 @@ class SpaceTimeMG:
         cfg.apply_variant = int(apply_variant)
         cfg.persistent = int(persistent)
         cfg.time_h = int(time_h)
+        cfg.arnoldi_form = int(arnoldi_form)
         self.cfg = cfg
         self.dim, self.r, self.k, self.n_sub = dim, r, k, int(n_sub)
         self.kt = self.n_sub * (k + 1)

@@ -224,15 +224,13 @@ static void fill_apply_reg_params(const LevelHost& H, ApplyRegParams<T>* p) {
   p->n_nodes = H.n_nodes; p->n_vel = H.n_vel; p->n_pres = H.n_pres;
   const int np = H.np;
   for (int i = 0; i < np * np; ++i) { p->M1[i] = (T)H.t1.M1[i]; p->K1[i] = (T)H.t1.K1[i]; }
-  if (H.dim == 2 && H.npm <= MAXPM2)
+  if (H.dim == 2)
     for (int d = 0; d < 2; ++d)
-      for (int m = 0; m < H.npm; ++m)
-        for (int iy = 0; iy < np; ++iy)
-          for (int ix = 0; ix < np; ++ix) {
-            const double fx = (d == 0 ? H.t1.G1 : H.t1.N1)[H.modes[m][0] * np + ix];
-            const double fy = (d == 1 ? H.t1.G1 : H.t1.N1)[H.modes[m][1] * np + iy];
-            p->CB[d][m][iy * np + ix] = (T)(fx * fy);
-          }
+      for (int e = 0; e <= H.r; ++e)
+        for (int i = 0; i < np; ++i) {
+          p->FX[d][e * np + i] = (T)(d == 0 ? H.t1.G1 : H.t1.N1)[e * np + i];
+          p->FY[d][e * np + i] = (T)(d == 1 ? H.t1.G1 : H.t1.N1)[e * np + i];
+        }
   for (int a = 0; a < H.kt; ++a) {
     for (int b = 0; b < H.kt; ++b) p->Kt[a * MAXKT + b] = (T)H.tt.K[a * H.kt + b];
     p->beta[a] = (T)(H.tt.M[a] * H.nu * std::pow(H.h, H.dim - 2));
@@ -324,6 +322,22 @@ static int dalloc(T** p, size_t count) {
 
 // with_inverses = false sets up only the operator and the work vectors (the finest level
 // always has FP64 operator data: FGMRES applies S in FP64 whatever the V-cycle precision)
+// the register-resident operator forms index the 2D pressure modes by mode_index
+static bool modes_graded_2d(const LevelHost& H) {
+  if (H.dim != 2 || (int)H.modes.size() != H.npm) return false;
+  for (int m = 0; m < H.npm; ++m)
+    if (mode_index(H.modes[m][0], H.modes[m][1]) != m) return false;
+  return true;
+}
+template <typename T>
+static bool reg_form_ok(const LevelHost& H) {
+  return H.dim == 2 && modes_graded_2d(H) && apply2d_reg_supported<T>(H.np, H.kt, H.npm);
+}
+template <typename T>
+static bool pair_form_ok(const LevelHost& H) {
+  return reg_form_ok<T>(H) && apply2d_pair_supported<T>(H.np, H.kt, H.npm);
+}
+
 template <typename T>
 static int setup_precision(stmg_handle* h, LevelDev& lv, const double* d_cls, const int* d_cls_of,
                            bool with_inverses = true) {
@@ -331,8 +345,10 @@ static int setup_precision(stmg_handle* h, LevelDev& lv, const double* d_cls, co
   const LevelHost& H = lv.H;
   fill_apply_params<T>(H, &P.ap, h->cfg.apply_variant);
   fill_apply_reg_params<T>(H, &P.rp);
-  if (H.dim == 2 && apply2d_reg_supported<T>(H.np, H.kt, H.npm) &&
-      (h->cfg.apply_variant == 0 || h->cfg.apply_variant == 3))
+  const int av = h->cfg.apply_variant;
+  if (pair_form_ok<T>(H) && av == 4)
+    P.ap.variant = 4;                    // its pair-split form, on request
+  else if (reg_form_ok<T>(H) && (av == 0 || av == 3 || av == 4))
     P.ap.variant = 3;                    // register-resident form where the cell tile fits
   CKS(dalloc(&P.b, H.size));
   CKS(dalloc(&P.x, H.size));
@@ -388,6 +404,9 @@ static int op_apply(stmg_handle* h, int l, const T* x, const T* b, T* y, int mod
   } else if (ap.variant == 3) {          // scatter-adds every row
     CK(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)lv.H.size, s));
     CK(launch_apply2d_reg<T>(lv.H.np, lv.pd<T>().rp, x, b, y, mode, s));
+  } else if (ap.variant == 4) {          // scatter-adds every row
+    CK(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)lv.H.size, s));
+    CK(launch_apply2d_pair<T>(lv.H.np, lv.pd<T>().rp, x, b, y, mode, s));
   } else {
     CK(cudaMemsetAsync(y, 0, sizeof(T) * lv.H.size, s));
     CK(launch_apply<T>(lv.H.dim, lv.H.np, ap, x, b, y, mode, s));
@@ -606,10 +625,16 @@ static int autotune_level(stmg_handle* h, int l) {
         if (ms < best) { best = ms; best_var = 2; best_tx = P.ap.tcx; best_ty = P.ap.tcy; }
       }
     }
-    if (lv.H.dim == 2 && (fixed == 0 || fixed == 3) && apply2d_reg_supported<T>(lv.H.np, lv.H.kt, lv.H.npm)) {
+    const bool pair = pair_form_ok<T>(lv.H);
+    if ((fixed == 0 || fixed == 3 || (fixed == 4 && !pair)) && reg_form_ok<T>(lv.H)) {
       P.ap.variant = 3;                  // register-resident form (no launch-shape parameter)
       CKS(time_it(h, [&]() { return op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, h->st); }, &ms));
       if (ms < best) { best = ms; best_var = 3; }
+    }
+    if ((fixed == 0 || fixed == 4) && pair) {
+      P.ap.variant = 4;                  // its pair-split form
+      CKS(time_it(h, [&]() { return op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, h->st); }, &ms));
+      if (ms < best) { best = ms; best_var = 4; }
     }
     P.ap.cpb = best_cpb;
     P.ap.variant = best_var;
@@ -982,7 +1007,7 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
       Prof pr(h, STMG_PROF_OTHER, s);
       // CGS2 and the normalisation of the next basis vector in one cooperative launch
       CK(launch_cgs2(D, j + 1, h->V, D, h->w, h->cgs_part, h->hcol, h->V + (size_t)(j + 1) * D, h->cgs_bar, h->d_err,
-                     h->cgs_blocks, s));
+                     h->cgs_blocks, h->cfg.arnoldi_form == 0, s));
       h->launches += 1;
     } else {
       Prof pr(h, STMG_PROF_OTHER, s);
@@ -1125,6 +1150,7 @@ int stmg_default_config(stmg_config* c) {
   c->apply_variant = 0;
   c->persistent = 1;
   c->time_h = 0;
+  c->arnoldi_form = 0;
   for (int i = 0; i < STMG_MAX_LEVELS; ++i) c->level_nsub[i] = 0;
   return STMG_OK;
 }
@@ -1231,12 +1257,13 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
   if ((c.precisions & 3) == 0) return STMG_ERR_ARG;
   if (c.sweep_variant < 0 || c.sweep_variant > 3) return STMG_ERR_ARG;
   if (c.transfer_variant < 0 || c.transfer_variant > 2) return STMG_ERR_ARG;
-  if (c.apply_variant < 0 || c.apply_variant > 3) return STMG_ERR_ARG;
+  if (c.apply_variant < 0 || c.apply_variant > 4) return STMG_ERR_ARG;
   if (c.persistent < 0 || c.persistent > 2) return STMG_ERR_ARG;
   if (c.precond_precision != STMG_FP64 && c.precond_precision != STMG_FP32) return STMG_ERR_ARG;
   if (!(c.precisions & (1 << c.precond_precision))) return STMG_ERR_ARG;
   h->tau = c.T / ((double)c.n_slabs * c.n_sub);
   if (c.time_h < 0 || c.time_h > 1) return STMG_ERR_ARG;
+  if (c.arnoldi_form < 0 || c.arnoldi_form > 1) return STMG_ERR_ARG;
   // levels (n, r, k, nsub) fine -> coarse; a level of fewer subintervals covers the same
   // system time span T / n_slabs with longer ones (h-coarsening in time, App. A)
   std::vector<std::array<int, 4>> lv;

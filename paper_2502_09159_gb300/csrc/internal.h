@@ -55,7 +55,8 @@ double legendre_unit(int i, double xi);                       // sqrt(2i+1) P_i(
 template <typename T>
 struct ApplyParams {
   int n, G, kt, npm, cpb;
-  int variant;                    // 1: per-cell kernel (k_apply), 2: node-centred 2D kernel (k_apply2d)
+  int variant;                    // 1: per-cell kernel (k_apply), 2: node-centred 2D kernel (k_apply2d),
+                                  // 3: register-resident 2D kernel, 4: its pair-split form (k_apply2d_reg)
   int tcx, tcy;                   // variant 2: cells per block in x and y
   long long n_nodes, n_vel, n_pres;
   T M1[MAXNP * MAXNP], K1[MAXNP * MAXNP], G1[MAXNP * MAXNP], N1[MAXNP * MAXNP];
@@ -68,12 +69,20 @@ struct ApplyParams {
 
 // register-resident 2D operator (k_apply2d_reg.cu): tables in the parameter bank
 constexpr int MAXPM2 = 15;  // pressure modes per cell in 2D, C(4+2, 2)
+// index of the 2D pressure mode (ex, ey) in a cell's mode list, ordered by degree
+// s = ex + ey, then by ey: m = s (s + 1) / 2 + ey (the order of the host's mode tables;
+// the register-resident operators rely on it)
+__host__ __device__ constexpr int mode_index(int ex, int ey) { return (ex + ey) * (ex + ey + 1) / 2 + ey; }
+
 template <typename T>
 struct ApplyRegParams {
   int n, G, kt, npm;
   long long n_nodes, n_vel, n_pres;
   T M1[MAXNP * MAXNP], K1[MAXNP * MAXNP];
-  T CB[2][MAXPM2][MAXNP * MAXNP];   // [component][mode][node ix + np iy] = F_x(mode, ix) F_y(mode, iy)
+  // B_h factors of the 2D Legendre pressure modes (ex, ey) of degree ex + ey <= r, by
+  // velocity component d: FX[d][ex * np + ix] along x, FY[d][ey * np + iy] along y
+  // (G1 = int L ell' in the direction of d, N1 = int L ell in the other one)
+  T FX[2][MAXNP * MAXNP], FY[2][MAXNP * MAXNP];
   T Kt[MAXKT * MAXKT];
   T hd, beta[MAXKT], bscale[MAXKT];
 };
@@ -146,6 +155,12 @@ cudaError_t launch_apply2d_reg(int np, const ApplyRegParams<T>& p, const T* x, c
                                cudaStream_t st);
 template <typename T>
 bool apply2d_reg_supported(int np, int kt, int npm);
+// its pair-split form (two lanes per cell item, Q3 only), y zero on entry as well
+template <typename T>
+cudaError_t launch_apply2d_pair(int np, const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode,
+                                cudaStream_t st);
+template <typename T>
+bool apply2d_pair_supported(int np, int kt, int npm);
 // node-centred form on 2D levels (k_apply2d.cu): writes every entry of y, no zero-fill needed
 template <typename T>
 cudaError_t launch_apply2d(int np, const ApplyParams<T>& p, const T* x, const T* b, T* y, int mode, cudaStream_t st);
@@ -228,8 +243,9 @@ cudaError_t launch_sqrt_inplace(double* v, cudaStream_t st);
 
 int multidot_blocks(long long n);
 // one CGS2 Arnoldi step in a cooperative launch (see k_vec.cu); bar: 2 zeroed unsigned
+// reg: take the register-resident form where it fits (nv <= 16, at most 2048 rows per block)
 cudaError_t launch_cgs2(long long n, int nv, const double* V, long long ld, double* w, double* partial, double* hcol,
-                        double* vnext, unsigned* bar, int* err, int nblocks, cudaStream_t st);
+                        double* vnext, unsigned* bar, int* err, int nblocks, bool reg, cudaStream_t st);
 int cgs2_blocks(int n_sm);       // co-resident blocks to launch (0: not available)
 int cgs2_max_vectors();
 int cgs2_scratch(int nblocks);   // doubles of partial-sum scratch for nblocks

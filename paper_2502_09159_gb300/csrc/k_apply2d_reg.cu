@@ -7,12 +7,12 @@
 // across the warp.  The thread holds the cell's NP x NP node values of its component in
 // registers and applies, with compile-time loop bounds and indices throughout:
 //   u~     = sum_b K_tau[a,b] u_b                                  (time combination)
-//   cont_m += sum_q CB_d[m][q] u_a[q]                              (continuity rows)
+//   cont_m += sum_q F_x(m, ix) F_y(m, iy) u_a[q]                   (continuity rows)
 //   A1     = h^d (M1 along y) u~ + beta_a (K1 along y) u_a,  A2 = (M1 along y) u_a
-//   y_q    = (M1 along x) A1 + beta_a (K1 along x) A2 + bscale_a sum_m CB_d[m][q] p_a[m]
-// with CB_d[m][q] = F(mode m, x, ix) F(mode m, y, iy), F = G1 = int L ell' in the direction
-// of component d and N1 = int L ell in the other one (the B_h^T / B_h factors of the
-// Legendre pressure modes).  Every row is scatter-added (nodes on cell faces belong to two
+//   y_q    = (M1 along x) A1 + beta_a (K1 along x) A2 + bscale_a sum_m F_x(m, ix) F_y(m, iy) p_a[m]
+// with F = G1 = int L ell' in the direction of component d and N1 = int L ell in the other
+// one (the B_h^T / B_h factors of the Legendre pressure modes), both B_h terms
+// sum-factorised over the modes (ex, ey): first along one direction, then the other.  Every row is scatter-added (nodes on cell faces belong to two
 // or four cells, a cell's pressure rows get one share per component; y zero-filled before
 // the launch).  Boundary rows are the identity, added by the cell that owns the node;
 // boundary columns read as 0.  LIFT reads only the boundary values of x and no pressure;
@@ -60,6 +60,46 @@ cudaError_t launch_apply2d_reg(int np, const ApplyRegParams<T>& p, const T* x, c
 #undef STMG_R2
   return cudaErrorInvalidValue;
 }
+
+// pair-split form: two lanes per (cell, temporal dof, component), NP even (Q3 in 2D)
+template <typename T, int NP, int KT>
+__global__ void __launch_bounds__(64) k_apply2d_pair(const ApplyRegParams<T> P, const T* __restrict__ x,
+                                                     const T* __restrict__ b, T* __restrict__ y, int mode) {
+  apply2d_pair_thread<T, NP, KT, false>(P, x, b, y, mode, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
+template <typename T, int NP, int KT>
+static cudaError_t launch_apply2d_pair_t(const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode,
+                                         cudaStream_t st) {
+  const long long tot = (long long)p.n * p.n * KT * 2 * 2;  // (cell, temporal dof, component, column half)
+  const unsigned blocks = (unsigned)((tot + 63) / 64);      // whole warps: every lane reaches the shuffles
+  k_apply2d_pair<T, NP, KT><<<blocks, 64, 0, st>>>(p, x, b, y, mode);
+  return cudaGetLastError();
+}
+
+template <typename T>
+bool apply2d_pair_supported(int np, int kt, int npm) {
+  return np == 4 && kt >= 1 && kt <= 4 && npm == np * (np - 1) / 2;
+}
+
+template <typename T>
+cudaError_t launch_apply2d_pair(int np, const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode,
+                                cudaStream_t st) {
+  if (!apply2d_pair_supported<T>(np, p.kt, p.npm)) return cudaErrorInvalidValue;
+  switch (p.kt) {
+    case 1: return launch_apply2d_pair_t<T, 4, 1>(p, x, b, y, mode, st);
+    case 2: return launch_apply2d_pair_t<T, 4, 2>(p, x, b, y, mode, st);
+    case 3: return launch_apply2d_pair_t<T, 4, 3>(p, x, b, y, mode, st);
+    default: return launch_apply2d_pair_t<T, 4, 4>(p, x, b, y, mode, st);
+  }
+}
+
+template cudaError_t launch_apply2d_pair<double>(int, const ApplyRegParams<double>&, const double*, const double*,
+                                                 double*, int, cudaStream_t);
+template cudaError_t launch_apply2d_pair<float>(int, const ApplyRegParams<float>&, const float*, const float*,
+                                                float*, int, cudaStream_t);
+template bool apply2d_pair_supported<double>(int, int, int);
+template bool apply2d_pair_supported<float>(int, int, int);
 
 template cudaError_t launch_apply2d_reg<double>(int, const ApplyRegParams<double>&, const double*, const double*,
                                                 double*, int, cudaStream_t);

@@ -83,7 +83,11 @@ template <typename T>
 __device__ void stage_apply_tables(const ApplyRegParams<T>& g, ApplyRegParams<T>* s) {
   const int t = threadIdx.x;
   if (t < 9) { s->M1[t] = g.M1[t]; s->K1[t] = g.K1[t]; }
-  if (t < 54) { const int d = t / 27, m = (t / 9) % 3, q = t % 9; s->CB[d][m][q] = g.CB[d][m][q]; }
+  if (t < 2 * MAXNP * MAXNP) {
+    const int d = t / (MAXNP * MAXNP), e = t % (MAXNP * MAXNP);
+    s->FX[d][e] = g.FX[d][e];
+    s->FY[d][e] = g.FY[d][e];
+  }
   if (t < MAXKT * MAXKT) s->Kt[t] = g.Kt[t];
   if (t < MAXKT) { s->beta[t] = g.beta[t]; s->bscale[t] = g.bscale[t]; }
   if (t == 0) {

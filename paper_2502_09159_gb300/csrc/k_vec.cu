@@ -393,13 +393,179 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2(long long n, int nv, const
   for (long long r = lo + threadIdx.x; r < hi; r += CGS_THREADS) vnext[r] = w[r] * inv;
 }
 
+// ------------------------------------------------------------------------------------
+// The same Arnoldi step with the block's rows of w held in registers from the first load
+// to the normalisation (at most CGS_RPT rows per thread), for nv <= CGS_RV basis vectors.
+// The update of each pass and the next pass's dot products share one load of V:
+//   pass 1: h = V^T w                                   (V read once)
+//   pass 2: w -= V h, then h2 = V^T w, row by row       (V read once)
+//   pass 3: w -= V h2, then ||w||^2                     (V read once)
+// so V is read three times instead of four, w once instead of five times, and w is never
+// written back (the step's outputs are hcol and vnext).  Each thread owns the rows
+// lo + threadIdx.x + u * CGS_THREADS, u < CGS_RPT, the rows the split form gives it, and
+// adds in the same order.  Every loop is unrolled over the compile-time vector count, so
+// all U * NV loads of a row group are in flight together.
+// ------------------------------------------------------------------------------------
+constexpr int CGS_RPT = 4;             // rows of w per thread held in registers
+constexpr int CGS_RV = 16;             // largest basis size of the register form
+
+template <int NV>
+__device__ __forceinline__ void block_partials_reg(const double* acc, double* __restrict__ out, double (*red)[8]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int v0 = 0; v0 < NV; v0 += 8) {
+    double a8[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a8[i] = v0 + i < NV ? acc[v0 + i] : 0.0;
+    int vi;
+    const double d = warp_reduce8(a8, lane, &vi);
+    if ((lane & 3) == 0) red[wid][vi] = d;
+    __syncthreads();
+    if (threadIdx.x < NV - v0 && threadIdx.x < 8) {
+      double t = 0.0;
+      for (int q = 0; q < CGS_THREADS / 32; ++q) t += red[q][threadIdx.x];
+      out[v0 + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(CGS_THREADS) k_cgs2r(long long n, const double* __restrict__ V, long long ld,
+                                                     const double* __restrict__ w, double* __restrict__ part,
+                                                     double* __restrict__ hcol, double* __restrict__ vnext,
+                                                     unsigned* bar, int* err) {
+  constexpr int U = NV <= 8 ? 4 : (NV <= 11 ? 2 : 1);   // rows whose V values are loaded together
+  static_assert(CGS_RPT % U == 0, "row groups must tile the thread's rows");
+  __shared__ double h[NV], h2[NV], red[CGS_THREADS / 32][8];
+  __shared__ int sh_ok;
+  __shared__ double nrm;
+  const unsigned G = gridDim.x;
+  const long long chunk = (n + G - 1) / G;
+  const long long lo = (long long)blockIdx.x * chunk;
+  const long long hi = lo + chunk < n ? lo + chunk : n;
+  unsigned* count = bar;
+  volatile unsigned* gen = bar + 1;
+  const size_t region = (size_t)G * CGS_MAXV;
+  long long row[CGS_RPT];
+  bool in[CGS_RPT];
+  double wr[CGS_RPT];
+#pragma unroll
+  for (int u = 0; u < CGS_RPT; ++u) {
+    row[u] = lo + threadIdx.x + (long long)u * CGS_THREADS;
+    in[u] = row[u] < hi;
+    wr[u] = in[u] ? w[row[u]] : 0.0;
+  }
+  auto load_group = [&](int u0, double (*vv)[NV]) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) vv[u][i] = in[u0 + u] ? __ldg(V + (size_t)i * ld + row[u0 + u]) : 0.0;
+  };
+  // pass 1
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+#pragma unroll
+  for (int u0 = 0; u0 < CGS_RPT; u0 += U) {
+    double vv[U][NV];
+    load_group(u0, vv);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) acc[i] += vv[u][i] * wr[u0 + u];
+  }
+  block_partials_reg<NV>(acc, part + (size_t)blockIdx.x * NV, red);
+  if (!grid_barrier(count, gen, G, err, &sh_ok)) return;
+  sum_partials(part, G, NV, h);
+  __syncthreads();
+  // pass 2
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+#pragma unroll
+  for (int u0 = 0; u0 < CGS_RPT; u0 += U) {
+    double vv[U][NV];
+    load_group(u0, vv);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      double s = 0.0;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) s += h[i] * vv[u][i];
+      wr[u0 + u] -= s;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) acc[i] += vv[u][i] * wr[u0 + u];
+    }
+  }
+  block_partials_reg<NV>(acc, part + region + (size_t)blockIdx.x * NV, red);
+  if (!grid_barrier(count, gen, G, err, &sh_ok)) return;
+  sum_partials(part + region, G, NV, h2);
+  __syncthreads();
+  // pass 3
+  double q = 0.0;
+#pragma unroll
+  for (int u0 = 0; u0 < CGS_RPT; u0 += U) {
+    double vv[U][NV];
+    load_group(u0, vv);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      double s = 0.0;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) s += h2[i] * vv[u][i];
+      wr[u0 + u] -= s;
+      q += wr[u0 + u] * wr[u0 + u];
+    }
+  }
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int off = 16; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off);
+    if (lane == 0) red[wid][0] = q;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < CGS_THREADS / 32; ++k) t += red[k][0];
+      part[2 * region + blockIdx.x] = t;
+    }
+  }
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < NV; i += CGS_THREADS) hcol[i] = h[i] + h2[i];
+  if (!grid_barrier(count, gen, G, err, &sh_ok)) return;
+  sum_partials(part + 2 * region, G, 1, &nrm);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    nrm = sqrt(nrm);
+    if (blockIdx.x == 0) hcol[NV] = nrm;
+  }
+  __syncthreads();
+  const double inv = 1.0 / nrm;
+#pragma unroll
+  for (int u = 0; u < CGS_RPT; ++u)
+    if (in[u]) vnext[row[u]] = wr[u] * inv;
+}
+
+template <int... I>
+struct CgsTable {
+  static inline const void* const fn[sizeof...(I)] = {(const void*)k_cgs2r<I + 1>...};
+};
+using CgsRegTable = CgsTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15>;
+
+// whether the register form takes nv vectors of n rows on nblocks blocks
+bool cgs2_reg_ok(long long n, int nv, int nblocks) {
+  const long long chunk = (n + nblocks - 1) / nblocks;
+  return nv >= 1 && nv <= CGS_RV && chunk <= (long long)CGS_RPT * CGS_THREADS;
+}
+
 int cgs2_scratch(int nblocks) { return 3 * nblocks * CGS_MAXV; }
 
 int cgs2_max_vectors() { return CGS_MAXV; }
 
 cudaError_t launch_cgs2(long long n, int nv, const double* V, long long ld, double* w, double* partial, double* hcol,
-                        double* vnext, unsigned* bar, int* err, int nblocks, cudaStream_t st) {
+                        double* vnext, unsigned* bar, int* err, int nblocks, bool reg, cudaStream_t st) {
   if (nv < 1 || nv > CGS_MAXV || nblocks < 1) return cudaErrorInvalidValue;
+  if (reg && cgs2_reg_ok(n, nv, nblocks)) {
+    const double* wc = w;
+    void* args[] = {&n, &V, &ld, &wc, &partial, &hcol, &vnext, &bar, &err};
+    return cudaLaunchCooperativeKernel(CgsRegTable::fn[nv - 1], dim3(nblocks), dim3(CGS_THREADS), args, 0, st);
+  }
   void* args[] = {&n, &nv, &V, &ld, &w, &partial, &hcol, &vnext, &bar, &err};
   return cudaLaunchCooperativeKernel((const void*)k_cgs2, dim3(nblocks), dim3(CGS_THREADS), args, 0, st);
 }
@@ -410,6 +576,13 @@ int cgs2_blocks(int n_sm) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs2, CGS_THREADS, 0) != cudaSuccess || per_sm < 1)
     return 0;
+  // the register form must fit one block per SM too
+  for (int v = 0; v < CGS_RV; ++v) {
+    per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, CgsRegTable::fn[v], CGS_THREADS, 0) != cudaSuccess ||
+        per_sm < 1)
+      return 0;
+  }
   return n_sm > 304 ? 304 : n_sm;
 }
 

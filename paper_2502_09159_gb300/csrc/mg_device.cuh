@@ -51,7 +51,8 @@ __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, c
   const long long base = (long long)(cy * E) * G + cx * E;      // global index of the cell's node (0, 0)
   // boundary lines of the cell's nodes (the mesh boundary crosses a cell only at its outer lines)
   const bool bx0 = cx == 0, bx1 = cx == n - 1, by0 = cy == 0, by1 = cy == n - 1;
-  const T* cb = &P.CB[d][0][0];                     // [mode][node] factors of component d
+  const T* fx = &P.FX[d][0];                        // [ex * NP + ix]: B_h factor along x of component d
+  const T* fy = &P.FY[d][0];                        // [ey * NP + iy]: along y
 
   T ut[NQ], ua[NQ], p[NPM];
 #pragma unroll
@@ -107,15 +108,43 @@ __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, c
     return HOIST_B ? bp[m % (HOIST_B ? NPM : 1)] : ldv<CG>(b + poff + (long long)a * P.n_pres + c * NPM + m);
   };
   const T beta = P.beta[a], bsc = P.bscale[a], hd = P.hd;
-  // continuity rows: this component's share
+  // continuity rows: this component's share, sum-factorised over the modes (ex, ey) of
+  // degree ex + ey <= R: cont[m(ex, ey)] = sum_iy fy[ey][iy] sum_ix fx[ex][ix] ua[iy][ix]
+  constexpr int R = NP - 2;
   T cont[NPM];
+  {
+    T tx[R + 1][NP];
 #pragma unroll
-  for (int m = 0; m < NPM; ++m) {
-    T s = 0;
+    for (int ex = 0; ex <= R; ++ex)
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) s += cb[m * (MAXNP * MAXNP) + q] * ua[q];
-    cont[m] = s;
+      for (int iy = 0; iy < NP; ++iy) {
+        T s = 0;
+#pragma unroll
+        for (int ix = 0; ix < NP; ++ix) s += fx[ex * NP + ix] * ua[iy * NP + ix];
+        tx[ex][iy] = s;
+      }
+#pragma unroll
+    for (int ex = 0; ex <= R; ++ex)
+#pragma unroll
+      for (int ey = 0; ey <= R - ex; ++ey) {
+        T s = 0;
+#pragma unroll
+        for (int iy = 0; iy < NP; ++iy) s += fy[ey * NP + iy] * tx[ex][iy];
+        cont[mode_index(ex, ey)] = s;
+      }
   }
+  // pressure gradient factor: sp[ex][iy] = sum_ey fy[ey][iy] p[m(ex, ey)], so that the
+  // B_h^T term of node (iy, ix) is sum_ex fx[ex][ix] sp[ex][iy]
+  T sp[R + 1][NP];
+#pragma unroll
+  for (int ex = 0; ex <= R; ++ex)
+#pragma unroll
+    for (int iy = 0; iy < NP; ++iy) {
+      T s = 0;
+#pragma unroll
+      for (int ey = 0; ey <= R - ex; ++ey) s += fy[ey * NP + iy] * p[mode_index(ex, ey)];
+      sp[ex][iy] = s;
+    }
   // y-pass: A1 = hd M1y ut + beta K1y ua, A2 = M1y ua (column by column)
   T A1[NQ], A2[NQ];
 #pragma unroll
@@ -160,7 +189,7 @@ __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, c
       }
       T bt = 0;
 #pragma unroll
-      for (int m = 0; m < NPM; ++m) bt += cb[m * (MAXNP * MAXNP) + iy * NP + i] * p[m];
+      for (int ex = 0; ex <= R; ++ex) bt += fx[ex * NP + i] * sp[ex][iy];
       T v = m1 + beta * k1 + bsc * bt;
       if (res) v = own ? bvel(iy, i) - v : -v;           // b enters once, through the owner
       atomicAdd(yd + off, v);
@@ -172,6 +201,198 @@ __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, c
     const long long gi = poff + (long long)a * P.n_pres + c * NPM + m;
     T v = bsc * cont[m];
     if (res) v = d == 0 ? bpre(m) - v : -v;
+    atomicAdd(y + gi, v);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Pair-split form of the register-resident 2D operator (NP even): the work of one
+// (cell, a, d) on two adjacent lanes.  Lane half hh = t & 1 owns the node columns
+// ix = hh * HC + il, il < HC = NP / 2.  Each lane
+//   - loads and combines in time its own columns (all rows),
+//   - runs the y-pass (along y, within a column) on them,
+//   - takes the partner's y-pass results of each row by shuffles and runs the x-pass for
+//     its own output columns,
+//   - forms the continuity sums of its columns; one shuffle-add completes them, and the
+//     pair splits the pressure rows between its lanes (even modes: lane 0).
+// The arithmetic per output is that of apply2d_reg_thread (the continuity sums add their
+// two column halves last); the serial chain per lane is half as long and there are twice
+// as many lanes, which spreads a level of few cells over more warps.  Every lane of a
+// warp takes part in the shuffles: lanes past the last item compute on cell 0 and store
+// nothing.
+// ------------------------------------------------------------------------------------
+template <typename T, int NP, int KT, bool CG>
+__device__ __forceinline__ void apply2d_pair_thread(const ApplyRegParams<T>& P, const T* __restrict__ x,
+                                                    const T* __restrict__ b, T* __restrict__ y, int mode,
+                                                    long long t) {
+  static_assert(NP % 2 == 0, "the pair split halves the node columns");
+  constexpr int E = NP - 1, R = NP - 2, HC = NP / 2;
+  constexpr int NPM = NP * (NP - 1) / 2;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int n = P.n, G = P.G;
+  const long long ncells = (long long)n * n;
+  const long long tp = t >> 1;
+  const int hh = (int)(t & 1);
+  const bool live = tp < ncells * KT * 2;
+  const long long tq = live ? tp : 0;
+  const long long ad = tq / ncells;
+  const long long c = tq - ad * ncells;
+  const int a = (int)(ad >> 1), d = (int)(ad & 1);
+  const int cx = (int)(c % n), cy = (int)(c / n);
+  const long long nvel = P.n_vel, nnod = P.n_nodes;
+  const long long poff = (long long)KT * nvel;
+  const bool res = mode == RESIDUAL || mode == LIFT;
+  const bool lift = mode == LIFT;
+  const bool tr = mode == APPLY_T;
+  const int c0 = hh * HC;                                         // first column of this lane
+  const long long base = (long long)(cy * E) * G + cx * E + c0;   // node (0, c0) of the cell
+  const bool bx0 = cx == 0, bx1 = cx == n - 1, by0 = cy == 0, by1 = cy == n - 1;
+  auto dirn = [&](int iy, int il) -> bool {
+    const int ix = c0 + il;
+    return (iy == 0 && by0) || (iy == E && by1) || (ix == 0 && bx0) || (ix == E && bx1);
+  };
+  const T* fy = &P.FY[d][0];
+  T fxo[R + 1][HC];                                 // x factors of this lane's columns
+#pragma unroll
+  for (int ex = 0; ex <= R; ++ex)
+#pragma unroll
+    for (int il = 0; il < HC; ++il) fxo[ex][il] = P.FX[d][ex * NP + c0 + il];
+
+  T ut[NP][HC], ua[NP][HC], p[NPM];
+#pragma unroll
+  for (int iy = 0; iy < NP; ++iy)
+#pragma unroll
+    for (int il = 0; il < HC; ++il) { ut[iy][il] = 0; ua[iy][il] = 0; }
+  T kt_row[KT];
+#pragma unroll
+  for (int bb = 0; bb < KT; ++bb) kt_row[bb] = tr ? P.Kt[bb * MAXKT + a] : P.Kt[a * MAXKT + bb];
+#pragma unroll
+  for (int bb = 0; bb < KT; ++bb) {
+    const T* xb = x + bb * nvel + d * nnod + base;
+    const T kb = kt_row[bb];
+#pragma unroll
+    for (int iy = 0; iy < NP; ++iy)
+#pragma unroll
+      for (int il = 0; il < HC; ++il) {
+        const bool dir = dirn(iy, il);
+        const bool take = lift ? dir : !dir;
+        const T v = take ? ldv<CG>(xb + iy * G + il) : T(0);
+        ut[iy][il] += kb * v;
+        if (bb == a) ua[iy][il] = v;
+      }
+  }
+#pragma unroll
+  for (int m = 0; m < NPM; ++m) p[m] = lift ? T(0) : ldv<CG>(x + poff + (long long)a * P.n_pres + c * NPM + m);
+  const T beta = P.beta[a], bsc = P.bscale[a], hd = P.hd;
+
+  // continuity: sum over this lane's columns, then the partner's half
+  T cont[NPM];
+  {
+    T ty[R + 1][HC];
+#pragma unroll
+    for (int ey = 0; ey <= R; ++ey)
+#pragma unroll
+      for (int il = 0; il < HC; ++il) {
+        T s = 0;
+#pragma unroll
+        for (int iy = 0; iy < NP; ++iy) s += fy[ey * NP + iy] * ua[iy][il];
+        ty[ey][il] = s;
+      }
+#pragma unroll
+    for (int ex = 0; ex <= R; ++ex)
+#pragma unroll
+      for (int ey = 0; ey <= R - ex; ++ey) {
+        T s = 0;
+#pragma unroll
+        for (int il = 0; il < HC; ++il) s += fxo[ex][il] * ty[ey][il];
+        cont[mode_index(ex, ey)] = s + __shfl_xor_sync(FULL, s, 1);
+      }
+  }
+  T sp[R + 1][NP];
+#pragma unroll
+  for (int ex = 0; ex <= R; ++ex)
+#pragma unroll
+    for (int iy = 0; iy < NP; ++iy) {
+      T s = 0;
+#pragma unroll
+      for (int ey = 0; ey <= R - ex; ++ey) s += fy[ey * NP + iy] * p[mode_index(ex, ey)];
+      sp[ex][iy] = s;
+    }
+  // y-pass on this lane's columns
+  T A1[NP][HC], A2[NP][HC];
+#pragma unroll
+  for (int il = 0; il < HC; ++il)
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T m1 = 0, k1 = 0, m2 = 0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        m1 += P.M1[i * NP + j] * ut[j][il];
+        k1 += P.K1[i * NP + j] * ua[j][il];
+        m2 += P.M1[i * NP + j] * ua[j][il];
+      }
+      A1[i][il] = hd * m1 + beta * k1;
+      A2[i][il] = m2;
+    }
+  // rows of M1 and K1 of this lane's output columns
+  T m1o[HC][NP], k1o[HC][NP];
+#pragma unroll
+  for (int io = 0; io < HC; ++io)
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      m1o[io][j] = P.M1[(c0 + io) * NP + j];
+      k1o[io][j] = P.K1[(c0 + io) * NP + j];
+    }
+  // x-pass, pressure gradient, scatter
+  T* yd = y + a * nvel + d * nnod + base;
+  const T* xd = x + a * nvel + d * nnod + base;
+  const T* bd = b + a * nvel + d * nnod + base;
+#pragma unroll
+  for (int iy = 0; iy < NP; ++iy) {
+    T f1[NP], f2[NP];                               // row iy of A1, A2 in column order
+#pragma unroll
+    for (int jl = 0; jl < HC; ++jl) {
+      const T o1 = __shfl_xor_sync(FULL, A1[iy][jl], 1), o2 = __shfl_xor_sync(FULL, A2[iy][jl], 1);
+      f1[jl] = hh ? o1 : A1[iy][jl];
+      f1[HC + jl] = hh ? A1[iy][jl] : o1;
+      f2[jl] = hh ? o2 : A2[iy][jl];
+      f2[HC + jl] = hh ? A2[iy][jl] : o2;
+    }
+    const bool dy = (iy == 0 && by0) || (iy == E && by1);
+    const bool oy = iy < E || by1;
+#pragma unroll
+    for (int io = 0; io < HC; ++io) {
+      const int ix = c0 + io;
+      const bool dir = dy || (ix == 0 && bx0) || (ix == E && bx1);
+      const bool own = oy && (ix < E || bx1);
+      const long long off = (long long)iy * G + io;
+      if (dir) {
+        if (own && live) {
+          const T xv = ldv<CG>(xd + off);
+          atomicAdd(yd + off, mode == RESIDUAL ? ldv<CG>(bd + off) - xv : xv);
+        }
+        continue;
+      }
+      T m1 = 0, k1 = 0, bt = 0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        m1 += m1o[io][j] * f1[j];
+        k1 += k1o[io][j] * f2[j];
+      }
+#pragma unroll
+      for (int ex = 0; ex <= R; ++ex) bt += fxo[ex][io] * sp[ex][iy];
+      T v = m1 + beta * k1 + bsc * bt;
+      if (res) v = own ? ldv<CG>(bd + off) - v : -v;
+      if (live) atomicAdd(yd + off, v);
+    }
+  }
+  // pressure rows of the cell: this component's share, modes split between the lanes
+#pragma unroll
+  for (int m = 0; m < NPM; ++m) {
+    if ((m & 1) != hh || !live) continue;
+    const long long gi = poff + (long long)a * P.n_pres + c * NPM + m;
+    T v = bsc * cont[m];
+    if (res) v = d == 0 ? ldv<CG>(b + gi) - v : -v;
     atomicAdd(y + gi, v);
   }
 }

@@ -10,7 +10,7 @@ Tolerances (relative, max-norm over max-norm of the reference):
 import numpy as np
 import pytest
 
-from oracle.stokes import MGConfig, Multigrid, Slab, march, slab_prolongation
+from oracle.stokes import MGConfig, Multigrid, Slab, fgmres, march, slab_prolongation
 from workloads import fourier_forcing_2d, manufactured_2d, random_vector, taylor_green_3d
 
 pytestmark = pytest.mark.gpu
@@ -93,13 +93,28 @@ def reg_supported(r, k, prec):
     return k + 1 <= 4 and r <= (3 if prec == "fp32" else 2)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+def pair_supported(r, k):
+    """The pair-split register form covers Q3 (r = 2) with k + 1 <= 4, in both precisions;
+    where it is forced on other levels they take the register-resident form."""
+    return r == 2 and k + 1 <= 4
+
+
+def forced_variant(variant, r, k, prec):
+    if variant == 4 and pair_supported(r, k):
+        return 4
+    if variant in (3, 4):
+        return 3 if reg_supported(r, k, prec) else 2
+    return variant
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 @pytest.mark.parametrize("case", [c for c in CASES if c[0] == 2], ids=[i for c, i in zip(CASES, IDS) if c[0] == 2])
 def test_apply_variants_2d(case, variant):
     """Every operator kernel forced on every 2D level: the per-cell form (atomics on shared
     nodes), the node-centred form (tiles of 4x4 cells, ragged tiles on 3x3 / 5x5 meshes,
     every output written once) and the register-resident form (one thread per cell and
-    temporal dof): apply, residual, S^T and the lift against the oracle."""
+    temporal dof) and its pair-split form (two lanes per item, Q3 levels; ragged warps on the
+    3x3 mesh): apply, residual, S^T and the lift against the oracle."""
     og, _ = setup_case(case)
     dim, n, r, k, levels = case
     levels = levels or stmg.host_default_hierarchy(n, r, k)
@@ -107,7 +122,7 @@ def test_apply_variants_2d(case, variant):
                          use_graphs=False, autotune=False, apply_variant=variant)
     for l, s in enumerate(og.slabs):
         lr, lk = levels[l][1], levels[l][2]
-        want = tuple(variant if variant != 3 or reg_supported(lr, lk, p) else 2 for p in ("fp64", "fp32"))
+        want = tuple(forced_variant(variant, lr, lk, p) for p in ("fp64", "fp32"))
         assert g.levels[l]["apply_variant"] == want
         x = random_vector(s.size, 63 + l)
         b = random_vector(s.size, 67 + l)
@@ -330,6 +345,33 @@ def test_solve_slab_matches_direct_solve():
     assert rel(xs, slab.remove_pressure_mean(xd)) < 1e-9
     for a in range(slab.kt):
         assert np.abs(slab.B @ slab.vel(x.cpu().numpy(), a)).max() < 1e-10
+
+
+def test_arnoldi_forms_agree():
+    """The Arnoldi step in its two forms (w held in registers across the passes for up to 16
+    basis vectors, else the split-pass form) on a solve of 25 iterations (the oracle's
+    count with omega = 0.3 to 1e-12), so that the register form's 16 instances and the
+    split form beyond them are all taken: the same iterations and solutions, and the
+    oracle's solution to 1e-9."""
+    pb = fourier_forcing_2d(nu=1.0)
+    levels = stmg.host_default_hierarchy(8, 1, 1)
+    og = Multigrid(2, levels, 1.0, 0.25, MGConfig(omega=0.3))
+    s0 = og.slabs[0]
+    F = s0.rhs_forcing(pb.forcing, 0.0)
+    xo, info_o = fgmres(lambda z: s0.S @ z, og.vcycle, F, tol=1e-12)
+    assert info_o.converged and info_o.iterations > 16
+    out = []
+    for form in (0, 1):
+        g = stmg.SpaceTimeMG(dim=2, n_cells=8, r=1, k=1, nu=1.0, T=1.0, n_slabs=4, levels=levels, omega=0.3,
+                             rel_tol=1e-12, precisions=("fp64",), arnoldi_form=form)
+        x, info = g.solve_slab(dev(F))
+        assert info["status"] == 0 and info["rel_residual"] <= 1e-12
+        out.append((s0.remove_pressure_mean(x.cpu().numpy()), info["iterations"]))
+        g.device_status()
+        g.close()
+    assert out[0][1] == out[1][1] and abs(out[0][1] - info_o.iterations) <= 1
+    assert rel(out[0][0], out[1][0]) < 1e-12
+    assert rel(out[0][0], s0.remove_pressure_mean(xo)) < 1e-9
 
 
 def test_forcing_and_slab_rhs():
