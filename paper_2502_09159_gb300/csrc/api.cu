@@ -68,6 +68,9 @@ struct stmg_handle {
   double *V = nullptr, *Z = nullptr, *w = nullptr, *hcol = nullptr, *tmp = nullptr, *partial = nullptr;
   double *bnorm = nullptr, *xhost_b = nullptr, *xhost_x = nullptr;
   int m_alloc = 0;
+  double* hc_host = nullptr;      // pinned: the Arnoldi column of H of each iteration
+  int* err_host = nullptr;        // pinned: the device error flag after each iteration
+  cudaEvent_t ev_it[2] = {nullptr, nullptr};   // ends of the (at most two) iterations in flight
   int* d_err = nullptr;           // device flag raised by bounded waits that expired
   double* dot_part = nullptr;     // per-block partial sums of stmg_dot (allocated on first use)
   unsigned* cgs_bar = nullptr;    // grid barrier of the cooperative CGS2 step (count, generation)
@@ -926,6 +929,14 @@ static int ensure_krylov(stmg_handle* h, int m) {
     CKS(dalloc(&h->cgs_part, (size_t)cgs2_scratch(h->cgs_blocks)));
   }
   CKS(dalloc(&h->bnorm, 4));
+  if (h->hc_host) cudaFreeHost(h->hc_host);
+  if (h->err_host) cudaFreeHost(h->err_host);
+  h->hc_host = nullptr;
+  h->err_host = nullptr;
+  CK(cudaMallocHost((void**)&h->hc_host, sizeof(double) * (size_t)(m + 1) * (m + 2)));
+  CK(cudaMallocHost((void**)&h->err_host, sizeof(int) * (size_t)(m + 1)));
+  for (int i = 0; i < 2; ++i)
+    if (!h->ev_it[i]) CK(cudaEventCreateWithFlags(&h->ev_it[i], cudaEventDisableTiming));
   h->m_alloc = m;
   return STMG_OK;
 }
@@ -957,7 +968,7 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
   LevelDev& l0 = h->L[0];
   const long long D = l0.H.size;
   cudaStream_t s = h->st;
-  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), hc(m + 2);
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
   double hv[2];
   info->iterations = 0; info->rel_residual = 0.0; info->status = STMG_OK; info->seconds = 0.0;
   if (h->cgs_bar) CK(cudaMemsetAsync(h->cgs_bar, 0, 2 * sizeof(unsigned), s));
@@ -994,42 +1005,69 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
   CK(launch_scale(D, 1.0 / beta, h->V, h->V, s));
   h->launches += 1;
   g[0] = beta;
-  int j = 0, status = STMG_ERR_NOT_CONVERGED;
-  for (j = 0; j < m; ++j) {
-    double* vj = h->V + (size_t)j * D;
-    double* zj = h->Z + (size_t)j * D;
+  // One FGMRES iteration on the device: precondition v_j, apply S, Arnoldi step (which
+  // writes v_{j+1}); then its column of H and the error flag are copied to pinned host
+  // slots and an event marks the end.  Nothing on the device waits for the host, so while
+  // the host reads iteration j the device can already run iteration j + 1: it is
+  // enqueued before the host waits whenever the residual history does not predict that
+  // iteration j converges (the residual estimate falls by a steady factor per iteration;
+  // a wrong "not yet" costs one iteration of device work that is discarded, a wrong
+  // "converged" one host round trip).  With profiling on, iterations are not overlapped.
+  auto enqueue_iteration = [&](int jj) -> int {
+    double* vj = h->V + (size_t)jj * D;
+    double* zj = h->Z + (size_t)jj * D;
     CKS(precondition(h, prec, vj, zj));
     {
       Prof pr(h, STMG_PROF_OPERATOR, s);
       CKS(op_apply<double>(h, 0, zj, nullptr, h->w, APPLY, s));
     }
-    if (h->cgs_blocks > 0 && j + 1 <= cgs2_max_vectors()) {
+    if (h->cgs_blocks > 0 && jj + 1 <= cgs2_max_vectors()) {
       Prof pr(h, STMG_PROF_OTHER, s);
       // CGS2 and the normalisation of the next basis vector in one cooperative launch
-      CK(launch_cgs2(D, j + 1, h->V, D, h->w, h->cgs_part, h->hcol, h->V + (size_t)(j + 1) * D, h->cgs_bar, h->d_err,
-                     h->cgs_blocks, h->cfg.arnoldi_form == 0, s));
+      CK(launch_cgs2(D, jj + 1, h->V, D, h->w, h->cgs_part, h->hcol, h->V + (size_t)(jj + 1) * D, h->cgs_bar,
+                     h->d_err, h->cgs_blocks, h->cfg.arnoldi_form == 0, s));
       h->launches += 1;
     } else {
       Prof pr(h, STMG_PROF_OTHER, s);
       const int nb = multidot_blocks(D);
       // CGS2: h = V^T w, w -= V h, twice; h accumulated in hcol
-      CK(launch_multidot(D, j + 1, h->V, D, h->w, h->partial, nb, s));
-      CK(launch_reduce_partials(j + 1, nb, h->partial, h->hcol, 0, s));
-      CK(launch_multiaxpy(D, j + 1, h->V, D, h->hcol, -1.0, h->w, s));
-      CK(launch_multidot(D, j + 1, h->V, D, h->w, h->partial, nb, s));
-      CK(launch_reduce_partials(j + 1, nb, h->partial, h->tmp, 0, s));
-      CK(launch_multiaxpy(D, j + 1, h->V, D, h->tmp, -1.0, h->w, s));
-      CK(launch_reduce_partials(j + 1, nb, h->partial, h->hcol, 1, s));
-      CKS(dev_norm(h, h->w, D, h->hcol + j + 1));
-      CK(launch_scale_by_inverse(D, h->hcol + j + 1, h->w, h->V + (size_t)(j + 1) * D, s));
+      CK(launch_multidot(D, jj + 1, h->V, D, h->w, h->partial, nb, s));
+      CK(launch_reduce_partials(jj + 1, nb, h->partial, h->hcol, 0, s));
+      CK(launch_multiaxpy(D, jj + 1, h->V, D, h->hcol, -1.0, h->w, s));
+      CK(launch_multidot(D, jj + 1, h->V, D, h->w, h->partial, nb, s));
+      CK(launch_reduce_partials(jj + 1, nb, h->partial, h->tmp, 0, s));
+      CK(launch_multiaxpy(D, jj + 1, h->V, D, h->tmp, -1.0, h->w, s));
+      CK(launch_reduce_partials(jj + 1, nb, h->partial, h->hcol, 1, s));
+      CKS(dev_norm(h, h->w, D, h->hcol + jj + 1));
+      CK(launch_scale_by_inverse(D, h->hcol + jj + 1, h->w, h->V + (size_t)(jj + 1) * D, s));
       h->launches += 8;
     }
-    CK(cudaMemcpyAsync(hc.data(), h->hcol, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
-    int ierr = 0;
-    CK(cudaMemcpyAsync(&ierr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpyAsync(h->hc_host + (size_t)jj * (m + 2), h->hcol, sizeof(double) * (jj + 2), cudaMemcpyDeviceToHost,
+                       s));
+    CK(cudaMemcpyAsync(h->err_host + jj, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(h->ev_it[jj & 1], s));
+    return STMG_OK;
+  };
+  const bool overlap = h->prof == 0;
+  std::vector<double> rest(m + 1, 0.0);           // residual estimate after i iterations
+  rest[0] = beta;
+  int j = 0, status = STMG_ERR_NOT_CONVERGED;
+  CKS(enqueue_iteration(0));
+  for (j = 0; j < m; ++j) {
+    bool ahead = false;
+    if (overlap && j + 1 < m) {
+      // predicted residual after iteration j: the last reduction factor applied once more
+      const double pred = j >= 1 ? rest[j] * (rest[j] / rest[j - 1]) : rest[j];
+      if (!(pred <= 4.0 * tol * bn)) {
+        CKS(enqueue_iteration(j + 1));
+        ahead = true;
+      }
+    }
+    CK(cudaEventSynchronize(h->ev_it[j & 1]));
     harvest_all(h);
-    if (ierr) {                       // a bounded wait expired (grid barrier or TMA pipeline)
+    const double* hc = h->hc_host + (size_t)j * (m + 2);
+    if (h->err_host[j]) {             // a bounded wait expired (grid barrier or TMA pipeline)
+      CK(cudaStreamSynchronize(s));   // the iteration enqueued ahead finishes first
       CK(cudaMemset(h->d_err, 0, sizeof(int)));
       if (h->cgs_bar) CK(cudaMemset(h->cgs_bar, 0, 2 * sizeof(unsigned)));
       if (h->mgp_bar) CK(cudaMemset(h->mgp_bar, 0, 2 * sizeof(unsigned)));
@@ -1038,7 +1076,10 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
       return STMG_ERR_TIMEOUT;
     }
     for (int i = 0; i <= j + 1; ++i) {
-      if (!std::isfinite(hc[i])) { info->status = STMG_ERR_NONFINITE; info->iterations = j + 1; return info->status; }
+      if (!std::isfinite(hc[i])) {
+        CK(cudaStreamSynchronize(s));
+        info->status = STMG_ERR_NONFINITE; info->iterations = j + 1; return info->status;
+      }
       H[(size_t)i * m + j] = hc[i];
     }
     for (int i = 0; i < j; ++i) {     // previous Givens rotations
@@ -1054,8 +1095,10 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
     H[(size_t)(j + 1) * m + j] = 0.0;
     g[j + 1] = -sn[j] * g[j];
     g[j] = cs[j] * g[j];
+    rest[j + 1] = std::fabs(g[j + 1]);
     if (std::fabs(g[j + 1]) <= tol * bn) { status = STMG_OK; ++j; break; }
     if (c == 0.0) { status = STMG_OK; ++j; break; }   // lucky breakdown: exact solution
+    if (!ahead && j + 1 < m) CKS(enqueue_iteration(j + 1));
   }
   const int kdim = j < m ? j : m;
   // back substitution H y = g, then x += Z y
@@ -1446,6 +1489,10 @@ void stmg_destroy(stmg_handle* h) {
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(h->V); f(h->Z); f(h->w); f(h->hcol); f(h->tmp); f(h->partial); f(h->bnorm);
   f(h->xhost_b); f(h->xhost_x); f(h->d_err); f(h->dot_part); f(h->cgs_bar); f(h->cgs_part);
+  if (h->hc_host) cudaFreeHost(h->hc_host);
+  if (h->err_host) cudaFreeHost(h->err_host);
+  for (auto e : h->ev_it)
+    if (e) cudaEventDestroy(e);
   if (h->cst) cudaStreamSynchronize(h->cst);
   for (int i = 0; i < 2; ++i) {
     f(h->mh_in[i]); f(h->mh_x[i]);
