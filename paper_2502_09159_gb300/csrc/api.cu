@@ -43,6 +43,7 @@ struct LevelDev {
   PrecDev<float> f;
   double* G = nullptr;      // coarsest level: bordered inverse, column-major
   double* Gacc = nullptr;   // coarsest level with D > 1024: FP64 accumulator of the tiled GEMV
+  float* Gf = nullptr;      // coarsest level: G rounded to FP32, for the FP32 V-cycle
   int streaming = 0;        // read the inverses with evict-first loads
   int sweep_var[2] = {1, 1};  // per precision: 1 = block per patch group, 2 = TMA-pipelined, 3 = pipelined block
   int ppb[2] = {1, 1};        // per precision: patches per block of the block sweeps
@@ -389,7 +390,7 @@ static int setup_precision(stmg_handle* h, LevelDev& lv, const double* d_cls, co
 
 static void free_level(LevelDev& lv) {
   auto f = [](void* p) { if (p) cudaFree(p); };
-  f(lv.dofs); f(lv.G); f(lv.Gacc);
+  f(lv.dofs); f(lv.G); f(lv.Gacc); f(lv.Gf);
   f(lv.d.inv); f(lv.d.b); f(lv.d.x); f(lv.d.r); f(lv.f.invh); f(lv.f.rsc);
   f(lv.f.inv); f(lv.f.b); f(lv.f.x); f(lv.f.r);
   lv = LevelDev();
@@ -467,11 +468,15 @@ static int op_prolongate_add(stmg_handle* h, int l, const T* yc, T* xf, cudaStre
 template <typename T>
 static int op_coarse(stmg_handle* h, const T* b, T* x, cudaStream_t s) {
   LevelDev& lv = h->L.back();
+  const int D = (int)lv.H.size;
+  const bool g32 = std::is_same<T, float>::value && lv.Gf;   // FP32 V-cycle: the FP32 copy of G
   if (lv.Gacc) {
-    CK(launch_coarse_tiled<T>((int)lv.H.size, lv.G, b, x, lv.Gacc, s));
+    if (g32) CK((launch_coarse_tiled<float, float>(D, lv.Gf, (const float*)b, (float*)x, lv.Gacc, s)));
+    else CK((launch_coarse_tiled<T, double>(D, lv.G, b, x, lv.Gacc, s)));
     h->launches += 2;
   } else {
-    CK(launch_coarse<T>((int)lv.H.size, lv.G, b, x, s));
+    if (g32) CK((launch_coarse<float, float>(D, lv.Gf, (const float*)b, (float*)x, s)));
+    else CK((launch_coarse<T, double>(D, lv.G, b, x, s)));
     h->launches += 1;
   }
   return STMG_OK;
@@ -1399,6 +1404,11 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
       if (!build_coarse_inverse(&H, &Gcm)) return STMG_ERR_SINGULAR;
       CKS(dalloc(&L.G, Gcm.size()));
       CK(cudaMemcpy(L.G, Gcm.data(), sizeof(double) * Gcm.size(), cudaMemcpyHostToDevice));
+      if (c.precisions & 2) {        // the FP32 V-cycle's copy: half the bytes, FP32 products
+        std::vector<float> Gf(Gcm.begin(), Gcm.end());
+        CKS(dalloc(&L.Gf, Gf.size()));
+        CK(cudaMemcpy(L.Gf, Gf.data(), sizeof(float) * Gf.size(), cudaMemcpyHostToDevice));
+      }
       if (H.size > 1024) {
         CKS(dalloc(&L.Gacc, H.size));
         CK(cudaMemset(L.Gacc, 0, sizeof(double) * H.size));   // the tiled product keeps it zero between solves

@@ -206,10 +206,11 @@ size_t transfer_smem(const TransferParams<T>& p, int restrict_);
 template <typename T>
 bool transfer_gather_supported(const TransferParams<T>& p);   // the gather form has this shape
 
-template <typename T>
-cudaError_t launch_coarse(int D, const double* Gcm, const T* b, T* x, cudaStream_t st);
-template <typename T>
-cudaError_t launch_coarse_tiled(int D, const double* Gcm, const T* b, T* x, double* acc, cudaStream_t st);
+// coarse direct solve x = G b; G stored in FP64 or (FP32 V-cycle) FP32, products in G's type
+template <typename T, typename M>
+cudaError_t launch_coarse(int D, const M* Gcm, const T* b, T* x, cudaStream_t st);
+template <typename T, typename M>
+cudaError_t launch_coarse_tiled(int D, const M* Gcm, const T* b, T* x, double* acc, cudaStream_t st);
 
 cudaError_t launch_mass_coupling(const MassParams& p, const double* vprev, double* b, cudaStream_t st);
 cudaError_t launch_forcing(const ForcingParams& p, const double* fq, double* F, cudaStream_t st);

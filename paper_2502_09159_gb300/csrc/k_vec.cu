@@ -586,40 +586,41 @@ int cgs2_blocks(int n_sm) {
   return n_sm > 304 ? 304 : n_sm;
 }
 
-// Coarse direct solve: x = G b, G column-major D x D in FP64; vectors of type T.
-template <typename T>
-__global__ void k_coarse(int D, const double* __restrict__ Gcm, const T* __restrict__ b, T* __restrict__ x) {
+// Coarse direct solve: x = G b, G column-major D x D, stored in FP64 (M = double) or, for
+// the FP32 V-cycle, as its FP32 rounding (M = float); vectors of type T, products in M.
+template <typename T, typename M>
+__global__ void k_coarse(int D, const M* __restrict__ Gcm, const T* __restrict__ b, T* __restrict__ x) {
   extern __shared__ double bs[];
   for (int i = threadIdx.x; i < D; i += blockDim.x) bs[i] = (double)b[i];
   __syncthreads();
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < D; row += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < D; ++c) s += Gcm[(size_t)c * D + row] * bs[c];
+    M s = 0;
+    for (int c = 0; c < D; ++c) s += Gcm[(size_t)c * D + row] * (M)bs[c];
     x[row] = (T)s;
   }
 }
 
 // Large coarse levels (D > 1024): tiles of 256 rows x 32 columns of G (enough tiles to
 // cover every SM several times), all 32 loads of a thread issued before the products,
-// eight independent FP64 accumulators per row, partial products accumulated in FP64
+// eight independent accumulators per row, each tile's partial sum accumulated in FP64
 // (acc, zeroed first), then rounded to the vector type.
-template <typename T>
-__global__ void __launch_bounds__(256) k_coarse_tiled(int D, const double* __restrict__ Gcm,
+template <typename T, typename M>
+__global__ void __launch_bounds__(256) k_coarse_tiled(int D, const M* __restrict__ Gcm,
                                                       const T* __restrict__ b, double* __restrict__ acc) {
   constexpr int CT = 32;
-  __shared__ double bs[CT];
+  __shared__ M bs[CT];
   const int c0 = blockIdx.y * CT;
   const int cn = min(CT, D - c0);
-  if (threadIdx.x < CT) bs[threadIdx.x] = threadIdx.x < cn ? (double)b[c0 + threadIdx.x] : 0.0;
+  if (threadIdx.x < CT) bs[threadIdx.x] = threadIdx.x < cn ? (M)b[c0 + threadIdx.x] : M(0);
   __syncthreads();
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= D) return;
-  const double* g = Gcm + (size_t)c0 * D + row;
-  double s[8];
+  const M* g = Gcm + (size_t)c0 * D + row;
+  M s[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) s[i] = 0.0;
+  for (int i = 0; i < 8; ++i) s[i] = 0;
   if (cn == CT) {
-    double v[CT];
+    M v[CT];
 #pragma unroll
     for (int c = 0; c < CT; ++c) v[c] = g[(size_t)c * D];
 #pragma unroll
@@ -627,7 +628,7 @@ __global__ void __launch_bounds__(256) k_coarse_tiled(int D, const double* __res
   } else {
     for (int c = 0; c < cn; ++c) s[0] += g[(size_t)c * D] * bs[c];
   }
-  atomicAdd(acc + row, ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])));
+  atomicAdd(acc + row, (double)(((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]))));
 }
 
 // x = acc, and acc = 0 again for the next solve (acc is zeroed once when it is allocated)
@@ -641,28 +642,32 @@ __global__ void k_coarse_finish(int D, double* __restrict__ acc, T* __restrict__
 }
 
 // acc: D doubles, zero on entry (and on return)
-template <typename T>
-cudaError_t launch_coarse_tiled(int D, const double* Gcm, const T* b, T* x, double* acc, cudaStream_t st) {
+template <typename T, typename M>
+cudaError_t launch_coarse_tiled(int D, const M* Gcm, const T* b, T* x, double* acc, cudaStream_t st) {
   const int nr = (D + 255) / 256, nc = (D + 31) / 32;
-  k_coarse_tiled<T><<<dim3(nr, nc), 256, 0, st>>>(D, Gcm, b, acc);
+  k_coarse_tiled<T, M><<<dim3(nr, nc), 256, 0, st>>>(D, Gcm, b, acc);
   k_coarse_finish<T><<<nr, 256, 0, st>>>(D, acc, x);
   return cudaGetLastError();
 }
-template cudaError_t launch_coarse_tiled<double>(int, const double*, const double*, double*, double*, cudaStream_t);
-template cudaError_t launch_coarse_tiled<float>(int, const double*, const float*, float*, double*, cudaStream_t);
+template cudaError_t launch_coarse_tiled<double, double>(int, const double*, const double*, double*, double*,
+                                                         cudaStream_t);
+template cudaError_t launch_coarse_tiled<float, double>(int, const double*, const float*, float*, double*,
+                                                        cudaStream_t);
+template cudaError_t launch_coarse_tiled<float, float>(int, const float*, const float*, float*, double*, cudaStream_t);
 
-template <typename T>
-cudaError_t launch_coarse(int D, const double* Gcm, const T* b, T* x, cudaStream_t st) {
+template <typename T, typename M>
+cudaError_t launch_coarse(int D, const M* Gcm, const T* b, T* x, cudaStream_t st) {
   const int blocks = (D + 255) / 256;
   const size_t smem = sizeof(double) * (size_t)D;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_coarse<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_coarse<T><<<blocks, 256, smem, st>>>(D, Gcm, b, x);
+  k_coarse<T, M><<<blocks, 256, smem, st>>>(D, Gcm, b, x);
   return cudaGetLastError();
 }
-template cudaError_t launch_coarse<double>(int, const double*, const double*, double*, cudaStream_t);
-template cudaError_t launch_coarse<float>(int, const double*, const float*, float*, cudaStream_t);
+template cudaError_t launch_coarse<double, double>(int, const double*, const double*, double*, cudaStream_t);
+template cudaError_t launch_coarse<float, double>(int, const double*, const float*, float*, cudaStream_t);
+template cudaError_t launch_coarse<float, float>(int, const float*, const float*, float*, cudaStream_t);
 
 }  // namespace stmg
