@@ -63,7 +63,7 @@ cudaError_t launch_apply2d_reg(int np, const ApplyRegParams<T>& p, const T* x, c
 
 // pair-split form: two lanes per (cell, temporal dof, component), NP even (Q3 in 2D)
 template <typename T, int NP, int KT>
-__global__ void __launch_bounds__(64) k_apply2d_pair(const ApplyRegParams<T> P, const T* __restrict__ x,
+__global__ void __launch_bounds__(32) k_apply2d_pair(const ApplyRegParams<T> P, const T* __restrict__ x,
                                                      const T* __restrict__ b, T* __restrict__ y, int mode) {
   apply2d_pair_thread<T, NP, KT, false>(P, x, b, y, mode, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
@@ -72,8 +72,10 @@ template <typename T, int NP, int KT>
 static cudaError_t launch_apply2d_pair_t(const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode,
                                          cudaStream_t st) {
   const long long tot = (long long)p.n * p.n * KT * 2 * 2;  // (cell, temporal dof, component, column half)
-  const unsigned blocks = (unsigned)((tot + 63) / 64);      // whole warps: every lane reaches the shuffles
-  k_apply2d_pair<T, NP, KT><<<blocks, 64, 0, st>>>(p, x, b, y, mode);
+  // one-warp blocks (every lane reaches the shuffles): on a level of few cells the warps
+  // then spread over the SMs in units of one warp, not two
+  const unsigned blocks = (unsigned)((tot + 31) / 32);
+  k_apply2d_pair<T, NP, KT><<<blocks, 32, 0, st>>>(p, x, b, y, mode);
   return cudaGetLastError();
 }
 

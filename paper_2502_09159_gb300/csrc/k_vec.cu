@@ -387,9 +387,10 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2(long long n, int nv, const
   if (threadIdx.x == 0) {
     nrm = sqrt(nrm);
     if (blockIdx.x == 0) hcol[nv] = nrm;
+    nrm = 1.0 / nrm;                  // one FP64 division per block, not per thread
   }
   __syncthreads();
-  const double inv = 1.0 / nrm;
+  const double inv = nrm;
   for (long long r = lo + threadIdx.x; r < hi; r += CGS_THREADS) vnext[r] = w[r] * inv;
 }
 
@@ -402,9 +403,9 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2(long long n, int nv, const
 //   pass 3: w -= V h2, then ||w||^2                     (V read once)
 // so V is read three times instead of four, w once instead of five times, and w is never
 // written back (the step's outputs are hcol and vnext).  Each thread owns the rows
-// lo + threadIdx.x + u * CGS_THREADS, u < CGS_RPT, the rows the split form gives it, and
-// adds in the same order.  Every loop is unrolled over the compile-time vector count, so
-// all U * NV loads of a row group are in flight together.
+// lo + threadIdx.x + u * CGS_THREADS, u < CGS_RPT, the rows the split form gives it.
+// Every loop is unrolled over the compile-time vector count, so all U * NV loads of a row
+// group are in flight together, and the updates' sums run as two interleaved chains.
 // ------------------------------------------------------------------------------------
 constexpr int CGS_RPT = 4;             // rows of w per thread held in registers
 constexpr int CGS_RV = 16;             // largest basis size of the register form
@@ -488,10 +489,13 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2r(long long n, const double
     load_group(u0, vv);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      double s = 0.0;
+      double s0 = 0.0, s1 = 0.0;        // two chains: half the dependent FP64 latency
 #pragma unroll
-      for (int i = 0; i < NV; ++i) s += h[i] * vv[u][i];
-      wr[u0 + u] -= s;
+      for (int i = 0; i < NV; i += 2) {
+        s0 += h[i] * vv[u][i];
+        if (i + 1 < NV) s1 += h[i + 1] * vv[u][i + 1];
+      }
+      wr[u0 + u] -= s0 + s1;
 #pragma unroll
       for (int i = 0; i < NV; ++i) acc[i] += vv[u][i] * wr[u0 + u];
     }
@@ -508,10 +512,13 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2r(long long n, const double
     load_group(u0, vv);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      double s = 0.0;
+      double s0 = 0.0, s1 = 0.0;
 #pragma unroll
-      for (int i = 0; i < NV; ++i) s += h2[i] * vv[u][i];
-      wr[u0 + u] -= s;
+      for (int i = 0; i < NV; i += 2) {
+        s0 += h2[i] * vv[u][i];
+        if (i + 1 < NV) s1 += h2[i + 1] * vv[u][i + 1];
+      }
+      wr[u0 + u] -= s0 + s1;
       q += wr[u0 + u] * wr[u0 + u];
     }
   }
@@ -534,9 +541,10 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2r(long long n, const double
   if (threadIdx.x == 0) {
     nrm = sqrt(nrm);
     if (blockIdx.x == 0) hcol[NV] = nrm;
+    nrm = 1.0 / nrm;                  // one FP64 division per block, not per thread
   }
   __syncthreads();
-  const double inv = 1.0 / nrm;
+  const double inv = nrm;
 #pragma unroll
   for (int u = 0; u < CGS_RPT; ++u)
     if (in[u]) vnext[row[u]] = wr[u] * inv;
