@@ -399,10 +399,11 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2(long long n, int nv, const
 // to the normalisation (at most CGS_RPT rows per thread), for nv <= CGS_RV basis vectors.
 // The update of each pass and the next pass's dot products share one load of V:
 //   pass 1: h = V^T w                                   (V read once)
-//   pass 2: w -= V h, then h2 = V^T w, row by row       (V read once)
-//   pass 3: w -= V h2, then ||w||^2                     (V read once)
-// so V is read three times instead of four, w once instead of five times, and w is never
-// written back (the step's outputs are hcol and vnext).  Each thread owns the rows
+//   pass 2: w -= V h, then h2 = V^T w and ||w||^2       (V read once)
+//   pass 3: v_next = (w - V h2) / ||w - V h2||          (V read once)
+// with ||w - V h2||^2 = ||w||^2 - ||h2||^2, so two grid barriers instead of three; V is
+// read three times instead of four, w once instead of five times, and w is never written
+// back (the step's outputs are hcol and vnext).  Each thread owns the rows
 // lo + threadIdx.x + u * CGS_THREADS, u < CGS_RPT, the rows the split form gives it.
 // Every loop is unrolled over the compile-time vector count, so all U * NV loads of a row
 // group are in flight together, and the updates' sums run as two interleaved chains.
@@ -438,7 +439,7 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2r(long long n, const double
                                                      unsigned* bar, int* err) {
   constexpr int U = NV <= 8 ? 4 : (NV <= 11 ? 2 : 1);   // rows whose V values are loaded together
   static_assert(CGS_RPT % U == 0, "row groups must tile the thread's rows");
-  __shared__ double h[NV], h2[NV], red[CGS_THREADS / 32][8];
+  __shared__ double h[NV], h2[NV + 1], red[CGS_THREADS / 32][8];
   __shared__ int sh_ok;
   __shared__ double nrm;
   const unsigned G = gridDim.x;
@@ -480,9 +481,10 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2r(long long n, const double
   if (!grid_barrier(count, gen, G, err, &sh_ok)) return;
   sum_partials(part, G, NV, h);
   __syncthreads();
-  // pass 2
+  // pass 2 (also ||w||^2 after the update, for the norm of pass 3's result)
+  double acc2[NV + 1];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  for (int i = 0; i <= NV; ++i) acc2[i] = 0.0;
 #pragma unroll
   for (int u0 = 0; u0 < CGS_RPT; u0 += U) {
     double vv[U][NV];
@@ -497,15 +499,30 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2r(long long n, const double
       }
       wr[u0 + u] -= s0 + s1;
 #pragma unroll
-      for (int i = 0; i < NV; ++i) acc[i] += vv[u][i] * wr[u0 + u];
+      for (int i = 0; i < NV; ++i) acc2[i] += vv[u][i] * wr[u0 + u];
+      acc2[NV] += wr[u0 + u] * wr[u0 + u];
     }
   }
-  block_partials_reg<NV>(acc, part + region + (size_t)blockIdx.x * NV, red);
+  block_partials_reg<NV + 1>(acc2, part + region + (size_t)blockIdx.x * (NV + 1), red);
   if (!grid_barrier(count, gen, G, err, &sh_ok)) return;
-  sum_partials(part + region, G, NV, h2);
+  sum_partials(part + region, G, NV + 1, h2);
   __syncthreads();
-  // pass 3
-  double q = 0.0;
+  // the norm of w - V h2 without a third pass over the blocks: the columns of V are
+  // orthonormal and h2 = V^T w, so ||w - V h2||^2 = ||w||^2 - ||h2||^2 (h2 is a rounding-
+  // level correction after the first pass, so nothing cancels unless w itself vanishes)
+  if (threadIdx.x == 0) {
+    double hh = 0.0;
+    for (int i = 0; i < NV; ++i) hh += h2[i] * h2[i];
+    const double n2 = h2[NV] - hh;
+    nrm = sqrt(n2 > 0.0 ? n2 : 0.0);
+    if (blockIdx.x == 0) hcol[NV] = nrm;
+    nrm = 1.0 / nrm;                  // one FP64 division per block, not per thread
+  }
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < NV; i += CGS_THREADS) hcol[i] = h[i] + h2[i];
+  __syncthreads();
+  const double inv = nrm;
+  // pass 3: w -= V h2, v_next = w / ||w||
 #pragma unroll
   for (int u0 = 0; u0 < CGS_RPT; u0 += U) {
     double vv[U][NV];
@@ -518,36 +535,9 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2r(long long n, const double
         s0 += h2[i] * vv[u][i];
         if (i + 1 < NV) s1 += h2[i + 1] * vv[u][i + 1];
       }
-      wr[u0 + u] -= s0 + s1;
-      q += wr[u0 + u] * wr[u0 + u];
+      if (in[u0 + u]) vnext[row[u0 + u]] = (wr[u0 + u] - (s0 + s1)) * inv;
     }
   }
-  {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int off = 16; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off);
-    if (lane == 0) red[wid][0] = q;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int k = 0; k < CGS_THREADS / 32; ++k) t += red[k][0];
-      part[2 * region + blockIdx.x] = t;
-    }
-  }
-  if (blockIdx.x == 0)
-    for (int i = threadIdx.x; i < NV; i += CGS_THREADS) hcol[i] = h[i] + h2[i];
-  if (!grid_barrier(count, gen, G, err, &sh_ok)) return;
-  sum_partials(part + 2 * region, G, 1, &nrm);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    nrm = sqrt(nrm);
-    if (blockIdx.x == 0) hcol[NV] = nrm;
-    nrm = 1.0 / nrm;                  // one FP64 division per block, not per thread
-  }
-  __syncthreads();
-  const double inv = nrm;
-#pragma unroll
-  for (int u = 0; u < CGS_RPT; ++u)
-    if (in[u]) vnext[row[u]] = wr[u] * inv;
 }
 
 template <int... I>
