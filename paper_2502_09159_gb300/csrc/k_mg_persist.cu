@@ -182,7 +182,7 @@ __device__ __noinline__ void phase_prolongate(const MGLevelDesc<T>& L, const MGL
                                               TransferParams<T>* sp) {
   stage_transfer_tables(L.tp, sp);
   const TransferParams<T>& P = *sp;
-  const long long tot = 2LL * P.Gf * P.Gf + (long long)P.nf * P.nf * P.npmf;
+  const long long tot = prolongate_g_items(P);
   for (long long t = item_first(); t < tot; t += item_stride()) {
     if (L.ht) prolongate_g_thread<T, 3, 3, 1, true>(P, C.x, L.x, t);
     else prolongate_g_thread<T, 3, 3, 0, true>(P, C.x, L.x, t);
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(PT, 2) k_mg_persist(const MGLevelDesc<T>* __re
   T* rs = reinterpret_cast<T*>(scratch);
   ApplyRegParams<T>* sap = reinterpret_cast<ApplyRegParams<T>*>(scratch);
   TransferParams<T>* stp = reinterpret_cast<TransferParams<T>*>(scratch);
-  __shared__ T tsh[PT];
+  __shared__ T tsh[2 * PT];
   __shared__ double bs[32];
   __shared__ int sh_ok;
   unsigned* count = bar;

@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(256) k_prolongate_g(const TransferParams<T> P,
 template <typename T, int NPF, int NPC, int HT>
 __global__ void __launch_bounds__(256) k_restrict_g(const TransferParams<T> P, const T* __restrict__ rf,
                                                     T* __restrict__ bc, T* __restrict__ zc) {
-  __shared__ T tsh[256];
+  __shared__ T tsh[512];
   restrict_g_block<T, NPF, NPC, HT, false>(P, rf, bc, zc, blockIdx.x, tsh);
 }
 
@@ -586,7 +586,7 @@ bool transfer_gather_supported(const TransferParams<T>& p) {
 template <typename T>
 cudaError_t launch_prolongate(const TransferParams<T>& p, const T* yc, T* xf, cudaStream_t st) {
   if (p.variant == 2 && transfer_gather_supported(p)) {
-    const long long tot = 2LL * p.Gf * p.Gf + (long long)p.nf * p.nf * p.npmf;
+    const long long tot = prolongate_g_items(p);
     const unsigned blocks = (unsigned)((tot + 255) / 256);
 #define STMG_PG(F, C, H) \
     if (p.npf == F && p.npc == C && p.h_type == H) { \

@@ -429,18 +429,22 @@ __device__ __forceinline__ T pres_map(const TransferParams<T>& P, int o, int mf,
   return T(1);
 }
 
-// threads of the prolongation: (component, fine node) for the velocity, then (fine cell,
-// fine mode) for the pressure; total 2 Gf^2 + nf^2 npmf
+// threads of the prolongation: one per fine node for the velocity (both components), then
+// one per (fine cell, fine mode) for the pressure
+template <typename T>
+__host__ __device__ __forceinline__ long long prolongate_g_items(const TransferParams<T>& P) {
+  return (long long)P.Gf * P.Gf + (long long)P.nf * P.nf * P.npmf;
+}
+
 template <typename T, int NPF, int NPC, int HT, bool CG>
 __device__ __forceinline__ void prolongate_g_thread(const TransferParams<T>& P, const T* __restrict__ yc,
                                                     T* __restrict__ xf, long long t) {
   constexpr int NS = HT ? 2 * (NPF - 1) + 1 : NPF;
   const int Gf = P.Gf, Gc = P.Gc, nc = P.nc, ktc = P.ktc, ktf = P.ktf;
-  const long long nvt = 2LL * Gf * Gf;                        // (component, fine node)
+  const long long nvt = (long long)Gf * Gf;                   // fine nodes, both components each
   if (t < nvt) {
-    const int comp = (int)(t / ((long long)Gf * Gf));
-    const int g = (int)(t - (long long)comp * Gf * Gf);
-    const int gx = g % Gf, gy = g / Gf;
+    const int g = (int)t;
+    const int gy = g / Gf, gx = g - gy * Gf;
     if (gx == 0 || gx == Gf - 1 || gy == 0 || gy == Gf - 1) return;
     const int cx = min(gx / (NS - 1), nc - 1), cy = min(gy / (NS - 1), nc - 1);
     const int sx = gx - cx * (NS - 1), sy = gy - cy * (NS - 1);
@@ -454,34 +458,53 @@ __device__ __forceinline__ void prolongate_g_thread(const TransferParams<T>& P, 
       dx[j] = Jx == 0 || Jx == Gc - 1;
       dy[j] = Jy == 0 || Jy == Gc - 1;
     }
-    T s[MAXKT];
+    // the coarse values of both components share the addresses (offset nnc): one address,
+    // two loads
+    const long long cbase = (long long)(cy * (NPC - 1)) * Gc + cx * (NPC - 1);
+    T s0[MAXKT], s1[MAXKT];
 #pragma unroll
     for (int ac = 0; ac < MAXKT; ++ac) {
-      s[ac] = T(0);
+      s0[ac] = T(0);
+      s1[ac] = T(0);
       if (ac < ktc) {
-        const T* yv = yc + ac * P.nvc + comp * P.nnc + (long long)(cy * (NPC - 1)) * Gc + cx * (NPC - 1);
-        T a = 0;
+        const T* yv = yc + ac * P.nvc + cbase;
+        T a0 = 0, a1 = 0;
 #pragma unroll
         for (int jy = 0; jy < NPC; ++jy) {
-          T row = 0;
+          T row0 = 0, row1 = 0;
 #pragma unroll
-          for (int jx = 0; jx < NPC; ++jx) row += wx[jx] * ((dx[jx] || dy[jy]) ? T(0) : ldv<CG>(yv + jy * Gc + jx));
-          a += wy[jy] * row;
+          for (int jx = 0; jx < NPC; ++jx) {
+            const bool z = dx[jx] || dy[jy];
+            const T* q = yv + jy * Gc + jx;
+            row0 += wx[jx] * (z ? T(0) : ldv<CG>(q));
+            row1 += wx[jx] * (z ? T(0) : ldv<CG>(q + P.nnc));
+          }
+          a0 += wy[jy] * row0;
+          a1 += wy[jy] * row1;
         }
-        s[ac] = a;
+        s0[ac] = a0;
+        s1[ac] = a1;
       }
     }
-    T old[MAXKT];                                     // the fine values first, all at once
+    T old0[MAXKT], old1[MAXKT];                       // the fine values first, all at once
 #pragma unroll
-    for (int af = 0; af < MAXKT; ++af) old[af] = af < ktf ? ldv<CG>(xf + af * P.nvf + comp * P.nnf + g) : T(0);
+    for (int af = 0; af < MAXKT; ++af) {
+      old0[af] = af < ktf ? ldv<CG>(xf + af * P.nvf + g) : T(0);
+      old1[af] = af < ktf ? ldv<CG>(xf + af * P.nvf + P.nnf + g) : T(0);
+    }
 #pragma unroll
     for (int af = 0; af < MAXKT; ++af) {
       if (af < ktf) {
-        T o = 0;
+        T o0 = 0, o1 = 0;
 #pragma unroll
         for (int ac = 0; ac < MAXKT; ++ac)
-          if (ac < ktc) o += P.Pt[af * MAXKT + ac] * s[ac];
-        xf[af * P.nvf + comp * P.nnf + g] = old[af] + o;
+          if (ac < ktc) {
+            const T pt = P.Pt[af * MAXKT + ac];
+            o0 += pt * s0[ac];
+            o1 += pt * s1[ac];
+          }
+        xf[af * P.nvf + g] = old0[af] + o0;
+        xf[af * P.nvf + P.nnf + g] = old1[af] + o1;
       }
     }
     return;
@@ -549,12 +572,13 @@ __device__ __forceinline__ void support_1d(const TransferParams<T>& P, int J, in
   }
 }
 
-// blocks of the restriction (256 threads): the velocity blocks first, threads (coarse node,
-// component, fine temporal dof), the latter fastest, meeting in tsh[256] for the temporal
-// restriction; then one thread per (coarse cell, coarse mode, coarse temporal dof).
+// blocks of the restriction (256 threads): the velocity blocks first, one thread per
+// (coarse node, fine temporal dof), the latter fastest, both components per thread (the
+// two share every address), meeting in tsh[512] for the temporal restriction; then one
+// thread per (coarse cell, coarse mode, coarse temporal dof).
 template <typename T>
 __host__ __device__ __forceinline__ long long restrict_g_velocity_blocks(const TransferParams<T>& P) {
-  const int npb = 256 / (2 * P.ktf);
+  const int npb = 256 / P.ktf;
   return ((long long)P.Gc * P.Gc + npb - 1) / npb;
 }
 
@@ -564,54 +588,70 @@ __host__ __device__ __forceinline__ long long restrict_g_blocks(const TransferPa
   return restrict_g_velocity_blocks(P) + (npt + 255) / 256;
 }
 
+// tsh: 512 values of shared memory
 template <typename T, int NPF, int NPC, int HT, bool CG>
 __device__ __forceinline__ void restrict_g_block(const TransferParams<T>& P, const T* __restrict__ rf,
                                                  T* __restrict__ bc, T* __restrict__ zc, long long vb, T* tsh) {
   constexpr int NS = HT ? 2 * (NPF - 1) + 1 : NPF;
   constexpr int BX = 2 * (NS - 1) + 1;
   const int Gf = P.Gf, Gc = P.Gc, ktc = P.ktc, ktf = P.ktf;
-  const int per = 2 * ktf;                                     // threads per coarse node
-  const int npb = 256 / per;                                   // coarse nodes per block
+  const int npb = 256 / ktf;                                   // coarse nodes per block
   const long long nnodes = (long long)Gc * Gc;
   const long long nvb = restrict_g_velocity_blocks(P);
   if (vb < nvb) {
-    const int nl = threadIdx.x / per, rr = threadIdx.x - nl * per;
-    const int comp = rr / ktf, af = rr - comp * ktf;
+    const int nl = threadIdx.x / ktf, af = threadIdx.x - nl * ktf;
     const long long Gi = vb * (long long)npb + nl;
     const bool active = nl < npb && Gi < nnodes;
     bool dirc = true;
     if (active) {
       const int Jx = (int)(Gi % Gc), Jy = (int)(Gi / Gc);
       dirc = Jx == 0 || Jx == Gc - 1 || Jy == 0 || Jy == Gc - 1;
-      T acc = 0;
+      T acc0 = 0, acc1 = 0;
       if (!dirc) {
         int ix0, nx, iy0, ny;
         T wx[BX], wy[BX];
         support_1d<T, NPC, NS, BX>(P, Jx, &ix0, &nx, wx);
         support_1d<T, NPC, NS, BX>(P, Jy, &iy0, &ny, wy);
+        (void)nx; (void)ny;
         // every load unconditional (indices clamped into the grid, weights 0 outside the
         // support), so that all of them are in flight at once
-        const T* r = rf + af * P.nvf + comp * P.nnf;
-        (void)nx; (void)ny;
+        int col[BX];
+#pragma unroll
+        for (int mx = 0; mx < BX; ++mx) col[mx] = min(ix0 + mx, Gf - 1);
+        const T* r0 = rf + af * P.nvf;
+        const T* r1 = r0 + P.nnf;
 #pragma unroll
         for (int my = 0; my < BX; ++my) {
-          const long long iy = min(iy0 + my, Gf - 1);
-          T row = 0;
+          const long long ro = (long long)min(iy0 + my, Gf - 1) * Gf;
+          T row0 = 0, row1 = 0;
 #pragma unroll
-          for (int mx = 0; mx < BX; ++mx) row += wx[mx] * ldv<CG>(r + iy * Gf + min(ix0 + mx, Gf - 1));
-          acc += wy[my] * row;
+          for (int mx = 0; mx < BX; ++mx) {
+            row0 += wx[mx] * ldv<CG>(r0 + ro + col[mx]);
+            row1 += wx[mx] * ldv<CG>(r1 + ro + col[mx]);
+          }
+          acc0 += wy[my] * row0;
+          acc1 += wy[my] * row1;
         }
       }
-      tsh[threadIdx.x] = acc;
+      tsh[2 * threadIdx.x] = acc0;
+      tsh[2 * threadIdx.x + 1] = acc1;
     }
     __syncthreads();
     if (active && af < ktc) {
       const int a = af;
-      T o = 0;
+      T o0 = 0, o1 = 0;
       if (!dirc)
-        for (int f = 0; f < ktf; ++f) o += P.Pt[f * MAXKT + a] * tsh[nl * per + comp * ktf + f];
-      bc[a * P.nvc + comp * P.nnc + Gi] = o;
-      if (zc) zc[a * P.nvc + comp * P.nnc + Gi] = T(0);
+        for (int f = 0; f < ktf; ++f) {
+          const T pt = P.Pt[f * MAXKT + a];
+          o0 += pt * tsh[2 * (nl * ktf + f)];
+          o1 += pt * tsh[2 * (nl * ktf + f) + 1];
+        }
+      bc[a * P.nvc + Gi] = o0;
+      bc[a * P.nvc + P.nnc + Gi] = o1;
+      if (zc) {
+        zc[a * P.nvc + Gi] = T(0);
+        zc[a * P.nvc + P.nnc + Gi] = T(0);
+      }
     }
     __syncthreads();                                           // tsh is reused by the next block
     return;
