@@ -519,6 +519,11 @@ __device__ __forceinline__ void prolongate_g_thread(const TransferParams<T>& P, 
   const int ccx = HT ? fx / 2 : fx, ccy = HT ? fy / 2 : fy;
   const int o = HT ? ((fx & 1) | ((fy & 1) << 1)) : 0;
   const long long cc = (long long)ccy * nc + ccx;
+  // the child map's coefficients of this thread's fine mode, once (each is a chain of
+  // dependent table reads; they do not depend on the temporal dof)
+  T pm[NPMC];
+#pragma unroll
+  for (int mc = 0; mc < NPMC; ++mc) pm[mc] = pres_map(P, o, mf, mc);
   T u[MAXKT];
 #pragma unroll
   for (int ac = 0; ac < MAXKT; ++ac) {
@@ -528,7 +533,7 @@ __device__ __forceinline__ void prolongate_g_thread(const TransferParams<T>& P, 
     for (int mc = 0; mc < NPMC; ++mc) yv[mc] = ac < ktc ? ldv<CG>(src + mc) : T(0);
     T s = 0;
 #pragma unroll
-    for (int mc = 0; mc < NPMC; ++mc) s += pres_map(P, o, mf, mc) * yv[mc];
+    for (int mc = 0; mc < NPMC; ++mc) s += pm[mc] * yv[mc];
     u[ac] = s;
   }
   T old[MAXKT];
@@ -674,6 +679,13 @@ __device__ __forceinline__ void restrict_g_block(const TransferParams<T>& P, con
     const int fx = HT ? 2 * ccx + (o & 1) : ccx, fy = HT ? 2 * ccy + ((o >> 1) & 1) : ccy;
     fcs[o] = (long long)fy * P.nf + fx;
   }
+  // the child map's coefficients of this thread's coarse mode, once (each is a chain of
+  // dependent table reads; they do not depend on the temporal dof)
+  T pm[nchild][NPMF];
+#pragma unroll
+  for (int o = 0; o < nchild; ++o)
+#pragma unroll
+    for (int mf = 0; mf < NPMF; ++mf) pm[o][mf] = pres_map(P, o, mf, mc);
   // fine temporal dofs in groups of four, every load of a group in flight at once
   T v = 0;
   for (int a0 = 0; a0 < ktf; a0 += 4) {
@@ -693,7 +705,7 @@ __device__ __forceinline__ void restrict_g_block(const TransferParams<T>& P, con
 #pragma unroll
         for (int o = 0; o < nchild; ++o)
 #pragma unroll
-          for (int mf = 0; mf < NPMF; ++mf) u += pres_map(P, o, mf, mc) * rv[q][o][mf];
+          for (int mf = 0; mf < NPMF; ++mf) u += pm[o][mf] * rv[q][o][mf];
         v += P.Pt[(a0 + q) * MAXKT + ac] * u;
       }
     }
