@@ -326,6 +326,15 @@ static int dalloc(T** p, size_t count) {
 
 // with_inverses = false sets up only the operator and the work vectors (the finest level
 // always has FP64 operator data: FGMRES applies S in FP64 whatever the V-cycle precision)
+// the operator kernels enumerate the pressure modes at compile time (mode_exp)
+static bool modes_in_kernel_order(const LevelHost& H) {
+  if ((int)H.modes.size() != H.npm) return false;
+  for (int m = 0; m < H.npm; ++m)
+    for (int k = 0; k < H.dim; ++k)
+      if (H.modes[m][k] != mode_exp(H.dim, H.r, m, k)) return false;
+  return true;
+}
+
 // the register-resident operator forms index the 2D pressure modes by mode_index
 static bool modes_graded_2d(const LevelHost& H) {
   if (H.dim != 2 || (int)H.modes.size() != H.npm) return false;
@@ -1351,6 +1360,7 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
     for (size_t i = 0; i < lv.size(); ++i) {
       LevelDev& L = h->L[i];
       init_level_geometry(&L.H, c.dim, lv[i][0], lv[i][1], lv[i][2], span / lv[i][3], c.nu, lv[i][3]);
+      if (!modes_in_kernel_order(L.H)) return STMG_ERR_ARG;   // host tables and kernels out of step
     }
   } catch (const std::exception&) {
     return STMG_ERR_ARG;

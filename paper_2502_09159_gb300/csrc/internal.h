@@ -74,6 +74,24 @@ constexpr int MAXPM2 = 15;  // pressure modes per cell in 2D, C(4+2, 2)
 // the register-resident operators rely on it)
 __host__ __device__ constexpr int mode_index(int ex, int ey) { return (ex + ey) * (ex + ey + 1) / 2 + ey; }
 
+// exponent k (0: x, 1: y, 2: z) of pressure mode m of degree <= r in the host's mode
+// order: degree s ascending; in 2D (s - j, j) with j ascending, in 3D (s - l - j, j, l)
+// with l, then j ascending.  Called with compile-time arguments it folds to a constant.
+__host__ __device__ constexpr int mode_exp(int dim, int r, int m, int k) {
+  int idx = 0;
+  for (int s = 0; s <= r; ++s) {
+    if (dim == 2) {
+      for (int j = 0; j <= s; ++j, ++idx)
+        if (idx == m) return k == 0 ? s - j : (k == 1 ? j : 0);
+    } else {
+      for (int l = 0; l <= s; ++l)
+        for (int j = 0; j <= s - l; ++j, ++idx)
+          if (idx == m) return k == 0 ? s - l - j : (k == 1 ? j : l);
+    }
+  }
+  return 0;
+}
+
 template <typename T>
 struct ApplyRegParams {
   int n, G, kt, npm;

@@ -47,6 +47,9 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams<T> P, const T* 
                                                int mode) {
   using S = Shape<DIM, NP>;
   constexpr int NQ = S::NQ, NL = S::NL;
+  // pressure modes per cell, C(r + d, d) with r = NP - 2; the host checks that P.npm and
+  // its mode table agree with this count and with mode_exp's order
+  constexpr int NPM = DIM == 2 ? NP * (NP - 1) / 2 : (NP + 1) * NP * (NP - 1) / 6;
   const int kt = P.kt, npm = P.npm, n = P.n, G = P.G;
   const int ncells = DIM == 2 ? n * n : n * n * n;
   const int c0 = blockIdx.x * P.cpb;
@@ -183,7 +186,9 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams<T> P, const T* 
           k1 += P.K1[i * NP + j] * t2[j];
         }
         T bt = 0;
-        for (int m = 0; m < npm; ++m) bt += Fx[P.modes[m][0] * NP + i] * Fy[P.modes[m][1] * NP + iy] * p[m];
+#pragma unroll
+        for (int m = 0; m < NPM; ++m)
+          bt += Fx[mode_exp(2, NP - 2, m, 0) * NP + i] * Fy[mode_exp(2, NP - 2, m, 1) * NP + iy] * p[m];
         YV[base + i] = m1 + be * k1 + P.bscale[a] * bt;
       }
     }
@@ -259,8 +264,10 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams<T> P, const T* 
           k1 += P.K1[i * NP + j] * c2[j];
         }
         T bt = 0;
-        for (int m = 0; m < npm; ++m)
-          bt += Fx[P.modes[m][0] * NP + i] * Fy[P.modes[m][1] * NP + iy] * Fz[P.modes[m][2] * NP + iz] * p[m];
+#pragma unroll
+        for (int m = 0; m < NPM; ++m)
+          bt += Fx[mode_exp(3, NP - 2, m, 0) * NP + i] * Fy[mode_exp(3, NP - 2, m, 1) * NP + iy] *
+                Fz[mode_exp(3, NP - 2, m, 2) * NP + iz] * p[m];
         YV[base + i] = m1 + be * k1 + P.bscale[a] * bt;
       }
     }
