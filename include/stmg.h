@@ -197,11 +197,9 @@ typedef struct {
   int       apply_cells_per_block[2];    /* apply / residual launch shape, per precision     */
   int       transfer_cells_per_block[2]; /* transfers to the next coarser level; 0: the
                                             gather form (one thread per value)           */
-  int       streaming;     /* 1: the sweep reads the stored inverses with evict-first loads.
-                              Counted from the coarse end, the levels whose FP32 inverses
-                              (with everything coarser, the coarse inverse's FP32 copy
-                              included) fit in 85 % of L2 read normally and stay
-                              L2-resident; the finer levels stream theirs past them      */
+  int       streaming;     /* 1: the sweep reads the stored inverses with evict-first loads
+                              (inverses larger than about a third of L2), so that the
+                              coarser levels' inverses stay L2-resident                   */
   int       apply_variant[2]; /* per precision: 1 = one thread block per group of cells
                                  (apply_cells_per_block), 2 = node-centred 2D form on tiles
                                  of apply_tile cells (no atomics), 3 = register-resident

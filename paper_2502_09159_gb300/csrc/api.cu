@@ -1399,6 +1399,8 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
       CK(cudaMemcpy(d_cls, H.class_inv.data(), sizeof(double) * H.class_inv.size(), cudaMemcpyHostToDevice));
       CKS(dalloc(&d_cls_of, H.patch_class.size()));
       CK(cudaMemcpy(d_cls_of, H.patch_class.data(), sizeof(int) * H.patch_class.size(), cudaMemcpyHostToDevice));
+      const double inv_bytes = (double)H.n_patches * H.B * H.Bc * 4.0;
+      L.streaming = inv_bytes > 48e6 ? 1 : 0;
       for (int w = 0; w < 2; ++w) {
         L.ppb[w] = std::max(1, std::min(8, 1024 / H.B));
         L.sweep_var[w] = c.sweep_variant == 2 ? 2 : 1;
@@ -1441,24 +1443,6 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
     if (c.transfer_variant == 2) {
       if (transfer_gather_supported(h->L[i].d.tp)) h->L[i].d.tp.variant = 2;
       if (transfer_gather_supported(h->L[i].f.tp)) h->L[i].f.tp.variant = 2;
-    }
-  }
-  // evict-first reads of the patch inverses: from the coarse end, the levels whose FP32
-  // inverses (with the coarse inverse's FP32 copy and everything coarser) fit in 85 % of L2
-  // read theirs normally, so that they stay L2-resident between V-cycles; the finer
-  // levels stream theirs evict-first past them
-  {
-    int l2 = 0, dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
-        l2 <= 0)
-      l2 = 96 << 20;
-    double held = h->L.back().Gf ? 4.0 * (double)h->L.back().H.size * h->L.back().H.size : 0.0;
-    bool fits = true;
-    for (int i = (int)h->L.size() - 2; i >= 0; --i) {
-      LevelDev& L = h->L[i];
-      held += (double)L.H.n_patches * L.H.B * L.H.Bc * 4.0;
-      fits = fits && held <= 0.85 * l2;
-      L.streaming = fits ? 0 : 1;
     }
   }
   const char* cache = std::getenv("STMG_TUNE_CACHE");
