@@ -194,7 +194,10 @@ typedef struct {
   long long inverse_bytes[2]; /* stored patch-inverse bytes for FP64 / FP32 (0: none)    */
   int       sweep_variant[2];            /* per precision: 1 block, 2 TMA, 3 pipelined block */
   int       patches_per_block[2];        /* block sweep launch shape, per precision          */
-  int       apply_cells_per_block[2];    /* apply / residual launch shape, per precision     */
+  int       apply_cells_per_block[2];    /* apply / residual launch shape, per precision:
+                                            cells per block (apply_variant 1), threads
+                                            per block (3: 64, or fewer so that every SM
+                                            gets the same number of items)           */
   int       transfer_cells_per_block[2]; /* transfers to the next coarser level; 0: the
                                             gather form (one thread per value)           */
   int       streaming;     /* 1: the sweep reads the stored inverses with evict-first loads

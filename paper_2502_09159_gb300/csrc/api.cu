@@ -363,6 +363,7 @@ static int setup_precision(stmg_handle* h, LevelDev& lv, const double* d_cls, co
     P.ap.variant = 4;                    // its pair-split form, on request
   else if (reg_form_ok<T>(H) && (av == 0 || av == 3 || av == 4))
     P.ap.variant = 3;                    // register-resident form where the cell tile fits
+  if (P.ap.variant >= 3) P.ap.cpb = 64;  // threads per block of the register forms (tuned later)
   CKS(dalloc(&P.b, H.size));
   CKS(dalloc(&P.x, H.size));
   CKS(dalloc(&P.r, H.size));
@@ -416,7 +417,7 @@ static int op_apply(stmg_handle* h, int l, const T* x, const T* b, T* y, int mod
     CK(launch_apply2d<T>(lv.H.np, ap, x, b, y, mode, s));
   } else if (ap.variant == 3) {          // scatter-adds every row
     CK(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)lv.H.size, s));
-    CK(launch_apply2d_reg<T>(lv.H.np, lv.pd<T>().rp, x, b, y, mode, s));
+    CK(launch_apply2d_reg<T>(lv.H.np, lv.pd<T>().rp, x, b, y, mode, ap.cpb >= 16 ? ap.cpb : 64, s));
   } else if (ap.variant == 4) {          // scatter-adds every row
     CK(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)lv.H.size, s));
     CK(launch_apply2d_pair<T>(lv.H.np, lv.pd<T>().rp, x, b, y, mode, s));
@@ -644,9 +645,19 @@ static int autotune_level(stmg_handle* h, int l) {
     }
     const bool pair = pair_form_ok<T>(lv.H);
     if ((fixed == 0 || fixed == 3 || (fixed == 4 && !pair)) && reg_form_ok<T>(lv.H)) {
-      P.ap.variant = 3;                  // register-resident form (no launch-shape parameter)
-      CKS(time_it(h, [&]() { return op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, h->st); }, &ms));
-      if (ms < best) { best = ms; best_var = 3; }
+      // register-resident form: 64 threads per block, or the block size that gives every
+      // SM the same number of items (k or k + 1 blocks per SM)
+      P.ap.variant = 3;
+      const long long items = (long long)lv.H.n * lv.H.n * lv.H.kt * 2;
+      const long long per = (items + 64LL * h->n_sm - 1) / (64LL * h->n_sm);   // blocks per SM at 64
+      int sizes[3] = {64, (int)((items + h->n_sm * per - 1) / (h->n_sm * per)),
+                      (int)((items + h->n_sm * (per + 1) - 1) / (h->n_sm * (per + 1)))};
+      for (int bs : sizes) {
+        if (bs < 16 || bs > 64) continue;
+        P.ap.cpb = bs;                   // the block size of this form
+        CKS(time_it(h, [&]() { return op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, h->st); }, &ms));
+        if (ms < best) { best = ms; best_var = 3; best_cpb = bs; }
+      }
     }
     if ((fixed == 0 || fixed == 4) && pair) {
       P.ap.variant = 4;                  // its pair-split form
@@ -895,7 +906,9 @@ static int run_vcycle(stmg_handle* h) {
 }
 
 // z = M v (FP64 in and out) with the V-cycle in precision prec
-static int precondition(stmg_handle* h, int prec, const double* v, double* z) {
+// ready: the FP32 V-cycle's b (= (float) v) and zero x are already in place (written by
+// the Arnoldi step that produced v)
+static int precondition(stmg_handle* h, int prec, const double* v, double* z, bool ready = false) {
   LevelDev& l0 = h->L[0];
   const long long D = l0.H.size;
   Prof pr(h, PROF_VCYCLE, h->st);
@@ -907,10 +920,13 @@ static int precondition(stmg_handle* h, int prec, const double* v, double* z) {
     h->launches += 1;
   } else {
     if (!l0.f.b) return STMG_ERR_ARG;
-    CK((launch_convert_zero<double, float>(D, v, l0.f.b, l0.f.x, h->st)));    // b = (float) v, x = 0
+    if (!ready) {
+      CK((launch_convert_zero<double, float>(D, v, l0.f.b, l0.f.x, h->st)));  // b = (float) v, x = 0
+      h->launches += 1;
+    }
     CKS(run_vcycle<float>(h));
     CK((launch_convert<float, double>(D, l0.f.x, z, h->st)));
-    h->launches += 2;
+    h->launches += 1;
   }
   return STMG_OK;
 }
@@ -1027,10 +1043,13 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
   // iteration j converges (the residual estimate falls by a steady factor per iteration;
   // a wrong "not yet" costs one iteration of device work that is discarded, a wrong
   // "converged" one host round trip).  With profiling on, iterations are not overlapped.
+  // ready32[jj]: the Arnoldi step that produced v_jj also wrote the FP32 V-cycle's inputs
+  std::vector<char> ready32(m + 1, 0);
+  const bool fuse32 = prec == STMG_FP32 && l0.f.b;
   auto enqueue_iteration = [&](int jj) -> int {
     double* vj = h->V + (size_t)jj * D;
     double* zj = h->Z + (size_t)jj * D;
-    CKS(precondition(h, prec, vj, zj));
+    CKS(precondition(h, prec, vj, zj, ready32[jj] != 0));
     {
       Prof pr(h, STMG_PROF_OPERATOR, s);
       CKS(op_apply<double>(h, 0, zj, nullptr, h->w, APPLY, s));
@@ -1038,8 +1057,11 @@ static int solve_impl(stmg_handle* h, const double* b, double* x, stmg_solve_inf
     if (h->cgs_blocks > 0 && jj + 1 <= cgs2_max_vectors()) {
       Prof pr(h, STMG_PROF_OTHER, s);
       // CGS2 and the normalisation of the next basis vector in one cooperative launch
-      CK(launch_cgs2(D, jj + 1, h->V, D, h->w, h->cgs_part, h->hcol, h->V + (size_t)(jj + 1) * D, h->cgs_bar,
-                     h->d_err, h->cgs_blocks, h->cfg.arnoldi_form == 0, s));
+      bool wrote = false;
+      CK(launch_cgs2(D, jj + 1, h->V, D, h->w, h->cgs_part, h->hcol, h->V + (size_t)(jj + 1) * D,
+                     fuse32 ? l0.f.b : nullptr, fuse32 ? l0.f.x : nullptr, &wrote, h->cgs_bar, h->d_err,
+                     h->cgs_blocks, h->cfg.arnoldi_form == 0, s));
+      ready32[jj + 1] = wrote ? 1 : 0;
       h->launches += 1;
     } else {
       Prof pr(h, STMG_PROF_OTHER, s);

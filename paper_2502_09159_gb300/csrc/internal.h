@@ -167,9 +167,9 @@ cudaError_t launch_apply(int dim, int np, const ApplyParams<T>& p, const T* x, c
 template <typename T>
 size_t apply_smem_bytes(int dim, int np, int kt, int npm, int cpb);
 // register-resident form on 2D levels (k_apply2d_reg.cu), kt <= 4: y must be zero on entry
-// (every row is scatter-added)
+// (every row is scatter-added); bs threads per block (1..64, else 64)
 template <typename T>
-cudaError_t launch_apply2d_reg(int np, const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode,
+cudaError_t launch_apply2d_reg(int np, const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode, int bs,
                                cudaStream_t st);
 template <typename T>
 bool apply2d_reg_supported(int np, int kt, int npm);
@@ -262,9 +262,12 @@ cudaError_t launch_sqrt_inplace(double* v, cudaStream_t st);
 
 int multidot_blocks(long long n);
 // one CGS2 Arnoldi step in a cooperative launch (see k_vec.cu); bar: 2 zeroed unsigned
-// reg: take the register-resident form where it fits (nv <= 16, at most 2048 rows per block)
+// reg: take the register-resident form where it fits (nv <= 16, at most 2048 rows per block).
+// vnext32, zero32 (optional): the register form also writes (float) vnext and zeroes
+// zero32; *wrote32 says whether it did
 cudaError_t launch_cgs2(long long n, int nv, const double* V, long long ld, double* w, double* partial, double* hcol,
-                        double* vnext, unsigned* bar, int* err, int nblocks, bool reg, cudaStream_t st);
+                        double* vnext, float* vnext32, float* zero32, bool* wrote32, unsigned* bar, int* err,
+                        int nblocks, bool reg, cudaStream_t st);
 int cgs2_blocks(int n_sm);       // co-resident blocks to launch (0: not available)
 int cgs2_max_vectors();
 int cgs2_scratch(int nblocks);   // doubles of partial-sum scratch for nblocks

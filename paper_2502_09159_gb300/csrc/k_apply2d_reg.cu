@@ -31,11 +31,14 @@ __global__ void __launch_bounds__(64) k_apply2d_reg(const ApplyRegParams<T> P, c
 }
 
 template <typename T, int NP, int KT>
-static cudaError_t launch_apply2d_reg_t(const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode,
+static cudaError_t launch_apply2d_reg_t(const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode, int bs,
                                         cudaStream_t st) {
   const long long tot = (long long)p.n * p.n * KT * 2;      // (cell, temporal dof, component)
-  const unsigned blocks = (unsigned)((tot + 63) / 64);      // small blocks: the finest levels have few cells
-  k_apply2d_reg<T, NP, KT><<<blocks, 64, 0, st>>>(p, x, b, y, mode);
+  // small blocks (the finest levels have few cells); bs < 64 spreads the items evenly
+  // over the SMs when 64 does not divide them into equal shares
+  const int threads = bs >= 1 && bs <= 64 ? bs : 64;
+  const unsigned blocks = (unsigned)((tot + threads - 1) / threads);
+  k_apply2d_reg<T, NP, KT><<<blocks, threads, 0, st>>>(p, x, b, y, mode);
   return cudaGetLastError();
 }
 
@@ -47,10 +50,10 @@ bool apply2d_reg_supported(int np, int kt, int npm) {
 }
 
 template <typename T>
-cudaError_t launch_apply2d_reg(int np, const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode,
+cudaError_t launch_apply2d_reg(int np, const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode, int bs,
                                cudaStream_t st) {
 #define STMG_R2(N, K) \
-  if (np == N && p.kt == K) return launch_apply2d_reg_t<T, N, K>(p, x, b, y, mode, st);
+  if (np == N && p.kt == K) return launch_apply2d_reg_t<T, N, K>(p, x, b, y, mode, bs, st);
   if (!apply2d_reg_supported<T>(np, p.kt, p.npm)) return cudaErrorInvalidValue;
   STMG_R2(3, 1) STMG_R2(3, 2) STMG_R2(3, 3) STMG_R2(3, 4)
   STMG_R2(4, 1) STMG_R2(4, 2) STMG_R2(4, 3) STMG_R2(4, 4)
@@ -104,9 +107,9 @@ template bool apply2d_pair_supported<double>(int, int, int);
 template bool apply2d_pair_supported<float>(int, int, int);
 
 template cudaError_t launch_apply2d_reg<double>(int, const ApplyRegParams<double>&, const double*, const double*,
-                                                double*, int, cudaStream_t);
+                                                double*, int, int, cudaStream_t);
 template cudaError_t launch_apply2d_reg<float>(int, const ApplyRegParams<float>&, const float*, const float*, float*,
-                                               int, cudaStream_t);
+                                               int, int, cudaStream_t);
 template bool apply2d_reg_supported<double>(int, int, int);
 template bool apply2d_reg_supported<float>(int, int, int);
 

@@ -436,6 +436,7 @@ template <int NV>
 __global__ void __launch_bounds__(CGS_THREADS) k_cgs2r(long long n, const double* __restrict__ V, long long ld,
                                                      const double* __restrict__ w, double* __restrict__ part,
                                                      double* __restrict__ hcol, double* __restrict__ vnext,
+                                                     float* __restrict__ vnext32, float* __restrict__ zero32,
                                                      unsigned* bar, int* err) {
   constexpr int U = NV <= 8 ? 4 : (NV <= 11 ? 2 : 1);   // rows whose V values are loaded together
   static_assert(CGS_RPT % U == 0, "row groups must tile the thread's rows");
@@ -535,7 +536,14 @@ __global__ void __launch_bounds__(CGS_THREADS) k_cgs2r(long long n, const double
         s0 += h2[i] * vv[u][i];
         if (i + 1 < NV) s1 += h2[i + 1] * vv[u][i + 1];
       }
-      if (in[u0 + u]) vnext[row[u0 + u]] = (wr[u0 + u] - (s0 + s1)) * inv;
+      if (in[u0 + u]) {
+        const double v = (wr[u0 + u] - (s0 + s1)) * inv;
+        vnext[row[u0 + u]] = v;
+        if (vnext32) {                  // the next FP32 V-cycle's right-hand side and zero iterate
+          vnext32[row[u0 + u]] = (float)v;
+          zero32[row[u0 + u]] = 0.0f;
+        }
+      }
     }
   }
 }
@@ -557,11 +565,14 @@ int cgs2_scratch(int nblocks) { return 3 * nblocks * CGS_MAXV; }
 int cgs2_max_vectors() { return CGS_MAXV; }
 
 cudaError_t launch_cgs2(long long n, int nv, const double* V, long long ld, double* w, double* partial, double* hcol,
-                        double* vnext, unsigned* bar, int* err, int nblocks, bool reg, cudaStream_t st) {
+                        double* vnext, float* vnext32, float* zero32, bool* wrote32, unsigned* bar, int* err,
+                        int nblocks, bool reg, cudaStream_t st) {
   if (nv < 1 || nv > CGS_MAXV || nblocks < 1) return cudaErrorInvalidValue;
+  if (wrote32) *wrote32 = false;
   if (reg && cgs2_reg_ok(n, nv, nblocks)) {
     const double* wc = w;
-    void* args[] = {&n, &V, &ld, &wc, &partial, &hcol, &vnext, &bar, &err};
+    if (wrote32) *wrote32 = vnext32 != nullptr;
+    void* args[] = {&n, &V, &ld, &wc, &partial, &hcol, &vnext, &vnext32, &zero32, &bar, &err};
     return cudaLaunchCooperativeKernel(CgsRegTable::fn[nv - 1], dim3(nblocks), dim3(CGS_THREADS), args, 0, st);
   }
   void* args[] = {&n, &nv, &V, &ld, &w, &partial, &hcol, &vnext, &bar, &err};
