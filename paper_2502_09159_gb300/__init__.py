@@ -52,7 +52,7 @@ class SpaceTimeMG:
                  sweep_variant: int = 0, autotune: bool = True, coarse_n: int = 1, k_min: int = 1,
                  n_sub: int = 1, half_inverses: bool = False, transfer_variant: int = 0,
                  apply_variant: int = 0, persistent: int = 1, time_h: bool = False,
-                 arnoldi_form: int = 0):
+                 arnoldi_form: int = 0, fuse_transfers: bool = True):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("SpaceTimeMG needs a CUDA device (no CPU fallback)")
@@ -85,6 +85,7 @@ class SpaceTimeMG:
         cfg.persistent = int(persistent)
         cfg.time_h = int(time_h)
         cfg.arnoldi_form = int(arnoldi_form)
+        cfg.fuse_transfers = int(fuse_transfers)
         self.cfg = cfg
         self.dim, self.r, self.k, self.n_sub = dim, r, k, int(n_sub)
         self.kt = self.n_sub * (k + 1)

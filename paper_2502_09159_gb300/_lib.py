@@ -26,7 +26,7 @@ class Config(C.Structure):
                 ("sweep_variant", C.c_int), ("autotune", C.c_int), ("coarse_n", C.c_int),
                 ("k_min", C.c_int), ("n_sub", C.c_int), ("half_inverses", C.c_int),
                 ("transfer_variant", C.c_int), ("apply_variant", C.c_int), ("persistent", C.c_int),
-                ("level_nsub", C.c_int * MAX_LEVELS), ("time_h", C.c_int), ("arnoldi_form", C.c_int)]
+                ("level_nsub", C.c_int * MAX_LEVELS), ("time_h", C.c_int), ("arnoldi_form", C.c_int), ("fuse_transfers", C.c_int)]
 
 
 class LevelInfo(C.Structure):

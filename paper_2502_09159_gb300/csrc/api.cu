@@ -26,6 +26,7 @@ struct PrecDev {
   T* b = nullptr;     // V-cycle right-hand side of this level
   T* x = nullptr;     // V-cycle iterate of this level
   T* r = nullptr;     // residual work vector
+  T* x2 = nullptr;    // FP32, 2D: the iterate after the prolongation fused into the residual
   ApplyParams<T> ap{};
   ApplyRegParams<T> rp{};   // tables of the register-resident 2D operator (apply variant 3)
   TransferParams<T> tp{};   // transfer between this level and the next coarser one
@@ -367,6 +368,7 @@ static int setup_precision(stmg_handle* h, LevelDev& lv, const double* d_cls, co
   CKS(dalloc(&P.b, H.size));
   CKS(dalloc(&P.x, H.size));
   CKS(dalloc(&P.r, H.size));
+  if (std::is_same<T, float>::value && H.dim == 2) CKS(dalloc(&P.x2, H.size));
   if (H.smoother >= 0 && with_inverses) {
     // omega / valence per dof (FP64), folded into the rows of every stored inverse
     std::vector<double> w(H.size, 0.0);
@@ -402,7 +404,7 @@ static void free_level(LevelDev& lv) {
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(lv.dofs); f(lv.G); f(lv.Gacc); f(lv.Gf);
   f(lv.d.inv); f(lv.d.b); f(lv.d.x); f(lv.d.r); f(lv.f.invh); f(lv.f.rsc);
-  f(lv.f.inv); f(lv.f.b); f(lv.f.x); f(lv.f.r);
+  f(lv.f.inv); f(lv.f.b); f(lv.f.x); f(lv.f.r); f(lv.f.x2); f(lv.d.x2);
   lv = LevelDev();
 }
 
@@ -825,7 +827,30 @@ static int autotune_impl(stmg_handle* h) {
   return STMG_OK;
 }
 
-// V-cycle on level l: input L[l].b, output L[l].x from the zero initial guess, Alg. 1.
+// Whether level l's post-smoothing residual takes the coarser level's correction through
+// the fused kernel (prolongation and residual in one launch, the result in x2): FP32, a 2D
+// register-resident level with a transfer shape the fused kernel covers, not inside the
+// persistent multigrid kernel.
+template <typename T>
+static bool fused_up(const stmg_handle* h, int l) {
+  if (!std::is_same<T, float>::value || !h->cfg.fuse_transfers || h->cfg.nu2 < 1) return false;
+  if (l + 1 >= (int)h->L.size()) return false;
+  const int w = prec_of<T>();
+  if (h->mgp_first[w] > 0 && l >= h->mgp_first[w]) return false;
+  const LevelDev& lv = h->L[l];
+  const PrecDev<float>& P = lv.f;
+  return P.x2 && reg_form_ok<float>(lv.H) &&
+         apply2d_reg_pro_supported(lv.H.np, lv.H.kt, lv.H.npm, P.tp.npc, P.tp.h_type, P.tp.ktc);
+}
+
+// where level l's V-cycle leaves its iterate
+template <typename T>
+static T* final_x(stmg_handle* h, int l) {
+  PrecDev<T>& P = h->L[l].pd<T>();
+  return fused_up<T>(h, l) ? P.x2 : P.x;
+}
+
+// V-cycle on level l: input L[l].b, output final_x(l) from the zero initial guess, Alg. 1.
 // L[l].x must be zero on entry: on the finest level the caller zeroes it (with the
 // conversion of the right-hand side), on the coarser ones the restriction does.
 template <typename T>
@@ -857,10 +882,27 @@ static int vcycle_level(stmg_handle* h, int l, cudaStream_t s) {
   PrecDev<T>& C = h->L[l + 1].pd<T>();
   CKS(op_restrict<T>(h, l, res, C.b, s, C.x));       // step 2/3 of Alg. 4 / 5; C.x = 0
   CKS(vcycle_level<T>(h, l + 1, s));
-  CKS(op_prolongate_add<T>(h, l, C.x, P.x, s));      // Alg. 6 / 7
-  for (int it = 0; it < h->cfg.nu2; ++it) {          // postsmoothing (Eq. Alg:VGMGPost)
-    CKS(op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, s));
-    CKS(op_sweep<T>(h, l, P.r, P.x, s));
+  const T* ec = final_x<T>(h, l + 1);
+  T* xu = P.x;
+  int it0 = 0;
+  if (fused_up<T>(h, l)) {
+    // x2 = x + P ec and r = b - S x2 in one launch (Alg. 6 / 7 and the first
+    // postsmoothing residual); the postsmoothing then updates x2
+    LevelDev& lf = h->L[l];
+    CK(cudaMemsetAsync(P.r, 0, sizeof(T) * (size_t)lf.H.size, s));
+    CK(launch_apply2d_reg_pro(lf.H.np, lf.f.rp, lf.f.tp, (const float*)P.x, (const float*)ec, (const float*)P.b,
+                              (float*)P.r, (float*)P.x2, lf.f.ap.variant == 3 && lf.f.ap.cpb >= 16 ? lf.f.ap.cpb : 64,
+                              s));
+    h->launches += 1;
+    xu = P.x2;
+    CKS(op_sweep<T>(h, l, P.r, xu, s));
+    it0 = 1;
+  } else {
+    CKS(op_prolongate_add<T>(h, l, ec, P.x, s));     // Alg. 6 / 7
+  }
+  for (int it = it0; it < h->cfg.nu2; ++it) {        // postsmoothing (Eq. Alg:VGMGPost)
+    CKS(op_apply<T>(h, l, xu, P.b, P.r, RESIDUAL, s));
+    CKS(op_sweep<T>(h, l, P.r, xu, s));
   }
   return STMG_OK;
 }
@@ -925,7 +967,7 @@ static int precondition(stmg_handle* h, int prec, const double* v, double* z, bo
       h->launches += 1;
     }
     CKS(run_vcycle<float>(h));
-    CK((launch_convert<float, double>(D, l0.f.x, z, h->st)));
+    CK((launch_convert<float, double>(D, final_x<float>(h, 0), z, h->st)));
     h->launches += 1;
   }
   return STMG_OK;
@@ -1230,6 +1272,7 @@ int stmg_default_config(stmg_config* c) {
   c->persistent = 1;
   c->time_h = 0;
   c->arnoldi_form = 0;
+  c->fuse_transfers = 1;
   for (int i = 0; i < STMG_MAX_LEVELS; ++i) c->level_nsub[i] = 0;
   return STMG_OK;
 }
@@ -1246,7 +1289,8 @@ static std::string tune_key(const stmg_handle* h) {
   std::string k = "v1 d" + std::to_string(c.dim) + " p" + std::to_string(c.precisions) + " h" +
                   std::to_string(c.half_inverses) + " sv" + std::to_string(c.sweep_variant) + " av" +
                   std::to_string(c.apply_variant) + " tv" + std::to_string(c.transfer_variant) + " pe" +
-                  std::to_string(c.persistent) + " nu" + std::to_string(c.nu1) + std::to_string(c.nu2);
+                  std::to_string(c.persistent) + " nu" + std::to_string(c.nu1) + std::to_string(c.nu2) + " fu" +
+                  std::to_string(c.fuse_transfers);
   for (const auto& L : h->L)
     k += " L" + std::to_string(L.H.n) + "." + std::to_string(L.H.r) + "." + std::to_string(L.H.k) + "." +
          std::to_string(L.H.nsub) + "." + std::to_string(L.H.smoother);
@@ -1343,6 +1387,7 @@ static int create_impl(const stmg_config* cfg, stmg_handle* h) {
   h->tau = c.T / ((double)c.n_slabs * c.n_sub);
   if (c.time_h < 0 || c.time_h > 1) return STMG_ERR_ARG;
   if (c.arnoldi_form < 0 || c.arnoldi_form > 1) return STMG_ERR_ARG;
+  if (c.fuse_transfers < 0 || c.fuse_transfers > 1) return STMG_ERR_ARG;
   // levels (n, r, k, nsub) fine -> coarse; a level of fewer subintervals covers the same
   // system time span T / n_slabs with longer ones (h-coarsening in time, App. A)
   std::vector<std::array<int, 4>> lv;

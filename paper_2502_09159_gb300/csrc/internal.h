@@ -173,6 +173,13 @@ cudaError_t launch_apply2d_reg(int np, const ApplyRegParams<T>& p, const T* x, c
                                cudaStream_t st);
 template <typename T>
 bool apply2d_reg_supported(int np, int kt, int npm);
+// the register-resident residual with the coarser level's correction prolongated on the
+// fly (single precision): x2 = x + P ec, y = b - S x2 (y zero on entry); q = the transfer
+// between the two levels (fine level = this one)
+bool apply2d_reg_pro_supported(int np, int kt, int npm, int npc, int ht, int ktc);
+cudaError_t launch_apply2d_reg_pro(int np, const ApplyRegParams<float>& p, const TransferParams<float>& q,
+                                   const float* x, const float* ec, const float* b, float* y, float* x2, int bs,
+                                   cudaStream_t st);
 // its pair-split form (two lanes per cell item, Q3 only), y zero on entry as well
 template <typename T>
 cudaError_t launch_apply2d_pair(int np, const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode,

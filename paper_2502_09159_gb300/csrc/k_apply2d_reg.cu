@@ -64,6 +64,43 @@ cudaError_t launch_apply2d_reg(int np, const ApplyRegParams<T>& p, const T* x, c
   return cudaErrorInvalidValue;
 }
 
+// residual with the coarser level's correction prolongated on the fly (single precision):
+// x2 = x + P ec, r = b - S x2 (y = r zero on entry); the transfer shapes of the gather form
+// with a register-resident fine level: Q3 <- Q2 on one mesh, Q2 <- Q2 on one mesh or on
+// the mesh of half the cells
+template <int NP, int KT, int NPC, int HT>
+__global__ void __launch_bounds__(64) k_apply2d_reg_pro(const ApplyRegParams<float> P, const TransferParams<float> Q,
+                                                        const float* __restrict__ x, const float* __restrict__ ec,
+                                                        const float* __restrict__ b, float* __restrict__ y,
+                                                        float* __restrict__ x2) {
+  apply2d_reg_thread<float, NP, KT, false, NPC, HT>(P, x, b, y, RESIDUAL, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                                                    &Q, ec, x2);
+}
+
+bool apply2d_reg_pro_supported(int np, int kt, int npm, int npc, int ht, int ktc) {
+  if (!apply2d_reg_supported<float>(np, kt, npm) || ktc > kt) return false;
+  return (np == 4 && npc == 3 && ht == 0) || (np == 3 && npc == 3 && (ht == 0 || ht == 1));
+}
+
+cudaError_t launch_apply2d_reg_pro(int np, const ApplyRegParams<float>& p, const TransferParams<float>& q,
+                                   const float* x, const float* ec, const float* b, float* y, float* x2, int bs,
+                                   cudaStream_t st) {
+  if (!apply2d_reg_pro_supported(np, p.kt, p.npm, q.npc, q.h_type, q.ktc)) return cudaErrorInvalidValue;
+  const long long tot = (long long)p.n * p.n * p.kt * 2;
+  const int threads = bs >= 1 && bs <= 64 ? bs : 64;
+  const unsigned blocks = (unsigned)((tot + threads - 1) / threads);
+#define STMG_PRO(N, K, C, H)                                                                            \
+  if (np == N && p.kt == K && q.npc == C && q.h_type == H) {                                            \
+    k_apply2d_reg_pro<N, K, C, H><<<blocks, threads, 0, st>>>(p, q, x, ec, b, y, x2);                 \
+    return cudaGetLastError();                                                                           \
+  }
+#define STMG_PRO_K(N, C, H) STMG_PRO(N, 1, C, H) STMG_PRO(N, 2, C, H) STMG_PRO(N, 3, C, H) STMG_PRO(N, 4, C, H)
+  STMG_PRO_K(4, 3, 0) STMG_PRO_K(3, 3, 0) STMG_PRO_K(3, 3, 1)
+#undef STMG_PRO_K
+#undef STMG_PRO
+  return cudaErrorInvalidValue;
+}
+
 // pair-split form: two lanes per (cell, temporal dof, component), NP even (Q3 in 2D)
 template <typename T, int NP, int KT>
 __global__ void __launch_bounds__(32) k_apply2d_pair(const ApplyRegParams<T> P, const T* __restrict__ x,

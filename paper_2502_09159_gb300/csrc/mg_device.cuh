@@ -22,6 +22,9 @@ __device__ __forceinline__ T ldv(const T* p) {
   return __ldg(p);
 }
 
+template <typename T>
+__device__ __forceinline__ T pres_map(const TransferParams<T>& P, int o, int mf, int mc);
+
 // ------------------------------------------------------------------------------------
 // Register-resident 2D operator (Sec. 4.5): thread t -> (temporal dof a, velocity
 // component d, cell c), cells fastest, so that a warp covers consecutive cells of one
@@ -29,11 +32,23 @@ __device__ __forceinline__ T ldv(const T* p) {
 // Every row of y is scatter-added (y zero on entry): the velocity rows of component d by
 // the cells holding the node, the pressure rows of a cell by its two component threads
 // (continuity is a sum over the components).
+//
+// With NPC > 0 (single precision, RESIDUAL mode) the thread first prolongates the coarser
+// level's correction ec onto its cell (App. A: the coarse function of NPC x NPC nodes per
+// coarse cell evaluated at the fine nodes, HT = 1 for a coarse cell of 2 x 2 fine cells,
+// combined in time with the temporal map; the pressure through the child map), forms
+// x2 = x + P ec on the fly, computes r = b - S x2 from it, and writes x2 (each velocity
+// node by the thread of its owner cell with a equal to the node's temporal dof, each
+// pressure dof by the d = 0 thread).  x is only read, so the cells sharing a node all see
+// the old value.
 // ------------------------------------------------------------------------------------
-template <typename T, int NP, int KT, bool CG>
+template <typename T, int NP, int KT, bool CG, int NPC = 0, int HT = 0>
 __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, const T* __restrict__ x,
                                                    const T* __restrict__ b, T* __restrict__ y, int mode,
-                                                   long long t) {
+                                                   long long t, const TransferParams<T>* tp = nullptr,
+                                                   const T* __restrict__ ec = nullptr, T* __restrict__ x2 = nullptr) {
+  constexpr bool PRO = NPC > 0;
+  static_assert(!PRO || sizeof(T) == 4, "the fused prolongation is a single-precision path");
   constexpr int E = NP - 1, NQ = NP * NP;
   constexpr int NPM = NP * (NP - 1) / 2;            // C(r + 2, 2) pressure modes, r = NP - 2
   const int n = P.n, G = P.G;
@@ -54,6 +69,70 @@ __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, c
   const T* fx = &P.FX[d][0];                        // [ex * NP + ix]: B_h factor along x of component d
   const T* fy = &P.FY[d][0];                        // [ey * NP + iy]: along y
 
+  // the prolongated coarse correction at this cell's nodes, component d, every temporal dof
+  T pe[PRO ? KT : 1][PRO ? NQ : 1];
+  if constexpr (PRO) {
+    const TransferParams<T>& Q = *tp;
+    const int Gc = Q.Gc, ccx = HT ? cx >> 1 : cx, ccy = HT ? cy >> 1 : cy;
+    const int ox = HT ? (cx & 1) * (NP - 1) : 0, oy = HT ? (cy & 1) * (NP - 1) : 0;
+    T ct[KT][NPC * NPC];                            // coarse nodal values, combined in time
+#pragma unroll
+    for (int bb = 0; bb < KT; ++bb)
+#pragma unroll
+      for (int q = 0; q < NPC * NPC; ++q) ct[bb][q] = 0;
+    const T* src = ec + d * Q.nnc + (long long)(ccy * (NPC - 1)) * Gc + ccx * (NPC - 1);
+#pragma unroll
+    for (int ac = 0; ac < KT; ++ac) {
+      if (ac < Q.ktc) {
+        T cv[NPC * NPC];
+#pragma unroll
+        for (int jy = 0; jy < NPC; ++jy)
+#pragma unroll
+          for (int jx = 0; jx < NPC; ++jx) {
+            const int Jx = ccx * (NPC - 1) + jx, Jy = ccy * (NPC - 1) + jy;
+            const bool dirc = Jx == 0 || Jx == Gc - 1 || Jy == 0 || Jy == Gc - 1;
+            cv[jy * NPC + jx] = dirc ? T(0) : ldv<CG>(src + ac * Q.nvc + (long long)jy * Gc + jx);
+          }
+#pragma unroll
+        for (int bb = 0; bb < KT; ++bb) {
+          const T w = Q.Pt[bb * MAXKT + ac];
+#pragma unroll
+          for (int q = 0; q < NPC * NPC; ++q) ct[bb][q] += w * cv[q];
+        }
+      }
+    }
+    T wx[NP][NPC], wy[NP][NPC];
+#pragma unroll
+    for (int i = 0; i < NP; ++i)
+#pragma unroll
+      for (int j = 0; j < NPC; ++j) {
+        wx[i][j] = Q.P1[(ox + i) * MAXNP + j];
+        wy[i][j] = Q.P1[(oy + i) * MAXNP + j];
+      }
+#pragma unroll
+    for (int bb = 0; bb < KT; ++bb) {
+      T tx[NPC][NP];                                // along x first, then along y
+#pragma unroll
+      for (int jy = 0; jy < NPC; ++jy)
+#pragma unroll
+        for (int ix = 0; ix < NP; ++ix) {
+          T s = 0;
+#pragma unroll
+          for (int jx = 0; jx < NPC; ++jx) s += wx[ix][jx] * ct[bb][jy * NPC + jx];
+          tx[jy][ix] = s;
+        }
+#pragma unroll
+      for (int iy = 0; iy < NP; ++iy)
+#pragma unroll
+        for (int ix = 0; ix < NP; ++ix) {
+          T s = 0;
+#pragma unroll
+          for (int jy = 0; jy < NPC; ++jy) s += wy[iy][jy] * tx[jy][ix];
+          pe[bb][iy * NP + ix] = s;
+        }
+    }
+  }
+
   T ut[NQ], ua[NQ], p[NPM];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) { ut[q] = 0; ua[q] = 0; }
@@ -72,7 +151,12 @@ __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, c
       for (int ix = 0; ix < NP; ++ix) {
         const bool dir = dy || (ix == 0 && bx0) || (ix == E && bx1);
         const bool take = lift ? dir : !dir;
-        const T v = take ? ldv<CG>(xb + iy * G + ix) : T(0);
+        T v = take ? ldv<CG>(xb + iy * G + ix) : T(0);
+        if constexpr (PRO) {
+          if (!dir) v += pe[bb % KT][iy * NP + ix];
+          const bool own = (iy < E || by1) && (ix < E || bx1);
+          if (own && bb == a) x2[bb * nvel + d * nnod + base + iy * G + ix] = dir ? ldv<CG>(xb + iy * G + ix) : v;
+        }
         ut[iy * NP + ix] += kb * v;
         if (bb == a) ua[iy * NP + ix] = v;
       }
@@ -87,6 +171,32 @@ __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, c
   }
 #pragma unroll
   for (int m = 0; m < NPM; ++m) p[m] = lift ? T(0) : ldv<CG>(x + poff + (long long)a * P.n_pres + c * NPM + m);
+  if constexpr (PRO) {
+    // the parent cell's pressure modes through the child map, combined in time
+    const TransferParams<T>& Q = *tp;
+    constexpr int NPMC = NPC * (NPC - 1) / 2;
+    const int o = HT ? ((cx & 1) | ((cy & 1) << 1)) : 0;
+    const long long cc = HT ? (long long)(cy >> 1) * Q.nc + (cx >> 1) : c;
+    T pc[NPMC];
+#pragma unroll
+    for (int mc = 0; mc < NPMC; ++mc) pc[mc] = 0;
+#pragma unroll
+    for (int ac = 0; ac < KT; ++ac)
+      if (ac < Q.ktc) {
+        const T w = Q.Pt[a * MAXKT + ac];
+        const T* srcp = ec + (long long)Q.ktc * Q.nvc + ac * Q.npc_tot + cc * NPMC;
+#pragma unroll
+        for (int mc = 0; mc < NPMC; ++mc) pc[mc] += w * ldv<CG>(srcp + mc);
+      }
+#pragma unroll
+    for (int m = 0; m < NPM; ++m) {
+      T s = 0;
+#pragma unroll
+      for (int mc = 0; mc < NPMC; ++mc) s += pres_map(Q, o, m, mc) * pc[mc];
+      p[m] += s;
+      if (d == 0) x2[poff + (long long)a * P.n_pres + c * NPM + m] = p[m];
+    }
+  }
   // the right-hand side rows this thread adds b to (residual / lift): loaded with x in
   // single precision (latency bound); in double precision the registers are scarcer and the
   // FP64 arithmetic hides the later loads

@@ -16,7 +16,7 @@ STRUCTS = {
                     "smoother", "omega", "nu1", "nu2", "precond_precision", "precisions", "gmres_max_iter",
                     "rel_tol", "use_graphs", "sweep_variant", "autotune", "coarse_n", "k_min", "n_sub",
                     "half_inverses", "transfer_variant", "apply_variant", "persistent", "level_nsub",
-                    "time_h", "arnoldi_form"],
+                    "time_h", "arnoldi_form", "fuse_transfers"],
     "stmg_level_info_t": ["n", "r", "k", "n_sub", "size", "n_vel", "n_pres", "smoother", "patch_size", "n_patches",
                           "n_patch_classes", "inverse_bytes", "sweep_variant", "patches_per_block",
                           "apply_cells_per_block", "transfer_cells_per_block", "streaming", "apply_variant",
@@ -72,6 +72,6 @@ def test_default_config_read_through_the_mirror():
     assert (cfg.nu1, cfg.nu2, cfg.gmres_max_iter, cfg.precisions) == (1, 1, 200, 3)
     assert (cfg.use_graphs, cfg.sweep_variant, cfg.autotune, cfg.coarse_n, cfg.k_min) == (1, 0, 1, 1, 1)
     assert (cfg.n_sub, cfg.half_inverses, cfg.transfer_variant, cfg.n_levels) == (1, 0, 0, 0)
-    assert cfg.apply_variant == 0 and cfg.persistent == 1 and cfg.time_h == 0 and cfg.arnoldi_form == 0
+    assert cfg.apply_variant == 0 and cfg.persistent == 1 and cfg.time_h == 0 and cfg.arnoldi_form == 0 and cfg.fuse_transfers == 1
     assert list(cfg.level_nsub) == [0] * len(cfg.level_nsub)
     assert list(cfg.smoother) == [_lib.CELL] * len(cfg.smoother)

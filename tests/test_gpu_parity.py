@@ -306,6 +306,33 @@ def test_persistent_levels_solve():
     assert rel(s0.remove_pressure_mean(xs[0][0]), s0.remove_pressure_mean(xs[1][0])) < 1e-8
 
 
+@pytest.mark.parametrize("case", [c for c in CASES if c[0] == 2], ids=[i for c, i in zip(CASES, IDS) if c[0] == 2])
+def test_fused_prolongation_residual(case):
+    """The FP32 V-cycle with the prolongation folded into the first postsmoothing residual
+    (the default on register-resident 2D levels: Q3 <- Q2 and Q2 <- Q2 on one mesh, Q2 <- Q2
+    from half the cells, ragged 3x3 and 5x5 meshes among them) against the oracle's V-cycle
+    (FP32 tolerance) and against the same V-cycle with separate kernels (two FP32
+    roundings apart), twice in a row (the second V-cycle starts from the buffers the first
+    left)."""
+    og, _ = setup_case(case)
+    dim, n, r, k, levels = case
+    levels = levels or stmg.host_default_hierarchy(n, r, k)
+    b = free_vec(og.slabs[0], 91)
+    ref = og.vcycle(b)
+    outs = {}
+    for fuse in (True, False):
+        g = stmg.SpaceTimeMG(dim=dim, n_cells=n, r=r, k=k, nu=NU, T=TAU * 5, n_slabs=5, levels=levels,
+                             use_graphs=False, autotune=False, apply_variant=3, precisions=("fp32",),
+                             precond_precision="fp32", fuse_transfers=fuse)
+        for rep in range(2):
+            x = g.vcycle(dev(b), "fp32")
+            assert rel(x, ref) < 1e-4
+        outs[fuse] = x.cpu().numpy()
+        g.device_status()
+        g.close()
+    assert rel(outs[True], outs[False]) < 2e-5
+
+
 def test_vcycle_graph_equals_eager():
     case = CASES[0]
     dim, n, r, k, _ = case
