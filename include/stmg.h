@@ -180,9 +180,11 @@ typedef struct {
                               2048 rows per SM), else 1 = the split-pass form that reads w
                               and V from memory in every pass; both give the same sums   */
   int    fuse_transfers;   /* 1 (default): on 2D register-resident levels of the FP32
-                              V-cycle, the prolongation of the coarser level's correction
-                              runs inside the first postsmoothing residual (one launch
-                              instead of two); 0: separate kernels                      */
+                              V-cycle, the residual after presmoothing is restricted in
+                              the same launch (no fine residual vector), and the
+                              prolongation of the coarser level's correction runs inside
+                              the first postsmoothing residual (one launch instead of
+                              two each way); 0: separate kernels                        */
 } stmg_config;
 
 typedef struct {

@@ -843,6 +843,20 @@ static bool fused_up(const stmg_handle* h, int l) {
          apply2d_reg_pro_supported(lv.H.np, lv.H.kt, lv.H.npm, P.tp.npc, P.tp.h_type, P.tp.ktc);
 }
 
+// Whether level l's descent computes its residual and restricts it in one launch: FP32,
+// the same levels and transfer shapes as fused_up, with presmoothing.
+template <typename T>
+static bool fused_down(const stmg_handle* h, int l) {
+  if (!std::is_same<T, float>::value || !h->cfg.fuse_transfers || h->cfg.nu1 < 1) return false;
+  if (l + 1 >= (int)h->L.size()) return false;
+  const int w = prec_of<T>();
+  if (h->mgp_first[w] > 0 && l >= h->mgp_first[w]) return false;
+  const LevelDev& lv = h->L[l];
+  const PrecDev<float>& P = lv.f;
+  return reg_form_ok<float>(lv.H) &&
+         apply2d_reg_pro_supported(lv.H.np, lv.H.kt, lv.H.npm, P.tp.npc, P.tp.h_type, P.tp.ktc);
+}
+
 // where level l's V-cycle leaves its iterate
 template <typename T>
 static T* final_x(stmg_handle* h, int l) {
@@ -874,13 +888,23 @@ static int vcycle_level(stmg_handle* h, int l, cudaStream_t s) {
       CKS(op_sweep<T>(h, l, P.r, P.x, s));
     }
   }
-  const T* res = P.b;
-  if (h->cfg.nu1 > 0) {                              // step 1 of Alg. 4 / 5
-    CKS(op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, s));
-    res = P.r;
-  }
   PrecDev<T>& C = h->L[l + 1].pd<T>();
-  CKS(op_restrict<T>(h, l, res, C.b, s, C.x));       // step 2/3 of Alg. 4 / 5; C.x = 0
+  if (fused_down<T>(h, l)) {
+    // steps 1-3 of Alg. 4 / 5 in one launch: C.b = P^T (b - S x), C.x = 0
+    LevelDev& lf = h->L[l];
+    LevelDev& lc = h->L[l + 1];
+    CK(cudaMemsetAsync(C.b, 0, sizeof(T) * (size_t)lc.H.size, s));
+    CK(launch_apply2d_reg_rst(lf.H.np, lf.f.rp, lf.f.tp, (const float*)P.x, (const float*)P.b, (float*)C.b,
+                              (float*)C.x, lf.f.ap.variant == 3 && lf.f.ap.cpb >= 16 ? lf.f.ap.cpb : 64, s));
+    h->launches += 1;
+  } else {
+    const T* res = P.b;
+    if (h->cfg.nu1 > 0) {                            // step 1 of Alg. 4 / 5
+      CKS(op_apply<T>(h, l, P.x, P.b, P.r, RESIDUAL, s));
+      res = P.r;
+    }
+    CKS(op_restrict<T>(h, l, res, C.b, s, C.x));     // step 2/3 of Alg. 4 / 5; C.x = 0
+  }
   CKS(vcycle_level<T>(h, l + 1, s));
   const T* ec = final_x<T>(h, l + 1);
   T* xu = P.x;

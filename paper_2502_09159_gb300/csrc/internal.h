@@ -180,6 +180,11 @@ bool apply2d_reg_pro_supported(int np, int kt, int npm, int npc, int ht, int ktc
 cudaError_t launch_apply2d_reg_pro(int np, const ApplyRegParams<float>& p, const TransferParams<float>& q,
                                    const float* x, const float* ec, const float* b, float* y, float* x2, int bs,
                                    cudaStream_t st);
+// the register-resident residual restricted to the coarser level in the same launch
+// (single precision): bc = P^T (b - S x) (bc zero on entry), xc = 0; the shapes of
+// apply2d_reg_pro_supported
+cudaError_t launch_apply2d_reg_rst(int np, const ApplyRegParams<float>& p, const TransferParams<float>& q,
+                                   const float* x, const float* b, float* bc, float* xc, int bs, cudaStream_t st);
 // its pair-split form (two lanes per cell item, Q3 only), y zero on entry as well
 template <typename T>
 cudaError_t launch_apply2d_pair(int np, const ApplyRegParams<T>& p, const T* x, const T* b, T* y, int mode,

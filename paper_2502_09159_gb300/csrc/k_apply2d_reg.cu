@@ -77,6 +77,35 @@ __global__ void __launch_bounds__(64) k_apply2d_reg_pro(const ApplyRegParams<flo
                                                     &Q, ec, x2);
 }
 
+// residual restricted to the coarser level in the same launch (single precision):
+// bc = P^T (b - S x) (bc zero on entry), xc = 0 at every coarse dof; same shapes
+template <int NP, int KT, int NPC, int HT>
+__global__ void __launch_bounds__(64) k_apply2d_reg_rst(const ApplyRegParams<float> P, const TransferParams<float> Q,
+                                                        const float* __restrict__ x, const float* __restrict__ b,
+                                                        float* __restrict__ bc, float* __restrict__ xc) {
+  apply2d_reg_thread<float, NP, KT, false, NPC, HT, true>(P, x, b, nullptr, RESIDUAL,
+                                                          blockIdx.x * (long long)blockDim.x + threadIdx.x, &Q, nullptr,
+                                                          nullptr, bc, xc);
+}
+
+cudaError_t launch_apply2d_reg_rst(int np, const ApplyRegParams<float>& p, const TransferParams<float>& q,
+                                   const float* x, const float* b, float* bc, float* xc, int bs, cudaStream_t st) {
+  if (!apply2d_reg_pro_supported(np, p.kt, p.npm, q.npc, q.h_type, q.ktc)) return cudaErrorInvalidValue;
+  const long long tot = (long long)p.n * p.n * p.kt * 2;
+  const int threads = bs >= 1 && bs <= 64 ? bs : 64;
+  const unsigned blocks = (unsigned)((tot + threads - 1) / threads);
+#define STMG_RST(N, K, C, H)                                                                            \
+  if (np == N && p.kt == K && q.npc == C && q.h_type == H) {                                            \
+    k_apply2d_reg_rst<N, K, C, H><<<blocks, threads, 0, st>>>(p, q, x, b, bc, xc);                    \
+    return cudaGetLastError();                                                                           \
+  }
+#define STMG_RST_K(N, C, H) STMG_RST(N, 1, C, H) STMG_RST(N, 2, C, H) STMG_RST(N, 3, C, H) STMG_RST(N, 4, C, H)
+  STMG_RST_K(4, 3, 0) STMG_RST_K(3, 3, 0) STMG_RST_K(3, 3, 1)
+#undef STMG_RST_K
+#undef STMG_RST
+  return cudaErrorInvalidValue;
+}
+
 bool apply2d_reg_pro_supported(int np, int kt, int npm, int npc, int ht, int ktc) {
   if (!apply2d_reg_supported<float>(np, kt, npm) || ktc > kt) return false;
   return (np == 4 && npc == 3 && ht == 0) || (np == 3 && npc == 3 && (ht == 0 || ht == 1));

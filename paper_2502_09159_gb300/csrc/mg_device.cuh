@@ -41,14 +41,25 @@ __device__ __forceinline__ T pres_map(const TransferParams<T>& P, int o, int mf,
 // node by the thread of its owner cell with a equal to the node's temporal dof, each
 // pressure dof by the d = 0 thread).  x is only read, so the cells sharing a node all see
 // the old value.
+//
+// With RST (single precision, RESIDUAL mode) the thread restricts its cell's residual to
+// the coarser level instead of scattering it (App. A: P^T, the transpose of the same
+// interpolation): the residual rows of the cell's non-Dirichlet nodes, b through the
+// owner cell, times the coarse basis functions of the parent cell at those nodes and the
+// temporal map, are added to bc (zero on entry) at the parent's non-Dirichlet coarse
+// nodes; the pressure rows through the child map.  The sum over the cells sharing a fine
+// node is the node's full residual, so bc = P^T (b - S x).  The (0, 0) child of each
+// coarse cell also zeroes the coarse iterate xc at the coarse dofs the coarse cell owns.
 // ------------------------------------------------------------------------------------
-template <typename T, int NP, int KT, bool CG, int NPC = 0, int HT = 0>
+template <typename T, int NP, int KT, bool CG, int NPC = 0, int HT = 0, bool RST = false>
 __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, const T* __restrict__ x,
                                                    const T* __restrict__ b, T* __restrict__ y, int mode,
                                                    long long t, const TransferParams<T>* tp = nullptr,
-                                                   const T* __restrict__ ec = nullptr, T* __restrict__ x2 = nullptr) {
-  constexpr bool PRO = NPC > 0;
-  static_assert(!PRO || sizeof(T) == 4, "the fused prolongation is a single-precision path");
+                                                   const T* __restrict__ ec = nullptr, T* __restrict__ x2 = nullptr,
+                                                   T* __restrict__ bc = nullptr, T* __restrict__ xc = nullptr) {
+  constexpr bool PRO = NPC > 0 && !RST;
+  static_assert(NPC > 0 || !RST, "the fused restriction needs the coarse shape");
+  static_assert(NPC == 0 || sizeof(T) == 4, "the fused transfers are a single-precision path");
   constexpr int E = NP - 1, NQ = NP * NP;
   constexpr int NPM = NP * (NP - 1) / 2;            // C(r + 2, 2) pressure modes, r = NP - 2
   const int n = P.n, G = P.G;
@@ -275,6 +286,7 @@ __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, c
   // x-pass, pressure gradient, scatter (row by row)
   T* yd = y + a * nvel + d * nnod + base;
   const T* xd = x + a * nvel + d * nnod + base;
+  T rl[RST ? NQ : 1];                               // RST: the cell's residual rows, slice a
 #pragma unroll
   for (int iy = 0; iy < NP; ++iy) {
     const bool dy = (iy == 0 && by0) || (iy == E && by1);
@@ -285,7 +297,9 @@ __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, c
       const bool own = oy && (i < E || bx1);
       const long long off = (long long)iy * G + i;
       if (dir) {
-        if (own) {
+        if constexpr (RST) {
+          rl[(iy * NP + i) % (RST ? NQ : 1)] = T(0);   // the restriction reads no fine Dirichlet row
+        } else if (own) {
           const T xv = ldv<CG>(xd + off);
           atomicAdd(yd + off, mode == RESIDUAL ? bvel(iy, i) - xv : xv);   // identity row, by its owner
         }
@@ -302,16 +316,71 @@ __device__ __forceinline__ void apply2d_reg_thread(const ApplyRegParams<T>& P, c
       for (int ex = 0; ex <= R; ++ex) bt += fx[ex * NP + i] * sp[ex][iy];
       T v = m1 + beta * k1 + bsc * bt;
       if (res) v = own ? bvel(iy, i) - v : -v;           // b enters once, through the owner
-      atomicAdd(yd + off, v);
+      if constexpr (RST)
+        rl[(iy * NP + i) % (RST ? NQ : 1)] = v;
+      else
+        atomicAdd(yd + off, v);
     }
   }
   // pressure rows of the cell: this component's share (b through component 0)
+  T rp[RST ? NPM : 1];
 #pragma unroll
   for (int m = 0; m < NPM; ++m) {
     const long long gi = poff + (long long)a * P.n_pres + c * NPM + m;
     T v = bsc * cont[m];
     if (res) v = d == 0 ? bpre(m) - v : -v;
-    atomicAdd(y + gi, v);
+    if constexpr (RST)
+      rp[m % (RST ? NPM : 1)] = v;
+    else
+      atomicAdd(y + gi, v);
+  }
+  if constexpr (RST) {
+    const TransferParams<T>& Q = *tp;
+    constexpr int NPMC = NPC * (NPC - 1) / 2;
+    const int Gc = Q.Gc, nc = Q.nc, ktc = Q.ktc;
+    const int ccx = HT ? cx >> 1 : cx, ccy = HT ? cy >> 1 : cy;
+    const int ox = HT ? (cx & 1) * (NP - 1) : 0, oy = HT ? (cy & 1) * (NP - 1) : 0;
+    // velocity: S[jy][jx] = sum_iy wy[iy][jy] sum_ix wx[ix][jx] rl[iy][ix]
+    T tx[NP][NPC];
+#pragma unroll
+    for (int iy = 0; iy < NP; ++iy)
+#pragma unroll
+      for (int jx = 0; jx < NPC; ++jx) {
+        T s = 0;
+#pragma unroll
+        for (int ix = 0; ix < NP; ++ix) s += Q.P1[(ox + ix) * MAXNP + jx] * rl[(iy * NP + ix) % (RST ? NQ : 1)];
+        tx[iy][jx] = s;
+      }
+    const bool zero_owner = HT ? ((cx & 1) == 0 && (cy & 1) == 0) : true;
+#pragma unroll
+    for (int jy = 0; jy < NPC; ++jy)
+#pragma unroll
+      for (int jx = 0; jx < NPC; ++jx) {
+        T s = 0;
+#pragma unroll
+        for (int iy = 0; iy < NP; ++iy) s += Q.P1[(oy + iy) * MAXNP + jy] * tx[iy][jx];
+        const int Jx = ccx * (NPC - 1) + jx, Jy = ccy * (NPC - 1) + jy;
+        const long long J = (long long)Jy * Gc + Jx;
+        const bool dirc = Jx == 0 || Jx == Gc - 1 || Jy == 0 || Jy == Gc - 1;
+#pragma unroll
+        for (int ac = 0; ac < KT; ++ac)
+          if (ac < ktc && !dirc) atomicAdd(bc + ac * Q.nvc + d * Q.nnc + J, Q.Pt[a * MAXKT + ac] * s);
+        const bool ownc = (jx < NPC - 1 || ccx == nc - 1) && (jy < NPC - 1 || ccy == nc - 1);
+        if (zero_owner && ownc && a < ktc) xc[a * Q.nvc + d * Q.nnc + J] = T(0);
+      }
+    // pressure: the parent's coarse modes through the child map
+    const int o = HT ? ((cx & 1) | ((cy & 1) << 1)) : 0;
+    const long long cc = (long long)ccy * nc + ccx;
+#pragma unroll
+    for (int mc = 0; mc < NPMC; ++mc) {
+      T s = 0;
+#pragma unroll
+      for (int m = 0; m < NPM; ++m) s += pres_map(Q, o, m, mc) * rp[m % (RST ? NPM : 1)];
+#pragma unroll
+      for (int ac = 0; ac < KT; ++ac)
+        if (ac < ktc) atomicAdd(bc + (long long)ktc * Q.nvc + ac * Q.npc_tot + cc * NPMC + mc, Q.Pt[a * MAXKT + ac] * s);
+      if (zero_owner && d == 0 && a < ktc) xc[(long long)ktc * Q.nvc + a * Q.npc_tot + cc * NPMC + mc] = T(0);
+    }
   }
 }
 

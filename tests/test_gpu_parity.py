@@ -308,12 +308,14 @@ def test_persistent_levels_solve():
 
 @pytest.mark.parametrize("case", [c for c in CASES if c[0] == 2], ids=[i for c, i in zip(CASES, IDS) if c[0] == 2])
 def test_fused_prolongation_residual(case):
-    """The FP32 V-cycle with the prolongation folded into the first postsmoothing residual
-    (the default on register-resident 2D levels: Q3 <- Q2 and Q2 <- Q2 on one mesh, Q2 <- Q2
-    from half the cells, ragged 3x3 and 5x5 meshes among them) against the oracle's V-cycle
-    (FP32 tolerance) and against the same V-cycle with separate kernels (two FP32
-    roundings apart), twice in a row (the second V-cycle starts from the buffers the first
-    left)."""
+    """The FP32 V-cycle with the transfers folded into the residuals (the default on
+    register-resident 2D levels: the descent's residual restricted in the same launch, the
+    coarser correction prolongated inside the first postsmoothing residual; Q3 <- Q2 and
+    Q2 <- Q2 on one mesh, Q2 <- Q2 from half the cells, ragged 3x3 and 5x5 meshes among
+    them) against the oracle's V-cycle (FP32 tolerance) and against the same V-cycle with
+    separate kernels (FP32 roundings apart), twice in a row (the second V-cycle starts from
+    the buffers the first left: the restriction must overwrite the coarse right-hand side
+    and zero the coarse iterate again)."""
     og, _ = setup_case(case)
     dim, n, r, k, levels = case
     levels = levels or stmg.host_default_hierarchy(n, r, k)
