@@ -870,6 +870,21 @@ static T* final_x(stmg_handle* h, int l) {
 template <typename T>
 static int vcycle_level(stmg_handle* h, int l, cudaStream_t s) {
   LevelDev& lv = h->L[l];
+  if (l == 0) {
+    // the coarser right-hand sides that the fused restrictions accumulate into, zeroed
+    // together in one launch (every V-cycle enters here at the finest level)
+    ZeroList z{};
+    for (int i = 0; i + 1 < (int)h->L.size() && z.count < ZeroList::MAX; ++i)
+      if (fused_down<T>(h, i)) {
+        z.p[z.count] = (float*)h->L[i + 1].f.b;
+        z.n[z.count] = h->L[i + 1].H.size;
+        ++z.count;
+      }
+    if (z.count > 0) {
+      CK(launch_zero_many(z, s));
+      h->launches += 1;
+    }
+  }
   PrecDev<T>& P = lv.pd<T>();
   const int w = prec_of<T>();
   if (h->mgp_first[w] > 0 && l == h->mgp_first[w]) {   // this level and all coarser ones in one launch
@@ -892,8 +907,7 @@ static int vcycle_level(stmg_handle* h, int l, cudaStream_t s) {
   if (fused_down<T>(h, l)) {
     // steps 1-3 of Alg. 4 / 5 in one launch: C.b = P^T (b - S x), C.x = 0
     LevelDev& lf = h->L[l];
-    LevelDev& lc = h->L[l + 1];
-    CK(cudaMemsetAsync(C.b, 0, sizeof(T) * (size_t)lc.H.size, s));
+    if (l >= ZeroList::MAX) CK(cudaMemsetAsync(C.b, 0, sizeof(T) * (size_t)h->L[l + 1].H.size, s));
     CK(launch_apply2d_reg_rst(lf.H.np, lf.f.rp, lf.f.tp, (const float*)P.x, (const float*)P.b, (float*)C.b,
                               (float*)C.x, lf.f.ap.variant == 3 && lf.f.ap.cpb >= 16 ? lf.f.ap.cpb : 64, s));
     h->launches += 1;

@@ -274,6 +274,15 @@ cudaError_t launch_sqrt_inplace(double* v, cudaStream_t st);
 
 int multidot_blocks(long long n);
 // one CGS2 Arnoldi step in a cooperative launch (see k_vec.cu); bar: 2 zeroed unsigned
+// a few float vectors zeroed in one launch
+struct ZeroList {
+  static constexpr int MAX = 8;
+  float* p[MAX];
+  long long n[MAX];
+  int count;
+};
+cudaError_t launch_zero_many(const ZeroList& z, cudaStream_t st);
+
 // reg: take the register-resident form where it fits (nv <= 16, at most 2048 rows per block).
 // vnext32, zero32 (optional): the register form also writes (float) vnext and zeroes
 // zero32; *wrote32 says whether it did

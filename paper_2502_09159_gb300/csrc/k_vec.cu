@@ -53,6 +53,26 @@ cudaError_t launch_convert_zero(long long n, const Ti* in, To* out, To* zero, cu
 template cudaError_t launch_convert_zero<double, float>(long long, const double*, float*, float*, cudaStream_t);
 template cudaError_t launch_convert_zero<double, double>(long long, const double*, double*, double*, cudaStream_t);
 
+// zero up to ZeroList::MAX float vectors in one launch (the coarser levels' right-hand
+// sides that the V-cycle's fused restrictions accumulate into)
+__global__ void k_zero_many(ZeroList z) {
+  long long total = 0;
+  for (int s = 0; s < z.count; ++s) total += z.n[s];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    long long j = i;
+    int s = 0;
+    while (s + 1 < z.count && j >= z.n[s]) j -= z.n[s++];
+    z.p[s][j] = 0.0f;
+  }
+}
+cudaError_t launch_zero_many(const ZeroList& z, cudaStream_t st) {
+  long long total = 0;
+  for (int s = 0; s < z.count; ++s) total += z.n[s];
+  if (total <= 0) return cudaSuccess;
+  k_zero_many<<<grid_for(total), 256, 0, st>>>(z);
+  return cudaGetLastError();
+}
+
 __global__ void k_scale(long long n, double a, const double* __restrict__ x, double* __restrict__ y) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = a * x[i];
