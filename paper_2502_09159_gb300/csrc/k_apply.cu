@@ -421,6 +421,8 @@ cudaError_t launch_mass_coupling(const MassParams& p, const double* vprev, doubl
 
 // ------------------------------------------------------------------------------------
 // Forcing (Eq. DefFn): F^a_i = tau/2 w_a sum_q w_q f(x_q, t^a) . chi_i(x_q)
+// The quadrature weight times the 1D basis value, W1[p][q] = w_q ell_p(x_q), is staged in
+// shared memory, and the tensor-product sum is factorised: along x, then y (then z).
 // ------------------------------------------------------------------------------------
 __global__ void k_forcing(const ForcingParams P, const double* __restrict__ fq, double* __restrict__ F) {
   const int dim = P.dim, np = P.np, n = P.n, G = P.G, nq = P.nq;
@@ -429,6 +431,9 @@ __global__ void k_forcing(const ForcingParams P, const double* __restrict__ fq, 
   const int ncells = dim == 2 ? n * n : n * n * n;
   const int c = blockIdx.x;
   if (c >= ncells) return;
+  __shared__ double W1[MAXNP * 10];
+  for (int e = threadIdx.x; e < np * nq; e += blockDim.x) W1[e] = P.wq[e % nq] * P.phiq[e];
+  __syncthreads();
   int cc[3] = {c % n, (c / n) % n, dim == 3 ? c / (n * n) : 0};
   const int tot = P.kt * dim * nnode;
   for (int w = threadIdx.x; w < tot; w += blockDim.x) {
@@ -438,12 +443,19 @@ __global__ void k_forcing(const ForcingParams P, const double* __restrict__ fq, 
     bool dir = gx == 0 || gx == G - 1 || gy == 0 || gy == G - 1 || (dim == 3 && (gz == 0 || gz == G - 1));
     if (dir) continue;
     const double* f = fq + ((long long)a * ncells + c) * nqc * dim;
+    const double* wx = W1 + ix * nq;
+    const double* wy = W1 + iy * nq;
+    const double* wz = W1 + iz * nq;
     double s = 0.0;
-    for (int q = 0; q < nqc; ++q) {
-      const int qx = q % nq, qy = (q / nq) % nq, qz = dim == 3 ? q / (nq * nq) : 0;
-      double wv = P.wq[qx] * P.wq[qy] * P.phiq[ix * nq + qx] * P.phiq[iy * nq + qy];
-      if (dim == 3) wv *= P.wq[qz] * P.phiq[iz * nq + qz];
-      s += wv * f[q * dim + comp];
+    for (int qz = 0; qz < (dim == 3 ? nq : 1); ++qz) {
+      double sy = 0.0;
+      for (int qy = 0; qy < nq; ++qy) {
+        const double* fr = f + ((long long)(qz * nq + qy) * nq) * dim + comp;
+        double sx = 0.0;
+        for (int qx = 0; qx < nq; ++qx) sx += wx[qx] * fr[qx * dim];
+        sy += wy[qy] * sx;
+      }
+      s += (dim == 3 ? wz[qz] : 1.0) * sy;
     }
     const long long g = gx + (long long)G * (gy + (long long)G * gz);
     atomicAdd(F + a * P.n_vel + comp * P.n_nodes + g, P.scale[a] * s);
