@@ -565,3 +565,27 @@ def test_mg_with_h_in_time_levels_equals_direct_solve():
     assert info.converged and info.iterations <= 40
     a, c = s0.remove_pressure_mean(x), s0.remove_pressure_mean(xd)
     assert np.abs(a - c).max() < 1e-8 * np.abs(c).max()
+
+
+def test_temporal_degree_zero_on_coarse_levels_degrades_with_the_mesh():
+    """Alg. 2 read with k coarsened to 0 (r: 2 -> 1 with k: 2 -> 1, then k: 1 -> 0, then
+    geometric to one cell with DG(0)) on slabs of the 2D Fourier-forced problem: FGMRES
+    to 1e-8 needs several times the iterations of the hierarchy that keeps DG(2) on every
+    level, and the gap widens under refinement (the behaviour the full-size measurement
+    shows).  Pins that finding to the oracle, independent of the GPU path."""
+    from workloads import fourier_forcing_2d
+    pb = fourier_forcing_2d(nu=1.0)
+    its = {}
+    for n in (8, 16):
+        k2 = [(n, 2, 2), (n, 1, 2)] + [(m, 1, 2) for m in (n // 2, n // 4) if m >= 4]
+        k0 = [(n, 2, 2), (n, 1, 1), (n, 1, 0)] + [(n >> i, 1, 0) for i in range(1, 8) if n >> i >= 1]
+        for name, lv in (("k2", k2), ("k0", k0)):
+            og = Multigrid(2, lv, 1.0, 1.0 / 16, MGConfig())
+            s0 = og.slabs[0]
+            F = s0.rhs_forcing(pb.forcing, 0.0)
+            _, info = fgmres(lambda z: s0.S @ z, og.vcycle, F, tol=1e-8, maxit=300)
+            assert info.converged
+            its[n, name] = info.iterations
+    assert its[8, "k0"] > 3 * its[8, "k2"]
+    assert its[16, "k0"] > 5 * its[16, "k2"]
+    assert its[16, "k0"] / its[16, "k2"] > its[8, "k0"] / its[8, "k2"]
