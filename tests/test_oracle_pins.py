@@ -433,6 +433,72 @@ def test_mg_iterations_bounded_in_h():
     assert max(its) <= 15 and its[-1] <= its[1] + 3
 
 
+@pytest.mark.parametrize("precond", ["identity", "vcycle"])
+def test_fgmres_iterates_minimise_the_residual_over_the_krylov_space(precond):
+    """The defining property of (F)GMRES with a fixed linear preconditioner M: the j-th
+    iterate minimises ||b - S x||_2 over x0 + M K_j(S M, r0).  The minimum is computed
+    here by least squares over a Krylov basis that numpy's QR orthonormalises, without
+    the Arnoldi process, the Givens rotations or the triangular solve of `fgmres`; its
+    true final residual and its running estimate must both equal that minimum.  A
+    dropped rotation, a wrong sign in g or an update with the wrong vectors fails."""
+    mg = Multigrid(2, [(2, 2, 1), (2, 1, 1), (1, 1, 1)], 1.0, 0.5)
+    S = mg.slabs[0].S
+    rng = np.random.default_rng(7)
+    b = S @ rng.standard_normal(S.shape[0])          # in the range of S (singular in p)
+    x0 = rng.standard_normal(S.shape[0])
+    M = (lambda v: v.copy()) if precond == "identity" else mg.vcycle
+    r0 = b - S @ x0
+    Q = (r0 / np.linalg.norm(r0))[:, None]
+    for j in range(1, 7):
+        SMQ = np.column_stack([S @ M(q) for q in Q.T])
+        y = np.linalg.lstsq(SMQ, r0, rcond=None)[0]
+        want = np.linalg.norm(r0 - SMQ @ y) / np.linalg.norm(b)
+        x, info = fgmres(lambda z: S @ z, M, b, x0=x0, tol=1e-300, maxit=j)
+        assert info.iterations == j
+        got = np.linalg.norm(b - S @ x) / np.linalg.norm(b)
+        assert abs(got - want) <= 1e-8 * want, (j, got, want)
+        assert abs(info.history[-1] - want) <= 1e-8 * want, (j, info.history[-1], want)
+        Q = np.linalg.qr(np.column_stack([Q, SMQ[:, -1]]))[0]   # K_{j+1} = K_j + S M K_j
+
+
+@pytest.mark.parametrize("dim,r,k", [(2, 1, 1), (2, 2, 2), (3, 1, 0)])
+def test_vanka_step_on_a_single_cell_is_the_direct_solve(dim, r, k):
+    """On a one-cell mesh the only cell patch holds every dof (valence 1), so one Vanka
+    step with omega = 1 is x + S^+ (b - S x): the solution of the slab system, equal to
+    scipy's sparse LU of the bordered system (pressure compared after removing its mean
+    per temporal dof, the constant being free)."""
+    s = Slab(dim, 1, r, k, 1.0, 0.5)
+    pats = cell_patches(s)
+    assert len(pats) == 1 and len(pats[0]) == s.size
+    from oracle.stokes import Vanka
+    W = Vanka(s, pats, 1.0)
+    rng = np.random.default_rng(3)
+    b = s.S @ rng.standard_normal(s.size)
+    b[s.S.diagonal() == 1.0] = 0.0                   # no data on the Dirichlet rows
+    x = W.step(b, rng.standard_normal(s.size))
+    want = s.remove_pressure_mean(s.direct_solve(b))
+    assert np.abs(s.remove_pressure_mean(x) - want).max() <= 1e-11 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("levels", [
+    [(4, 2, 2), (4, 1, 2)],                           # p in space
+    [(4, 1, 1), (2, 1, 1)],                           # h in space
+    [(2, 1, 2), (2, 1, 1)],                           # p in time
+])
+def test_coarse_correction_is_the_galerkin_projection(levels):
+    """Without smoothing (nu1 = nu2 = 0) a two-level cycle is x = P S_c^+ P^T b, and
+    with S_c = P^T S P the residual left after it is orthogonal to the range of P:
+    P^T (b - S x) = 0 for every b in the range of S.  A correction added with the wrong
+    sign, a restriction other than P^T or a coarse solve on the wrong level fails."""
+    mg = Multigrid(2, levels, 1.0, 0.5, MGConfig(nu1=0, nu2=0))
+    S, P = mg.slabs[0].S, mg.P[0]
+    b = S @ np.random.default_rng(5).standard_normal(S.shape[0])
+    x = mg.vcycle(b)
+    Pb = P.T @ b
+    assert np.linalg.norm(Pb) > 1e-3 * np.linalg.norm(b)
+    assert np.abs(P.T @ (b - S @ x)).max() <= 1e-11 * np.abs(Pb).max()
+
+
 @pytest.mark.parametrize("dim,n,r,k", [(2, 3, 2, 2), (3, 2, 1, 1), (2, 4, 1, 0), (3, 2, 2, 1)])
 def test_slab_rows_equal_assembled_rows(dim, n, r, k):
     """Row-wise evaluation of S x from element matrices (used for full-size sampled parity)
