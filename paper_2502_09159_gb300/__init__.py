@@ -22,6 +22,7 @@ from ._lib import CELL, FP32, FP64, VSP, StmgError, check, load
 
 __all__ = ["SpaceTimeMG", "StmgError", "FP64", "FP32", "CELL", "VSP", "host_default_hierarchy",
            "host_tables_1d", "host_time_tables", "host_patch", "host_valence", "host_coarse_inverse",
+           "host_invert",
            "build"]
 
 _PREC = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}
@@ -553,3 +554,14 @@ def host_coarse_inverse(dim, n, r, k, nu, tau):
     G = np.zeros(D.value * D.value)
     check("stmg_host_coarse_inverse", lib.stmg_host_coarse_inverse(dim, n, r, k, nu, tau, _dp(G), C.byref(D)))
     return G.reshape(D.value, D.value).T.copy()     # column-major -> row-major
+
+
+def host_invert(A, threads=0):
+    """Inverse of the square FP64 matrix A by the library's setup routine (host only)."""
+    lib = load()
+    M = np.ascontiguousarray(A, dtype=np.float64).copy()
+    n = M.shape[0]
+    if M.ndim != 2 or M.shape[1] != n:
+        raise ValueError("host_invert: A must be square")
+    check("stmg_host_invert", lib.stmg_host_invert(_dp(M), n, threads))
+    return M

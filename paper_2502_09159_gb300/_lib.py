@@ -111,6 +111,7 @@ _SIGS = {
                              C.POINTER(_I), C.POINTER(_LL), C.POINTER(_I)]),
     "stmg_host_valence": (_I, [_I, _I, _I, _I, _I, C.POINTER(_I), C.POINTER(_LL)]),
     "stmg_host_coarse_inverse": (_I, [_I, _I, _I, _I, _D, _D, C.POINTER(_D), C.POINTER(_LL)]),
+    "stmg_host_invert": (_I, [C.POINTER(_D), _I, _I]),
 }
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libstmg.so")

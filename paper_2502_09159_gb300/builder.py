@@ -42,7 +42,7 @@ def _flags(cuda):
     inc = ["-I", CSRC, "-I", INCLUDE, "-I", os.path.join(cuda, "include")]
     nv = [os.path.join(cuda, "bin", "nvcc"), "-std=c++17", "-O3", *ARCH, "-lineinfo",
           "-Xcompiler", "-fPIC", "-diag-suppress", "177", *inc]
-    cxx = [os.environ.get("CXX", "g++"), "-std=c++17", "-O2", "-fPIC", "-Wall", *inc]
+    cxx = [os.environ.get("CXX", "g++"), "-std=c++17", "-O3", "-fPIC", "-Wall", *inc]
     return nv, cxx
 
 

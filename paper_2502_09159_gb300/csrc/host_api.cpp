@@ -118,4 +118,16 @@ int stmg_host_coarse_inverse(int dim, int n, int r, int k, double nu, double tau
   return STMG_OK;
 }
 
+// In-place inverse of a row-major n x n matrix by the routine that inverts the patch
+// matrices and the coarse bordered matrix.
+int stmg_host_invert(double* A, int n, int threads) {
+  if (!A || n < 1 || threads < 0) return STMG_ERR_ARG;
+  try {
+    if (!invert_gauss_jordan(A, n, threads)) return STMG_ERR_SINGULAR;
+  } catch (const std::exception&) {
+    return STMG_ERR_OOM;
+  }
+  return STMG_OK;
+}
+
 }  // extern "C"

@@ -6,8 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
-#include <condition_variable>
-#include <mutex>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <stdexcept>
@@ -292,62 +291,176 @@ void assemble_submatrix(const LevelHost& L, const std::vector<long long>& idx, c
     }
 }
 
-// Multithreaded in-place Gauss-Jordan (same arithmetic, rows of each elimination step
-// split over threads) for the large dense matrices of coarse levels.
-static bool invert_gauss_jordan_mt(double* A, int n, int nth) {
+// Barrier for the threads of one blocked inversion: spins briefly, then yields, so that
+// it stays cheap when every thread has a core and does not starve anyone when they do not.
+class SpinBarrier {
+ public:
+  explicit SpinBarrier(int n) : n_(n) {}
+  void wait() {
+    const unsigned g = gen_.load(std::memory_order_acquire);
+    if (count_.fetch_add(1, std::memory_order_acq_rel) + 1 == n_) {
+      count_.store(0, std::memory_order_relaxed);
+      gen_.fetch_add(1, std::memory_order_acq_rel);
+      return;
+    }
+    for (int spins = 0; gen_.load(std::memory_order_acquire) == g; ++spins)
+      if (spins > 2000) std::this_thread::yield();
+  }
+
+ private:
+  const int n_;
+  std::atomic<int> count_{0};
+  std::atomic<unsigned> gen_{0};
+};
+
+// r[j] += sum_k a[k] T[k][j] and s[j] += sum_k b[k] T[k][j] for j in [j0, j1) (two
+// rows of the matrix at once; T row-major with row length n).  Rows of T are taken four
+// at a time: each loaded T element serves eight multiply-adds, each r[j], s[j] is loaded
+// and stored once per four.
+static void rank_update2(double* __restrict r, double* __restrict s, const double* a, const double* b,
+                         const double* __restrict T, long long n, int kb, int j0, int j1) {
+  int k = 0;
+  for (; k + 4 <= kb; k += 4) {
+    const double a0 = a[k], a1 = a[k + 1], a2 = a[k + 2], a3 = a[k + 3];
+    const double b0 = b[k], b1 = b[k + 1], b2 = b[k + 2], b3 = b[k + 3];
+    const double* __restrict t0 = T + (size_t)k * n;
+    const double* __restrict t1 = t0 + n;
+    const double* __restrict t2 = t1 + n;
+    const double* __restrict t3 = t2 + n;
+    for (int j = j0; j < j1; ++j) {
+      const double u0 = t0[j], u1 = t1[j], u2 = t2[j], u3 = t3[j];
+      r[j] += a0 * u0 + a1 * u1 + a2 * u2 + a3 * u3;
+      s[j] += b0 * u0 + b1 * u1 + b2 * u2 + b3 * u3;
+    }
+  }
+  for (; k < kb; ++k) {
+    const double ak = a[k], bk = b[k];
+    const double* __restrict tk = T + (size_t)k * n;
+    for (int j = j0; j < j1; ++j) {
+      r[j] += ak * tk[j];
+      s[j] += bk * tk[j];
+    }
+  }
+}
+
+// The same for one row.
+static void rank_update1(double* __restrict r, const double* a, const double* __restrict T, long long n, int kb,
+                         int j0, int j1) {
+  int k = 0;
+  for (; k + 4 <= kb; k += 4) {
+    const double a0 = a[k], a1 = a[k + 1], a2 = a[k + 2], a3 = a[k + 3];
+    if (a0 == 0.0 && a1 == 0.0 && a2 == 0.0 && a3 == 0.0) continue;
+    const double* __restrict t0 = T + (size_t)k * n;
+    const double* __restrict t1 = t0 + n;
+    const double* __restrict t2 = t1 + n;
+    const double* __restrict t3 = t2 + n;
+    for (int j = j0; j < j1; ++j) r[j] += a0 * t0[j] + a1 * t1[j] + a2 * t2[j] + a3 * t3[j];
+  }
+  for (; k < kb; ++k) {
+    const double ak = a[k];
+    if (ak == 0.0) continue;
+    const double* __restrict tk = T + (size_t)k * n;
+    for (int j = j0; j < j1; ++j) r[j] += ak * tk[j];
+  }
+}
+
+// Blocked in-place Gauss-Jordan with partial pivoting, for the large dense matrices of
+// coarse levels and 3D patches.  The columns are taken in panels of NB.  Inside a panel
+// the elimination steps update only the panel's columns (every row, pivot search and row
+// interchanges as in the scalar method).  With P the panel's pivot rows, K its columns,
+// R the other columns and E the pivot block before the panel, the NB steps together map
+// [P,K] -> E^-1, [others,K] -> -[others,K] E^-1, and, what is left to do afterwards,
+// [P,R] -> E^-1 [P,R] and [others,R] -> [others,R] - [others,K] E^-1 [P,R]: one rank-NB
+// update of every row with T = the old [P,R] (steps of Gauss-Jordan on a set of pivots
+// compose into this block step).  Each matrix row is then streamed once per panel
+// instead of once per column.  Rows are split over nth threads in contiguous ranges.
+static bool invert_gauss_jordan_blocked(double* A, int n, int nth) {
+  constexpr int NB = 64;
+  nth = std::max(1, std::min(nth, n / 32));
   std::vector<int> piv(n);
   double amax = 0.0;
   for (size_t i = 0; i < (size_t)n * n; ++i) amax = std::max(amax, std::fabs(A[i]));
-  std::mutex mu;
-  std::condition_variable cv;
-  int arrived = 0;
-  long long gen = 0;
-  auto barrier = [&]() {
-    std::unique_lock<std::mutex> lk(mu);
-    const long long g = gen;
-    if (++arrived == nth) { arrived = 0; ++gen; cv.notify_all(); }
-    else cv.wait(lk, [&] { return gen != g; });
-  };
-  bool ok = true;
+  std::vector<double> T((size_t)NB * n);
+  std::vector<double> best(nth);
+  std::vector<int> where(nth);
+  SpinBarrier bar(nth);
+  std::atomic<bool> ok{true};
   auto worker = [&](int t) {
-    for (int c = 0; c < n; ++c) {
-      if (t == 0) {
-        int p = c;
-        double best = std::fabs(A[(size_t)c * n + c]);
-        for (int i = c + 1; i < n; ++i) {
+    const int lo = (int)((long long)n * t / nth), hi = (int)((long long)n * (t + 1) / nth);
+    double a[NB], b[NB];
+    for (int c0 = 0; c0 < n; c0 += NB) {
+      const int kb = std::min(NB, n - c0), c1 = c0 + kb;
+      for (int c = c0; c < c1; ++c) {
+        // pivot: the first row (in order) of largest magnitude in column c among rows >= c
+        double bv = -1.0;
+        int bi = -1;
+        for (int i = std::max(lo, c); i < hi; ++i) {
           const double v = std::fabs(A[(size_t)i * n + c]);
-          if (v > best) { best = v; p = i; }
+          if (v > bv) { bv = v; bi = i; }
         }
-        if (!(best > 1e-14 * amax)) ok = false;
-        piv[c] = p;
-        if (ok) {
-          if (p != c)
-            for (int j = 0; j < n; ++j) std::swap(A[(size_t)c * n + j], A[(size_t)p * n + j]);
-          const double inv = 1.0 / A[(size_t)c * n + c];
-          A[(size_t)c * n + c] = 1.0;
-          double* rc = A + (size_t)c * n;
-          for (int j = 0; j < n; ++j) rc[j] *= inv;
+        best[t] = bv;
+        where[t] = bi;
+        bar.wait();
+        if (t == 0) {
+          double b = -1.0;
+          int p = -1;
+          for (int u = 0; u < nth; ++u)
+            if (where[u] >= 0 && best[u] > b) { b = best[u]; p = where[u]; }
+          if (!(b > 1e-14 * amax)) {
+            ok.store(false);
+          } else {
+            piv[c] = p;
+            if (p != c)
+              for (int j = 0; j < n; ++j) std::swap(A[(size_t)c * n + j], A[(size_t)p * n + j]);
+            double* rc = A + (size_t)c * n;
+            const double inv = 1.0 / rc[c];
+            rc[c] = 1.0;
+            for (int j = c0; j < c1; ++j) rc[j] *= inv;
+          }
+        }
+        bar.wait();
+        if (!ok.load()) return;
+        const double* rc = A + (size_t)c * n;
+        for (int i = lo; i < hi; ++i) {
+          if (i == c) continue;
+          double* ri = A + (size_t)i * n;
+          const double f = ri[c];
+          if (f == 0.0) continue;
+          ri[c] = 0.0;
+          for (int j = c0; j < c1; ++j) ri[j] -= f * rc[j];
         }
       }
-      barrier();
-      if (!ok) return;
-      const double* rc = A + (size_t)c * n;
-      for (int i = t; i < n; i += nth) {
-        if (i == c) continue;
+      bar.wait();                               // the panel is complete in every row
+      for (int q = t; q < kb; q += nth) {       // T = old [P,R]; [P,R] = 0 (gets E^-1 T below)
+        double* rp = A + (size_t)(c0 + q) * n;
+        double* tq = T.data() + (size_t)q * n;
+        for (int j = 0; j < c0; ++j) { tq[j] = rp[j]; rp[j] = 0.0; }
+        for (int j = c1; j < n; ++j) { tq[j] = rp[j]; rp[j] = 0.0; }
+      }
+      bar.wait();
+      int i = lo;
+      for (; i + 2 <= hi; i += 2) {
         double* ri = A + (size_t)i * n;
-        const double f = ri[c];
-        if (f == 0.0) continue;
-        ri[c] = 0.0;
-        for (int j = 0; j < n; ++j) ri[j] -= f * rc[j];
+        double* rs = ri + n;
+        for (int q = 0; q < kb; ++q) { a[q] = ri[c0 + q]; b[q] = rs[c0 + q]; }
+        rank_update2(ri, rs, a, b, T.data(), n, kb, 0, c0);
+        rank_update2(ri, rs, a, b, T.data(), n, kb, c1, n);
       }
-      barrier();
+      if (i < hi) {
+        double* ri = A + (size_t)i * n;
+        for (int q = 0; q < kb; ++q) a[q] = ri[c0 + q];
+        rank_update1(ri, a, T.data(), n, kb, 0, c0);
+        rank_update1(ri, a, T.data(), n, kb, c1, n);
+      }
+      // no barrier here: the next panel's first step reads only the thread's own rows
+      // before its barrier, and T is rewritten only after the next panel's barriers
     }
   };
   std::vector<std::thread> th;
   for (int t = 1; t < nth; ++t) th.emplace_back(worker, t);
   worker(0);
   for (auto& x : th) x.join();
-  if (!ok) return false;
+  if (!ok.load()) return false;
   for (int c = n - 1; c >= 0; --c)
     if (piv[c] != c)
       for (int i = 0; i < n; ++i) std::swap(A[(size_t)i * n + c], A[(size_t)i * n + piv[c]]);
@@ -355,10 +468,11 @@ static bool invert_gauss_jordan_mt(double* A, int n, int nth) {
 }
 
 // In-place inverse of the row-major n x n matrix A (Gauss-Jordan, partial pivoting).
-bool invert_gauss_jordan(double* A, int n) {
-  if (n >= 768) {
-    const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
-    if (nth > 1) return invert_gauss_jordan_mt(A, n, nth);
+// nth: threads for the blocked form (n >= 256); 0 = the machine's, capped at 32.
+bool invert_gauss_jordan(double* A, int n, int nth) {
+  if (n >= 256) {
+    if (nth <= 0) nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    return invert_gauss_jordan_blocked(A, n, nth);
   }
   std::vector<int> piv(n);
   std::vector<double> row(n);
@@ -397,6 +511,10 @@ bool invert_gauss_jordan(double* A, int n) {
 
 bool build_class_inverses(LevelHost* L) {
   const int nc = (int)L->class_rep.size(), B = L->B;
+  // classes run in parallel; a large inverse gets the threads the classes leave free
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const unsigned nth = std::max(1u, std::min(16u, hw));
+  const int inner = nc <= 1 ? 0 : std::max(1, (int)(hw / std::min<unsigned>(nth, (unsigned)nc)));
   L->class_inv.assign((size_t)nc * B * B, 0.0);
   std::vector<int> ok(nc, 1);
   const long long poff = (long long)L->kt * L->n_vel;
@@ -420,16 +538,15 @@ bool build_class_inverses(LevelHost* L) {
         A[(size_t)i * bb + b + a] = 1.0;
         A[(size_t)(b + a) * bb + i] = 1.0;
       }
-      if (!invert_gauss_jordan(A.data(), bb)) { ok[c] = 0; return; }
+      if (!invert_gauss_jordan(A.data(), bb, inner)) { ok[c] = 0; return; }
       for (int i = 0; i < b; ++i)
         std::memcpy(&L->class_inv[((size_t)c * B + i) * B], &A[(size_t)i * bb], sizeof(double) * b);
       return;
     }
-    if (!invert_gauss_jordan(S.data(), b)) { ok[c] = 0; return; }
+    if (!invert_gauss_jordan(S.data(), b, inner)) { ok[c] = 0; return; }
     for (int i = 0; i < b; ++i)
       std::memcpy(&L->class_inv[((size_t)c * B + i) * B], &S[(size_t)i * b], sizeof(double) * b);
   };
-  unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
   if (nc <= 1 || nth <= 1) {
     for (int c = 0; c < nc; ++c) work(c);
   } else {

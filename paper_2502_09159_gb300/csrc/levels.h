@@ -34,7 +34,7 @@ void init_level_geometry(LevelHost* L, int dim, int n, int r, int k, double tau,
 void build_patches(LevelHost* L, int kind);
 void assemble_submatrix(const LevelHost& L, const std::vector<long long>& idx, const std::vector<char>& dir,
                         std::vector<double>* S);
-bool invert_gauss_jordan(double* A, int n);
+bool invert_gauss_jordan(double* A, int n, int nth = 0);
 bool build_class_inverses(LevelHost* L);
 bool build_coarse_inverse(LevelHost* L, std::vector<double>* Gcm);
 

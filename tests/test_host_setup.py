@@ -127,3 +127,48 @@ def test_coarse_inverse_matches_oracle(pkg, dim, n, r, k):
     mg = Multigrid(dim, [(n, r, k)], nu, tau, MGConfig())
     G = pkg.host_coarse_inverse(dim, n, r, k, nu, tau)
     assert np.abs(G - mg.coarse_inv).max() <= 1e-10 * np.abs(mg.coarse_inv).max()
+
+
+@pytest.mark.parametrize("n", [1, 7, 255, 256, 300, 383, 640])
+@pytest.mark.parametrize("threads", [1, 3, 0])
+def test_host_invert_matches_numpy(pkg, n, threads):
+    """The setup's Gauss-Jordan (blocked in panels of 64 columns from n = 256 on, rows
+    split over threads) against numpy's LU-based inverse: sizes on both sides of the
+    blocked form, ragged last panels, uneven row ranges per thread."""
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n)) + np.sqrt(n) * np.eye(n)
+    X = pkg.host_invert(A, threads)
+    ref = np.linalg.inv(A)
+    assert np.abs(X - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n", [5, 300])
+def test_host_invert_pivots(pkg, n):
+    """A matrix whose diagonal is zero and whose largest entries sit off it (a scaled
+    cyclic shift plus a small perturbation) can only be inverted with row interchanges."""
+    rng = np.random.default_rng(1)
+    A = 10.0 * np.roll(np.eye(n), 1, axis=1) + 0.01 * rng.standard_normal((n, n))
+    np.fill_diagonal(A, 0.0)
+    X = pkg.host_invert(A, 0)
+    assert np.abs(X @ A - np.eye(n)).max() < 1e-12
+
+
+@pytest.mark.parametrize("n", [6, 290])
+def test_host_invert_reports_singular(pkg, n):
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((n, n))
+    A[:, -1] = A[:, 0] + 2.0 * A[:, 1]               # rank n - 1
+    with pytest.raises(pkg.StmgError):
+        pkg.host_invert(A, 0)
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_coarse_inverse_blocked_path_matches_oracle(pkg, n):
+    """Coarse levels large enough for the blocked, threaded form: D = 630 and D = 2310 (the
+    coarsest level of the 64x64 Q3/P2 DG(2) hierarchy with an 8x8 coarsest mesh), each
+    with 3 bordering rows."""
+    dim, r, k, nu, tau = 2, 1, 2, 1.0, 1.0 / 16
+    mg = Multigrid(dim, [(n, r, k)], nu, tau, MGConfig())
+    G = pkg.host_coarse_inverse(dim, n, r, k, nu, tau)
+    assert G.shape[0] >= 256
+    assert np.abs(G - mg.coarse_inv).max() <= 1e-10 * np.abs(mg.coarse_inv).max()
