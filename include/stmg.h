@@ -525,7 +525,7 @@ int  stmg_host_coarse_inverse(int dim, int n, int r, int k, double nu, double ta
 
 /* In-place inverse of the row-major n x n matrix A (host memory, caller-owned) by the
    routine stmg_create uses for patch matrices and the coarse bordered matrix: Gauss-Jordan
-   with partial pivoting in FP64, blocked in panels of 64 columns for n >= 256 with the
+   with partial pivoting in FP64, blocked in panels of 32 columns for n >= 256 with the
    rows split over `threads` threads (0 = the machine's, at most 32).  Returns
    STMG_ERR_SINGULAR, A partly overwritten, when no pivot exceeds 1e-14 max|A|. */
 int  stmg_host_invert(double* A, int n, int threads);

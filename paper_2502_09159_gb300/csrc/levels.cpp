@@ -6,7 +6,11 @@
 
 #include <algorithm>
 #include <cmath>
+#include <sched.h>
+
 #include <atomic>
+#include <condition_variable>
+#include <mutex>
 #include <cstring>
 #include <map>
 #include <stdexcept>
@@ -291,26 +295,43 @@ void assemble_submatrix(const LevelHost& L, const std::vector<long long>& idx, c
     }
 }
 
-// Barrier for the threads of one blocked inversion: spins briefly, then yields, so that
-// it stays cheap when every thread has a core and does not starve anyone when they do not.
-class SpinBarrier {
+// CPUs this process may run on (its affinity mask), at least 1.
+static int usable_cpus() {
+  cpu_set_t set;
+  CPU_ZERO(&set);
+  if (sched_getaffinity(0, sizeof(set), &set) == 0) return std::max(1, CPU_COUNT(&set));
+  return (int)std::max(1u, std::thread::hardware_concurrency());
+}
+
+// Barrier for the threads of one blocked inversion: a waiting thread spins for a short
+// while (cheap when every thread has a core), then sleeps on a condition variable (so
+// that threads without a core of their own do not hold up the ones still working).
+class HybridBarrier {
  public:
-  explicit SpinBarrier(int n) : n_(n) {}
+  explicit HybridBarrier(int n) : n_(n) {}
   void wait() {
     const unsigned g = gen_.load(std::memory_order_acquire);
     if (count_.fetch_add(1, std::memory_order_acq_rel) + 1 == n_) {
       count_.store(0, std::memory_order_relaxed);
-      gen_.fetch_add(1, std::memory_order_acq_rel);
+      {
+        std::lock_guard<std::mutex> lk(mu_);
+        gen_.fetch_add(1, std::memory_order_acq_rel);
+      }
+      cv_.notify_all();
       return;
     }
-    for (int spins = 0; gen_.load(std::memory_order_acquire) == g; ++spins)
-      if (spins > 2000) std::this_thread::yield();
+    for (int spins = 0; spins < 4000; ++spins)
+      if (gen_.load(std::memory_order_acquire) != g) return;
+    std::unique_lock<std::mutex> lk(mu_);
+    cv_.wait(lk, [&] { return gen_.load(std::memory_order_acquire) != g; });
   }
 
  private:
   const int n_;
   std::atomic<int> count_{0};
   std::atomic<unsigned> gen_{0};
+  std::mutex mu_;
+  std::condition_variable cv_;
 };
 
 // r[j] += sum_k a[k] T[k][j] and s[j] += sum_k b[k] T[k][j] for j in [j0, j1) (two
@@ -373,64 +394,66 @@ static void rank_update1(double* __restrict r, const double* a, const double* __
 // [P,R] -> E^-1 [P,R] and [others,R] -> [others,R] - [others,K] E^-1 [P,R]: one rank-NB
 // update of every row with T = the old [P,R] (steps of Gauss-Jordan on a set of pivots
 // compose into this block step).  Each matrix row is then streamed once per panel
-// instead of once per column.  Rows are split over nth threads in contiguous ranges.
+// instead of once per column.  One thread eliminates the panel (n x NB values, cache
+// resident); the rank-NB update, nearly all of the arithmetic, is split over nth threads
+// by contiguous row ranges, so the threads meet three times per panel.
 static bool invert_gauss_jordan_blocked(double* A, int n, int nth) {
-  constexpr int NB = 64;
+  constexpr int NB = 32, JB = 256;
   nth = std::max(1, std::min(nth, n / 32));
   std::vector<int> piv(n);
   double amax = 0.0;
   for (size_t i = 0; i < (size_t)n * n; ++i) amax = std::max(amax, std::fabs(A[i]));
-  std::vector<double> T((size_t)NB * n);
-  std::vector<double> best(nth);
-  std::vector<int> where(nth);
-  SpinBarrier bar(nth);
+  std::vector<double> T((size_t)NB * n), W((size_t)n * NB);
+  HybridBarrier bar(nth);
   std::atomic<bool> ok{true};
+  // the panel's columns [c0, c1) of every row are eliminated in W (n x kb, contiguous:
+  // the column walks of the pivot search and the updates stay within a few MB instead of
+  // touching one page per matrix row); a row interchange swaps the rows' W parts and the
+  // rest of the rows in A
+  auto panel = [&](int c0, int c1) {
+    const int kb = c1 - c0;
+    for (int i = 0; i < n; ++i) std::memcpy(&W[(size_t)i * kb], A + (size_t)i * n + c0, sizeof(double) * kb);
+    bool good = true;
+    for (int c = c0; c < c1 && good; ++c) {
+      const int lc = c - c0;
+      // pivot: the first row (in order) of largest magnitude in column c among rows >= c
+      int p = c;
+      double best = std::fabs(W[(size_t)c * kb + lc]);
+      for (int i = c + 1; i < n; ++i) {
+        const double v = std::fabs(W[(size_t)i * kb + lc]);
+        if (v > best) { best = v; p = i; }
+      }
+      if (!(best > 1e-14 * amax)) { good = false; break; }
+      piv[c] = p;
+      if (p != c) {
+        for (int j = 0; j < kb; ++j) std::swap(W[(size_t)c * kb + j], W[(size_t)p * kb + j]);
+        for (int j = 0; j < c0; ++j) std::swap(A[(size_t)c * n + j], A[(size_t)p * n + j]);
+        for (int j = c1; j < n; ++j) std::swap(A[(size_t)c * n + j], A[(size_t)p * n + j]);
+      }
+      double* rc = &W[(size_t)c * kb];
+      const double inv = 1.0 / rc[lc];
+      rc[lc] = 1.0;
+      for (int j = 0; j < kb; ++j) rc[j] *= inv;
+      for (int i = 0; i < n; ++i) {
+        if (i == c) continue;
+        double* ri = &W[(size_t)i * kb];
+        const double f = ri[lc];
+        if (f == 0.0) continue;
+        ri[lc] = 0.0;
+        for (int j = 0; j < kb; ++j) ri[j] -= f * rc[j];
+      }
+    }
+    for (int i = 0; i < n; ++i) std::memcpy(A + (size_t)i * n + c0, &W[(size_t)i * kb], sizeof(double) * kb);
+    return good;
+  };
   auto worker = [&](int t) {
     const int lo = (int)((long long)n * t / nth), hi = (int)((long long)n * (t + 1) / nth);
     double a[NB], b[NB];
     for (int c0 = 0; c0 < n; c0 += NB) {
       const int kb = std::min(NB, n - c0), c1 = c0 + kb;
-      for (int c = c0; c < c1; ++c) {
-        // pivot: the first row (in order) of largest magnitude in column c among rows >= c
-        double bv = -1.0;
-        int bi = -1;
-        for (int i = std::max(lo, c); i < hi; ++i) {
-          const double v = std::fabs(A[(size_t)i * n + c]);
-          if (v > bv) { bv = v; bi = i; }
-        }
-        best[t] = bv;
-        where[t] = bi;
-        bar.wait();
-        if (t == 0) {
-          double b = -1.0;
-          int p = -1;
-          for (int u = 0; u < nth; ++u)
-            if (where[u] >= 0 && best[u] > b) { b = best[u]; p = where[u]; }
-          if (!(b > 1e-14 * amax)) {
-            ok.store(false);
-          } else {
-            piv[c] = p;
-            if (p != c)
-              for (int j = 0; j < n; ++j) std::swap(A[(size_t)c * n + j], A[(size_t)p * n + j]);
-            double* rc = A + (size_t)c * n;
-            const double inv = 1.0 / rc[c];
-            rc[c] = 1.0;
-            for (int j = c0; j < c1; ++j) rc[j] *= inv;
-          }
-        }
-        bar.wait();
-        if (!ok.load()) return;
-        const double* rc = A + (size_t)c * n;
-        for (int i = lo; i < hi; ++i) {
-          if (i == c) continue;
-          double* ri = A + (size_t)i * n;
-          const double f = ri[c];
-          if (f == 0.0) continue;
-          ri[c] = 0.0;
-          for (int j = c0; j < c1; ++j) ri[j] -= f * rc[j];
-        }
-      }
+      if (t == 0 && !panel(c0, c1)) ok.store(false);
       bar.wait();                               // the panel is complete in every row
+      if (!ok.load()) return;
       for (int q = t; q < kb; q += nth) {       // T = old [P,R]; [P,R] = 0 (gets E^-1 T below)
         double* rp = A + (size_t)(c0 + q) * n;
         double* tq = T.data() + (size_t)q * n;
@@ -438,22 +461,28 @@ static bool invert_gauss_jordan_blocked(double* A, int n, int nth) {
         for (int j = c1; j < n; ++j) { tq[j] = rp[j]; rp[j] = 0.0; }
       }
       bar.wait();
-      int i = lo;
-      for (; i + 2 <= hi; i += 2) {
-        double* ri = A + (size_t)i * n;
-        double* rs = ri + n;
-        for (int q = 0; q < kb; ++q) { a[q] = ri[c0 + q]; b[q] = rs[c0 + q]; }
-        rank_update2(ri, rs, a, b, T.data(), n, kb, 0, c0);
-        rank_update2(ri, rs, a, b, T.data(), n, kb, c1, n);
+      // columns in chunks of JB: the chunk of T (kb x JB, 64 KB) stays in the core's
+      // cache while the thread's rows pass through it
+      for (int j0 = 0; j0 < n; j0 += JB) {
+        const int j1 = std::min(n, j0 + JB);
+        const int ja = std::min(j1, c0), jb = std::max(j0, c1);   // the chunk without the panel
+        if (ja <= j0 && jb >= j1) continue;
+        int i = lo;
+        for (; i + 2 <= hi; i += 2) {
+          double* ri = A + (size_t)i * n;
+          double* rs = ri + n;
+          for (int q = 0; q < kb; ++q) { a[q] = ri[c0 + q]; b[q] = rs[c0 + q]; }
+          if (ja > j0) rank_update2(ri, rs, a, b, T.data(), n, kb, j0, ja);
+          if (jb < j1) rank_update2(ri, rs, a, b, T.data(), n, kb, jb, j1);
+        }
+        if (i < hi) {
+          double* ri = A + (size_t)i * n;
+          for (int q = 0; q < kb; ++q) a[q] = ri[c0 + q];
+          if (ja > j0) rank_update1(ri, a, T.data(), n, kb, j0, ja);
+          if (jb < j1) rank_update1(ri, a, T.data(), n, kb, jb, j1);
+        }
       }
-      if (i < hi) {
-        double* ri = A + (size_t)i * n;
-        for (int q = 0; q < kb; ++q) a[q] = ri[c0 + q];
-        rank_update1(ri, a, T.data(), n, kb, 0, c0);
-        rank_update1(ri, a, T.data(), n, kb, c1, n);
-      }
-      // no barrier here: the next panel's first step reads only the thread's own rows
-      // before its barrier, and T is rewritten only after the next panel's barriers
+      bar.wait();                               // every row is up to date for the next panel
     }
   };
   std::vector<std::thread> th;
@@ -468,10 +497,11 @@ static bool invert_gauss_jordan_blocked(double* A, int n, int nth) {
 }
 
 // In-place inverse of the row-major n x n matrix A (Gauss-Jordan, partial pivoting).
-// nth: threads for the blocked form (n >= 256); 0 = the machine's, capped at 32.
+// nth: threads for the blocked form (n >= 256); 0 = the CPUs the process may use, at
+// most 32.
 bool invert_gauss_jordan(double* A, int n, int nth) {
   if (n >= 256) {
-    if (nth <= 0) nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    if (nth <= 0) nth = std::min(32, usable_cpus());
     return invert_gauss_jordan_blocked(A, n, nth);
   }
   std::vector<int> piv(n);
@@ -512,7 +542,7 @@ bool invert_gauss_jordan(double* A, int n, int nth) {
 bool build_class_inverses(LevelHost* L) {
   const int nc = (int)L->class_rep.size(), B = L->B;
   // classes run in parallel; a large inverse gets the threads the classes leave free
-  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const unsigned hw = (unsigned)usable_cpus();
   const unsigned nth = std::max(1u, std::min(16u, hw));
   const int inner = nc <= 1 ? 0 : std::max(1, (int)(hw / std::min<unsigned>(nth, (unsigned)nc)));
   L->class_inv.assign((size_t)nc * B * B, 0.0);

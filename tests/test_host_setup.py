@@ -132,7 +132,7 @@ def test_coarse_inverse_matches_oracle(pkg, dim, n, r, k):
 @pytest.mark.parametrize("n", [1, 7, 255, 256, 300, 383, 640])
 @pytest.mark.parametrize("threads", [1, 3, 0])
 def test_host_invert_matches_numpy(pkg, n, threads):
-    """The setup's Gauss-Jordan (blocked in panels of 64 columns from n = 256 on, rows
+    """The setup's Gauss-Jordan (blocked in panels of 32 columns from n = 256 on, rows
     split over threads) against numpy's LU-based inverse: sizes on both sides of the
     blocked form, ragged last panels, uneven row ranges per thread."""
     rng = np.random.default_rng(n)
