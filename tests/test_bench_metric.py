@@ -1,0 +1,58 @@
+"""The numerator of bench.py's throughput (space-time dofs per march) and the paper's
+throughput its lid-driven lines compare against, pinned to the numbers Sec. 5.2 and
+Table 3 print (tests/golden/dof_counts.txt).  CPU only."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+GOLDEN = os.path.join(ROOT, "tests", "golden", "dof_counts.txt")
+
+# Table 3, n_sm = 1: wall time W in seconds of the march on 13,824 CPU ranks
+TABLE3_W = {(4, 2): 149.4, (5, 2): 329.0, (4, 3): 629.4}
+
+
+def _golden():
+    rows = {}
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                c, r, _, per_slab, total = line.split()
+                rows[(int(c), int(r))] = (None if per_slab == "-" else int(per_slab), int(total))
+    return rows
+
+
+def test_slab_dofs_match_the_papers_counts():
+    """slab_dofs(w) x (16 * 2^c slabs) is Table 3's global space-time dof count for every
+    printed (c, r), and the per-slab count Sec. 5.2 prints where it prints one."""
+    for (c, r), (per_slab, total) in _golden().items():
+        n = 2 ** c
+        D = bench.slab_dofs(dict(dim=3, n_cells=n, r=r, k=r))
+        if per_slab is not None:
+            assert D == per_slab
+        assert D * 16 * n == total
+
+
+@pytest.mark.parametrize("name,c,r", [("lid", 4, 2), ("lid5", 5, 2), ("lid_r3", 4, 3)])
+def test_lid_workloads_are_table3_rows(name, c, r):
+    """Each lid-driven workload is the Table 3 row it is compared with: mesh 2^c, Q_{r+1}/P_r,
+    DG(r), 16 * 2^c slabs on [0, 8]; its whole march has Table 3's dof count, and the
+    paper's throughput it divides by is that count over Table 3's wall time."""
+    w = bench.WORKLOADS[name][0]
+    assert (w["dim"], w["n_cells"], w["r"], w["k"], w["T"], w["n_slabs"]) == (3, 2 ** c, r, r, 8.0, 16 * 2 ** c)
+    total = _golden()[(c, r)][1]
+    assert bench.slab_dofs(w) * w["n_slabs"] == total
+    assert bench.PAPER_THETA[name] == pytest.approx(total / TABLE3_W[(c, r)], rel=1e-12)
+
+
+def test_headline_workload_size():
+    """64x64 Q3/P2 DG(2): 3 (2 * 193^2 + 6 * 64^2) = 297,222 dofs per slab (Eq. DefX layout)."""
+    w = bench.WORKLOADS["c2"][0]
+    assert bench.slab_dofs(w) == 3 * (2 * 193 ** 2 + 6 * 64 ** 2) == 297222
+    assert bench.aggregate_value(1, w["n_slabs"], bench.slab_dofs(w), 1000.0) == 16 * 297222
