@@ -56,3 +56,18 @@ def test_headline_workload_size():
     w = bench.WORKLOADS["c2"][0]
     assert bench.slab_dofs(w) == 3 * (2 * 193 ** 2 + 6 * 64 ** 2) == 297222
     assert bench.aggregate_value(1, w["n_slabs"], bench.slab_dofs(w), 1000.0) == 16 * 297222
+
+
+def test_sweep_bytes_of_the_headline_finest_level():
+    """The roofline's algorithmic bytes per finest-level FP32 sweep: n_patches B^2 4 + 3 D 4,
+    with the patch count and size of the library's own patch tables (4096 cells; B = 114,
+    the Q3/P2 DG(2) cell patch of Table 2(b)), and the 9 distinct patch matrices of a
+    uniform mesh (interior, 4 edges, 4 corners)."""
+    import paper_2502_09159_gb300 as p
+    p.build()
+    w = bench.WORKLOADS["c2"][0]
+    hp = p.host_patch(2, 64, 2, 2, 1.0, 1.0 / 16, p.CELL, 0, with_inverse=False)
+    assert (hp["B"], hp["n_patches"], hp["n_classes"]) == (114, 4096, 9)
+    level = {"n_patches": hp["n_patches"], "patch_size": hp["B"], "size": bench.slab_dofs(w)}
+    assert bench.sweep_alg_bytes(level, "fp32") == 216493128
+    assert bench.sweep_alg_bytes(level, "fp64") == 2 * 216493128
