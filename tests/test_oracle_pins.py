@@ -238,6 +238,8 @@ def test_hierarchy_examples():
     ((2, 2, 3, 2), (2, 2, 1, 1)),     # p in space and time
     ((2, 4, 1, 2), (2, 2, 1, 1)),     # h in space, p in time
     ((3, 2, 1, 1), (3, 1, 1, 1)),     # 3D h
+    ((3, 1, 2, 2), (3, 1, 1, 1)),     # 3D p in space and time
+    ((3, 2, 2, 0), (3, 2, 1, 0)),     # 3D p in space, DG(0)
 ])
 def test_galerkin_identity(fine, coarse):
     """Nested conforming spaces, same forms, exact integration => P^T S_f P = S_c on free dofs."""
