@@ -71,3 +71,28 @@ def test_sweep_bytes_of_the_headline_finest_level():
     level = {"n_patches": hp["n_patches"], "patch_size": hp["B"], "size": bench.slab_dofs(w)}
     assert bench.sweep_alg_bytes(level, "fp32") == 216493128
     assert bench.sweep_alg_bytes(level, "fp64") == 2 * 216493128
+
+
+def test_parity_key_ignores_only_the_pressure_constants():
+    """The bench line's `parity` compares slab 1 with the oracle's after removing the
+    pressure mean of each temporal dof: a constant added to the pressure of one temporal
+    dof (mode 0 of every cell) leaves the error at zero; any other change is reported."""
+    import math
+    import numpy as np
+    w = bench.WORKLOAD
+    d, n, r, k = w["dim"], w["n_cells"], w["r"], w["k"]
+    D = bench.slab_dofs(w)
+    nv, npm, kt = d * ((r + 1) * n + 1) ** d, math.comb(r + d, d), k + 1
+    rng = np.random.default_rng(0)
+    ref = rng.standard_normal(D)
+    x = ref.copy()
+    for a in range(kt):                                  # p += c_a on temporal dof a
+        x[kt * nv + a * npm * n ** d:kt * nv + (a + 1) * npm * n ** d:npm] += 3.0 * (a + 1)
+    out = bench.parity_against_oracle(ref, x, None)
+    assert out["fp32_vcycle"]["rel_err_max"] < 1e-14 and "fp64_vcycle" not in out
+    y = x.copy()
+    y[kt * nv + 1] += 1e-3                               # a non-constant pressure mode
+    y[5] -= 2e-3                                         # a velocity entry
+    e = bench.parity_against_oracle(ref, x, y)["fp64_vcycle"]
+    assert abs(e["rel_err_max"] - 2e-3 / np.abs(ref).max()) < 1e-9
+    assert e["rel_err_velocity_l2"] > 0 and e["rel_err_pressure_l2"] > 0
