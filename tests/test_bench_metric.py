@@ -96,3 +96,18 @@ def test_parity_key_ignores_only_the_pressure_constants():
     e = bench.parity_against_oracle(ref, x, y)["fp64_vcycle"]
     assert abs(e["rel_err_max"] - 2e-3 / np.abs(ref).max()) < 1e-9
     assert e["rel_err_velocity_l2"] > 0 and e["rel_err_pressure_l2"] > 0
+
+
+def test_clock_samples_summary():
+    """The `clocks` key from nvidia-smi rows: median SM clock under load, the maximum, and
+    every throttle reason that was active in any sample (unreadable values skipped)."""
+    rows = ["0, 2070, 2070, 655.20, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+            "0, 1980, 2070, 1391.00, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+            "0, 2070, 2070, 1380.50, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+            "0, [N/A], 2070, [N/A], [N/A], Not Active, Not Active, Not Active, Not Active\n",
+            "garbage line\n"]
+    s = bench.summarise_clocks(rows)
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 4}
+    s = bench.summarise_clocks(rows[:1] + ["0, 1500, 2070, 700, 0x8, Active, Active, Not Active, Not Active"])
+    assert s["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"] and s["sm_mhz"] == 1785.0
+    assert bench.summarise_clocks([]) is None and bench.summarise_clocks(["a, b"]) is None
