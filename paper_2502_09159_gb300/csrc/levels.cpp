@@ -485,8 +485,22 @@ static bool invert_gauss_jordan_blocked(double* A, int n, int nth) {
       bar.wait();                               // every row is up to date for the next panel
     }
   };
+  // the helper threads wait at a gate until all of them exist: if one cannot be created,
+  // the others are sent home before they reach a barrier and the work runs on one thread
+  std::atomic<int> gate{0};                   // 0 wait, 1 run, -1 cancelled
   std::vector<std::thread> th;
-  for (int t = 1; t < nth; ++t) th.emplace_back(worker, t);
+  try {
+    for (int t = 1; t < nth; ++t)
+      th.emplace_back([&, t]() {
+        while (gate.load(std::memory_order_acquire) == 0) std::this_thread::yield();
+        if (gate.load(std::memory_order_acquire) > 0) worker(t);
+      });
+  } catch (const std::exception&) {
+    gate.store(-1, std::memory_order_release);
+    for (auto& x : th) x.join();
+    return invert_gauss_jordan_blocked(A, n, 1);
+  }
+  gate.store(1, std::memory_order_release);
   worker(0);
   for (auto& x : th) x.join();
   if (!ok.load()) return false;
