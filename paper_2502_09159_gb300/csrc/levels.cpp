@@ -595,9 +595,18 @@ bool build_class_inverses(LevelHost* L) {
     for (int c = 0; c < nc; ++c) work(c);
   } else {
     std::vector<std::thread> th;
-    for (unsigned t = 0; t < nth; ++t)
-      th.emplace_back([&, t]() { for (int c = (int)t; c < nc; c += (int)nth) work(c); });
+    unsigned started = 0;
+    try {
+      for (unsigned t = 0; t < nth; ++t) {
+        th.emplace_back([&, t]() { for (int c = (int)t; c < nc; c += (int)nth) work(c); });
+        ++started;
+      }
+    } catch (const std::exception&) {
+      // a thread could not be created: its classes run here after the others
+    }
     for (auto& t : th) t.join();
+    for (unsigned t = started; t < nth; ++t)
+      for (int c = (int)t; c < nc; c += (int)nth) work(c);
   }
   for (int c = 0; c < nc; ++c) if (!ok[c]) return false;
   return true;
