@@ -309,7 +309,7 @@ class SpaceFE:
         _, _, psi, qidx = self._ref_values(x)
         wq = np.prod(w[qidx], axis=1) * self.h ** self.dim
         Mpe = (psi * wq) @ psi.T
-        return sp.block_diag([Mpe] * self.n_cells, format="csr")
+        return sp.block_diag([sp.csr_matrix(Mpe)] * self.n_cells, format="csr")
 
     def vel_dirichlet(self):
         """Boolean mask over the M^v velocity dofs: True on the boundary."""
